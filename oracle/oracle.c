@@ -1,0 +1,428 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle for the interpolated EMRI mode summation.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU-baseline leg
+ * of the benchmark may load this file's library.  It shares no code, header, table or
+ * helper with the CUDA path; the product never calls it.
+ *
+ * What it computes (arXiv:2104.04582):
+ *   * Sec. 3.C (Interpolated Summation): every real array on the sparse trajectory grid is
+ *     fitted with a "not-a-knot" cubic spline; all arrays share one knot grid.
+ *   * Sec. 4, Schwarzschild mode sum:
+ *         h(t) = (mu/d_L) sum_{lmn} A_lmn(t) -2Y_lm(theta,phi) exp(-i Phi_mn(t)),
+ *         Phi_mn = m Phi_phi + n Phi_r,
+ *     with h = h_+ - i h_x (Sec. 2).
+ *   * Eq. (amp_symmetry) with k = 0: A_{l,-m,-n} = (-1)^l conj(A_lmn); only m >= 0 modes are
+ *     given, and the m < 0 partner is added for m > 0 only; the m = 0 modes of the list are
+ *     taken literally, since (l,0,n) and (l,0,-n) are separate entries of the 3843-mode grid.
+ *   * Sec. 6 overlap/mismatch with S_n = 1 (time-domain form via Parseval).
+ *
+ * Spin-weighted spherical harmonics (named a utility in Sec. 3.D; the paper gives no
+ * formula): sY_lm(theta,phi) = (-1)^s sqrt((2l+1)/(4 pi)) d^l_{m,-s}(theta) e^{i m phi},
+ * with the Wigner small-d matrix written as its explicit finite factorial sum (Goldberg et
+ * al. 1967 convention, Condon-Shortley phase).
+ *
+ * Every function here is pinned by closed forms, identities, brute force or a library
+ * routine in the CPU test suite (tests/test_oracle_*.py).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_OK 0
+#define OR_ERR_ARG 1
+#define OR_ERR_KNOTS 2
+#define OR_ERR_RANGE 4
+
+static const double TWO_PI = 6.283185307179586476925286766559;
+
+/* ------------------------------------------------------------------ spline (Sec. 3.C) */
+
+/*
+ * Not-a-knot cubic spline through (t_k, y_k), k = 0..K-1, K >= 4.
+ * Unknowns: the knot slopes s_k.  Interior rows are the C2 conditions
+ *   h_k s_{k-1} + 2(h_{k-1}+h_k) s_k + h_{k-1} s_{k+1} = 3 (h_k d_{k-1} + h_{k-1} d_k),
+ * with h_k = t_{k+1}-t_k and d_k = (y_{k+1}-y_k)/h_k.  The end rows impose a continuous
+ * third derivative at t_1 and at t_{K-2} (the not-a-knot condition); after eliminating
+ * s_2 (resp. s_{K-3}) with the neighbouring interior row they read
+ *   h_1 s_0 + (h_0+h_1) s_1 = ((2h_1+3h_0) h_1 d_0 + h_0^2 d_1) / (h_0+h_1),
+ *   (h_{K-2}+h_{K-3}) s_{K-2} + h_{K-3} s_{K-1}
+ *        = (h_{K-2}^2 d_{K-3} + (2h_{K-3}+3h_{K-2}) h_{K-3} d_{K-2}) / (h_{K-3}+h_{K-2}).
+ * The tridiagonal system is solved by Gaussian elimination WITH partial pivoting (row
+ * swaps create one extra super-diagonal), one system per call.
+ * Output: coef[k*4 + p], p = 0..3, the cubic on [t_k, t_{k+1}] in x = t - t_k:
+ *   c0 = y_k, c1 = s_k, c2 = (3 d_k - 2 s_k - s_{k+1})/h_k, c3 = (s_k + s_{k+1} - 2 d_k)/h_k^2.
+ */
+int oracle_spline_nak(const double *t, int K, const double *y, double *coef)
+{
+    if (K < 4) return OR_ERR_KNOTS;
+    for (int k = 0; k + 1 < K; ++k)
+        if (!(t[k + 1] > t[k])) return OR_ERR_KNOTS;
+    int n = K;
+    double *h = malloc(sizeof(double) * (n - 1));
+    double *d = malloc(sizeof(double) * (n - 1));
+    double *dl = calloc(n, sizeof(double));   /* sub-diagonal: dl[k] = A[k+1][k] */
+    double *dg = calloc(n, sizeof(double));   /* diagonal */
+    double *du = calloc(n, sizeof(double));   /* super-diagonal: du[k] = A[k][k+1] */
+    double *du2 = calloc(n, sizeof(double));  /* fill-in: du2[k] = A[k][k+2] */
+    double *b = calloc(n, sizeof(double));
+    double *s = calloc(n, sizeof(double));
+    for (int k = 0; k < n - 1; ++k) {
+        h[k] = t[k + 1] - t[k];
+        d[k] = (y[k + 1] - y[k]) / h[k];
+    }
+    /* row 0 */
+    dg[0] = h[1];
+    du[0] = h[0] + h[1];
+    b[0] = ((2.0 * h[1] + 3.0 * h[0]) * h[1] * d[0] + h[0] * h[0] * d[1]) / (h[0] + h[1]);
+    /* interior rows */
+    for (int k = 1; k <= n - 2; ++k) {
+        dl[k - 1] = h[k];
+        dg[k] = 2.0 * (h[k - 1] + h[k]);
+        du[k] = h[k - 1];
+        b[k] = 3.0 * (h[k] * d[k - 1] + h[k - 1] * d[k]);
+    }
+    /* last row */
+    {
+        double a = h[n - 2], c = h[n - 3];
+        dl[n - 2] = a + c;
+        dg[n - 1] = c;
+        b[n - 1] = (a * a * d[n - 3] + (2.0 * c + 3.0 * a) * c * d[n - 2]) / (c + a);
+    }
+    /* forward elimination with partial pivoting */
+    for (int k = 0; k < n - 1; ++k) {
+        if (fabs(dg[k]) >= fabs(dl[k])) {
+            double mult = dl[k] / dg[k];
+            dg[k + 1] -= mult * du[k];
+            b[k + 1] -= mult * b[k];
+            du2[k] = 0.0;
+        } else {
+            /* swap rows k and k+1; the new pivot row is the old row k+1 */
+            double mult = dg[k] / dl[k];
+            double old_dg1 = dg[k + 1];
+            double old_du1 = (k + 1 < n - 1) ? du[k + 1] : 0.0;
+            double old_duk = du[k];
+            dg[k] = dl[k];
+            du[k] = old_dg1;
+            du2[k] = old_du1;
+            dg[k + 1] = old_duk - mult * old_dg1;
+            if (k + 1 < n - 1) du[k + 1] = -mult * old_du1;
+            double bk = b[k];
+            b[k] = b[k + 1];
+            b[k + 1] = bk - mult * b[k];
+        }
+    }
+    /* back substitution */
+    s[n - 1] = b[n - 1] / dg[n - 1];
+    s[n - 2] = (b[n - 2] - du[n - 2] * s[n - 1]) / dg[n - 2];
+    for (int k = n - 3; k >= 0; --k)
+        s[k] = (b[k] - du[k] * s[k + 1] - du2[k] * s[k + 2]) / dg[k];
+    for (int k = 0; k < n - 1; ++k) {
+        coef[4 * k + 0] = y[k];
+        coef[4 * k + 1] = s[k];
+        coef[4 * k + 2] = (3.0 * d[k] - 2.0 * s[k] - s[k + 1]) / h[k];
+        coef[4 * k + 3] = (s[k] + s[k + 1] - 2.0 * d[k]) / (h[k] * h[k]);
+    }
+    free(h); free(d); free(dl); free(dg); free(du); free(du2); free(b); free(s);
+    return OR_OK;
+}
+
+/* Segment of t: the k with t_k <= t < t_{k+1}; a sample on the last knot uses K-2. */
+static int find_segment(const double *t, int K, double x)
+{
+    int lo = 0, hi = K - 2;
+    if (x >= t[K - 2]) return K - 2;
+    while (lo < hi) {               /* largest k in [0, K-2] with t_k <= x */
+        int mid = (lo + hi + 1) / 2;
+        if (t[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+/* Evaluate the spline at n points (Horner in x = t - t_k). */
+void oracle_spline_eval(const double *t, int K, const double *coef, const double *x, int64_t n,
+                        double *out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        int k = find_segment(t, K, x[i]);
+        double u = x[i] - t[k];
+        const double *c = coef + 4 * k;
+        out[i] = ((c[3] * u + c[2]) * u + c[1]) * u + c[0];
+    }
+}
+
+/* ------------------------------------------------------------------ harmonics */
+
+static long double factl(int n)
+{
+    long double r = 1.0L;
+    for (int i = 2; i <= n; ++i) r *= (long double)i;
+    return r;
+}
+
+/* Wigner small-d d^j_{mp,m}(beta), Wigner's explicit finite sum over k. */
+static long double wigner_small_d(int j, int mp, int m, long double beta)
+{
+    long double c = cosl(0.5L * beta), s = sinl(0.5L * beta);
+    long double pre = sqrtl(factl(j + mp) * factl(j - mp) * factl(j + m) * factl(j - m));
+    int kmin = (m - mp > 0) ? (m - mp) : 0;
+    int kmax = (j + m < j - mp) ? (j + m) : (j - mp);
+    long double sum = 0.0L;
+    for (int k = kmin; k <= kmax; ++k) {
+        long double sign = ((mp - m + k) & 1) ? -1.0L : 1.0L;
+        long double num = powl(c, (long double)(2 * j + m - mp - 2 * k)) *
+                          powl(s, (long double)(mp - m + 2 * k));
+        long double den = factl(j + m - k) * factl(k) * factl(mp - m + k) * factl(j - mp - k);
+        sum += sign * num / den;
+    }
+    return pre * sum;
+}
+
+/* sY_lm(theta, phi) for integer spin s (|s| <= l, |m| <= l, else 0). */
+void oracle_swsh(int s, int l, int m, double theta, double phi, double *re, double *im)
+{
+    if (l < abs(s) || abs(m) > l || l < 0) { *re = 0.0; *im = 0.0; return; }
+    long double d = wigner_small_d(l, m, -s, (long double)theta);
+    long double norm = sqrtl((2.0L * l + 1.0L) / (4.0L * 3.14159265358979323846264338327950288L));
+    if (s & 1) norm = -norm;                      /* (-1)^s */
+    long double v = norm * d;
+    *re = (double)(v * cosl((long double)m * phi));
+    *im = (double)(v * sinl((long double)m * phi));
+}
+
+/* ------------------------------------------------------------------ mode sum (Sec. 4) */
+
+typedef struct {
+    int K, N;
+    const double *t;
+    double *cphi, *cr;            /* [K-1][4] phase splines (rad) */
+    double *cre, *cim;            /* [N][K-1][4] amplitude splines */
+    double *yp_re, *yp_im;        /* -2Y_{l,m} per mode */
+    double *ym_re, *ym_im;        /* (-1)^l -2Y_{l,-m} per mode (0 for m = 0) */
+} oracle_model;
+
+static int model_build(oracle_model *M, const double *t, int K, const double *phi_phi,
+                       const double *phi_r, const int *l, const int *m, int N,
+                       const double *amp_re, const double *amp_im, double theta, double phi)
+{
+    int S = K - 1, rc;
+    M->K = K; M->N = N; M->t = t;
+    M->cphi = malloc(sizeof(double) * 4 * S);
+    M->cr = malloc(sizeof(double) * 4 * S);
+    M->cre = malloc(sizeof(double) * 4 * S * (size_t)N);
+    M->cim = malloc(sizeof(double) * 4 * S * (size_t)N);
+    M->yp_re = malloc(sizeof(double) * N); M->yp_im = malloc(sizeof(double) * N);
+    M->ym_re = malloc(sizeof(double) * N); M->ym_im = malloc(sizeof(double) * N);
+    double *col = malloc(sizeof(double) * K);
+    if ((rc = oracle_spline_nak(t, K, phi_phi, M->cphi))) goto done;
+    if ((rc = oracle_spline_nak(t, K, phi_r, M->cr))) goto done;
+    for (int i = 0; i < N; ++i) {
+        for (int k = 0; k < K; ++k) col[k] = amp_re[(size_t)k * N + i];
+        if ((rc = oracle_spline_nak(t, K, col, M->cre + (size_t)4 * S * i))) goto done;
+        for (int k = 0; k < K; ++k) col[k] = amp_im[(size_t)k * N + i];
+        if ((rc = oracle_spline_nak(t, K, col, M->cim + (size_t)4 * S * i))) goto done;
+        oracle_swsh(-2, l[i], m[i], theta, phi, &M->yp_re[i], &M->yp_im[i]);
+        if (m[i] > 0) {
+            double a, b;
+            oracle_swsh(-2, l[i], -m[i], theta, phi, &a, &b);
+            double sg = (l[i] & 1) ? -1.0 : 1.0;
+            M->ym_re[i] = sg * a; M->ym_im[i] = sg * b;
+        } else {
+            M->ym_re[i] = 0.0; M->ym_im[i] = 0.0;
+        }
+    }
+done:
+    free(col);
+    return rc;
+}
+
+static void model_free(oracle_model *M)
+{
+    free(M->cphi); free(M->cr); free(M->cre); free(M->cim);
+    free(M->yp_re); free(M->yp_im); free(M->ym_re); free(M->ym_im);
+}
+
+static double horner(const double *c, double x)
+{
+    return ((c[3] * x + c[2]) * x + c[1]) * x + c[0];
+}
+
+/*
+ * h(t_i) for i in [i_begin, i_begin+count), t_i = t0 + i*dt; out[2*j], out[2*j+1] = Re, Im.
+ * At each sample: both phase splines are evaluated (rad) and reduced modulo 2 pi separately,
+ * in turns (x - rint(x)); per mode the integer combination m*f_phi + n*f_r is reduced again
+ * and passed to FP64 sin/cos; the m >= 0 term A Y+ e^{-i Phi} and, for m > 0, the partner
+ * (-1)^l conj(A) -2Y_{l,-m} e^{+i Phi} are added (Eq. amp_symmetry with k = 0).
+ */
+int oracle_waveform(const double *t, int K, const double *phi_phi, const double *phi_r,
+                    const int *l, const int *m, const int *n, int N,
+                    const double *amp_re, const double *amp_im,
+                    double theta, double phi, double scale, double t0, double dt,
+                    int64_t i_begin, int64_t count, double *out, int nthreads)
+{
+    if (K < 4 || N < 1 || !(dt > 0.0) || count < 0) return OR_ERR_ARG;
+    double t_last = t0 + (double)(i_begin + count - 1) * dt;
+    if (count > 0 && (t0 + (double)i_begin * dt < t[0] || t_last > t[K - 1])) return OR_ERR_RANGE;
+    oracle_model M;
+    int rc = model_build(&M, t, K, phi_phi, phi_r, l, m, N, amp_re, amp_im, theta, phi);
+    if (rc) { model_free(&M); return rc; }
+    int S = K - 1;
+    if (nthreads < 1) nthreads = 1;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+#endif
+    for (int64_t j = 0; j < count; ++j) {
+        double ti = t0 + (double)(i_begin + j) * dt;
+        int k = find_segment(t, K, ti);
+        double x = ti - t[k];
+        double xphi = horner(M.cphi + 4 * k, x) / TWO_PI;
+        double xr = horner(M.cr + 4 * k, x) / TWO_PI;
+        double fphi = xphi - rint(xphi);
+        double fr = xr - rint(xr);
+        double hr = 0.0, hi = 0.0;
+        for (int i = 0; i < N; ++i) {
+            const double *are = M.cre + (size_t)4 * S * i + 4 * k;
+            const double *aim = M.cim + (size_t)4 * S * i + 4 * k;
+            double Ar = horner(are, x), Ai = horner(aim, x);
+            double ph = (double)m[i] * fphi + (double)n[i] * fr;
+            ph -= rint(ph);
+            double c = cos(TWO_PI * ph), s = sin(TWO_PI * ph);
+            /* A Y+ (c - i s) */
+            double ayr = Ar * M.yp_re[i] - Ai * M.yp_im[i];
+            double ayi = Ar * M.yp_im[i] + Ai * M.yp_re[i];
+            hr += ayr * c + ayi * s;
+            hi += ayi * c - ayr * s;
+            if (m[i] > 0) {
+                /* conj(A) Y- (c + i s) */
+                double byr = Ar * M.ym_re[i] + Ai * M.ym_im[i];
+                double byi = Ar * M.ym_im[i] - Ai * M.ym_re[i];
+                hr += byr * c - byi * s;
+                hi += byi * c + byr * s;
+            }
+        }
+        out[2 * j] = scale * hr;
+        out[2 * j + 1] = scale * hi;
+    }
+    model_free(&M);
+    return OR_OK;
+}
+
+/*
+ * Brute-force mode sum for tiny inputs: the m < 0 modes are appended explicitly to a signed
+ * list with A_{l,-m,-n} = (-1)^l conj(A_lmn) (Eq. amp_symmetry, k = 0); every signed mode is
+ * summed directly as A -2Y_{lm} e^{-i(m Phi_phi + n Phi_r)} in long double, with the phases
+ * left unreduced and no folding of partner terms.
+ */
+int oracle_direct_sum(const double *t, int K, const double *phi_phi, const double *phi_r,
+                      const int *l, const int *m, const int *n, int N,
+                      const double *amp_re, const double *amp_im,
+                      double theta, double phi, double scale, double t0, double dt,
+                      int64_t count, double *out)
+{
+    if (K < 4 || N < 1 || !(dt > 0.0)) return OR_ERR_ARG;
+    oracle_model M;
+    int rc = model_build(&M, t, K, phi_phi, phi_r, l, m, N, amp_re, amp_im, theta, phi);
+    if (rc) { model_free(&M); return rc; }
+    int S = K - 1;
+    int Ns = 0;
+    for (int i = 0; i < N; ++i) Ns += (m[i] > 0) ? 2 : 1;
+    int *sl = malloc(sizeof(int) * Ns), *sm = malloc(sizeof(int) * Ns), *sn = malloc(sizeof(int) * Ns);
+    int *src = malloc(sizeof(int) * Ns), *cj = malloc(sizeof(int) * Ns);
+    long double *yr = malloc(sizeof(long double) * Ns), *yi = malloc(sizeof(long double) * Ns);
+    int q = 0;
+    for (int i = 0; i < N; ++i) {
+        double a, b;
+        sl[q] = l[i]; sm[q] = m[i]; sn[q] = n[i]; src[q] = i; cj[q] = 0;
+        oracle_swsh(-2, l[i], m[i], theta, phi, &a, &b); yr[q] = a; yi[q] = b; ++q;
+        if (m[i] > 0) {
+            sl[q] = l[i]; sm[q] = -m[i]; sn[q] = -n[i]; src[q] = i; cj[q] = 1;
+            oracle_swsh(-2, l[i], -m[i], theta, phi, &a, &b); yr[q] = a; yi[q] = b; ++q;
+        }
+    }
+    for (int64_t j = 0; j < count; ++j) {
+        long double ti = (long double)t0 + (long double)j * (long double)dt;
+        int k = find_segment(t, K, (double)ti);
+        long double x = ti - (long double)t[k];
+        const double *cp = M.cphi + 4 * k, *cq = M.cr + 4 * k;
+        long double Pphi = ((cp[3] * x + cp[2]) * x + cp[1]) * x + cp[0];
+        long double Pr = ((cq[3] * x + cq[2]) * x + cq[1]) * x + cq[0];
+        long double hr = 0.0L, hi = 0.0L;
+        for (int p = 0; p < Ns; ++p) {
+            int i = src[p];
+            const double *are = M.cre + (size_t)4 * S * i + 4 * k;
+            const double *aim = M.cim + (size_t)4 * S * i + 4 * k;
+            long double Ar = ((are[3] * x + are[2]) * x + are[1]) * x + are[0];
+            long double Ai = ((aim[3] * x + aim[2]) * x + aim[1]) * x + aim[0];
+            if (cj[p]) {                            /* (-1)^l conj(A) */
+                long double sg = (sl[p] & 1) ? -1.0L : 1.0L;
+                Ar = sg * Ar; Ai = -sg * Ai;
+            }
+            long double Phi = (long double)sm[p] * Pphi + (long double)sn[p] * Pr;
+            long double c = cosl(Phi), s = sinl(Phi);
+            long double vr = Ar * yr[p] - Ai * yi[p];
+            long double vi = Ar * yi[p] + Ai * yr[p];
+            hr += vr * c + vi * s;
+            hi += vi * c - vr * s;
+        }
+        out[2 * j] = (double)(scale * hr);
+        out[2 * j + 1] = (double)(scale * hi);
+    }
+    free(sl); free(sm); free(sn); free(src); free(cj); free(yr); free(yi);
+    model_free(&M);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ mismatch (Sec. 6) */
+
+/*
+ * overlap(a,b) = <a|b>/sqrt(<a|a><b|b>), mismatch = 1 - overlap, with S_n = 1.  For complex
+ * time series h = h_+ - i h_x, Parseval turns the frequency-domain inner product into
+ * sum_i Re(conj(a_i) b_i) (the sum of the + and x inner products), up to a constant factor
+ * that cancels in the ratio.  Computed in long double.  Returns NaN for a zero series.
+ */
+double oracle_overlap(const double *a, const double *b, int64_t n)
+{
+    long double ab = 0.0L, aa = 0.0L, bb = 0.0L;
+    for (int64_t i = 0; i < n; ++i) {
+        long double ar = a[2 * i], ai = a[2 * i + 1], br = b[2 * i], bi = b[2 * i + 1];
+        ab += ar * br + ai * bi;
+        aa += ar * ar + ai * ai;
+        bb += br * br + bi * bi;
+    }
+    if (aa == 0.0L || bb == 0.0L) return NAN;
+    return (double)(ab / sqrtl(aa * bb));
+}
+
+/*
+ * mismatch = 1 - overlap, evaluated without cancellation as 0.5*||a/|a| - b/|b|||^2, which
+ * equals 1 - Re<a/|a|, b/|b|> exactly for unit vectors.
+ */
+double oracle_mismatch(const double *a, const double *b, int64_t n)
+{
+    long double aa = 0.0L, bb = 0.0L;
+    for (int64_t i = 0; i < n; ++i) {
+        aa += (long double)a[2 * i] * a[2 * i] + (long double)a[2 * i + 1] * a[2 * i + 1];
+        bb += (long double)b[2 * i] * b[2 * i] + (long double)b[2 * i + 1] * b[2 * i + 1];
+    }
+    if (aa == 0.0L || bb == 0.0L) return NAN;
+    long double na = 1.0L / sqrtl(aa), nb = 1.0L / sqrtl(bb), acc = 0.0L;
+    for (int64_t i = 0; i < n; ++i) {
+        long double dr = a[2 * i] * na - b[2 * i] * nb;
+        long double di = a[2 * i + 1] * na - b[2 * i + 1] * nb;
+        acc += dr * dr + di * di;
+    }
+    return (double)(0.5L * acc);
+}
+
+int oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
