@@ -1,0 +1,454 @@
+#!/usr/bin/env python3
+"""Benchmark of the interpolated EMRI mode summation on GB300.
+
+Workload (the configuration the headline metric is quoted on): one 1-yr waveform at dt = 10 s
+(3,155,760 samples), K = 100 knots, the full 3843-mode Schwarzschild grid (l = 2..10,
+m = 0..l, n = -30..30), synthetic seeded inputs.  A step is one pass of the whole hot path
+with the knot data resident in HBM: spline build (all 7688 splines), harmonics, fold and the
+per-sample mode sum, written to a device buffer.
+
+Default arm (--impl gb300): the mixed-precision path (the fast path); the plain FP64 GPU path
+is measured beside it.  Reference arm (--impl reference): the FP64 CPU oracle on the host cores,
+on a bounded sample of the same workload, same metric.
+
+One JSON line on stdout (rank 0).  Multi-GPU (torchrun): every rank computes its own
+waveforms (independent problems, weak scaling, no collective on the data path); value is the
+sum over ranks, timing the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2104_04582_gb300 import workloads as W  # noqa: E402
+
+METRIC = "1-yr waveforms/s (3843 modes, dt=10 s) at mismatch<=1e-6; mode-samples/s vs plain FP64 path"
+UNIT = "waveforms/s"
+WORKLOAD = ("1-yr waveform, dt=10 s (3,155,760 samples), K=100 knots, 3843 modes "
+            "(l=2..10, m=0..l, n=-30..30), m<0 by symmetry")
+N_SMS = 152
+FP32_LANES_PER_SM = 128
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def _peaks_file():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh)
+    return {}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "sm_mhz_min": min(sm), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ CPU baseline (oracle)
+
+def cpu_baseline(w, target_s: float = 12.0, max_samples=None):
+    """The oracle, as it stands, on a bounded prefix of the workload; all host cores."""
+    import oracle
+    threads = os.cpu_count() or 1
+    calib = 200
+    t0 = time.perf_counter()
+    oracle.waveform_inputs(w, 0, calib, nthreads=threads)
+    dt_c = max(time.perf_counter() - t0, 1e-4)
+    n = int(min(w.n_samples, max(2000, calib * target_s / dt_c)))
+    if max_samples:
+        n = min(n, max_samples)
+    t0 = time.perf_counter()
+    h = oracle.waveform_inputs(w, 0, n, nthreads=threads)
+    el = time.perf_counter() - t0
+    value = (n / el) / w.n_samples
+    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {n} of {w.n_samples} samples of the 1-yr 3843-mode waveform "
+                      f"({n * w.N:.3g} mode-samples, {el:.1f} s wall, {threads} OpenMP threads); "
+                      "waveforms/s scaled by the sample fraction",
+            "mode_samples_per_s": n * w.N / el, "seconds": el}, h
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def _mismatch(a, b) -> float:
+    """1 - overlap with unit noise (time-domain form), as 0.5*||a/|a| - b/|b|||^2."""
+    a = np.asarray(a, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    d = a / np.linalg.norm(a) - b / np.linalg.norm(b)
+    return float(0.5 * np.vdot(d, d).real)
+
+
+def l2_flush_buffer(torch, dev):
+    return torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+
+def measure_peaks(dev_index: int):
+    """FP32 FMA, FP64 FMA and SFU rates from the probe library (ops/s, FMA = 1 op)."""
+    import ctypes
+    from paper_2104_04582_gb300 import _build
+    if not os.path.exists(_build.PROBE_LIB):
+        return {}
+    L = ctypes.CDLL(_build.PROBE_LIB)
+    L.fewprobe_measure.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)]
+    out = {}
+    for which, name, it0 in ((0, "fp32_fma_per_s", 20000), (1, "fp64_fma_per_s", 400),
+                             (2, "sfu_sin_per_s", 4000)):
+        r, ms = ctypes.c_double(), ctypes.c_float()
+        if L.fewprobe_measure(dev_index, which, it0, ctypes.byref(r), ctypes.byref(ms)):
+            continue
+        iters = int(it0 * max(1.0, 60.0 / max(ms.value, 1e-3)))
+        if L.fewprobe_measure(dev_index, which, iters, ctypes.byref(r), ctypes.byref(ms)):
+            continue
+        out[name] = r.value
+    return out
+
+
+def run_gpu(args, rank: int, world: int, local_rank: int):
+    import torch
+    from paper_2104_04582_gb300 import _build
+    from paper_2104_04582_gb300 import fewsum as F
+    from paper_2104_04582_gb300 import runtime as RT
+
+    _build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = W.config2(W.SEEDS["C2"] + rank)
+    ctx = RT.Context(local_rank)
+    F.few_ctx_set_timing(ctx.handle, True)
+    stream = torch.cuda.current_stream(dev)
+    sh = int(stream.cuda_stream)
+    prec = F.FEW_MIXED if args.prec == "mixed" else F.FEW_FP64
+    c64 = prec == F.FEW_MIXED
+
+    tr = RT.Trajectory(ctx, w.t_knots, w.modes)
+    dev_in = tr.upload_inputs(w.phi_phi, w.phi_r, w.amp_re, w.amp_im)
+    out = RT.alloc_out(w.n_samples, c64, local_rank)
+    req = RT.request(tr, out, w.n_samples, w.t0, w.dt, w.theta, w.phi, prec)
+    flush = l2_flush_buffer(torch, dev)
+    K_, N_, slots = tr.info
+
+    def step():
+        F.few_traj_set_data(ctx.handle, tr.handle, *dev_in, stream=sh)
+        F.few_waveform(ctx.handle, req, sh)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ctx.sync_status() != F.FEW_OK:
+        raise RuntimeError("device error during warm-up")
+
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sum_ms = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()  # evict L2 between timed steps (outside the step's events)
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+        kt = F.few_last_timing(ctx.handle)
+        sum_ms.append(kt[3])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop() if sampler else None
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_local = sum(step_ms) / len(step_ms)
+    if ctx.sync_status() != F.FEW_OK:
+        raise RuntimeError("device error during the timed region")
+    h_fast = out.cpu().numpy().astype(np.complex128) if rank == 0 else None
+    kernel_ms = [float(x) for x in sum_ms if x > 0]
+    last_t = F.few_last_timing(ctx.handle)
+
+    # plain FP64 path on the same inputs (fewer steps: it is ~50x slower)
+    plain = None
+    h_plain = None
+    if rank == 0 and not args.no_plain and prec == F.FEW_MIXED:
+        out64 = RT.alloc_out(w.n_samples, False, local_rank)
+        req64 = RT.request(tr, out64, w.n_samples, w.t0, w.dt, w.theta, w.phi, F.FEW_FP64)
+        F.few_traj_set_data(ctx.handle, tr.handle, *dev_in, stream=sh)
+        F.few_waveform(ctx.handle, req64, sh)
+        torch.cuda.synchronize()
+        pk = max(2, min(5, args.steps))
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(pk)]
+        sum64 = []
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            F.few_traj_set_data(ctx.handle, tr.handle, *dev_in, stream=sh)
+            F.few_waveform(ctx.handle, req64, sh)
+            b.record(stream)
+            sum64.append(F.few_last_timing(ctx.handle)[3])
+        torch.cuda.synchronize()
+        ms64 = sum(a.elapsed_time(b) for a, b in ev) / pk
+        h_plain = out64.cpu().numpy()
+        plain = {"ms_per_step": ms64, "value": 1000.0 / ms64, "unit": UNIT,
+                 "mode_samples_per_s": w.N * w.n_samples / (ms64 * 1e-3),
+                 "sum_kernel_ms": sum(sum64) / len(sum64), "dtype": "f64"}
+        del out64
+
+    # e2e through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if rank == 0:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        h_in = [pin(a) for a in (w.phi_phi, w.phi_r, w.amp_re, w.amp_im)]
+        host_out = torch.empty(w.n_samples, dtype=torch.complex64 if c64 else torch.complex128
+                               ).pin_memory().numpy()
+        req_h = RT.request(tr, host_out, w.n_samples, w.t0, w.dt, w.theta, w.phi, prec,
+                           out_where=F.FEW_MEM_HOST)
+        e_steps = max(3, min(args.steps, 10))
+        for _ in range(2):
+            F.few_traj_set_data(ctx.handle, tr.handle, *h_in, stream=sh)
+            F.few_waveform(ctx.handle, req_h, sh)
+        torch.cuda.synchronize()
+        t_e = []
+        for _ in range(e_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            F.few_traj_set_data(ctx.handle, tr.handle, *h_in, stream=sh)
+            F.few_waveform(ctx.handle, req_h, sh)  # host output: returns after the D2H copy
+            t_e.append(time.perf_counter() - t0)
+        h2d = sum(a.nbytes for a in h_in)
+        d2h = host_out.nbytes
+        e2e = {"value": 1.0 / statistics.mean(t_e), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": 1000.0 * statistics.mean(t_e), "steps": e_steps,
+               "timer": "host wall clock around the two C-ABI calls (the call with host output "
+                        "returns after its device-to-host copy)"}
+
+    # pipe peaks
+    peaks = measure_peaks(local_rank) if rank == 0 and not args.no_probe else {}
+
+    torch.cuda.synchronize()
+    tr.release()
+    ctx.close()
+    return dict(w=w, ms_local=ms_local, step_ms=step_ms, kernel_ms=kernel_ms, last_t=last_t,
+                clocks=clocks, plain=plain, e2e=e2e, peaks=peaks, slots=slots,
+                h_fast=h_fast, h_plain=h_plain, prec=prec)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-probe", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        w = W.config2()
+        per_step = []
+        cb = None
+        for k in range(args.warmup + args.steps):
+            cb, _ = cpu_baseline(w, target_s=max(1.0, min(args.cpu_seconds, 60.0 / max(1, args.steps))))
+            if k >= args.warmup:
+                per_step.append(cb["seconds"])
+        v = cb["value"]
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "seed": W.SEEDS["C2"],
+                           "note": "each step times the oracle on a bounded prefix of the waveform"},
+                "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    res = run_gpu(args, rank, world, local_rank)
+    ms = res["ms_local"]
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=torch.device("cuda", local_rank))
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+
+    w = res["w"]
+    value = world * 1000.0 / ms  # every rank computed one waveform per step
+    mode_samples = w.N * w.n_samples
+    slots = res["slots"]
+    kms = statistics.mean(res["kernel_ms"]) if res["kernel_ms"] else float("nan")
+    fp32 = res["prec"] == 1
+    # algorithmic arithmetic of the summation kernel: one complex cubic (6 FMA) and one complex
+    # Horner step (4 FMA) per (harmonic slot, sample); an FMA is 2 flops
+    flops = 20.0 * slots * w.n_samples
+    achieved = flops / (kms * 1e-3) / 1e12
+    clocks = res["clocks"] or {}
+    mp = _peaks_file()
+    sm_max = float(mp.get("sm_max_mhz", 2070.0))
+    if fp32:
+        peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        peak_src = (f"FP32 FMA: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz "
+                    "(max SM clock)")
+    else:
+        peak = FP64_NOMINAL_TFLOPS
+        peak_src = "FP64 nominal 1.25 TFLOP/s"
+    probe = res["peaks"]
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "k_sum<float,R> (mixed)" if fp32 else "k_sum<double,R> (fp64)",
+            "kernel_ms": kms, "flops_per_launch": flops,
+            "peak_source": peak_src}
+    if probe:
+        key = "fp32_fma_per_s" if fp32 else "fp64_fma_per_s"
+        if key in probe:
+            pm = 2 * probe[key] / 1e12
+            roof["peak_probe_tflops"] = pm
+            roof["frac_of_probe"] = achieved / pm
+    if clocks.get("sm_mhz"):
+        roof["frac_at_measured_clock"] = achieved / (peak * clocks["sm_mhz"] / sm_max)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if fp32 else "f64",
+        "precision": ("mixed: FP64 phase splines and mod-2pi reduction; FP32 amplitudes, "
+                      "exponential powers and accumulation") if fp32 else "fp64 throughout",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "seed": W.SEEDS["C2"], "knots": w.K, "modes": w.N,
+                   "samples": w.n_samples, "harmonic_slots": slots,
+                   "l2": "flushed (256 MB write) between timed steps",
+                   "step": "spline build + harmonics + fold + mode sum, inputs resident in HBM",
+                   "parallelism": f"replicas x{world}"},
+        "mode_samples_per_s": world * mode_samples / (ms * 1e-3),
+        "kernel_ms": {"build": res["last_t"][0], "harmonics": res["last_t"][1],
+                      "fold": res["last_t"][2], "sum": kms},
+        "roofline": roof,
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks or None,
+        "e2e": res["e2e"],
+    }
+    if res["plain"]:
+        line["plain_fp64"] = res["plain"]
+        line["speedup_vs_plain_fp64"] = res["plain"]["ms_per_step"] / ms
+    if probe:
+        line["measured_pipe_peaks"] = {k: v for k, v in probe.items()}
+    # accuracy of this run's outputs
+    acc = {}
+    if res["h_plain"] is not None:
+        acc["mismatch_mixed_vs_fp64_full_series"] = _mismatch(res["h_fast"], res["h_plain"])
+    if not args.no_cpu:
+        cb, h_or = cpu_baseline(w, target_s=args.cpu_seconds)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        import oracle
+        n = len(h_or)
+        acc["mismatch_vs_oracle_window"] = oracle.mismatch(res["h_fast"][:n], h_or)
+        acc["rel_l2_vs_oracle_window"] = float(np.linalg.norm(res["h_fast"][:n] - h_or)
+                                               / np.linalg.norm(h_or))
+        if res["h_plain"] is not None:
+            hp = res["h_plain"]
+            acc["fp64_rel_l2_vs_oracle_window"] = float(np.linalg.norm(hp[:n] - h_or)
+                                                        / np.linalg.norm(h_or))
+        acc["oracle_window_samples"] = n
+    line["accuracy"] = acc
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

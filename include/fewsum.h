@@ -1,0 +1,262 @@
+/*
+ * fewsum.h -- C ABI of libfewsum.so: GB300-native interpolated EMRI mode summation.
+ *
+ * The library computes the Schwarzschild-eccentric waveform of arXiv:2104.04582 Sec. 4,
+ *
+ *     h(t) = h_+ - i h_x = (mu/d_L) sum_{l,m,n} A_lmn(t) -2Y_lm(theta, phi) exp(-i Phi_mn(t)),
+ *     Phi_mn(t) = m Phi_phi(t) + n Phi_r(t),
+ *
+ * by the "interpolated summation" of Sec. 3.C: the orbital phases Phi_phi, Phi_r and every
+ * selected mode's complex amplitude A_lmn are given on a sparse trajectory grid t_0 < ... <
+ * t_{K-1}; each real array is fitted with a not-a-knot cubic spline on that shared grid, and
+ * the mode sum is evaluated at every dense sample t_i = t0 + i*dt.  Only modes with m >= 0 are
+ * passed in; the m < 0 modes follow from Eq. (amp_symmetry) with k = 0,
+ * A_{l,-m,-n} = (-1)^l conj(A_lmn), and are added for m > 0 only (an m = 0 mode of the list is
+ * used as given; (l,0,n) and (l,0,-n) are distinct entries of the paper's 3843-mode grid).
+ *
+ * Everything between the inputs and h runs in this library's CUDA kernels on one GPU:
+ * the batched spline build, the spin-weighted harmonics, the per-request fold of harmonics
+ * into the spline coefficients, and the per-sample evaluation and mode sum.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Errors: every call returns a few_status; nothing throws or aborts across the ABI.  Inputs are
+ *   validated on the host before any work is queued; on a validation error nothing is queued
+ *   and no output is touched.  Problems that can only be seen on the device (a NaN in
+ *   device-resident inputs, a bounded wait that expired) latch into the context and are
+ *   returned by few_sync_status().  A CUDA runtime error is returned as FEW_ERR_CUDA.
+ * Ownership: the caller owns every pointer it passes (host or device) and may free or reuse
+ *   host input memory as soon as the call returns.  Device inputs and outputs must stay valid
+ *   until the work queued on the given stream has completed.  The library owns the context,
+ *   trajectory and batch handles and all memory they hold.
+ * Streams: calls that take a `stream` (a cudaStream_t passed as void*; NULL = the legacy
+ *   default stream) queue their device work on it and return without waiting, unless
+ *   documented otherwise.  Work on one handle from several streams must be ordered by the
+ *   caller.
+ * Threads: a context may be used from several host threads; every call on a context takes
+ *   the context's lock.
+ * Layouts: complex outputs are interleaved (re, im) pairs, complex128 (2 x f64) or
+ *   complex64 (2 x f32).  Per-knot mode arrays are row-major [K][N] (modes contiguous).
+ * Limits: K >= 4 knots; 1 <= N modes; 2 <= l <= 32, 0 <= m <= l, |n| <= 1024, no duplicate
+ *   (l,m,n); n_samples <= 2^31 - 1.  The per-segment harmonic table must fit in shared
+ *   memory (see few_mode_slots): at most FEW_MAX_SLOTS_FP64 slots for FEW_FP64 and
+ *   FEW_MAX_SLOTS_MIXED for FEW_MIXED; larger mode sets fail with FEW_ERR_LIMIT.
+ */
+#ifndef FEWSUM_H
+#define FEWSUM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FEW_ABI_VERSION 1
+#define FEW_MAX_SLOTS_FP64 1776
+#define FEW_MAX_SLOTS_MIXED 3552
+
+typedef enum few_status {
+    FEW_OK = 0,
+    FEW_ERR_INVALID_ARG = 1, /* null pointer, bad enum, non-finite scalar, NaN in device data */
+    FEW_ERR_KNOTS = 2,       /* K < 4, knots not strictly increasing or not finite */
+    FEW_ERR_MODES = 3,       /* N < 1, l < 2, m < 0, m > l, |n| > 1024, duplicate (l,m,n) */
+    FEW_ERR_RANGE = 4,       /* samples outside [t_0, t_{K-1}], dt <= 0, n_samples too big */
+    FEW_ERR_NOMEM = 5,       /* device or host allocation failed */
+    FEW_ERR_BUDGET = 6,      /* the call would exceed the context's HBM budget */
+    FEW_ERR_CUDA = 7,        /* a CUDA runtime call failed */
+    FEW_ERR_TIMEOUT = 8,     /* a bounded device-side wait expired (latched) */
+    FEW_ERR_LIMIT = 9,       /* a size exceeds an on-chip limit of the kernels */
+    FEW_ERR_STATE = 10       /* handle used in the wrong state (e.g. no data set) */
+} few_status;
+
+typedef enum few_precision {
+    FEW_FP64 = 0,  /* plain path: every step in FP64 */
+    FEW_MIXED = 1  /* FP64 phase splines + mod-2pi reduction; FP32 amplitudes, exponentials, sum */
+} few_precision;
+
+typedef enum few_mem {
+    FEW_MEM_HOST = 0,   /* pointer is host memory (pageable or pinned) */
+    FEW_MEM_DEVICE = 1  /* pointer is device memory of the context's GPU */
+} few_mem;
+
+typedef struct few_ctx few_ctx;
+typedef struct few_traj few_traj;
+typedef struct few_batch few_batch;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *few_strerror(few_status s);
+
+/* Library ABI version (FEW_ABI_VERSION of the build). */
+int few_abi_version(void);
+
+/*
+ * Create a context on CUDA device `device`.  `hbm_budget_bytes` caps the device memory the
+ * library may hold at once for this context (trajectories, per-call scratch, staging); 0 means
+ * no cap beyond the device's free memory.  Allocations go through a stream-ordered pool owned
+ * by the context.  Blocking.
+ */
+few_status few_ctx_create(few_ctx **out, int device, size_t hbm_budget_bytes);
+
+/* Wait for the device, free everything the context owns (including live trajectories and
+ * batches), and destroy it.  NULL is accepted. */
+few_status few_ctx_destroy(few_ctx *ctx);
+
+/* Bytes of device memory the context currently holds (allocated by the library). */
+few_status few_ctx_memory(few_ctx *ctx, size_t *bytes_in_use, size_t *budget_bytes);
+
+/*
+ * Create a trajectory: the knot grid and the mode list (Sec. 3.C: all splines share one knot
+ * grid; Sec. 4: the (l,m,n) mode set with m >= 0).
+ *   t_knots [K]: strictly increasing finite times (s), host memory, copied.
+ *   l, m, n [N]: mode indices, host memory, copied.
+ * Plans the shared tridiagonal factorization on the device (one launch on an internal stream)
+ * and waits for it.  Spline data are set with few_traj_set_data before first use.
+ * Errors: FEW_ERR_KNOTS, FEW_ERR_MODES, FEW_ERR_BUDGET, FEW_ERR_NOMEM, FEW_ERR_CUDA.
+ */
+few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int *l, const int *m,
+                           const int *n, int N, few_traj **out);
+
+/*
+ * Set the values on the trajectory grid and build every spline (Sec. 3.C: batched not-a-knot
+ * cubic splines for both phases and for the real and imaginary part of every amplitude; one
+ * tridiagonal solve per spline, all sharing the knot matrix).
+ *   phi_phi, phi_r [K]: orbital phases (rad) at the knots.
+ *   amp_re, amp_im [K][N]: Re and Im of A_lmn at the knots, row-major, modes contiguous.
+ *   where: FEW_MEM_HOST (copied to the device first; the copy is ordered on `stream` and the
+ *          host arrays may be reused when the call returns) or FEW_MEM_DEVICE (read in place by
+ *          the build kernel; must stay valid until the work on `stream` completes).
+ * Asynchronous on `stream`.  Non-finite values are detected on the device and latched as
+ * FEW_ERR_INVALID_ARG (see few_sync_status).
+ */
+few_status few_traj_set_data(few_ctx *ctx, few_traj *traj, const double *phi_phi,
+                             const double *phi_r, const double *amp_re, const double *amp_im,
+                             few_mem where, void *stream);
+
+/* Release a trajectory and its device memory (after the device is idle on its work). */
+few_status few_traj_release(few_ctx *ctx, few_traj *traj);
+
+/* Knot count, mode count and harmonic slots per segment of a trajectory. */
+few_status few_traj_info(const few_traj *traj, int *K, int *N, int *n_slots);
+
+/*
+ * One waveform request.  Output sample i (0 <= i < n_samples) is h(t0 + i*dt), Sec. 4 sum.
+ *   theta, phi: source-frame viewing angles (rad) of -2Y_lm (Sec. 2.A).
+ *   scale: the real prefactor mu/d_L (1 for the dimensionless sum).
+ *   dphi_phi0, dphi_r0: constant offsets (rad) added to Phi_phi and Phi_r -- a change of the
+ *     initial phases Phi_phi,0 and Phi_r,0 without rebuilding the splines.
+ *   t0, dt: first sample time and cadence (s); every sample must lie in [t_0, t_{K-1}].
+ *   prec: FEW_FP64 or FEW_MIXED.
+ *   out: n_samples complex values, complex64 if out_c64 else complex128; device memory if
+ *     out_where == FEW_MEM_DEVICE, else host memory (the library stages the result on the
+ *     device and copies it back on `stream`).
+ */
+typedef struct few_request {
+    const few_traj *traj;
+    double theta, phi;
+    double scale;
+    double dphi_phi0, dphi_r0;
+    double t0, dt;
+    int64_t n_samples;
+    int prec;       /* few_precision */
+    int out_c64;    /* 1: complex64 output, 0: complex128 output */
+    int out_where;  /* few_mem of `out` */
+    int reserved;
+    void *out;
+} few_request;
+
+/*
+ * Compute one waveform (Sec. 3.C interpolated summation of the Sec. 4 sum).  Validates and
+ * plans on the host, then queues the harmonic, fold and summation kernels on `stream`.
+ * n_samples == 0 is a no-op.  Errors: FEW_ERR_INVALID_ARG, FEW_ERR_STATE, FEW_ERR_RANGE,
+ * FEW_ERR_LIMIT, FEW_ERR_BUDGET, FEW_ERR_NOMEM, FEW_ERR_CUDA.
+ */
+few_status few_waveform(few_ctx *ctx, const few_request *req, void *stream);
+
+/*
+ * The per-sample phase step on its own (Sec. 2 phase integrals, interpolated as in Sec. 3.C):
+ * for sample i, t_i = t0 + i*dt, writes the orbital phases Phi_phi(t_i) + dphi_phi0 and
+ * Phi_r(t_i) + dphi_r0 reduced modulo 2 pi and expressed in turns, each in [-1/2, 1/2]:
+ * out_dev[2i] = f_phi, out_dev[2i+1] = f_r (device memory, n_samples x 2 doubles).  The same
+ * FP64 evaluation and reduction feed both summation paths.  Asynchronous on `stream`.
+ * Errors: as few_waveform (FEW_ERR_STATE, FEW_ERR_RANGE, FEW_ERR_INVALID_ARG, ...).
+ */
+few_status few_phase_samples(few_ctx *ctx, const few_traj *traj, double t0, double dt,
+                             int64_t n_samples, double dphi_phi0, double dphi_r0, double *out_dev,
+                             void *stream);
+
+/* Flags of few_batch_plan. */
+#define FEW_BATCH_REBUILD_SPLINES 1u  /* each run also rebuilds every distinct trajectory's
+                                         splines from its device-resident knot data */
+#define FEW_BATCH_NO_GRAPH 2u         /* run by direct launches instead of a CUDA graph */
+
+/*
+ * Plan a batch of requests (all with the same `prec`; any mix of trajectories, durations,
+ * cadences and mode counts) executed as one persistent summation launch whose CTAs take
+ * equal-cost slices of the concatenated (waveform, sample) work.  The plan holds its own
+ * scratch; the kernels are captured once into a CUDA graph (unless FEW_BATCH_NO_GRAPH), and
+ * each few_batch_run replays it.  Every request must use out_where == FEW_MEM_DEVICE.  The
+ * trajectories and output buffers must stay valid while the batch exists.  Blocking (uploads
+ * the plan and, for the graph, captures it).
+ */
+few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned flags,
+                          few_batch **out);
+
+/* Run a planned batch on `stream` (graph launch or direct launches). Asynchronous. */
+few_status few_batch_run(few_ctx *ctx, few_batch *batch, void *stream);
+
+/* Release a batch plan (after the device is idle on its work). */
+few_status few_batch_release(few_ctx *ctx, few_batch *batch);
+
+/*
+ * Wait for all work on the context's device, then return and clear the device-side error
+ * latch (FEW_ERR_INVALID_ARG for non-finite device inputs, FEW_ERR_TIMEOUT for an expired
+ * bounded wait), or FEW_ERR_CUDA if the device reported an error.  FEW_OK otherwise.
+ */
+few_status few_sync_status(few_ctx *ctx);
+
+/*
+ * Tile configuration of the summation kernel for one precision: samples per thread (R) and
+ * threads per block.  Supported: FEW_FP64: R in {1, 2}; FEW_MIXED: R in {2, 4, 8}; threads
+ * in {128, 256}.  Affects speed only: every configuration gives bit-identical results.
+ */
+few_status few_set_tiles(few_ctx *ctx, int prec, int samples_per_thread, int threads_per_block);
+few_status few_get_tiles(few_ctx *ctx, int prec, int *samples_per_thread, int *threads_per_block);
+
+/*
+ * Per-kernel device timing.  With timing enabled, the library records a CUDA event pair on the
+ * launch stream around each kernel it queues.  few_last_timing waits for the most recent pairs
+ * and returns their durations in ms: ms[0] spline build (last few_traj_set_data), ms[1]
+ * harmonics, ms[2] fold, ms[3] summation (last few_waveform or few_batch_run without a graph).
+ * Entries never recorded are returned as -1.
+ */
+few_status few_ctx_set_timing(few_ctx *ctx, int enable);
+few_status few_last_timing(few_ctx *ctx, float *ms);
+
+/* ---------------------------------------------------------------- host-only planning
+ * These run on the host only (no GPU needed) and expose the planning step of few_waveform.
+ */
+
+/*
+ * Sample range of every segment (Sec. 3.C: all arrays share one knot grid): segment k
+ * (0 <= k < K-1) owns samples [seg_start[k], seg_start[k+1]) with seg_start[k] =
+ * clamp(ceil((t_k - t0)/dt), 0, n_samples) for k >= 1, seg_start[0] = 0 and
+ * seg_start[K-1] = n_samples (a sample on a knot belongs to the segment that starts there;
+ * one on the last knot belongs to the last segment).  seg_start has K entries.
+ * Validates as few_waveform does (FEW_ERR_KNOTS, FEW_ERR_RANGE).
+ */
+few_status few_plan_segments(const double *t_knots, int K, double t0, double dt, int64_t n_samples,
+                             int64_t *seg_start);
+
+/*
+ * Harmonic slot plan of a mode list: the distinct signed (m, n) frequencies that the m >= 0
+ * modes and their m < 0 partners (Eq. amp_symmetry) occupy, laid out as rows of constant m
+ * (zero-filled between n = 0 and the row's extreme n).  Returns the slot count per segment and
+ * the number of rows.  Validates the modes (FEW_ERR_MODES).
+ */
+few_status few_mode_slots(const int *l, const int *m, const int *n, int N, int *n_slots, int *n_rows);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEWSUM_H */

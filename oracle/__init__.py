@@ -63,6 +63,9 @@ def _bind(L: ctypes.CDLL) -> ctypes.CDLL:
     L.oracle_overlap.restype = ctypes.c_double
     L.oracle_mismatch.argtypes = [_dp, _dp, i64]
     L.oracle_mismatch.restype = ctypes.c_double
+    L.oracle_phases.argtypes = [_dp, ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                i64, i64, _dp]
+    L.oracle_phases.restype = ctypes.c_int
     L.oracle_max_threads.argtypes = []
     L.oracle_max_threads.restype = ctypes.c_int
     return L
@@ -181,6 +184,17 @@ def direct_sum(t, phi_phi, phi_r, modes, amp_re, amp_im, theta, phi, scale=1.0, 
         raise OracleError(f"oracle_direct_sum: status {rc}")
     del keep
     return out.view(np.complex128)
+
+
+def phases(t, phi_phi, phi_r, t0, dt, i_begin, count) -> np.ndarray:
+    """Orbital phases at the samples, each reduced mod 2 pi, in turns: float64 [count, 2]."""
+    t, pp, pr = _d(t), _d(phi_phi), _d(phi_r)
+    out = np.zeros(2 * int(count))
+    rc = lib().oracle_phases(_p(t), len(t), _p(pp), _p(pr), float(t0), float(dt), int(i_begin),
+                             int(count), _p(out))
+    if rc:
+        raise OracleError(f"oracle_phases: status {rc}")
+    return out.reshape(-1, 2)
 
 
 def _c(a) -> np.ndarray:

@@ -53,26 +53,27 @@ static const double TWO_PI = 6.283185307179586476925286766559;
  *   (h_{K-2}+h_{K-3}) s_{K-2} + h_{K-3} s_{K-1}
  *        = (h_{K-2}^2 d_{K-3} + (2h_{K-3}+3h_{K-2}) h_{K-3} d_{K-2}) / (h_{K-3}+h_{K-2}).
  * The tridiagonal system is solved by Gaussian elimination WITH partial pivoting (row
- * swaps create one extra super-diagonal), one system per call.
+ * swaps create one extra super-diagonal), one system per call, in long double.
  * Output: coef[k*4 + p], p = 0..3, the cubic on [t_k, t_{k+1}] in x = t - t_k:
  *   c0 = y_k, c1 = s_k, c2 = (3 d_k - 2 s_k - s_{k+1})/h_k, c3 = (s_k + s_{k+1} - 2 d_k)/h_k^2.
  */
-int oracle_spline_nak(const double *t, int K, const double *y, double *coef)
+static int nak_solve(const double *t, int K, const long double *y, long double *coef)
 {
+    typedef long double R;
     if (K < 4) return OR_ERR_KNOTS;
     for (int k = 0; k + 1 < K; ++k)
         if (!(t[k + 1] > t[k])) return OR_ERR_KNOTS;
     int n = K;
-    double *h = malloc(sizeof(double) * (n - 1));
-    double *d = malloc(sizeof(double) * (n - 1));
-    double *dl = calloc(n, sizeof(double));   /* sub-diagonal: dl[k] = A[k+1][k] */
-    double *dg = calloc(n, sizeof(double));   /* diagonal */
-    double *du = calloc(n, sizeof(double));   /* super-diagonal: du[k] = A[k][k+1] */
-    double *du2 = calloc(n, sizeof(double));  /* fill-in: du2[k] = A[k][k+2] */
-    double *b = calloc(n, sizeof(double));
-    double *s = calloc(n, sizeof(double));
+    R *h = malloc(sizeof(R) * (n - 1));
+    R *d = malloc(sizeof(R) * (n - 1));
+    R *dl = calloc(n, sizeof(R));   /* sub-diagonal: dl[k] = A[k+1][k] */
+    R *dg = calloc(n, sizeof(R));   /* diagonal */
+    R *du = calloc(n, sizeof(R));   /* super-diagonal: du[k] = A[k][k+1] */
+    R *du2 = calloc(n, sizeof(R));  /* fill-in: du2[k] = A[k][k+2] */
+    R *b = calloc(n, sizeof(R));
+    R *s = calloc(n, sizeof(R));
     for (int k = 0; k < n - 1; ++k) {
-        h[k] = t[k + 1] - t[k];
+        h[k] = (R)t[k + 1] - (R)t[k];
         d[k] = (y[k + 1] - y[k]) / h[k];
     }
     /* row 0 */
@@ -88,30 +89,30 @@ int oracle_spline_nak(const double *t, int K, const double *y, double *coef)
     }
     /* last row */
     {
-        double a = h[n - 2], c = h[n - 3];
+        R a = h[n - 2], c = h[n - 3];
         dl[n - 2] = a + c;
         dg[n - 1] = c;
         b[n - 1] = (a * a * d[n - 3] + (2.0 * c + 3.0 * a) * c * d[n - 2]) / (c + a);
     }
     /* forward elimination with partial pivoting */
     for (int k = 0; k < n - 1; ++k) {
-        if (fabs(dg[k]) >= fabs(dl[k])) {
-            double mult = dl[k] / dg[k];
+        if (fabsl(dg[k]) >= fabsl(dl[k])) {
+            R mult = dl[k] / dg[k];
             dg[k + 1] -= mult * du[k];
             b[k + 1] -= mult * b[k];
             du2[k] = 0.0;
         } else {
             /* swap rows k and k+1; the new pivot row is the old row k+1 */
-            double mult = dg[k] / dl[k];
-            double old_dg1 = dg[k + 1];
-            double old_du1 = (k + 1 < n - 1) ? du[k + 1] : 0.0;
-            double old_duk = du[k];
+            R mult = dg[k] / dl[k];
+            R old_dg1 = dg[k + 1];
+            R old_du1 = (k + 1 < n - 1) ? du[k + 1] : 0.0;
+            R old_duk = du[k];
             dg[k] = dl[k];
             du[k] = old_dg1;
             du2[k] = old_du1;
             dg[k + 1] = old_duk - mult * old_dg1;
             if (k + 1 < n - 1) du[k + 1] = -mult * old_du1;
-            double bk = b[k];
+            R bk = b[k];
             b[k] = b[k + 1];
             b[k + 1] = bk - mult * b[k];
         }
@@ -129,6 +130,31 @@ int oracle_spline_nak(const double *t, int K, const double *y, double *coef)
     }
     free(h); free(d); free(dl); free(dg); free(du); free(du2); free(b); free(s);
     return OR_OK;
+}
+
+/* Double-precision interface: inputs and coefficients in double, the solve in long double. */
+int oracle_spline_nak(const double *t, int K, const double *y, double *coef)
+{
+    if (K < 4) return OR_ERR_KNOTS;
+    long double *yl = malloc(sizeof(long double) * K);
+    long double *cl = malloc(sizeof(long double) * 4 * (K - 1));
+    for (int k = 0; k < K; ++k) yl[k] = y[k];
+    int rc = nak_solve(t, K, yl, cl);
+    if (!rc)
+        for (int q = 0; q < 4 * (K - 1); ++q) coef[q] = (double)cl[q];
+    free(yl);
+    free(cl);
+    return rc;
+}
+
+/* Long-double coefficients (used for the orbital phases, which reach 1e5-1e7 rad). */
+static int spline_nak_ld(const double *t, int K, const double *y, long double *coef)
+{
+    long double *yl = malloc(sizeof(long double) * K);
+    for (int k = 0; k < K; ++k) yl[k] = y[k];
+    int rc = nak_solve(t, K, yl, coef);
+    free(yl);
+    return rc;
 }
 
 /* Segment of t: the k with t_k <= t < t_{k+1}; a sample on the last knot uses K-2. */
@@ -199,7 +225,9 @@ void oracle_swsh(int s, int l, int m, double theta, double phi, double *re, doub
 typedef struct {
     int K, N;
     const double *t;
-    double *cphi, *cr;            /* [K-1][4] phase splines (rad) */
+    long double *cphi, *cr;       /* [K-1][4] phase splines (rad), long double: the phases
+                                     reach 1e5-1e7 rad, where a double ulp times |m|+|n|
+                                     approaches the 1e-9 rad scale of the FP64 comparison */
     double *cre, *cim;            /* [N][K-1][4] amplitude splines */
     double *yp_re, *yp_im;        /* -2Y_{l,m} per mode */
     double *ym_re, *ym_im;        /* (-1)^l -2Y_{l,-m} per mode (0 for m = 0) */
@@ -211,15 +239,15 @@ static int model_build(oracle_model *M, const double *t, int K, const double *ph
 {
     int S = K - 1, rc;
     M->K = K; M->N = N; M->t = t;
-    M->cphi = malloc(sizeof(double) * 4 * S);
-    M->cr = malloc(sizeof(double) * 4 * S);
+    M->cphi = malloc(sizeof(long double) * 4 * S);
+    M->cr = malloc(sizeof(long double) * 4 * S);
     M->cre = malloc(sizeof(double) * 4 * S * (size_t)N);
     M->cim = malloc(sizeof(double) * 4 * S * (size_t)N);
     M->yp_re = malloc(sizeof(double) * N); M->yp_im = malloc(sizeof(double) * N);
     M->ym_re = malloc(sizeof(double) * N); M->ym_im = malloc(sizeof(double) * N);
     double *col = malloc(sizeof(double) * K);
-    if ((rc = oracle_spline_nak(t, K, phi_phi, M->cphi))) goto done;
-    if ((rc = oracle_spline_nak(t, K, phi_r, M->cr))) goto done;
+    if ((rc = spline_nak_ld(t, K, phi_phi, M->cphi))) goto done;
+    if ((rc = spline_nak_ld(t, K, phi_r, M->cr))) goto done;
     for (int i = 0; i < N; ++i) {
         for (int k = 0; k < K; ++k) col[k] = amp_re[(size_t)k * N + i];
         if ((rc = oracle_spline_nak(t, K, col, M->cre + (size_t)4 * S * i))) goto done;
@@ -251,6 +279,22 @@ static double horner(const double *c, double x)
     return ((c[3] * x + c[2]) * x + c[1]) * x + c[0];
 }
 
+static long double horner_ld(const long double *c, long double x)
+{
+    return ((c[3] * x + c[2]) * x + c[1]) * x + c[0];
+}
+
+/* Orbital phases at t, reduced modulo one turn (each in [-1/2, 1/2] turns). */
+static void reduced_phases(const oracle_model *M, int k, double ti, double *fphi, double *fr)
+{
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    long double x = (long double)ti - (long double)M->t[k];
+    long double xphi = horner_ld(M->cphi + 4 * k, x) / two_pi;
+    long double xr = horner_ld(M->cr + 4 * k, x) / two_pi;
+    *fphi = (double)(xphi - rintl(xphi));
+    *fr = (double)(xr - rintl(xr));
+}
+
 /*
  * h(t_i) for i in [i_begin, i_begin+count), t_i = t0 + i*dt; out[2*j], out[2*j+1] = Re, Im.
  * At each sample: both phase splines are evaluated (rad) and reduced modulo 2 pi separately,
@@ -279,10 +323,8 @@ int oracle_waveform(const double *t, int K, const double *phi_phi, const double 
         double ti = t0 + (double)(i_begin + j) * dt;
         int k = find_segment(t, K, ti);
         double x = ti - t[k];
-        double xphi = horner(M.cphi + 4 * k, x) / TWO_PI;
-        double xr = horner(M.cr + 4 * k, x) / TWO_PI;
-        double fphi = xphi - rint(xphi);
-        double fr = xr - rint(xr);
+        double fphi, fr;
+        reduced_phases(&M, k, ti, &fphi, &fr);
         double hr = 0.0, hi = 0.0;
         for (int i = 0; i < N; ++i) {
             const double *are = M.cre + (size_t)4 * S * i + 4 * k;
@@ -309,6 +351,34 @@ int oracle_waveform(const double *t, int K, const double *phi_phi, const double 
     }
     model_free(&M);
     return OR_OK;
+}
+
+/*
+ * The orbital phases at t_i = t0 + i*dt, i in [i_begin, i_begin+count), each reduced modulo
+ * 2 pi and expressed in turns: out[2j] = f_phi, out[2j+1] = f_r, in [-1/2, 1/2].
+ */
+int oracle_phases(const double *t, int K, const double *phi_phi, const double *phi_r,
+                  double t0, double dt, int64_t i_begin, int64_t count, double *out)
+{
+    if (K < 4 || !(dt > 0.0) || count < 0) return OR_ERR_ARG;
+    int S = K - 1;
+    oracle_model M;
+    memset(&M, 0, sizeof(M));
+    M.K = K; M.t = t;
+    M.cphi = malloc(sizeof(long double) * 4 * S);
+    M.cr = malloc(sizeof(long double) * 4 * S);
+    int rc = spline_nak_ld(t, K, phi_phi, M.cphi);
+    if (!rc) rc = spline_nak_ld(t, K, phi_r, M.cr);
+    if (!rc) {
+        for (int64_t j = 0; j < count; ++j) {
+            double ti = t0 + (double)(i_begin + j) * dt;
+            if (ti < t[0] || ti > t[K - 1]) { rc = OR_ERR_RANGE; break; }
+            reduced_phases(&M, find_segment(t, K, ti), ti, &out[2 * j], &out[2 * j + 1]);
+        }
+    }
+    free(M.cphi);
+    free(M.cr);
+    return rc;
 }
 
 /*
@@ -347,9 +417,8 @@ int oracle_direct_sum(const double *t, int K, const double *phi_phi, const doubl
         long double ti = (long double)t0 + (long double)j * (long double)dt;
         int k = find_segment(t, K, (double)ti);
         long double x = ti - (long double)t[k];
-        const double *cp = M.cphi + 4 * k, *cq = M.cr + 4 * k;
-        long double Pphi = ((cp[3] * x + cp[2]) * x + cp[1]) * x + cp[0];
-        long double Pr = ((cq[3] * x + cq[2]) * x + cq[1]) * x + cq[0];
+        long double Pphi = horner_ld(M.cphi + 4 * k, x);
+        long double Pr = horner_ld(M.cr + 4 * k, x);
         long double hr = 0.0L, hi = 0.0L;
         for (int p = 0; p < Ns; ++p) {
             int i = src[p];

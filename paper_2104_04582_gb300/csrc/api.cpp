@@ -1,0 +1,1053 @@
+// api.cpp -- host side of libfewsum.so: the C ABI declared in include/fewsum.h.
+//
+// Responsibilities: input validation, the planning step (mode -> harmonic slot layout,
+// segment sample ranges, equal-cost CTA slices), device memory from a context-owned
+// stream-ordered pool with an HBM budget, plan uploads through pinned staging buffers, kernel
+// launches, CUDA-graph capture of batches, and the device error latch.  No arithmetic of the
+// waveform itself happens here; every numerical step runs in the kernels.
+#include "../../include/fewsum.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <set>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "fewsum_internal.h"
+
+using namespace fewsum;
+
+// ------------------------------------------------------------------------------ utilities
+
+namespace {
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+#define FEW_CUDA_TRY(expr)                                  \
+    do {                                                    \
+        cudaError_t e__ = (expr);                           \
+        if (e__ != cudaSuccess) {                           \
+            (void)cudaGetLastError();                       \
+            return e__ == cudaErrorMemoryAllocation ? FEW_ERR_NOMEM : FEW_ERR_CUDA; \
+        }                                                   \
+    } while (0)
+
+// Pinned host staging blocks for plan uploads, reused once their copy has completed.
+struct PinnedPool {
+    struct Block {
+        void *p = nullptr;
+        size_t bytes = 0;
+        cudaEvent_t ev = nullptr;
+        bool pending = false;
+    };
+    std::vector<Block> blocks;
+
+    ~PinnedPool() { release(); }
+    void release()
+    {
+        for (auto &b : blocks) {
+            if (b.ev) cudaEventDestroy(b.ev);
+            if (b.p) cudaFreeHost(b.p);
+        }
+        blocks.clear();
+    }
+    // A block of at least `bytes` that no queued copy still reads.
+    Block *acquire(size_t bytes)
+    {
+        for (auto &b : blocks) {
+            if (b.bytes < bytes) continue;
+            if (b.pending) {
+                if (cudaEventQuery(b.ev) != cudaSuccess) continue;
+                b.pending = false;
+            }
+            return &b;
+        }
+        Block nb;
+        nb.bytes = align_up(std::max(bytes, (size_t)1 << 16), 4096);
+        if (cudaHostAlloc(&nb.p, nb.bytes, cudaHostAllocDefault) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        if (cudaEventCreateWithFlags(&nb.ev, cudaEventDisableTiming) != cudaSuccess) {
+            (void)cudaGetLastError();
+            cudaFreeHost(nb.p);
+            return nullptr;
+        }
+        blocks.push_back(nb);
+        return &blocks.back();
+    }
+};
+
+}  // namespace
+
+struct few_traj;
+struct few_batch;
+
+struct few_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t budget = 0;  // 0: unlimited
+    size_t in_use = 0;
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t internal = nullptr;
+    unsigned *d_err = nullptr;
+    std::recursive_mutex mu;
+    std::unordered_map<void *, size_t> sizes;
+    std::set<few_traj *> trajs;
+    std::set<few_batch *> batches;
+    PinnedPool pinned;
+    int tile_R[2] = {1, 4};
+    int tile_T[2] = {256, 256};
+    std::map<std::tuple<int, int, int, int>, int> occ_cache;
+    bool timing = false;
+    cudaEvent_t tev[8] = {};
+    bool trec[4] = {false, false, false, false};
+};
+
+namespace {
+
+few_status dev_alloc(few_ctx *c, size_t bytes, cudaStream_t st, void **out)
+{
+    *out = nullptr;
+    if (bytes == 0) bytes = 256;
+    bytes = align_up(bytes, 256);
+    if (c->budget && c->in_use + bytes > c->budget) return FEW_ERR_BUDGET;
+    cudaError_t e = cudaMallocFromPoolAsync(out, bytes, c->pool, st);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        *out = nullptr;
+        return e == cudaErrorMemoryAllocation ? FEW_ERR_NOMEM : FEW_ERR_CUDA;
+    }
+    c->in_use += bytes;
+    c->sizes[*out] = bytes;
+    return FEW_OK;
+}
+
+void dev_free(few_ctx *c, void *p, cudaStream_t st)
+{
+    if (!p) return;
+    auto it = c->sizes.find(p);
+    if (it != c->sizes.end()) {
+        c->in_use -= it->second;
+        c->sizes.erase(it);
+    }
+    cudaFreeAsync(p, st);
+}
+
+// Event pair `slot` (0 build, 1 harmonics, 2 fold, 3 summation) around a kernel launch.
+void tmark(few_ctx *c, int slot, bool end, cudaStream_t st)
+{
+    if (!c->timing) return;
+    cudaEventRecord(c->tev[2 * slot + (end ? 1 : 0)], st);
+    if (end) c->trec[slot] = true;
+}
+
+// Copy a host image to the device through a pinned staging block, ordered on `st`.
+few_status upload(few_ctx *c, void *dst, const void *src, size_t bytes, cudaStream_t st)
+{
+    if (bytes == 0) return FEW_OK;
+    PinnedPool::Block *b = c->pinned.acquire(bytes);
+    if (!b) return FEW_ERR_NOMEM;
+    std::memcpy(b->p, src, bytes);
+    FEW_CUDA_TRY(cudaMemcpyAsync(dst, b->p, bytes, cudaMemcpyHostToDevice, st));
+    FEW_CUDA_TRY(cudaEventRecord(b->ev, st));
+    b->pending = true;
+    return FEW_OK;
+}
+
+bool is_fin(double x) { return std::isfinite(x); }
+
+few_status check_knots(const double *t, int K)
+{
+    if (!t || K < 4) return FEW_ERR_KNOTS;
+    for (int k = 0; k < K; ++k)
+        if (!is_fin(t[k])) return FEW_ERR_KNOTS;
+    for (int k = 0; k + 1 < K; ++k)
+        if (!(t[k + 1] > t[k])) return FEW_ERR_KNOTS;
+    return FEW_OK;
+}
+
+// Harmonic slot plan of a mode list (host planning of the fold and the Horner order).
+struct SlotPlan {
+    int n_slots = 0, n_rows_pos = 0, n_rows_neg = 0;
+    std::vector<int2> pair_lm;
+    std::vector<int> mode_pair;
+    std::vector<int> slot_ptr, contrib;
+    std::vector<int2> rows;
+};
+
+few_status plan_slots(const int *l, const int *m, const int *n, int N, SlotPlan &P)
+{
+    if (!l || !m || !n || N < 1) return FEW_ERR_MODES;
+    std::set<std::tuple<int, int, int>> seen;
+    int mmax = 0;
+    for (int i = 0; i < N; ++i) {
+        if (l[i] < 2 || l[i] > kMaxL || m[i] < 0 || m[i] > l[i] || n[i] < -kMaxAbsN ||
+            n[i] > kMaxAbsN)
+            return FEW_ERR_MODES;
+        if (!seen.insert(std::make_tuple(l[i], m[i], n[i])).second) return FEW_ERR_MODES;
+        mmax = std::max(mmax, m[i]);
+    }
+    // (l, m) pairs
+    std::map<std::pair<int, int>, int> pairs;
+    P.mode_pair.resize(N);
+    for (int i = 0; i < N; ++i) {
+        auto key = std::make_pair(l[i], m[i]);
+        auto it = pairs.find(key);
+        if (it == pairs.end()) {
+            const int id = (int)P.pair_lm.size();
+            pairs.emplace(key, id);
+            P.pair_lm.push_back(make_int2(l[i], m[i]));
+            P.mode_pair[i] = id;
+        } else {
+            P.mode_pair[i] = it->second;
+        }
+    }
+    // per signed m: extreme positive n (np = max n + 1) and negative n (nn = max -n)
+    bool any_neg = false;
+    for (int i = 0; i < N; ++i) any_neg |= (m[i] > 0);
+    const int mneg = any_neg ? mmax : 0;
+    std::vector<int> npos(2 * mmax + 1, 0), nneg(2 * mmax + 1, 0);
+    auto touch = [&](int ms, int ns) {
+        const int r = ms + mmax;
+        if (ns >= 0) npos[r] = std::max(npos[r], ns + 1);
+        else nneg[r] = std::max(nneg[r], -ns);
+    };
+    for (int i = 0; i < N; ++i) {
+        touch(m[i], n[i]);
+        if (m[i] > 0) touch(-m[i], -n[i]);
+    }
+    // rows: m = mmax..0, then m = -mneg..-1; slot offsets in that order
+    std::map<std::pair<int, int>, int> slot_of;  // (signed m, n) -> slot
+    int slot = 0;
+    auto emit_row = [&](int ms) {
+        const int r = ms + mmax;
+        P.rows.push_back(make_int2(npos[r], nneg[r]));
+        for (int q = npos[r] - 1; q >= 0; --q) slot_of[std::make_pair(ms, q)] = slot++;
+        for (int q = nneg[r]; q >= 1; --q) slot_of[std::make_pair(ms, -q)] = slot++;
+    };
+    for (int ms = mmax; ms >= 0; --ms) emit_row(ms);
+    P.n_rows_pos = mmax + 1;
+    for (int ms = -mneg; ms <= -1; ++ms) emit_row(ms);
+    P.n_rows_neg = mneg;
+    P.n_slots = slot;
+    // contributions CSR
+    std::vector<std::vector<int>> lists(slot);
+    for (int i = 0; i < N; ++i) {
+        lists[slot_of[std::make_pair(m[i], n[i])]].push_back(2 * i);
+        if (m[i] > 0) lists[slot_of[std::make_pair(-m[i], -n[i])]].push_back(2 * i + 1);
+    }
+    P.slot_ptr.assign(slot + 1, 0);
+    for (int s = 0; s < slot; ++s) P.slot_ptr[s + 1] = P.slot_ptr[s] + (int)lists[s].size();
+    P.contrib.clear();
+    P.contrib.reserve(P.slot_ptr[slot]);
+    for (int s = 0; s < slot; ++s) P.contrib.insert(P.contrib.end(), lists[s].begin(), lists[s].end());
+    return FEW_OK;
+}
+
+few_status segments(const double *t, int K, double t0, double dt, int64_t ns, int64_t *seg)
+{
+    few_status st = check_knots(t, K);
+    if (st) return st;
+    if (!is_fin(t0) || !is_fin(dt) || !(dt > 0.0) || ns < 0 || ns > 2147483647LL) return FEW_ERR_RANGE;
+    if (ns > 0) {
+        const double last = std::fma((double)(ns - 1), dt, t0);
+        if (t0 < t[0] || last > t[K - 1]) return FEW_ERR_RANGE;
+    }
+    seg[0] = 0;
+    for (int k = 1; k < K - 1; ++k) {
+        double x = std::ceil((t[k] - t0) / dt);
+        int64_t v = x <= 0.0 ? 0 : (x >= (double)ns ? ns : (int64_t)x);
+        seg[k] = std::max(v, seg[k - 1]);
+    }
+    seg[K - 1] = ns;
+    return FEW_OK;
+}
+
+}  // namespace
+
+struct few_traj {
+    few_ctx *ctx = nullptr;
+    int K = 0, N = 0, J = 0, S = 0;
+    std::vector<double> t_host;
+    SlotPlan plan;
+    void *dmem = nullptr;
+    double *ybuf = nullptr;  // device staging for host-provided knot data (lazy)
+    BuildJob *job_dev = nullptr;
+    TrajDev dev{};
+    bool has_data = false;
+    // device pointers of the current knot data (for batched rebuilds)
+    const double *src_phi_phi = nullptr, *src_phi_r = nullptr, *src_re = nullptr, *src_im = nullptr;
+};
+
+struct few_batch {
+    few_ctx *ctx = nullptr;
+    bool fp64 = false;
+    int n = 0;
+    void *blob_dev = nullptr;
+    void *scratch_dev = nullptr;
+    void *jobs_dev = nullptr;
+    int n_jobs = 0, build_blocks = 0;
+    int grid = 0, threads = 0, R = 0, smem = 0, total_pairs = 0, total_fold = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+// Host image of a plan (the blob) plus its scratch requirements.
+struct PlanImage {
+    std::vector<unsigned char> blob;
+    size_t off_waves = 0, off_cta = 0, off_seg = 0;
+    size_t scratch_bytes = 0;
+    std::vector<size_t> fcoef_off, ylm_off;
+    bool fp64 = false;
+    int grid = 0, threads = 0, R = 0, smem = 0, buf_bytes = 0, total_pairs = 0, total_fold = 0;
+};
+
+int occupancy(few_ctx *c, bool fp64, int R, int T, int smem)
+{
+    auto key = std::make_tuple((int)fp64, R, T, smem);
+    auto it = c->occ_cache.find(key);
+    if (it != c->occ_cache.end()) return it->second;
+    const int o = sum_occupancy(fp64, R, T, smem);
+    c->occ_cache[key] = o;
+    return o;
+}
+
+few_status validate_request(const few_request &r, bool need_device_out)
+{
+    if (!r.traj || !r.out) return FEW_ERR_INVALID_ARG;
+    if (!r.traj->has_data) return FEW_ERR_STATE;
+    if (r.prec != FEW_FP64 && r.prec != FEW_MIXED) return FEW_ERR_INVALID_ARG;
+    if (r.out_where != FEW_MEM_HOST && r.out_where != FEW_MEM_DEVICE) return FEW_ERR_INVALID_ARG;
+    if (need_device_out && r.out_where != FEW_MEM_DEVICE) return FEW_ERR_INVALID_ARG;
+    if (!is_fin(r.theta) || !is_fin(r.phi) || !is_fin(r.scale) || !is_fin(r.dphi_phi0) ||
+        !is_fin(r.dphi_r0))
+        return FEW_ERR_INVALID_ARG;
+    if (!is_fin(r.t0) || !is_fin(r.dt) || !(r.dt > 0.0) || r.n_samples < 0 ||
+        r.n_samples > 2147483647LL)
+        return FEW_ERR_RANGE;
+    const few_traj *tr = r.traj;
+    if (r.n_samples > 0) {
+        const double last = std::fma((double)(r.n_samples - 1), r.dt, r.t0);
+        if (r.t0 < tr->t_host[0] || last > tr->t_host[tr->K - 1]) return FEW_ERR_RANGE;
+    }
+    const int lim = r.prec == FEW_FP64 ? kMaxSlotsFp64 : kMaxSlotsMixed;
+    if (tr->plan.n_slots > lim) return FEW_ERR_LIMIT;
+    return FEW_OK;
+}
+
+// Build the host image of a plan for `n` requests of one precision.
+few_status build_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P)
+{
+    P.fp64 = reqs[0].prec == FEW_FP64;
+    const int pi = P.fp64 ? 0 : 1;
+    P.R = c->tile_R[pi];
+    P.threads = c->tile_T[pi];
+    const size_t elem = P.fp64 ? 8 : 4;
+    int max_slots = 1;
+    for (int q = 0; q < n; ++q) max_slots = std::max(max_slots, reqs[q].traj->plan.n_slots);
+    P.buf_bytes = (int)align_up((size_t)max_slots * 8 * elem, 128);
+    P.smem = 2 * P.buf_bytes;
+    const int occ = occupancy(c, P.fp64, P.R, P.threads, P.smem);
+    if (occ <= 0) return FEW_ERR_LIMIT;
+    P.grid = c->sm_count * occ;
+
+    // layout of the blob
+    size_t off = align_up(sizeof(PlanHdr), 64);
+    P.off_waves = off;
+    off = align_up(off + sizeof(WaveDev) * n, 64);
+    P.off_cta = off;
+    off = align_up(off + sizeof(CtaStart) * (P.grid + 1), 64);
+    P.off_seg = off;
+    size_t seg_ints = 0;
+    for (int q = 0; q < n; ++q) seg_ints += reqs[q].traj->K;
+    off = align_up(off + sizeof(int) * seg_ints, 256);
+    P.blob.assign(off, 0);
+
+    // scratch: folded coefficients and harmonic tables per wave
+    size_t s_off = 0;
+    P.fcoef_off.resize(n);
+    P.ylm_off.resize(n);
+    for (int q = 0; q < n; ++q) {
+        const few_traj *tr = reqs[q].traj;
+        P.fcoef_off[q] = s_off;
+        s_off = align_up(s_off + (size_t)tr->S * tr->plan.n_slots * 8 * elem, 256);
+        P.ylm_off[q] = s_off;
+        s_off = align_up(s_off + (size_t)tr->plan.pair_lm.size() * 2 * sizeof(double2), 256);
+    }
+    P.scratch_bytes = s_off;
+    return FEW_OK;
+}
+
+// Fill the blob now that the device addresses of blob and scratch are known.
+void fill_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P, unsigned char *blob_dev,
+                unsigned char *scratch_dev, void *const *outs)
+{
+    PlanHdr *hdr = reinterpret_cast<PlanHdr *>(P.blob.data());
+    WaveDev *wv = reinterpret_cast<WaveDev *>(P.blob.data() + P.off_waves);
+    CtaStart *cta = reinterpret_cast<CtaStart *>(P.blob.data() + P.off_cta);
+    int *seg = reinterpret_cast<int *>(P.blob.data() + P.off_seg);
+    size_t seg_pos = 0;
+    int pair_begin = 0, fold_begin = 0;
+    std::vector<int64_t> tmp;
+    std::vector<long double> cum(n + 1, 0.0L);
+    for (int q = 0; q < n; ++q) {
+        const few_request &r = reqs[q];
+        const few_traj *tr = r.traj;
+        WaveDev &W = wv[q];
+        std::memset(&W, 0, sizeof(W));
+        W.tr = tr->dev;
+        W.theta = r.theta;
+        W.phi = r.phi;
+        W.scale = r.scale;
+        W.dphi_phi = r.dphi_phi0;
+        W.dphi_r = r.dphi_r0;
+        W.t0 = r.t0;
+        W.dt = r.dt;
+        W.n_samples = (int)r.n_samples;
+        W.out_c64 = r.out_c64 ? 1 : 0;
+        W.out = outs[q];
+        W.fcoef = scratch_dev + P.fcoef_off[q];
+        W.ylm = reinterpret_cast<double2 *>(scratch_dev + P.ylm_off[q]);
+        tmp.resize(tr->K);
+        segments(tr->t_host.data(), tr->K, r.t0, r.dt, r.n_samples, tmp.data());
+        for (int k = 0; k < tr->K; ++k) seg[seg_pos + k] = (int)tmp[k];
+        W.seg_start = reinterpret_cast<const int *>(blob_dev + P.off_seg) + seg_pos;
+        seg_pos += tr->K;
+        W.pair_begin = pair_begin;
+        pair_begin += (int)tr->plan.pair_lm.size();
+        W.fold_blocks_per_seg = (tr->plan.n_slots + kFoldThreads - 1) / kFoldThreads;
+        W.fold_begin = fold_begin;
+        fold_begin += tr->S * W.fold_blocks_per_seg;
+        // cost of a sample: one Horner step per slot plus the fixed per-sample phase work
+        cum[q + 1] = cum[q] + (long double)r.n_samples * (long double)(tr->plan.n_slots + 16);
+    }
+    P.total_pairs = pair_begin;
+    P.total_fold = fold_begin;
+    // equal-cost CTA slices of the concatenated (wave, sample) space
+    const long double total = cum[n];
+    int q = 0;
+    cta[P.grid] = CtaStart{n, 0};
+    for (int g = 0; g < P.grid; ++g) {
+        if (total <= 0.0L) {
+            cta[g] = CtaStart{n, 0};
+            continue;
+        }
+        const long double x = total * g / P.grid;
+        while (q < n - 1 && cum[q + 1] <= x) ++q;
+        const long double per = (long double)(reqs[q].traj->plan.n_slots + 16);
+        long double si = std::ceil((x - cum[q]) / per);
+        int sample = (int)std::min<long double>(si, (long double)reqs[q].n_samples);
+        cta[g] = CtaStart{q, sample};
+    }
+    hdr->n_waves = n;
+    hdr->total_pairs = P.total_pairs;
+    hdr->total_fold_blocks = P.total_fold;
+    hdr->grid_sum = P.grid;
+    hdr->buf_bytes = P.buf_bytes;
+    hdr->waves = reinterpret_cast<const WaveDev *>(blob_dev + P.off_waves);
+    hdr->cta = reinterpret_cast<const CtaStart *>(blob_dev + P.off_cta);
+    hdr->err = c->d_err;
+}
+
+few_status launch_kernels(few_ctx *c, const PlanHdr *hdr_dev, int total_pairs, int total_fold,
+                          int grid, int threads, int R, int smem, bool fp64, cudaStream_t st)
+{
+    tmark(c, 1, false, st);
+    FEW_CUDA_TRY(launch_ylm(hdr_dev, total_pairs, st));
+    tmark(c, 1, true, st);
+    tmark(c, 2, false, st);
+    FEW_CUDA_TRY(launch_fold(hdr_dev, total_fold, fp64, st));
+    tmark(c, 2, true, st);
+    tmark(c, 3, false, st);
+    FEW_CUDA_TRY(launch_sum(hdr_dev, grid, threads, R, smem, fp64, st));
+    tmark(c, 3, true, st);
+    return FEW_OK;
+}
+
+const char *kNames[] = {"FEW_OK",           "FEW_ERR_INVALID_ARG", "FEW_ERR_KNOTS",
+                        "FEW_ERR_MODES",    "FEW_ERR_RANGE",       "FEW_ERR_NOMEM",
+                        "FEW_ERR_BUDGET",   "FEW_ERR_CUDA",        "FEW_ERR_TIMEOUT",
+                        "FEW_ERR_LIMIT",    "FEW_ERR_STATE"};
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+const char *few_strerror(few_status s)
+{
+    const int i = (int)s;
+    if (i < 0 || i >= (int)(sizeof(kNames) / sizeof(kNames[0]))) return "FEW_ERR_UNKNOWN";
+    return kNames[i];
+}
+
+int few_abi_version(void) { return FEW_ABI_VERSION; }
+
+few_status few_ctx_create(few_ctx **out, int device, size_t hbm_budget_bytes)
+{
+    if (!out) return FEW_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return FEW_ERR_CUDA;
+    }
+    if (device < 0 || device >= ndev) return FEW_ERR_INVALID_ARG;
+    few_ctx *c = new (std::nothrow) few_ctx();
+    if (!c) return FEW_ERR_NOMEM;
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    auto fail = [&](few_status s) {
+        if (c->d_err) cudaFree(c->d_err);
+        if (c->internal) cudaStreamDestroy(c->internal);
+        if (c->pool) cudaMemPoolDestroy(c->pool);
+        (void)cudaGetLastError();
+        delete c;
+        return s;
+    };
+    if (cudaSetDevice(device) != cudaSuccess) return fail(FEW_ERR_CUDA);
+    if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return fail(FEW_ERR_CUDA);
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&c->pool, &props) != cudaSuccess) return fail(FEW_ERR_CUDA);
+    uint64_t thresh = UINT64_MAX;
+    cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thresh);
+    if (cudaStreamCreateWithFlags(&c->internal, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(FEW_ERR_CUDA);
+    if (cudaMalloc(&c->d_err, sizeof(unsigned)) != cudaSuccess) return fail(FEW_ERR_NOMEM);
+    if (cudaMemset(c->d_err, 0, sizeof(unsigned)) != cudaSuccess) return fail(FEW_ERR_CUDA);
+    if (sum_configure() != cudaSuccess) return fail(FEW_ERR_CUDA);
+    for (auto &e : c->tev)
+        if (cudaEventCreate(&e) != cudaSuccess) return fail(FEW_ERR_CUDA);
+    *out = c;
+    return FEW_OK;
+}
+
+few_status few_batch_release(few_ctx *ctx, few_batch *b);
+few_status few_traj_release(few_ctx *ctx, few_traj *t);
+
+few_status few_ctx_destroy(few_ctx *ctx)
+{
+    if (!ctx) return FEW_OK;
+    {
+        std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+        cudaSetDevice(ctx->device);
+        cudaDeviceSynchronize();
+        auto bs = ctx->batches;
+        for (few_batch *b : bs) few_batch_release(ctx, b);
+        auto ts = ctx->trajs;
+        for (few_traj *t : ts) few_traj_release(ctx, t);
+        cudaStreamSynchronize(ctx->internal);
+        for (auto &e : ctx->tev)
+            if (e) cudaEventDestroy(e);
+        ctx->pinned.release();
+        cudaFree(ctx->d_err);
+        cudaStreamDestroy(ctx->internal);
+        cudaMemPoolDestroy(ctx->pool);
+        (void)cudaGetLastError();
+    }
+    delete ctx;
+    return FEW_OK;
+}
+
+few_status few_ctx_memory(few_ctx *ctx, size_t *bytes_in_use, size_t *budget_bytes)
+{
+    if (!ctx) return FEW_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (bytes_in_use) *bytes_in_use = ctx->in_use;
+    if (budget_bytes) *budget_bytes = ctx->budget;
+    return FEW_OK;
+}
+
+few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int *l, const int *m,
+                           const int *n, int N, few_traj **out)
+{
+    if (!ctx || !out) return FEW_ERR_INVALID_ARG;
+    *out = nullptr;
+    few_status st = check_knots(t_knots, K);
+    if (st) return st;
+    SlotPlan plan;
+    if ((st = plan_slots(l, m, n, N, plan))) return st;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    few_traj *tr = new (std::nothrow) few_traj();
+    if (!tr) return FEW_ERR_NOMEM;
+    tr->ctx = ctx;
+    tr->K = K;
+    tr->N = N;
+    tr->J = 2 + 2 * N;
+    tr->S = K - 1;
+    tr->t_host.assign(t_knots, t_knots + K);
+    tr->plan = std::move(plan);
+    const SlotPlan &P = tr->plan;
+
+    // one device allocation for every trajectory array
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    const size_t o_t = take(sizeof(double) * K), o_h = take(sizeof(double) * K),
+                 o_ih = take(sizeof(double) * K), o_w = take(sizeof(double) * K),
+                 o_ip = take(sizeof(double) * K), o_up = take(sizeof(double) * K),
+                 o_coef = take(sizeof(double) * 4 * (size_t)tr->S * tr->J),
+                 o_pair = take(sizeof(int2) * P.pair_lm.size()), o_mp = take(sizeof(int) * N),
+                 o_sp = take(sizeof(int) * P.slot_ptr.size()),
+                 o_ct = take(sizeof(int) * std::max<size_t>(1, P.contrib.size())),
+                 o_rows = take(sizeof(int2) * P.rows.size()), o_job = take(sizeof(BuildJob));
+    if ((st = dev_alloc(ctx, off, ctx->internal, &tr->dmem))) {
+        delete tr;
+        return st;
+    }
+    unsigned char *d = static_cast<unsigned char *>(tr->dmem);
+    // host image of the small arrays
+    std::vector<unsigned char> img(o_coef, 0);
+    std::memcpy(img.data() + o_t, t_knots, sizeof(double) * K);
+    std::vector<unsigned char> img2(off - o_pair, 0);
+    auto put = [&](size_t o, const void *src, size_t bytes) {
+        if (bytes) std::memcpy(img2.data() + (o - o_pair), src, bytes);
+    };
+    put(o_pair, P.pair_lm.data(), sizeof(int2) * P.pair_lm.size());
+    put(o_mp, P.mode_pair.data(), sizeof(int) * N);
+    put(o_sp, P.slot_ptr.data(), sizeof(int) * P.slot_ptr.size());
+    put(o_ct, P.contrib.data(), sizeof(int) * P.contrib.size());
+    put(o_rows, P.rows.data(), sizeof(int2) * P.rows.size());
+
+    TrajDev &D = tr->dev;
+    D.K = K;
+    D.N = N;
+    D.J = tr->J;
+    D.S = tr->S;
+    D.n_pairs = (int)P.pair_lm.size();
+    D.n_slots = P.n_slots;
+    D.n_rows_pos = P.n_rows_pos;
+    D.n_rows_neg = P.n_rows_neg;
+    D.t = reinterpret_cast<const double *>(d + o_t);
+    D.h = reinterpret_cast<const double *>(d + o_h);
+    D.inv_h = reinterpret_cast<const double *>(d + o_ih);
+    D.fac_w = reinterpret_cast<const double *>(d + o_w);
+    D.fac_ip = reinterpret_cast<const double *>(d + o_ip);
+    D.fac_up = reinterpret_cast<const double *>(d + o_up);
+    D.coef = reinterpret_cast<double *>(d + o_coef);
+    D.pair_lm = reinterpret_cast<const int2 *>(d + o_pair);
+    D.mode_pair = reinterpret_cast<const int *>(d + o_mp);
+    D.slot_ptr = reinterpret_cast<const int *>(d + o_sp);
+    D.contrib = reinterpret_cast<const int *>(d + o_ct);
+    D.rows = reinterpret_cast<const int2 *>(d + o_rows);
+    tr->job_dev = reinterpret_cast<BuildJob *>(d + o_job);
+
+    cudaStream_t s = ctx->internal;
+    few_status us = upload(ctx, d, img.data(), o_h, s);  // knot times
+    if (!us) us = upload(ctx, d + o_pair, img2.data(), off - o_pair, s);
+    cudaError_t e = cudaSuccess;
+    if (!us) e = launch_factor(D.t, K, const_cast<double *>(D.h), const_cast<double *>(D.inv_h),
+                               const_cast<double *>(D.fac_w), const_cast<double *>(D.fac_ip),
+                               const_cast<double *>(D.fac_up), s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    if (us || e != cudaSuccess || e2 != cudaSuccess) {
+        (void)cudaGetLastError();
+        dev_free(ctx, tr->dmem, s);
+        cudaStreamSynchronize(s);
+        delete tr;
+        return us ? us : FEW_ERR_CUDA;
+    }
+    ctx->trajs.insert(tr);
+    *out = tr;
+    return FEW_OK;
+}
+
+few_status few_traj_set_data(few_ctx *ctx, few_traj *tr, const double *phi_phi, const double *phi_r,
+                             const double *amp_re, const double *amp_im, few_mem where, void *stream)
+{
+    if (!ctx || !tr || tr->ctx != ctx) return FEW_ERR_INVALID_ARG;
+    if (!phi_phi || !phi_r || !amp_re || !amp_im) return FEW_ERR_INVALID_ARG;
+    if (where != FEW_MEM_HOST && where != FEW_MEM_DEVICE) return FEW_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t K = tr->K, N = tr->N;
+    BuildJob job{};
+    job.tr = tr->dev;
+    if (where == FEW_MEM_HOST) {
+        if (!tr->ybuf) {
+            void *p = nullptr;
+            few_status s = dev_alloc(ctx, sizeof(double) * (2 * K + 2 * K * N), ctx->internal, &p);
+            if (s) return s;
+            if (cudaStreamSynchronize(ctx->internal) != cudaSuccess) return FEW_ERR_CUDA;
+            tr->ybuf = static_cast<double *>(p);
+        }
+        double *y = tr->ybuf;
+        FEW_CUDA_TRY(cudaMemcpyAsync(y, phi_phi, sizeof(double) * K, cudaMemcpyHostToDevice, st));
+        FEW_CUDA_TRY(cudaMemcpyAsync(y + K, phi_r, sizeof(double) * K, cudaMemcpyHostToDevice, st));
+        FEW_CUDA_TRY(cudaMemcpyAsync(y + 2 * K, amp_re, sizeof(double) * K * N, cudaMemcpyHostToDevice, st));
+        FEW_CUDA_TRY(cudaMemcpyAsync(y + 2 * K + K * N, amp_im, sizeof(double) * K * N,
+                                     cudaMemcpyHostToDevice, st));
+        // the caller may reuse its host arrays on return: wait for these copies only
+        cudaEvent_t ev = nullptr;
+        FEW_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        cudaError_t e1 = cudaEventRecord(ev, st);
+        cudaError_t e2 = e1 == cudaSuccess ? cudaEventSynchronize(ev) : e1;
+        cudaEventDestroy(ev);
+        FEW_CUDA_TRY(e2);
+        job.phi_phi = y;
+        job.phi_r = y + K;
+        job.amp_re = y + 2 * K;
+        job.amp_im = y + 2 * K + K * N;
+    } else {
+        job.phi_phi = phi_phi;
+        job.phi_r = phi_r;
+        job.amp_re = amp_re;
+        job.amp_im = amp_im;
+    }
+    job.block_begin = 0;
+    few_status s = upload(ctx, tr->job_dev, &job, sizeof(job), st);
+    if (s) return s;
+    const int blocks = (tr->J + kBuildThreads - 1) / kBuildThreads;
+    tmark(ctx, 0, false, st);
+    FEW_CUDA_TRY(launch_build(tr->job_dev, 1, blocks, ctx->d_err, st));
+    tmark(ctx, 0, true, st);
+    tr->src_phi_phi = job.phi_phi;
+    tr->src_phi_r = job.phi_r;
+    tr->src_re = job.amp_re;
+    tr->src_im = job.amp_im;
+    tr->has_data = true;
+    return FEW_OK;
+}
+
+few_status few_traj_release(few_ctx *ctx, few_traj *tr)
+{
+    if (!ctx || !tr || tr->ctx != ctx) return FEW_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    dev_free(ctx, tr->ybuf, ctx->internal);
+    dev_free(ctx, tr->dmem, ctx->internal);
+    cudaStreamSynchronize(ctx->internal);
+    (void)cudaGetLastError();
+    ctx->trajs.erase(tr);
+    delete tr;
+    return FEW_OK;
+}
+
+few_status few_traj_info(const few_traj *tr, int *K, int *N, int *n_slots)
+{
+    if (!tr) return FEW_ERR_INVALID_ARG;
+    if (K) *K = tr->K;
+    if (N) *N = tr->N;
+    if (n_slots) *n_slots = tr->plan.n_slots;
+    return FEW_OK;
+}
+
+few_status few_waveform(few_ctx *ctx, const few_request *req, void *stream)
+{
+    if (!ctx || !req) return FEW_ERR_INVALID_ARG;
+    few_status st = validate_request(*req, false);
+    if (st) return st;
+    if (req->traj->ctx != ctx) return FEW_ERR_INVALID_ARG;
+    if (req->n_samples == 0) return FEW_OK;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PlanImage P;
+    if ((st = build_image(ctx, req, 1, P))) return st;
+    const size_t out_bytes = (size_t)req->n_samples * (req->out_c64 ? 8 : 16);
+    void *blob = nullptr, *scratch = nullptr, *dout = nullptr;
+    if ((st = dev_alloc(ctx, P.blob.size(), s, &blob))) return st;
+    if ((st = dev_alloc(ctx, P.scratch_bytes, s, &scratch))) {
+        dev_free(ctx, blob, s);
+        return st;
+    }
+    void *out_dev = req->out;
+    if (req->out_where == FEW_MEM_HOST) {
+        if ((st = dev_alloc(ctx, out_bytes, s, &dout))) {
+            dev_free(ctx, scratch, s);
+            dev_free(ctx, blob, s);
+            return st;
+        }
+        out_dev = dout;
+    }
+    fill_image(ctx, req, 1, P, static_cast<unsigned char *>(blob),
+               static_cast<unsigned char *>(scratch), &out_dev);
+    st = upload(ctx, blob, P.blob.data(), P.blob.size(), s);
+    if (!st)
+        st = launch_kernels(ctx, static_cast<const PlanHdr *>(blob), P.total_pairs, P.total_fold,
+                            P.grid, P.threads, P.R, P.smem, P.fp64, s);
+    if (!st && req->out_where == FEW_MEM_HOST) {
+        cudaError_t e = cudaMemcpyAsync(req->out, dout, out_bytes, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            st = FEW_ERR_CUDA;
+        }
+    }
+    dev_free(ctx, dout, s);
+    dev_free(ctx, scratch, s);
+    dev_free(ctx, blob, s);
+    if (!st && req->out_where == FEW_MEM_HOST) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            (void)cudaGetLastError();
+            st = FEW_ERR_CUDA;
+        }
+    }
+    return st;
+}
+
+few_status few_phase_samples(few_ctx *ctx, const few_traj *tr, double t0, double dt, int64_t n,
+                             double dphi_phi0, double dphi_r0, double *out_dev, void *stream)
+{
+    if (!ctx || !tr || tr->ctx != ctx || !out_dev) return FEW_ERR_INVALID_ARG;
+    if (!tr->has_data) return FEW_ERR_STATE;
+    if (!is_fin(dphi_phi0) || !is_fin(dphi_r0)) return FEW_ERR_INVALID_ARG;
+    std::vector<int64_t> seg(tr->K);
+    few_status st = segments(tr->t_host.data(), tr->K, t0, dt, n, seg.data());
+    if (st) return st;
+    if (n == 0) return FEW_OK;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<int> seg32(seg.begin(), seg.end());
+    void *d = nullptr;
+    if ((st = dev_alloc(ctx, sizeof(int) * seg32.size(), s, &d))) return st;
+    st = upload(ctx, d, seg32.data(), sizeof(int) * seg32.size(), s);
+    if (!st) {
+        cudaError_t e = launch_phases(tr->dev, static_cast<const int *>(d), t0, dt, (int)n,
+                                      dphi_phi0, dphi_r0, out_dev, s);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            st = FEW_ERR_CUDA;
+        }
+    }
+    dev_free(ctx, d, s);
+    return st;
+}
+
+few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned flags, few_batch **out)
+{
+    if (!ctx || !reqs || n < 1 || !out) return FEW_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int q = 0; q < n; ++q) {
+        few_status st = validate_request(reqs[q], true);
+        if (st) return st;
+        if (reqs[q].traj->ctx != ctx || reqs[q].prec != reqs[0].prec) return FEW_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    PlanImage P;
+    few_status st = build_image(ctx, reqs, n, P);
+    if (st) return st;
+    few_batch *b = new (std::nothrow) few_batch();
+    if (!b) return FEW_ERR_NOMEM;
+    b->ctx = ctx;
+    b->fp64 = P.fp64;
+    b->n = n;
+    cudaStream_t s = ctx->internal;
+    auto fail = [&](few_status e) {
+        dev_free(ctx, b->jobs_dev, s);
+        dev_free(ctx, b->scratch_dev, s);
+        dev_free(ctx, b->blob_dev, s);
+        cudaStreamSynchronize(s);
+        (void)cudaGetLastError();
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        delete b;
+        return e;
+    };
+    if ((st = dev_alloc(ctx, P.blob.size(), s, &b->blob_dev))) return fail(st);
+    if ((st = dev_alloc(ctx, P.scratch_bytes, s, &b->scratch_dev))) return fail(st);
+    std::vector<void *> outs(n);
+    for (int q = 0; q < n; ++q) outs[q] = reqs[q].out;
+    fill_image(ctx, reqs, n, P, static_cast<unsigned char *>(b->blob_dev),
+               static_cast<unsigned char *>(b->scratch_dev), outs.data());
+    if ((st = upload(ctx, b->blob_dev, P.blob.data(), P.blob.size(), s))) return fail(st);
+    if (flags & FEW_BATCH_REBUILD_SPLINES) {
+        std::vector<BuildJob> jobs;
+        std::set<const few_traj *> seen;
+        int blocks = 0;
+        for (int q = 0; q < n; ++q) {
+            const few_traj *tr = reqs[q].traj;
+            if (!seen.insert(tr).second) continue;
+            BuildJob j{};
+            j.tr = tr->dev;
+            j.phi_phi = tr->src_phi_phi;
+            j.phi_r = tr->src_phi_r;
+            j.amp_re = tr->src_re;
+            j.amp_im = tr->src_im;
+            j.block_begin = blocks;
+            blocks += (tr->J + kBuildThreads - 1) / kBuildThreads;
+            jobs.push_back(j);
+        }
+        if ((st = dev_alloc(ctx, sizeof(BuildJob) * jobs.size(), s, &b->jobs_dev))) return fail(st);
+        if ((st = upload(ctx, b->jobs_dev, jobs.data(), sizeof(BuildJob) * jobs.size(), s)))
+            return fail(st);
+        b->n_jobs = (int)jobs.size();
+        b->build_blocks = blocks;
+    }
+    b->grid = P.grid;
+    b->threads = P.threads;
+    b->R = P.R;
+    b->smem = P.smem;
+    b->total_pairs = P.total_pairs;
+    b->total_fold = P.total_fold;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(FEW_ERR_CUDA);
+    if (!(flags & FEW_BATCH_NO_GRAPH)) {
+        cudaStream_t cap = nullptr;
+        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return fail(FEW_ERR_CUDA);
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const PlanHdr *hd = static_cast<const PlanHdr *>(b->blob_dev);
+            if (b->n_jobs)
+                launch_build(static_cast<const BuildJob *>(b->jobs_dev), b->n_jobs, b->build_blocks,
+                             ctx->d_err, cap);
+            launch_ylm(hd, b->total_pairs, cap);
+            launch_fold(hd, b->total_fold, b->fp64, cap);
+            launch_sum(hd, b->grid, b->threads, b->R, b->smem, b->fp64, cap);
+            e = cudaStreamEndCapture(cap, &b->graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) return fail(FEW_ERR_CUDA);
+    }
+    ctx->batches.insert(b);
+    *out = b;
+    return FEW_OK;
+}
+
+few_status few_batch_run(few_ctx *ctx, few_batch *b, void *stream)
+{
+    if (!ctx || !b || b->ctx != ctx) return FEW_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (b->exec) {
+        FEW_CUDA_TRY(cudaGraphLaunch(b->exec, s));
+        return FEW_OK;
+    }
+    const PlanHdr *hd = static_cast<const PlanHdr *>(b->blob_dev);
+    if (b->n_jobs) {
+        tmark(ctx, 0, false, s);
+        FEW_CUDA_TRY(launch_build(static_cast<const BuildJob *>(b->jobs_dev), b->n_jobs,
+                                  b->build_blocks, ctx->d_err, s));
+        tmark(ctx, 0, true, s);
+    }
+    return launch_kernels(ctx, hd, b->total_pairs, b->total_fold, b->grid, b->threads, b->R,
+                          b->smem, b->fp64, s);
+}
+
+few_status few_batch_release(few_ctx *ctx, few_batch *b)
+{
+    if (!ctx || !b || b->ctx != ctx) return FEW_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    dev_free(ctx, b->jobs_dev, ctx->internal);
+    dev_free(ctx, b->scratch_dev, ctx->internal);
+    dev_free(ctx, b->blob_dev, ctx->internal);
+    cudaStreamSynchronize(ctx->internal);
+    (void)cudaGetLastError();
+    ctx->batches.erase(b);
+    delete b;
+    return FEW_OK;
+}
+
+few_status few_sync_status(few_ctx *ctx)
+{
+    if (!ctx) return FEW_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        (void)cudaGetLastError();
+        return FEW_ERR_CUDA;
+    }
+    unsigned bits = 0;
+    if (cudaMemcpy(&bits, ctx->d_err, sizeof(bits), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return FEW_ERR_CUDA;
+    if (bits && cudaMemset(ctx->d_err, 0, sizeof(unsigned)) != cudaSuccess) return FEW_ERR_CUDA;
+    if (bits & ERRBIT_TIMEOUT) return FEW_ERR_TIMEOUT;
+    if (bits & ERRBIT_NONFINITE) return FEW_ERR_INVALID_ARG;
+    if (bits & ERRBIT_INTERNAL) return FEW_ERR_CUDA;
+    return FEW_OK;
+}
+
+few_status few_ctx_set_timing(few_ctx *ctx, int enable)
+{
+    if (!ctx) return FEW_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    ctx->timing = enable != 0;
+    for (bool &r : ctx->trec) r = false;
+    return FEW_OK;
+}
+
+few_status few_last_timing(few_ctx *ctx, float *ms)
+{
+    if (!ctx || !ms) return FEW_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    for (int i = 0; i < 4; ++i) {
+        ms[i] = -1.0f;
+        if (!ctx->trec[i]) continue;
+        FEW_CUDA_TRY(cudaEventSynchronize(ctx->tev[2 * i + 1]));
+        FEW_CUDA_TRY(cudaEventElapsedTime(&ms[i], ctx->tev[2 * i], ctx->tev[2 * i + 1]));
+    }
+    return FEW_OK;
+}
+
+few_status few_set_tiles(few_ctx *ctx, int prec, int R, int threads)
+{
+    if (!ctx) return FEW_ERR_INVALID_ARG;
+    if (threads != 128 && threads != 256) return FEW_ERR_INVALID_ARG;
+    if (prec == FEW_FP64) {
+        if (R != 1 && R != 2) return FEW_ERR_INVALID_ARG;
+    } else if (prec == FEW_MIXED) {
+        if (R != 2 && R != 4 && R != 8) return FEW_ERR_INVALID_ARG;
+    } else {
+        return FEW_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    ctx->tile_R[prec] = R;
+    ctx->tile_T[prec] = threads;
+    return FEW_OK;
+}
+
+few_status few_get_tiles(few_ctx *ctx, int prec, int *R, int *threads)
+{
+    if (!ctx || (prec != FEW_FP64 && prec != FEW_MIXED)) return FEW_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (R) *R = ctx->tile_R[prec];
+    if (threads) *threads = ctx->tile_T[prec];
+    return FEW_OK;
+}
+
+few_status few_plan_segments(const double *t_knots, int K, double t0, double dt, int64_t n_samples,
+                             int64_t *seg_start)
+{
+    if (!seg_start) return FEW_ERR_INVALID_ARG;
+    return segments(t_knots, K, t0, dt, n_samples, seg_start);
+}
+
+few_status few_mode_slots(const int *l, const int *m, const int *n, int N, int *n_slots, int *n_rows)
+{
+    SlotPlan P;
+    few_status st = plan_slots(l, m, n, N, P);
+    if (st) return st;
+    if (n_slots) *n_slots = P.n_slots;
+    if (n_rows) *n_rows = P.n_rows_pos + P.n_rows_neg;
+    return FEW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// fewsum_internal.h -- device-side descriptors shared by the host API (api.cpp) and the
+// kernels (spline.cu, fold.cu, sum.cu).  Plain structs: the host fills them, uploads them in
+// one plan blob per call or batch, and the kernels read them.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fewsum {
+
+// Device error latch bits (few_ctx::d_err); decoded by few_sync_status.
+enum : unsigned {
+    ERRBIT_NONFINITE = 1u,  // non-finite value in device-resident inputs
+    ERRBIT_TIMEOUT = 2u,    // a bounded mbarrier wait expired
+    ERRBIT_INTERNAL = 4u    // a decoded index fell outside its table (should not happen)
+};
+
+constexpr int kMaxL = 32;
+constexpr int kMaxAbsN = 1024;
+constexpr int kMaxSlotsFp64 = 1776;   // 2 buffers x slots x 64 B <= 227 KB
+constexpr int kMaxSlotsMixed = 3552;  // 2 buffers x slots x 32 B <= 227 KB
+constexpr int kFoldThreads = 128;
+constexpr int kYlmThreads = 64;
+constexpr int kBuildThreads = 64;
+
+// Trajectory-resident data (one per few_traj).
+struct TrajDev {
+    int K, N, J, S;        // knots, modes, splines (2 + 2N), segments (K - 1)
+    int n_pairs;           // distinct (l, m) pairs
+    int n_slots;           // harmonic slots per segment
+    int n_rows_pos;        // rows with m >= 0 (ordered m = M..0)
+    int n_rows_neg;        // rows with m < 0 (ordered m = -M'..-1)
+    const double *t;       // [K] knot times
+    const double *inv_h;   // [S] 1/(t_{k+1}-t_k)
+    const double *h;       // [S] t_{k+1}-t_k
+    const double *fac_w;   // [K] forward multipliers of the shared tridiagonal factorization
+    const double *fac_ip;  // [K] inverse pivots
+    const double *fac_up;  // [K] super-diagonal
+    double *coef;          // [S][J][4] spline coefficients in u = (t - t_k)/h_k;
+                           //   columns 0,1 = Phi_phi, Phi_r (rad),
+                           //   column 2+2i / 3+2i = Re / Im A_i
+    const int2 *pair_lm;   // [n_pairs] (l, m)
+    const int *mode_pair;  // [N] pair index of each mode
+    const int *slot_ptr;   // [n_slots + 1] CSR into contrib
+    const int *contrib;    // [n_contrib] mode * 2 + kind (0: A Y+, 1: conj(A) Y-)
+    const int2 *rows;      // [n_rows_pos + n_rows_neg] (np, nn) slots per half row
+};
+
+// One spline-build job: a trajectory and the knot data to fit.
+struct BuildJob {
+    TrajDev tr;
+    const double *phi_phi;  // [K] rad
+    const double *phi_r;    // [K] rad
+    const double *amp_re;   // [K][N]
+    const double *amp_im;   // [K][N]
+    int block_begin;        // first block of this job in the flattened grid
+    int pad;
+};
+
+// One waveform of a plan (a request).
+struct WaveDev {
+    TrajDev tr;
+    double theta, phi, scale;
+    double dphi_phi, dphi_r;    // phase offsets (rad)
+    double t0, dt;
+    int n_samples;
+    int out_c64;
+    void *out;
+    void *fcoef;          // [S][n_slots][8] folded coefficients (float or double)
+    double2 *ylm;         // [n_pairs][2]: Y+ = -2Y_{l,m}, Y- = (-1)^l -2Y_{l,-m} (0 if m = 0)
+    const int *seg_start; // [K] sample range of each segment
+    int pair_begin;       // first global pair index of this wave (ylm kernel)
+    int fold_begin;       // first fold block of this wave
+    int fold_blocks_per_seg;
+    int pad;
+};
+
+// Start of one CTA's slice of the summation work: (wave, sample).
+struct CtaStart {
+    int wave;
+    int sample;
+};
+
+// Header of a plan blob.  The blob is [PlanHdr][WaveDev x n][CtaStart x (grid+1)][ints...].
+struct PlanHdr {
+    int n_waves;
+    int total_pairs;
+    int total_fold_blocks;
+    int grid_sum;
+    int buf_bytes;   // bytes of one shared-memory coefficient buffer (max slots x 8 x sizeof)
+    int pad;
+    const WaveDev *waves;
+    const CtaStart *cta;
+    unsigned *err;
+};
+
+// Kernel launchers (defined in the .cu files; every launcher returns the launch error).
+cudaError_t launch_factor(const double *t, int K, double *h, double *inv_h, double *fac_w,
+                          double *fac_ip, double *fac_up, cudaStream_t st);
+cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks, unsigned *err,
+                         cudaStream_t st);
+cudaError_t launch_ylm(const PlanHdr *hdr_dev, int total_pairs, cudaStream_t st);
+cudaError_t launch_fold(const PlanHdr *hdr_dev, int total_fold_blocks, bool fp64, cudaStream_t st);
+cudaError_t launch_sum(const PlanHdr *hdr_dev, int grid, int threads, int samples_per_thread,
+                       int smem_bytes, bool fp64, cudaStream_t st);
+cudaError_t launch_phases(const TrajDev &tr, const int *seg_start, double t0, double dt, int n,
+                          double dphi_phi, double dphi_r, double *out, cudaStream_t st);
+// Maximum resident CTAs per SM of the summation kernel for a configuration (0 if invalid).
+int sum_occupancy(bool fp64, int samples_per_thread, int threads, int smem_bytes);
+// One-time kernel attribute setup (dynamic shared memory opt-in).
+cudaError_t sum_configure();
+
+}  // namespace fewsum

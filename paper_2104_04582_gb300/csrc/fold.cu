@@ -1,0 +1,187 @@
+// fold.cu -- per-request harmonics and fold of the harmonics into the spline coefficients.
+//
+// Sec. 4 sum: h = scale * sum_{lmn} A_lmn(t) -2Y_lm(theta, phi) e^{-i Phi_mn}, with the m < 0
+// modes given by Eq. (amp_symmetry), k = 0: A_{l,-m,-n} = (-1)^l conj(A_lmn).  Grouping every
+// term by its signed frequency (m, n) gives
+//     h = sum_{(m,n) signed} K_{m,n}(u) e^{-i (m Phi_phi + n Phi_r)},
+//     K_{m,n}   = scale * sum_l A_lmn(u) Y+_lm                        (m >= 0 entries),
+//     K_{-m,-n} = scale * sum_l conj(A_lmn(u)) Y-_lm,  Y- = (-1)^l -2Y_{l,-m}   (m > 0),
+// and each K is again a complex cubic in u per segment (a fixed linear combination of the
+// amplitude splines).  k_fold forms these "slot" cubics for one request; the summation kernel
+// then evaluates sum K z_phi^m z_r^n by Horner's rule.  This is exact algebra on the
+// coefficients (only the rounding order differs from summing mode by mode).
+//
+// Spin-weighted harmonics (the paper lists them as a utility, Sec. 3.D, without a formula):
+//     sY_lm(theta, phi) = (-1)^s sqrt((2l+1)/(4 pi)) d^l_{m,-s}(theta) e^{i m phi},  s = -2,
+// with the Wigner small-d evaluated through its Jacobi-polynomial form
+//     d^l_{m',m}(b) = xi sqrt(k! (k+mu+nu)! / ((k+mu)! (k+nu)!)) sin^mu(b/2) cos^nu(b/2)
+//                      P_k^{(mu,nu)}(cos b),
+//     mu = |m - m'|, nu = |m + m'|, k = l - (mu+nu)/2, xi = 1 if m >= m' else (-1)^(m-m'),
+// and the Jacobi polynomial by its three-term recurrence in the degree.
+#include "fewsum_internal.h"
+
+namespace fewsum {
+
+__device__ double jacobi_p(int n, int a, int b, double x)
+{
+    if (n == 0) return 1.0;
+    double p0 = 1.0;
+    double p1 = (a + 1) + 0.5 * (a + b + 2) * (x - 1.0);
+    for (int k = 2; k <= n; ++k) {
+        const double c = 2.0 * k + a + b;
+        const double a1 = 2.0 * k * (k + a + b) * (c - 2.0);
+        const double a2 = (c - 1.0) * (c * (c - 2.0) * x + (double)(a * a - b * b));
+        const double a3 = 2.0 * (k + a - 1) * (k + b - 1) * c;
+        const double p2 = (a2 * p1 - a3 * p0) / a1;
+        p0 = p1;
+        p1 = p2;
+    }
+    return p1;
+}
+
+__device__ double ipow(double x, int e)
+{
+    double r = 1.0;
+    for (int k = 0; k < e; ++k) r *= x;
+    return r;
+}
+
+// -2Y_{l,m}(theta, phi)
+__device__ double2 swsh_m2(int l, int m, double theta, double phi)
+{
+    const int mu = abs(2 - m), nu = abs(2 + m);
+    const int k = l - ((mu + nu) >> 1);
+    if (k < 0) return make_double2(0.0, 0.0);
+    double ratio = 1.0;
+    for (int q = 1; q <= mu; ++q) ratio *= (double)(k + nu + q) / (double)(k + q);
+    const double xi = (m <= 2) ? 1.0 : ((m & 1) ? -1.0 : 1.0);
+    double sh, ch;
+    sincos(0.5 * theta, &sh, &ch);
+    const double d = xi * sqrt(ratio) * ipow(sh, mu) * ipow(ch, nu) * jacobi_p(k, mu, nu, cos(theta));
+    const double kInv4Pi = 0.079577471545947667884;  // 1/(4 pi)
+    const double amp = sqrt((2.0 * l + 1.0) * kInv4Pi) * d;
+    double s, c;
+    sincos((double)m * phi, &s, &c);
+    return make_double2(amp * c, amp * s);
+}
+
+__device__ __forceinline__ int wave_of(const WaveDev *waves, int n, int g, bool by_pair)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int b = by_pair ? waves[mid].pair_begin : waves[mid].fold_begin;
+        if (b <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One thread per (wave, (l, m) pair).
+__global__ void __launch_bounds__(kYlmThreads) k_ylm(const PlanHdr *__restrict__ hp)
+{
+    const PlanHdr h = *hp;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= h.total_pairs) return;
+    const int w = wave_of(h.waves, h.n_waves, g, true);
+    const WaveDev &W = h.waves[w];
+    const int p = g - W.pair_begin;
+    if (p >= W.tr.n_pairs) {
+        atomicOr(h.err, ERRBIT_INTERNAL);
+        return;
+    }
+    const int2 lm = W.tr.pair_lm[p];
+    const double2 yp = swsh_m2(lm.x, lm.y, W.theta, W.phi);
+    double2 ym = make_double2(0.0, 0.0);
+    if (lm.y > 0) {
+        ym = swsh_m2(lm.x, -lm.y, W.theta, W.phi);
+        if (lm.x & 1) ym = make_double2(-ym.x, -ym.y);
+    }
+    W.ylm[2 * p] = yp;
+    W.ylm[2 * p + 1] = ym;
+}
+
+cudaError_t launch_ylm(const PlanHdr *hdr_dev, int total_pairs, cudaStream_t st)
+{
+    if (total_pairs <= 0) return cudaSuccess;
+    k_ylm<<<(total_pairs + kYlmThreads - 1) / kYlmThreads, kYlmThreads, 0, st>>>(hdr_dev);
+    return cudaGetLastError();
+}
+
+template <typename T> struct Slot8;
+template <> struct Slot8<double> {
+    __device__ static void store(double *dst, const double (&re)[4], const double (&im)[4])
+    {
+        double2 *d = reinterpret_cast<double2 *>(dst);
+        d[0] = make_double2(re[0], re[1]);
+        d[1] = make_double2(re[2], re[3]);
+        d[2] = make_double2(im[0], im[1]);
+        d[3] = make_double2(im[2], im[3]);
+    }
+};
+template <> struct Slot8<float> {
+    __device__ static void store(float *dst, const float (&re)[4], const float (&im)[4])
+    {
+        float4 *d = reinterpret_cast<float4 *>(dst);
+        d[0] = make_float4(re[0], re[1], re[2], re[3]);
+        d[1] = make_float4(im[0], im[1], im[2], im[3]);
+    }
+};
+
+// One thread per (wave, segment, slot): K_slot = scale * sum of its contributions.
+// T is the arithmetic and storage type of the folded coefficients (double for FEW_FP64,
+// float for FEW_MIXED, whose amplitudes are FP32 by design).
+template <typename T>
+__global__ void __launch_bounds__(kFoldThreads) k_fold(const PlanHdr *__restrict__ hp)
+{
+    const PlanHdr h = *hp;
+    const int b = blockIdx.x;
+    const int w = wave_of(h.waves, h.n_waves, b, false);
+    const WaveDev &W = h.waves[w];
+    const int local = b - W.fold_begin;
+    const int s = local / W.fold_blocks_per_seg;
+    const int slot = (local % W.fold_blocks_per_seg) * kFoldThreads + threadIdx.x;
+    const TrajDev &tr = W.tr;
+    if (s >= tr.S || slot >= tr.n_slots) return;
+    T re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
+    const int c0 = tr.slot_ptr[slot], c1 = tr.slot_ptr[slot + 1];
+    const double *__restrict__ cs = tr.coef + (size_t)s * tr.J * 4;
+    for (int c = c0; c < c1; ++c) {
+        const int code = tr.contrib[c];
+        const int i = code >> 1, kind = code & 1;
+        const double2 Yd = W.ylm[2 * tr.mode_pair[i] + kind];
+        const T yr = (T)Yd.x, yi = (T)Yd.y;
+        const double2 *ca = reinterpret_cast<const double2 *>(cs + (size_t)(2 + 2 * i) * 4);
+        const double2 r01 = ca[0], r23 = ca[1], i01 = ca[2], i23 = ca[3];
+        const T ar[4] = {(T)r01.x, (T)r01.y, (T)r23.x, (T)r23.y};
+        T ai[4] = {(T)i01.x, (T)i01.y, (T)i23.x, (T)i23.y};
+        if (kind) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) ai[q] = -ai[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            re[q] += ar[q] * yr - ai[q] * yi;
+            im[q] += ar[q] * yi + ai[q] * yr;
+        }
+    }
+    const T sc = (T)W.scale;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        re[q] *= sc;
+        im[q] *= sc;
+    }
+    T *dst = reinterpret_cast<T *>(W.fcoef) + ((size_t)s * tr.n_slots + slot) * 8;
+    Slot8<T>::store(dst, re, im);
+}
+
+cudaError_t launch_fold(const PlanHdr *hdr_dev, int total_fold_blocks, bool fp64, cudaStream_t st)
+{
+    if (total_fold_blocks <= 0) return cudaSuccess;
+    if (fp64)
+        k_fold<double><<<total_fold_blocks, kFoldThreads, 0, st>>>(hdr_dev);
+    else
+        k_fold<float><<<total_fold_blocks, kFoldThreads, 0, st>>>(hdr_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace fewsum

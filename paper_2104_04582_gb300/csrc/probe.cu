@@ -1,0 +1,88 @@
+// probe.cu -- measured throughput of the arithmetic pipes the summation kernels use.
+//
+// The roofline of the summation is set by plain ALU pipes, not by HBM or tensor cores: FP32 FMA
+// (mixed path), FP64 FMA (plain path) and the SFU.  Each probe runs many independent dependency
+// chains per thread over a grid of several CTAs per SM, long enough (tens of ms) to reach the
+// clocks of a sustained load, and reports operations per second timed with CUDA events.
+#include <cuda_runtime.h>
+
+namespace {
+
+constexpr int kChains = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma(T *out, int iters, T b, T c)
+{
+    T a[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) a[j] = (T)(threadIdx.x + j) * (T)1e-3;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < kChains; ++j) a[j] = fma(a[j], b, c);
+    }
+    T s = 0;
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) s += a[j];
+    if (s == (T)12345.678) out[blockIdx.x] = s;  // keeps the chains alive
+}
+
+__global__ void __launch_bounds__(256) k_sfu(float *out, int iters)
+{
+    float a[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) a[j] = (float)(threadIdx.x + j) * 1e-3f;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < kChains; ++j) a[j] = __sinf(a[j]);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) s += a[j];
+    if (s == 12345.678f) out[blockIdx.x] = s;
+}
+
+}  // namespace
+
+extern "C" {
+
+// which: 0 = FP32 FMA, 1 = FP64 FMA, 2 = SFU sine (__sinf).  Returns 0 on success and writes the
+// measured rate (operations per second; an FMA counts as one operation) and the elapsed ms.
+int fewprobe_measure(int device, int which, int iters, double *ops_per_s, float *ms_out)
+{
+    if (cudaSetDevice(device) != cudaSuccess) return 1;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 1;
+    const int threads = 256, blocks = sms * 8;
+    float *out = nullptr;
+    if (cudaMalloc(&out, sizeof(float) * 2 * blocks) != cudaSuccess) return 1;
+    cudaStream_t st;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto launch = [&](int it) {
+        if (which == 0) k_fma<float><<<blocks, threads, 0, st>>>(out, it, 0.9999f, 1e-4f);
+        else if (which == 1)
+            k_fma<double><<<blocks, threads, 0, st>>>(reinterpret_cast<double *>(out), it, 0.9999, 1e-4);
+        else k_sfu<<<blocks, threads, 0, st>>>(out, it);
+    };
+    launch(iters / 8 + 1);  // warm-up
+    cudaEventRecord(e0, st);
+    launch(iters);
+    cudaEventRecord(e1, st);
+    int rc = 0;
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = 1;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    cudaFree(out);
+    if (cudaGetLastError() != cudaSuccess) rc = 1;
+    if (rc) return rc;
+    *ms_out = ms;
+    *ops_per_s = (double)blocks * threads * (double)iters * kChains / (ms * 1e-3);
+    return 0;
+}
+
+}  // extern "C"

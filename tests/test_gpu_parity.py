@@ -1,0 +1,277 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Sizes: the one-week workload in full (60,480 samples x 132 modes, many passes and segments, a
+ragged tail), the one-year 3843-mode workload at full size in the benchmark's launch
+configuration (oracle on windows at the start, across knots, and at the end), the four-year
+workload's mixed path on a 1e5-sample window, and tiny cases with ragged sample counts.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_04582_gb300 import fewsum as F
+from paper_2104_04582_gb300 import runtime as RT
+from paper_2104_04582_gb300 import workloads as W
+from tests.gpu_common import (FP64_PHASE, FP64_REL_L2, MIXED_MISMATCH, max_phase_err,
+                              oracle_threads, rel_l2, to_host)
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu(ctx, w, prec, c64=None, device_data=True, **kw):
+    import torch
+    tr = RT.from_inputs(ctx, w, device_data=device_data)
+    out = RT.waveform_inputs(ctx, tr, w, prec, c64, **kw)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == F.FEW_OK
+    h = to_host(out)
+    tr.release()
+    return h
+
+
+def _oracle(w, i_begin=0, count=None):
+    return oracle.waveform_inputs(w, i_begin, count, nthreads=oracle_threads())
+
+
+def test_week_fp64_full(gpu_ctx):
+    w = W.config1()
+    g = _gpu(gpu_ctx, w, F.FEW_FP64)
+    o = _oracle(w)
+    assert rel_l2(g, o) <= FP64_REL_L2
+    assert max_phase_err(g, o) <= FP64_PHASE
+
+
+def test_week_mixed_full(gpu_ctx):
+    w = W.config1()
+    g = _gpu(gpu_ctx, w, F.FEW_MIXED)
+    o = _oracle(w)
+    mm = oracle.mismatch(g, o)
+    assert mm <= MIXED_MISMATCH, mm
+    # stated expectation for FP32 amplitudes and exponentials: well below the gate
+    assert rel_l2(g, o) <= 1e-4
+    assert max_phase_err(g, o) <= 1e-3
+
+
+@pytest.fixture(scope="module")
+def year():
+    return W.config2()
+
+
+def _windows(w):
+    ns = w.n_samples
+    seg = F.few_plan_segments(w.t_knots, w.t0, w.dt, ns)
+    mid = int(seg[len(seg) // 2]) - 1000          # straddles a knot
+    late = int(seg[-3]) - 700                      # short late segments
+    return [(0, 2000), (mid, 2000), (late, 1500), (ns - 1700, 1700)]
+
+
+def test_year_fp64_windows(gpu_ctx, year):
+    g = _gpu(gpu_ctx, year, F.FEW_FP64)
+    assert g.shape[0] == year.n_samples
+    for i0, n in _windows(year):
+        o = _oracle(year, i0, n)
+        assert rel_l2(g[i0:i0 + n], o) <= FP64_REL_L2, (i0, rel_l2(g[i0:i0 + n], o))
+        assert max_phase_err(g[i0:i0 + n], o) <= FP64_PHASE, i0
+
+
+def test_year_mixed_windows_and_full_series(gpu_ctx, year):
+    gm = _gpu(gpu_ctx, year, F.FEW_MIXED)
+    for i0, n in _windows(year):
+        o = _oracle(year, i0, n)
+        assert oracle.mismatch(gm[i0:i0 + n], o) <= MIXED_MISMATCH, i0
+    g64 = _gpu(gpu_ctx, year, F.FEW_FP64)
+    assert oracle.mismatch(gm, g64) <= MIXED_MISMATCH
+
+
+def test_four_year_mixed_window(gpu_ctx):
+    w = W.config5()
+    g = _gpu(gpu_ctx, w, F.FEW_MIXED)
+    assert g.shape[0] == 63115200
+    n = 100000
+    i0 = w.n_samples - n
+    o = _oracle(w, i0, n)
+    assert oracle.mismatch(g[i0:], o) <= MIXED_MISMATCH
+    o2 = _oracle(w, 0, 2000)
+    assert oracle.mismatch(g[:2000], o2) <= MIXED_MISMATCH
+
+
+TINY = [(1, 6, 1), (2, 7, 7), (3, 5, 255), (4, 9, 256), (5, 4, 257), (6, 12, 1023),
+        (7, 8, 1025), (8, 30, 5000)]
+
+
+@pytest.mark.parametrize("seed,K,ns", TINY)
+def test_tiny_ragged(gpu_ctx, seed, K, ns):
+    w = W.tiny_inputs(seed, K=K, n_samples=max(ns, 2))
+    w.n_samples = ns
+    o = _oracle(w)
+    g = _gpu(gpu_ctx, w, F.FEW_FP64)
+    assert rel_l2(g, o) <= FP64_REL_L2
+    gm = _gpu(gpu_ctx, w, F.FEW_MIXED)
+    assert oracle.mismatch(gm, o) <= MIXED_MISMATCH
+
+
+MODESETS = {
+    "single_22": [(2, 2, 0)],
+    "m0_only": [(2, 0, -3), (2, 0, 3), (3, 0, 0), (4, 0, 1)],
+    "odd_l": [(3, 1, 2), (3, 3, -4), (5, 2, 7), (7, 7, -1)],
+    "wide_n": [(2, 2, -30), (2, 2, 30), (2, 1, 17), (10, 10, -25)],
+    "high_l": [(12, 5, 3), (20, 20, -2), (32, 0, 1), (32, 31, 0)],
+}
+
+
+@pytest.mark.parametrize("name", sorted(MODESETS))
+def test_mode_sets(gpu_ctx, name):
+    modes = np.asarray(MODESETS[name], dtype=np.int32)
+    w = W.tiny_inputs(42, K=10, n_samples=3000, modes=modes)
+    o = _oracle(w)
+    g = _gpu(gpu_ctx, w, F.FEW_FP64)
+    assert rel_l2(g, o) <= FP64_REL_L2, rel_l2(g, o)
+    gm = _gpu(gpu_ctx, w, F.FEW_MIXED)
+    assert oracle.mismatch(gm, o) <= MIXED_MISMATCH
+
+
+def test_offset_start_and_last_knot(gpu_ctx):
+    """Samples from the middle of the trajectory up to exactly its last knot."""
+    w = W.config1()
+    dt = 7.0
+    n = 20000
+    t0 = w.t_knots[-1] - (n - 1) * dt
+    w.t0, w.dt, w.n_samples = t0, dt, n
+    o = _oracle(w)
+    g = _gpu(gpu_ctx, w, F.FEW_FP64)
+    assert rel_l2(g, o) <= FP64_REL_L2
+
+
+def test_phase_offsets_and_scale(gpu_ctx):
+    import torch
+    w = W.config1()
+    dpp, dpr, sc = 1.234, -2.5, 3.75
+    tr = RT.from_inputs(gpu_ctx, w)
+    out = RT.waveform(gpu_ctx, tr, w.n_samples, w.t0, w.dt, w.theta, w.phi, F.FEW_FP64,
+                      scale=sc, dphi_phi0=dpp, dphi_r0=dpr)
+    torch.cuda.synchronize()
+    g = to_host(out)
+    tr.release()
+    o = oracle.waveform(w.t_knots, w.phi_phi + dpp, w.phi_r + dpr, w.modes, w.amp_re, w.amp_im,
+                        w.theta, w.phi, sc, w.t0, w.dt, 0, w.n_samples, oracle_threads())
+    assert rel_l2(g, o) <= FP64_REL_L2
+
+
+def test_host_buffers_match_device_path(gpu_ctx):
+    import torch
+    w = W.config1()
+    g_dev = _gpu(gpu_ctx, w, F.FEW_FP64)
+    tr = RT.from_inputs(gpu_ctx, w, device_data=False)
+    host = np.zeros(w.n_samples, dtype=np.complex128)
+    req = RT.request(tr, host, w.n_samples, w.t0, w.dt, w.theta, w.phi, F.FEW_FP64,
+                     out_where=F.FEW_MEM_HOST)
+    F.few_waveform(gpu_ctx.handle, req, RT.current_stream())
+    torch.cuda.synchronize()
+    tr.release()
+    np.testing.assert_array_equal(host, g_dev)
+
+
+def test_tiles_are_bit_identical(gpu_ctx):
+    w = W.config1()
+    ref = {}
+    saved = {p: gpu_ctx.get_tiles(p) for p in (F.FEW_FP64, F.FEW_MIXED)}
+    try:
+        for prec, Rs in ((F.FEW_FP64, (1, 2)), (F.FEW_MIXED, (2, 4, 8))):
+            for R in Rs:
+                for T in (128, 256):
+                    gpu_ctx.set_tiles(prec, R, T)
+                    g = _gpu(gpu_ctx, w, prec)
+                    if prec not in ref:
+                        ref[prec] = g
+                    np.testing.assert_array_equal(g, ref[prec])
+    finally:
+        for p, (R, T) in saved.items():
+            gpu_ctx.set_tiles(p, R, T)
+
+
+def test_errors_and_noop(gpu_ctx):
+    import torch
+    w = W.tiny_inputs(3)
+    tr = RT.Trajectory(gpu_ctx, w.t_knots, w.modes)
+    out = RT.alloc_out(10, False)
+    with pytest.raises(F.FewError) as e:  # no spline data yet
+        F.few_waveform(gpu_ctx.handle, RT.request(tr, out, 10, 0.0, w.dt, 0.3, 0.2), 0)
+    assert e.value.status == F.FEW_ERR_STATE
+    tr.set_data_host(w.phi_phi, w.phi_r, w.amp_re, w.amp_im)
+    with pytest.raises(F.FewError) as e:
+        F.few_waveform(gpu_ctx.handle, RT.request(tr, out, 10, -1.0, w.dt, 0.3, 0.2), 0)
+    assert e.value.status == F.FEW_ERR_RANGE
+    with pytest.raises(F.FewError) as e:
+        F.few_waveform(gpu_ctx.handle, RT.request(tr, out, 10, 0.0, w.T, 0.3, 0.2), 0)
+    assert e.value.status == F.FEW_ERR_RANGE
+    with pytest.raises(F.FewError) as e:
+        F.few_waveform(gpu_ctx.handle, RT.request(tr, out, 10, 0.0, w.dt, float("nan"), 0.2), 0)
+    assert e.value.status == F.FEW_ERR_INVALID_ARG
+    # n_samples = 0 is a no-op
+    F.few_waveform(gpu_ctx.handle, RT.request(tr, out, 0, 0.0, w.dt, 0.3, 0.2), 0)
+    torch.cuda.synchronize()
+    assert gpu_ctx.sync_status() == F.FEW_OK
+    # a NaN in device-resident knot data is detected by the build kernel and latched
+    bad = w.amp_re.copy()
+    bad[2, 1] = np.nan
+    tr.set_data_host(w.phi_phi, w.phi_r, bad, w.amp_im)
+    assert gpu_ctx.sync_status() == F.FEW_ERR_INVALID_ARG
+    assert gpu_ctx.sync_status() == F.FEW_OK  # latch cleared
+    tr.release()
+    with pytest.raises(F.FewError) as e:
+        RT.Trajectory(gpu_ctx, [0.0, 1.0, 2.0], w.modes)
+    assert e.value.status == F.FEW_ERR_KNOTS
+
+
+def test_budget_is_enforced():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w = W.config1()
+    with RT.Context(0, hbm_budget_bytes=1 << 20) as ctx:
+        with pytest.raises(F.FewError) as e:
+            RT.Trajectory(ctx, w.t_knots, W.mode_grid(10, 30))
+        assert e.value.status == F.FEW_ERR_BUDGET
+        used, budget = ctx.memory()
+        assert used == 0 and budget == 1 << 20
+
+
+def _gpu_phases(ctx, w, dpp=0.0, dpr=0.0):
+    import torch
+    tr = RT.from_inputs(ctx, w)
+    buf = torch.empty(2 * w.n_samples, dtype=torch.float64, device="cuda")
+    F.few_phase_samples(ctx.handle, tr.handle, w.t0, w.dt, w.n_samples, buf.data_ptr(), dpp, dpr,
+                        RT.current_stream())
+    torch.cuda.synchronize()
+    tr.release()
+    return buf.cpu().numpy().reshape(-1, 2)
+
+
+@pytest.mark.parametrize("cfg", ["year", "four_year"])
+def test_phase_step_matches_oracle(gpu_ctx, cfg):
+    """Per-sample orbital phases (reduced, in turns) against the long-double oracle.
+
+    Gate: every mode phase m*Phi_phi + n*Phi_r (|m| <= 10, |n| <= 30) within 1e-9 rad, i.e. each
+    orbital phase within 1e-9/40 rad.
+    """
+    w = W.config2() if cfg == "year" else W.config5()
+    g = _gpu_phases(gpu_ctx, w)
+    worst = 0.0
+    for i0 in (0, w.n_samples // 3, w.n_samples // 2 + 12345, w.n_samples - 3000):
+        o = oracle.phases(w.t_knots, w.phi_phi, w.phi_r, w.t0, w.dt, i0, 3000)
+        d = g[i0:i0 + 3000] - o
+        d -= np.round(d)
+        worst = max(worst, float(np.max(np.abs(d))) * 2 * math.pi)
+    assert worst <= 1e-9 / 40, worst
+
+
+def test_phase_step_offsets(gpu_ctx):
+    w = W.config1()
+    dpp, dpr = 1.0e3 + 0.25, -7.5
+    g = _gpu_phases(gpu_ctx, w, dpp, dpr)
+    o = oracle.phases(w.t_knots, w.phi_phi + dpp, w.phi_r + dpr, w.t0, w.dt, 0, w.n_samples)
+    d = g - o
+    d -= np.round(d)
+    assert np.max(np.abs(d)) * 2 * math.pi <= 1e-9 / 40
