@@ -174,6 +174,29 @@ typedef struct few_request {
 few_status few_waveform(few_ctx *ctx, const few_request *req, void *stream);
 
 /*
+ * Allocation-free variant of few_waveform.  The paper has no counterpart: this entry point is
+ * for callers that must not allocate memory once they are running -- e.g. a sampler or a
+ * real-time pipeline that reserves all device memory at start-up, or code under a policy that
+ * forbids cudaMalloc (and the synchronisation it can imply) on the call path.  It computes
+ * exactly what few_waveform computes for the same request, but keeps its scratch (plan,
+ * harmonic table, folded coefficients) in one fixed device array of FEW_NOALLOC_SCRATCH_BYTES
+ * that is part of the library image (reserved on every GPU that loads the library, until the
+ * process exits) and calls no allocator of any kind.
+ *   req->out_where must be FEW_MEM_DEVICE; the trajectory and the output buffer are the
+ *   caller's, as for few_waveform.
+ * Limits: the request's scratch (about 8 x slots x K x 4 bytes for FEW_MIXED, twice that for
+ *   FEW_FP64, plus a few KB) must fit in FEW_NOALLOC_SCRATCH_BYTES and K <= 4096; otherwise it
+ *   returns FEW_ERR_LIMIT without queuing work.  The one-year 3843-mode waveform fits in both
+ *   precisions; the four-year one (K = 300) fits only for FEW_MIXED.
+ * The first call made on a device looks up the array's device address (once per device);
+ *   make that first call before any stream capture.  All calls share the array: every call
+ *   rewrites what it uses, but calls whose work overlaps on the GPU race on it -- order them
+ *   (one stream, or events).  Asynchronous on `stream`.
+ */
+#define FEW_NOALLOC_SCRATCH_BYTES (16u << 20)
+few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req, void *stream);
+
+/*
  * The per-sample phase step on its own (Sec. 2 phase integrals, interpolated as in Sec. 3.C):
  * for sample i, t_i = t0 + i*dt, writes the orbital phases Phi_phi(t_i) + dphi_phi0 and
  * Phi_r(t_i) + dphi_r0 reduced modulo 2 pi and expressed in turns, each in [-1/2, 1/2]:

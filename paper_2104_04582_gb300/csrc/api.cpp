@@ -1051,3 +1051,31 @@ few_status few_mode_slots(const int *l, const int *m, const int *n, int N, int *
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------ read-only views
+// Used by the allocation-free entry point (noalloc.cu), which plans a request itself.
+
+namespace fewsum {
+
+bool ctx_traj_view(few_ctx *ctx, const few_traj *tr, CtxTrajView *v)
+{
+    if (!ctx || !tr || !v || tr->ctx != ctx) return false;
+    v->device = ctx->device;
+    v->sm_count = ctx->sm_count;
+    v->d_err = ctx->d_err;
+    v->tile_R[0] = ctx->tile_R[0];
+    v->tile_R[1] = ctx->tile_R[1];
+    v->tile_T[0] = ctx->tile_T[0];
+    v->tile_T[1] = ctx->tile_T[1];
+    v->has_data = tr->has_data;
+    v->K = tr->K;
+    v->n_slots = tr->plan.n_slots;
+    v->n_pairs = (int)tr->plan.pair_lm.size();
+    v->t_host = tr->t_host.data();
+    v->dev = tr->dev;
+    return true;
+}
+
+std::recursive_mutex &ctx_mutex(few_ctx *ctx) { return ctx->mu; }
+
+}  // namespace fewsum

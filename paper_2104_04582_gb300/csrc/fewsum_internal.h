@@ -4,7 +4,10 @@
 #pragma once
 
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
+
+#include "fewsum.h"
 
 namespace fewsum {
 
@@ -109,5 +112,18 @@ cudaError_t launch_phases(const TrajDev &tr, const int *seg_start, double t0, do
 int sum_occupancy(bool fp64, int samples_per_thread, int threads, int smem_bytes);
 // One-time kernel attribute setup (dynamic shared memory opt-in).
 cudaError_t sum_configure();
+
+// Read-only snapshot of a context and one of its trajectories (filled by api.cpp).
+struct CtxTrajView {
+    int device, sm_count;
+    unsigned *d_err;
+    int tile_R[2], tile_T[2];
+    bool has_data;
+    int K, n_slots, n_pairs;
+    const double *t_host;
+    TrajDev dev;
+};
+bool ctx_traj_view(few_ctx *ctx, const few_traj *tr, CtxTrajView *v);
+std::recursive_mutex &ctx_mutex(few_ctx *ctx);
 
 }  // namespace fewsum

@@ -1,0 +1,199 @@
+// noalloc.cu -- few_waveform_noalloc: one waveform without any memory allocation.
+//
+// Why it exists: some callers may not allocate device memory on the call path at all -- for
+// example a sampler or a real-time pipeline that reserves every byte at start-up and must not
+// touch the allocator (or its synchronisation) afterwards, or host code running under a
+// memory policy where cudaMalloc is forbidden after initialisation.  few_waveform takes its
+// scratch (the plan, the harmonic table and the folded coefficients) from the context's pool on
+// every call; this entry point instead places all of that in one fixed device array that is
+// part of the library image, so a call performs no allocation of any kind.
+//
+// The array (kScratchBytes, 16 MiB) is reserved on every GPU that loads the library and stays
+// there until the process exits.  Its address is looked up once per device with
+// cudaGetSymbolAddress during the first call made with that device current; that first call
+// should therefore come before any stream capture.  All calls share the array: nothing in it
+// has to start at zero (every call rewrites the whole region it uses before reading it), but
+// two calls whose work overlaps on the GPU (different streams, no ordering) race on it.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "fewsum_internal.h"
+
+namespace fewsum {
+
+namespace {
+
+constexpr size_t kScratchBytes = (size_t)16 << 20;  // FEW_NOALLOC_SCRATCH_BYTES
+constexpr int kMaxDevices = 64;
+constexpr int kMaxKnots = 4096;
+constexpr int kMaxGrid = 4096;
+constexpr int kChunk = 3072;  // plan bytes carried by one copy launch (kernel parameters)
+constexpr size_t kBlobMax = 64 * 1024;
+
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+// Host-side table of the array's device address, per device.
+std::mutex g_setup_mu;
+void *g_scratch_dev[kMaxDevices] = {};
+
+// Host image of one plan, rebuilt under a lock on every call (no heap use).
+std::mutex g_blob_mu;
+alignas(256) unsigned char g_blob[kBlobMax];
+
+struct ChunkParams {
+    unsigned char bytes[kChunk];
+};
+
+// Copies one chunk of the plan, passed by value as kernel parameters, into the array.
+__global__ void k_put_chunk(unsigned char *dst, ChunkParams p, int n)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = p.bytes[i];
+}
+
+inline size_t up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+few_status scratch_address(int device, unsigned char **out)
+{
+    if (device < 0 || device >= kMaxDevices) return FEW_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    if (!g_scratch_dev[device]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
+            (void)cudaGetLastError();
+            return FEW_ERR_CUDA;
+        }
+        g_scratch_dev[device] = p;
+    }
+    *out = static_cast<unsigned char *>(g_scratch_dev[device]);
+    return FEW_OK;
+}
+
+}  // namespace
+
+}  // namespace fewsum
+
+using namespace fewsum;
+
+extern "C" few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req, void *stream)
+{
+    if (!ctx || !req || !req->traj || !req->out) return FEW_ERR_INVALID_ARG;
+    const few_request &r = *req;
+    if (r.prec != FEW_FP64 && r.prec != FEW_MIXED) return FEW_ERR_INVALID_ARG;
+    if (r.out_where != FEW_MEM_DEVICE) return FEW_ERR_INVALID_ARG;
+    if (!std::isfinite(r.theta) || !std::isfinite(r.phi) || !std::isfinite(r.scale) ||
+        !std::isfinite(r.dphi_phi0) || !std::isfinite(r.dphi_r0))
+        return FEW_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx_mutex(ctx));
+    CtxTrajView v;
+    if (!ctx_traj_view(ctx, r.traj, &v)) return FEW_ERR_INVALID_ARG;
+    if (!v.has_data) return FEW_ERR_STATE;
+    if (!std::isfinite(r.t0) || !std::isfinite(r.dt) || !(r.dt > 0.0) || r.n_samples < 0 ||
+        r.n_samples > 2147483647LL)
+        return FEW_ERR_RANGE;
+    const int K = v.K, S = K - 1;
+    if (r.n_samples > 0) {
+        const double last = std::fma((double)(r.n_samples - 1), r.dt, r.t0);
+        if (r.t0 < v.t_host[0] || last > v.t_host[K - 1]) return FEW_ERR_RANGE;
+    }
+    const bool fp64 = r.prec == FEW_FP64;
+    if (v.n_slots > (fp64 ? kMaxSlotsFp64 : kMaxSlotsMixed)) return FEW_ERR_LIMIT;
+    if (K > kMaxKnots) return FEW_ERR_LIMIT;
+    if (r.n_samples == 0) return FEW_OK;
+    if (cudaSetDevice(v.device) != cudaSuccess) return FEW_ERR_CUDA;
+    unsigned char *base = nullptr;
+    few_status st = scratch_address(v.device, &base);
+    if (st) return st;
+
+    // tile shape and grid as in few_waveform
+    const int pi = fp64 ? 0 : 1;
+    const int R = v.tile_R[pi], T = v.tile_T[pi];
+    const size_t elem = fp64 ? 8 : 4;
+    const int buf_bytes = (int)up((size_t)v.n_slots * 8 * elem, 128);
+    const int smem = 2 * buf_bytes;
+    const int occ = sum_occupancy(fp64, R, T, smem);
+    if (occ <= 0) return FEW_ERR_LIMIT;
+    const int grid = v.sm_count * occ;
+    if (grid > kMaxGrid) return FEW_ERR_LIMIT;
+
+    // layout inside the fixed array: [plan | folded coefficients | harmonic table]
+    const size_t off_waves = up(sizeof(PlanHdr), 64);
+    const size_t off_cta = up(off_waves + sizeof(WaveDev), 64);
+    const size_t off_seg = up(off_cta + sizeof(CtaStart) * (grid + 1), 64);
+    const size_t blob_bytes = up(off_seg + sizeof(int) * K, 256);
+    const size_t fcoef_bytes = up((size_t)S * v.n_slots * 8 * elem, 256);
+    const size_t ylm_bytes = up((size_t)v.n_pairs * 2 * sizeof(double2), 256);
+    if (blob_bytes > kBlobMax || blob_bytes + fcoef_bytes + ylm_bytes > kScratchBytes)
+        return FEW_ERR_LIMIT;
+    unsigned char *d_fcoef = base + blob_bytes;
+    unsigned char *d_ylm = d_fcoef + fcoef_bytes;
+
+    std::lock_guard<std::mutex> blk(g_blob_mu);
+    std::memset(g_blob, 0, blob_bytes);
+    PlanHdr *hdr = reinterpret_cast<PlanHdr *>(g_blob);
+    WaveDev *W = reinterpret_cast<WaveDev *>(g_blob + off_waves);
+    CtaStart *cta = reinterpret_cast<CtaStart *>(g_blob + off_cta);
+    int *seg = reinterpret_cast<int *>(g_blob + off_seg);
+
+    // segment sample ranges: seg[k] = clamp(ceil((t_k - t0)/dt), 0, n)
+    const int64_t ns = r.n_samples;
+    seg[0] = 0;
+    for (int k = 1; k < K - 1; ++k) {
+        const double x = std::ceil((v.t_host[k] - r.t0) / r.dt);
+        int64_t val = x <= 0.0 ? 0 : (x >= (double)ns ? ns : (int64_t)x);
+        if (val < seg[k - 1]) val = seg[k - 1];
+        seg[k] = (int)val;
+    }
+    seg[K - 1] = (int)ns;
+
+    W->tr = v.dev;
+    W->theta = r.theta;
+    W->phi = r.phi;
+    W->scale = r.scale;
+    W->dphi_phi = r.dphi_phi0;
+    W->dphi_r = r.dphi_r0;
+    W->t0 = r.t0;
+    W->dt = r.dt;
+    W->n_samples = (int)ns;
+    W->out_c64 = r.out_c64 ? 1 : 0;
+    W->out = r.out;
+    W->fcoef = d_fcoef;
+    W->ylm = reinterpret_cast<double2 *>(d_ylm);
+    W->seg_start = reinterpret_cast<const int *>(base + off_seg);
+    W->pair_begin = 0;
+    W->fold_begin = 0;
+    W->fold_blocks_per_seg = (v.n_slots + kFoldThreads - 1) / kFoldThreads;
+
+    // equal slices of the samples (one waveform: equal cost per sample)
+    for (int g = 0; g < grid; ++g) {
+        const long double x = (long double)ns * g / grid;
+        cta[g] = CtaStart{0, (int)std::ceil(x)};
+    }
+    cta[grid] = CtaStart{1, 0};
+
+    hdr->n_waves = 1;
+    hdr->total_pairs = v.n_pairs;
+    hdr->total_fold_blocks = S * W->fold_blocks_per_seg;
+    hdr->grid_sum = grid;
+    hdr->buf_bytes = buf_bytes;
+    hdr->waves = reinterpret_cast<const WaveDev *>(base + off_waves);
+    hdr->cta = reinterpret_cast<const CtaStart *>(base + off_cta);
+    hdr->err = v.d_err;
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (size_t off = 0; off < blob_bytes; off += kChunk) {
+        const int n = (int)((blob_bytes - off) < (size_t)kChunk ? (blob_bytes - off) : kChunk);
+        ChunkParams p;
+        std::memcpy(p.bytes, g_blob + off, (size_t)n);
+        k_put_chunk<<<1, 256, 0, s>>>(base + off, p, n);
+    }
+    if (cudaGetLastError() != cudaSuccess) return FEW_ERR_CUDA;
+    const PlanHdr *hd = reinterpret_cast<const PlanHdr *>(base);
+    if (launch_ylm(hd, v.n_pairs, s) != cudaSuccess ||
+        launch_fold(hd, hdr->total_fold_blocks, fp64, s) != cudaSuccess ||
+        launch_sum(hd, grid, T, R, smem, fp64, s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return FEW_ERR_CUDA;
+    }
+    return FEW_OK;
+}

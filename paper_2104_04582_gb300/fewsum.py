@@ -41,7 +41,7 @@ EXPORTED = [
     "few_traj_create", "few_traj_set_data", "few_traj_release", "few_traj_info", "few_waveform",
     "few_batch_plan", "few_batch_run", "few_batch_release", "few_sync_status", "few_set_tiles",
     "few_get_tiles", "few_plan_segments", "few_mode_slots", "few_ctx_set_timing",
-    "few_last_timing", "few_phase_samples",
+    "few_last_timing", "few_phase_samples", "few_waveform_noalloc",
 ]
 
 
@@ -102,6 +102,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
             "few_traj_release": (ctypes.c_int, [_vp, _vp]),
             "few_traj_info": (ctypes.c_int, [_vp, _ip, _ip, _ip]),
             "few_waveform": (ctypes.c_int, [_vp, ctypes.POINTER(few_request), _vp]),
+            "few_waveform_noalloc": (ctypes.c_int, [_vp, ctypes.POINTER(few_request), _vp]),
             "few_batch_plan": (ctypes.c_int, [_vp, ctypes.POINTER(few_request), ctypes.c_int,
                                               ctypes.c_uint, ctypes.POINTER(_vp)]),
             "few_batch_run": (ctypes.c_int, [_vp, _vp, _vp]),
@@ -219,6 +220,15 @@ def make_request(traj: int, out_ptr: int, n_samples: int, t0: float, dt: float, 
 
 def few_waveform(ctx: int, req: few_request, stream: int = 0) -> None:
     _check("few_waveform", load().few_waveform(ctx, ctypes.byref(req), stream))
+
+
+def few_waveform_noalloc(ctx: int, req: few_request, stream: int = 0) -> None:
+    """few_waveform without any allocation (scratch in a fixed array inside the library).
+
+    For callers that must not allocate once running; see include/fewsum.h for the size limit
+    and the rule that overlapping calls must be ordered.
+    """
+    _check("few_waveform_noalloc", load().few_waveform_noalloc(ctx, ctypes.byref(req), stream))
 
 
 def few_batch_plan(ctx: int, reqs: Sequence[few_request], flags: int = 0) -> int:
