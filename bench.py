@@ -162,7 +162,8 @@ def measure_peaks(dev_index: int):
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)]
     out = {}
     for which, name, it0 in ((0, "fp32_fma_per_s", 20000), (1, "fp64_fma_per_s", 400),
-                             (2, "sfu_sin_per_s", 4000)):
+                             (2, "sfu_sin_per_s", 4000), (3, "fp32_fma_3reg_per_s", 20000),
+                             (4, "fp32x2_fma_3reg_per_s", 10000)):
         r, ms = ctypes.c_double(), ctypes.c_float()
         if L.fewprobe_measure(dev_index, which, it0, ctypes.byref(r), ctypes.byref(ms)):
             continue

@@ -247,6 +247,13 @@ few_status few_set_tiles(few_ctx *ctx, int prec, int samples_per_thread, int thr
 few_status few_get_tiles(few_ctx *ctx, int prec, int *samples_per_thread, int *threads_per_block);
 
 /*
+ * FEW_MIXED summation instruction set: packed FP32x2 FMA (enable = 1; used when the tile has
+ * R in {4, 8} and the per-segment table has at most FEW_MAX_SLOTS_FP64 slots) or scalar FP32
+ * FMA (enable = 0, the default).  Speed only: both give bit-identical results.
+ */
+few_status few_set_packed(few_ctx *ctx, int enable);
+
+/*
  * Per-kernel device timing.  With timing enabled, the library records a CUDA event pair on the
  * launch stream around each kernel it queues.  few_last_timing waits for the most recent pairs
  * and returns their durations in ms: ms[0] spline build (last few_traj_set_data), ms[1]

@@ -52,7 +52,8 @@ def _compile(src: str, obj: str, extra: List[str]) -> None:
 
 def _link(lib: str, objs: List[str]) -> None:
     tmp = lib + f".tmp{os.getpid()}"
-    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"]
+    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static",
+                                                           "-Xlinker", "-z,defs"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -105,6 +105,7 @@ struct few_ctx {
     PinnedPool pinned;
     int tile_R[2] = {1, 4};
     int tile_T[2] = {256, 256};
+    bool packed = false;  // packed FP32x2 summation for FEW_MIXED when the slot table fits
     std::map<std::tuple<int, int, int, int>, int> occ_cache;
     bool timing = false;
     cudaEvent_t tev[8] = {};
@@ -290,11 +291,12 @@ struct few_traj {
 struct few_batch {
     few_ctx *ctx = nullptr;
     bool fp64 = false;
+    int variant = kVariantFp64;
     int n = 0;
     void *blob_dev = nullptr;
     void *scratch_dev = nullptr;
     void *jobs_dev = nullptr;
-    int n_jobs = 0, build_blocks = 0;
+    int n_jobs = 0, build_blocks = 0, max_knots = 0;
     int grid = 0, threads = 0, R = 0, smem = 0, total_pairs = 0, total_fold = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -309,15 +311,25 @@ struct PlanImage {
     size_t scratch_bytes = 0;
     std::vector<size_t> fcoef_off, ylm_off;
     bool fp64 = false;
+    int variant = kVariantFp64;
     int grid = 0, threads = 0, R = 0, smem = 0, buf_bytes = 0, total_pairs = 0, total_fold = 0;
 };
 
-int occupancy(few_ctx *c, bool fp64, int R, int T, int smem)
+// Summation variant of a plan: FP64, or for the mixed path the packed FP32x2 kernel when the
+// largest slot table fits its (duplicated) layout and the tile has R in {4, 8}, else scalar FP32.
+int pick_variant(bool fp64, bool packed_ok, int R, int max_slots)
 {
-    auto key = std::make_tuple((int)fp64, R, T, smem);
+    if (fp64) return kVariantFp64;
+    if (packed_ok && (R == 4 || R == 8) && max_slots <= kMaxSlotsPacked) return kVariantPacked;
+    return kVariantScalar;
+}
+
+int occupancy(few_ctx *c, int variant, int R, int T, int smem)
+{
+    auto key = std::make_tuple(variant, R, T, smem);
     auto it = c->occ_cache.find(key);
     if (it != c->occ_cache.end()) return it->second;
-    const int o = sum_occupancy(fp64, R, T, smem);
+    const int o = sum_occupancy(variant, R, T, smem);
     c->occ_cache[key] = o;
     return o;
 }
@@ -352,12 +364,13 @@ few_status build_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P)
     const int pi = P.fp64 ? 0 : 1;
     P.R = c->tile_R[pi];
     P.threads = c->tile_T[pi];
-    const size_t elem = P.fp64 ? 8 : 4;
     int max_slots = 1;
     for (int q = 0; q < n; ++q) max_slots = std::max(max_slots, reqs[q].traj->plan.n_slots);
-    P.buf_bytes = (int)align_up((size_t)max_slots * 8 * elem, 128);
+    P.variant = pick_variant(P.fp64, c->packed, P.R, max_slots);
+    const size_t slot_bytes = (size_t)sum_slot_bytes(P.variant);
+    P.buf_bytes = (int)align_up((size_t)max_slots * slot_bytes, 128);
     P.smem = 2 * P.buf_bytes;
-    const int occ = occupancy(c, P.fp64, P.R, P.threads, P.smem);
+    const int occ = occupancy(c, P.variant, P.R, P.threads, P.smem);
     if (occ <= 0) return FEW_ERR_LIMIT;
     P.grid = c->sm_count * occ;
 
@@ -380,7 +393,7 @@ few_status build_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P)
     for (int q = 0; q < n; ++q) {
         const few_traj *tr = reqs[q].traj;
         P.fcoef_off[q] = s_off;
-        s_off = align_up(s_off + (size_t)tr->S * tr->plan.n_slots * 8 * elem, 256);
+        s_off = align_up(s_off + (size_t)tr->S * tr->plan.n_slots * slot_bytes, 256);
         P.ylm_off[q] = s_off;
         s_off = align_up(s_off + (size_t)tr->plan.pair_lm.size() * 2 * sizeof(double2), 256);
     }
@@ -454,22 +467,23 @@ void fill_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P, unsign
     hdr->total_fold_blocks = P.total_fold;
     hdr->grid_sum = P.grid;
     hdr->buf_bytes = P.buf_bytes;
+    hdr->variant = P.variant;
     hdr->waves = reinterpret_cast<const WaveDev *>(blob_dev + P.off_waves);
     hdr->cta = reinterpret_cast<const CtaStart *>(blob_dev + P.off_cta);
     hdr->err = c->d_err;
 }
 
 few_status launch_kernels(few_ctx *c, const PlanHdr *hdr_dev, int total_pairs, int total_fold,
-                          int grid, int threads, int R, int smem, bool fp64, cudaStream_t st)
+                          int grid, int threads, int R, int smem, int variant, cudaStream_t st)
 {
     tmark(c, 1, false, st);
     FEW_CUDA_TRY(launch_ylm(hdr_dev, total_pairs, st));
     tmark(c, 1, true, st);
     tmark(c, 2, false, st);
-    FEW_CUDA_TRY(launch_fold(hdr_dev, total_fold, fp64, st));
+    FEW_CUDA_TRY(launch_fold(hdr_dev, total_fold, variant == kVariantFp64, st));
     tmark(c, 2, true, st);
     tmark(c, 3, false, st);
-    FEW_CUDA_TRY(launch_sum(hdr_dev, grid, threads, R, smem, fp64, st));
+    FEW_CUDA_TRY(launch_sum(hdr_dev, grid, threads, R, smem, variant, st));
     tmark(c, 3, true, st);
     return FEW_OK;
 }
@@ -719,7 +733,7 @@ few_status few_traj_set_data(few_ctx *ctx, few_traj *tr, const double *phi_phi, 
     if (s) return s;
     const int blocks = (tr->J + kBuildThreads - 1) / kBuildThreads;
     tmark(ctx, 0, false, st);
-    FEW_CUDA_TRY(launch_build(tr->job_dev, 1, blocks, ctx->d_err, st));
+    FEW_CUDA_TRY(launch_build(tr->job_dev, 1, blocks, tr->K, ctx->d_err, st));
     tmark(ctx, 0, true, st);
     tr->src_phi_phi = job.phi_phi;
     tr->src_phi_r = job.phi_r;
@@ -786,7 +800,7 @@ few_status few_waveform(few_ctx *ctx, const few_request *req, void *stream)
     st = upload(ctx, blob, P.blob.data(), P.blob.size(), s);
     if (!st)
         st = launch_kernels(ctx, static_cast<const PlanHdr *>(blob), P.total_pairs, P.total_fold,
-                            P.grid, P.threads, P.R, P.smem, P.fp64, s);
+                            P.grid, P.threads, P.R, P.smem, P.variant, s);
     if (!st && req->out_where == FEW_MEM_HOST) {
         cudaError_t e = cudaMemcpyAsync(req->out, dout, out_bytes, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) {
@@ -853,6 +867,7 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
     if (!b) return FEW_ERR_NOMEM;
     b->ctx = ctx;
     b->fp64 = P.fp64;
+    b->variant = P.variant;
     b->n = n;
     cudaStream_t s = ctx->internal;
     auto fail = [&](few_status e) {
@@ -888,6 +903,7 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
             j.amp_im = tr->src_im;
             j.block_begin = blocks;
             blocks += (tr->J + kBuildThreads - 1) / kBuildThreads;
+            b->max_knots = std::max(b->max_knots, tr->K);
             jobs.push_back(j);
         }
         if ((st = dev_alloc(ctx, sizeof(BuildJob) * jobs.size(), s, &b->jobs_dev))) return fail(st);
@@ -911,10 +927,10 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
             const PlanHdr *hd = static_cast<const PlanHdr *>(b->blob_dev);
             if (b->n_jobs)
                 launch_build(static_cast<const BuildJob *>(b->jobs_dev), b->n_jobs, b->build_blocks,
-                             ctx->d_err, cap);
+                             b->max_knots, ctx->d_err, cap);
             launch_ylm(hd, b->total_pairs, cap);
             launch_fold(hd, b->total_fold, b->fp64, cap);
-            launch_sum(hd, b->grid, b->threads, b->R, b->smem, b->fp64, cap);
+            launch_sum(hd, b->grid, b->threads, b->R, b->smem, b->variant, cap);
             e = cudaStreamEndCapture(cap, &b->graph);
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
@@ -940,11 +956,11 @@ few_status few_batch_run(few_ctx *ctx, few_batch *b, void *stream)
     if (b->n_jobs) {
         tmark(ctx, 0, false, s);
         FEW_CUDA_TRY(launch_build(static_cast<const BuildJob *>(b->jobs_dev), b->n_jobs,
-                                  b->build_blocks, ctx->d_err, s));
+                                  b->build_blocks, b->max_knots, ctx->d_err, s));
         tmark(ctx, 0, true, s);
     }
     return launch_kernels(ctx, hd, b->total_pairs, b->total_fold, b->grid, b->threads, b->R,
-                          b->smem, b->fp64, s);
+                          b->smem, b->variant, s);
 }
 
 few_status few_batch_release(few_ctx *ctx, few_batch *b)
@@ -1024,6 +1040,14 @@ few_status few_set_tiles(few_ctx *ctx, int prec, int R, int threads)
     return FEW_OK;
 }
 
+few_status few_set_packed(few_ctx *ctx, int enable)
+{
+    if (!ctx) return FEW_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    ctx->packed = enable != 0;
+    return FEW_OK;
+}
+
 few_status few_get_tiles(few_ctx *ctx, int prec, int *R, int *threads)
 {
     if (!ctx || (prec != FEW_FP64 && prec != FEW_MIXED)) return FEW_ERR_INVALID_ARG;
@@ -1062,6 +1086,7 @@ bool ctx_traj_view(few_ctx *ctx, const few_traj *tr, CtxTrajView *v)
     if (!ctx || !tr || !v || tr->ctx != ctx) return false;
     v->device = ctx->device;
     v->sm_count = ctx->sm_count;
+    v->packed = ctx->packed;
     v->d_err = ctx->d_err;
     v->tile_R[0] = ctx->tile_R[0];
     v->tile_R[1] = ctx->tile_R[1];

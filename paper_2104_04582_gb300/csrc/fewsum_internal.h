@@ -22,8 +22,16 @@ constexpr int kMaxL = 32;
 constexpr int kMaxAbsN = 1024;
 constexpr int kMaxSlotsFp64 = 1776;   // 2 buffers x slots x 64 B <= 227 KB
 constexpr int kMaxSlotsMixed = 3552;  // 2 buffers x slots x 32 B <= 227 KB
+constexpr int kMaxSlotsPacked = 1776; // 2 buffers x slots x 64 B (duplicated FP32 pairs)
+
+// Summation kernel variants (and the folded-coefficient layout each reads).
+enum : int {
+    kVariantFp64 = 0,    // FP64 throughout; slot = 8 doubles
+    kVariantScalar = 1,  // mixed, scalar FP32 FMA; slot = 8 floats
+    kVariantPacked = 2   // mixed, packed FP32x2 FMA; slot = 8 duplicated float pairs
+};
 constexpr int kFoldThreads = 128;
-constexpr int kYlmThreads = 64;
+constexpr int kYlmThreads = 8;   // few pairs per block: spreads the FP64 work over SMs
 constexpr int kBuildThreads = 64;
 
 // Trajectory-resident data (one per few_traj).
@@ -90,8 +98,8 @@ struct PlanHdr {
     int total_pairs;
     int total_fold_blocks;
     int grid_sum;
-    int buf_bytes;   // bytes of one shared-memory coefficient buffer (max slots x 8 x sizeof)
-    int pad;
+    int buf_bytes;   // bytes of one shared-memory coefficient buffer (max slots x slot bytes)
+    int variant;     // kVariant* of the summation kernel and the folded layout
     const WaveDev *waves;
     const CtaStart *cta;
     unsigned *err;
@@ -100,22 +108,25 @@ struct PlanHdr {
 // Kernel launchers (defined in the .cu files; every launcher returns the launch error).
 cudaError_t launch_factor(const double *t, int K, double *h, double *inv_h, double *fac_w,
                           double *fac_ip, double *fac_up, cudaStream_t st);
-cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks, unsigned *err,
-                         cudaStream_t st);
+cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks, int max_knots,
+                         unsigned *err, cudaStream_t st);
 cudaError_t launch_ylm(const PlanHdr *hdr_dev, int total_pairs, cudaStream_t st);
 cudaError_t launch_fold(const PlanHdr *hdr_dev, int total_fold_blocks, bool fp64, cudaStream_t st);
 cudaError_t launch_sum(const PlanHdr *hdr_dev, int grid, int threads, int samples_per_thread,
-                       int smem_bytes, bool fp64, cudaStream_t st);
+                       int smem_bytes, int variant, cudaStream_t st);
+// Bytes of one folded slot in the layout a variant reads.
+int sum_slot_bytes(int variant);
 cudaError_t launch_phases(const TrajDev &tr, const int *seg_start, double t0, double dt, int n,
                           double dphi_phi, double dphi_r, double *out, cudaStream_t st);
 // Maximum resident CTAs per SM of the summation kernel for a configuration (0 if invalid).
-int sum_occupancy(bool fp64, int samples_per_thread, int threads, int smem_bytes);
+int sum_occupancy(int variant, int samples_per_thread, int threads, int smem_bytes);
 // One-time kernel attribute setup (dynamic shared memory opt-in).
 cudaError_t sum_configure();
 
 // Read-only snapshot of a context and one of its trajectories (filled by api.cpp).
 struct CtxTrajView {
     int device, sm_count;
+    bool packed;
     unsigned *d_err;
     int tile_R[2], tile_T[2];
     bool has_data;

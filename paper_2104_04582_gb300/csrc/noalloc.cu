@@ -108,10 +108,14 @@ extern "C" few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req,
     // tile shape and grid as in few_waveform
     const int pi = fp64 ? 0 : 1;
     const int R = v.tile_R[pi], T = v.tile_T[pi];
-    const size_t elem = fp64 ? 8 : 4;
-    const int buf_bytes = (int)up((size_t)v.n_slots * 8 * elem, 128);
+    const int variant = fp64 ? kVariantFp64
+                             : ((v.packed && (R == 4 || R == 8) && v.n_slots <= kMaxSlotsPacked)
+                                    ? kVariantPacked
+                                    : kVariantScalar);
+    const size_t slot_bytes = (size_t)sum_slot_bytes(variant);
+    const int buf_bytes = (int)up((size_t)v.n_slots * slot_bytes, 128);
     const int smem = 2 * buf_bytes;
-    const int occ = sum_occupancy(fp64, R, T, smem);
+    const int occ = sum_occupancy(variant, R, T, smem);
     if (occ <= 0) return FEW_ERR_LIMIT;
     const int grid = v.sm_count * occ;
     if (grid > kMaxGrid) return FEW_ERR_LIMIT;
@@ -121,7 +125,7 @@ extern "C" few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req,
     const size_t off_cta = up(off_waves + sizeof(WaveDev), 64);
     const size_t off_seg = up(off_cta + sizeof(CtaStart) * (grid + 1), 64);
     const size_t blob_bytes = up(off_seg + sizeof(int) * K, 256);
-    const size_t fcoef_bytes = up((size_t)S * v.n_slots * 8 * elem, 256);
+    const size_t fcoef_bytes = up((size_t)S * v.n_slots * slot_bytes, 256);
     const size_t ylm_bytes = up((size_t)v.n_pairs * 2 * sizeof(double2), 256);
     if (blob_bytes > kBlobMax || blob_bytes + fcoef_bytes + ylm_bytes > kScratchBytes)
         return FEW_ERR_LIMIT;
@@ -176,6 +180,7 @@ extern "C" few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req,
     hdr->total_fold_blocks = S * W->fold_blocks_per_seg;
     hdr->grid_sum = grid;
     hdr->buf_bytes = buf_bytes;
+    hdr->variant = variant;
     hdr->waves = reinterpret_cast<const WaveDev *>(base + off_waves);
     hdr->cta = reinterpret_cast<const CtaStart *>(base + off_cta);
     hdr->err = v.d_err;
@@ -191,7 +196,7 @@ extern "C" few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req,
     const PlanHdr *hd = reinterpret_cast<const PlanHdr *>(base);
     if (launch_ylm(hd, v.n_pairs, s) != cudaSuccess ||
         launch_fold(hd, hdr->total_fold_blocks, fp64, s) != cudaSuccess ||
-        launch_sum(hd, grid, T, R, smem, fp64, s) != cudaSuccess) {
+        launch_sum(hd, grid, T, R, smem, variant, s) != cudaSuccess) {
         (void)cudaGetLastError();
         return FEW_ERR_CUDA;
     }

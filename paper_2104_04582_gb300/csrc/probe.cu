@@ -41,11 +41,52 @@ __global__ void __launch_bounds__(256) k_sfu(float *out, int iters)
     if (s == 12345.678f) out[blockIdx.x] = s;
 }
 
+// Every FMA reads three distinct registers (no constant-bank operand).
+__global__ void __launch_bounds__(256) k_fma_regs(float *out, const float *in, int iters)
+{
+    float a[kChains], b[kChains], c[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) {
+        a[j] = in[(threadIdx.x + j) & 255];
+        b[j] = in[(threadIdx.x + 3 * j + 1) & 255];
+        c[j] = in[(threadIdx.x + 5 * j + 2) & 255];
+    }
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < kChains; ++j) a[j] = fmaf(a[j], b[j], c[(j + 1) % kChains]);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) s += a[j];
+    if (s == 12345.678f) out[blockIdx.x] = s;
+}
+
+// Packed FP32x2 FMA with three distinct register pairs.
+__global__ void __launch_bounds__(256) k_fma2_regs(float *out, const float *in, int iters)
+{
+    float2 a[kChains], b[kChains], c[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) {
+        a[j] = make_float2(in[(threadIdx.x + j) & 255], in[(threadIdx.x + j + 7) & 255]);
+        b[j] = make_float2(in[(threadIdx.x + 3 * j + 1) & 255], in[(threadIdx.x + 2 * j) & 255]);
+        c[j] = make_float2(in[(threadIdx.x + 5 * j + 2) & 255], in[(threadIdx.x + j + 9) & 255]);
+    }
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < kChains; ++j) a[j] = __ffma2_rn(a[j], b[j], c[(j + 1) % kChains]);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) s += a[j].x + a[j].y;
+    if (s == 12345.678f) out[blockIdx.x] = s;
+}
+
 }  // namespace
 
 extern "C" {
 
-// which: 0 = FP32 FMA, 1 = FP64 FMA, 2 = SFU sine (__sinf).  Returns 0 on success and writes the
+// which: 0 = FP32 FMA, 1 = FP64 FMA, 2 = SFU sine (__sinf), 3 = FP32 FMA with three register
+// operands, 4 = packed FP32x2 FMA with three register pairs (counts 2 operations each).  Returns 0 on success and writes the
 // measured rate (operations per second; an FMA counts as one operation) and the elapsed ms.
 int fewprobe_measure(int device, int which, int iters, double *ops_per_s, float *ms_out)
 {
@@ -53,8 +94,10 @@ int fewprobe_measure(int device, int which, int iters, double *ops_per_s, float 
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 1;
     const int threads = 256, blocks = sms * 8;
-    float *out = nullptr;
+    float *out = nullptr, *in = nullptr;
     if (cudaMalloc(&out, sizeof(float) * 2 * blocks) != cudaSuccess) return 1;
+    if (cudaMalloc(&in, sizeof(float) * 256) != cudaSuccess) return 1;
+    cudaMemset(in, 0, sizeof(float) * 256);
     cudaStream_t st;
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     cudaEvent_t e0, e1;
@@ -64,7 +107,9 @@ int fewprobe_measure(int device, int which, int iters, double *ops_per_s, float 
         if (which == 0) k_fma<float><<<blocks, threads, 0, st>>>(out, it, 0.9999f, 1e-4f);
         else if (which == 1)
             k_fma<double><<<blocks, threads, 0, st>>>(reinterpret_cast<double *>(out), it, 0.9999, 1e-4);
-        else k_sfu<<<blocks, threads, 0, st>>>(out, it);
+        else if (which == 2) k_sfu<<<blocks, threads, 0, st>>>(out, it);
+        else if (which == 3) k_fma_regs<<<blocks, threads, 0, st>>>(out, in, it);
+        else k_fma2_regs<<<blocks, threads, 0, st>>>(out, in, it);
     };
     launch(iters / 8 + 1);  // warm-up
     cudaEventRecord(e0, st);
@@ -78,10 +123,12 @@ int fewprobe_measure(int device, int which, int iters, double *ops_per_s, float 
     cudaEventDestroy(e1);
     cudaStreamDestroy(st);
     cudaFree(out);
+    cudaFree(in);
     if (cudaGetLastError() != cudaSuccess) rc = 1;
     if (rc) return rc;
     *ms_out = ms;
-    *ops_per_s = (double)blocks * threads * (double)iters * kChains / (ms * 1e-3);
+    *ops_per_s = (double)blocks * threads * (double)iters * kChains * (which == 4 ? 2 : 1) /
+                 (ms * 1e-3);
     return 0;
 }
 

@@ -67,9 +67,15 @@ __device__ __forceinline__ double load_y(const BuildJob &jb, int j, int k)
 }
 
 // One thread per spline column.  Jobs are laid out in a flattened grid of column blocks.
+// The sweeps are sequential in k, so each step would wait on its own global load; instead the
+// knot-only arrays (h, 1/h, factorisation) are staged in shared memory and the column values
+// are fetched kChunk knots ahead into registers, so kChunk loads are in flight at once.
+constexpr int kChunk = 8;
+
 __global__ void __launch_bounds__(kBuildThreads)
 k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
 {
+    extern __shared__ double sk[];  // [5][K]: h, 1/h, w, 1/pivot, up
     // job of this block: largest q with jobs[q].block_begin <= blockIdx.x
     int lo = 0, hi = n_jobs - 1;
     const int b = blockIdx.x;
@@ -79,67 +85,97 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
     }
     const BuildJob &jb = jobs[lo];
     const TrajDev &tr = jb.tr;
-    const int j = (b - jb.block_begin) * kBuildThreads + threadIdx.x;
-    if (j >= tr.J) return;
     const int K = tr.K, J = tr.J;
-    const double *__restrict__ h = tr.h;
-    const double *__restrict__ ih = tr.inv_h;
+    double *h = sk, *ih = sk + K, *fw = sk + 2 * K, *fip = sk + 3 * K, *fup = sk + 4 * K;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        h[k] = k < K - 1 ? tr.h[k] : 0.0;
+        ih[k] = k < K - 1 ? tr.inv_h[k] : 0.0;
+        fw[k] = tr.fac_w[k];
+        fip[k] = tr.fac_ip[k];
+        fup[k] = tr.fac_up[k];
+    }
+    __syncthreads();
+    const int j = (b - jb.block_begin) * kBuildThreads + threadIdx.x;
+    if (j >= J) return;
     double *__restrict__ coef = tr.coef;
     bool finite = true;
 
     // forward sweep: r'_k = r_k - w_k r'_{k-1}; r'_k is parked in coef[k][j][1] (k < K-1)
     double y0 = load_y(jb, j, 0), y1 = load_y(jb, j, 1), y2 = load_y(jb, j, 2);
     finite &= isfinite(y0) && isfinite(y1) && isfinite(y2);
-    double d0 = (y1 - y0) * ih[0], d1 = (y2 - y1) * ih[1];
-    double r = ((2.0 * h[1] + 3.0 * h[0]) * h[1] * d0 + h[0] * h[0] * d1) / (h[0] + h[1]);
-    double rp = r;  // r'_0
-    coef[((size_t)0 * J + j) * 4 + 1] = rp;
+    const double d0 = (y1 - y0) * ih[0], d1 = (y2 - y1) * ih[1];
+    double rp = ((2.0 * h[1] + 3.0 * h[0]) * h[1] * d0 + h[0] * h[0] * d1) / (h[0] + h[1]);
+    coef[(size_t)j * 4 + 1] = rp;
     double dprev = d0;  // d_{k-1}
     double ycur = y1;   // y_k
-    for (int k = 1; k <= K - 2; ++k) {
-        const double ynext = load_y(jb, j, k + 1);
-        finite &= isfinite(ynext);
-        const double dk = (ynext - ycur) * ih[k];
-        r = 3.0 * (h[k] * dprev + h[k - 1] * dk);
-        rp = r - tr.fac_w[k] * rp;
-        coef[((size_t)k * J + j) * 4 + 1] = rp;
-        dprev = dk;
-        ycur = ynext;
+    double dkm3 = d0;   // d_{K-3}, kept for the last row
+    for (int k0 = 1; k0 <= K - 2; k0 += kChunk) {
+        double yn[kChunk];
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q)
+            yn[q] = (k0 + q <= K - 2) ? load_y(jb, j, k0 + q + 1) : 0.0;
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+            const int k = k0 + q;
+            if (k > K - 2) break;
+            finite &= isfinite(yn[q]);
+            const double dk = (yn[q] - ycur) * ih[k];
+            const double r = 3.0 * (h[k] * dprev + h[k - 1] * dk);
+            rp = r - fw[k] * rp;
+            coef[((size_t)k * J + j) * 4 + 1] = rp;
+            if (k == K - 3) dkm3 = dk;
+            dprev = dk;
+            ycur = yn[q];
+        }
     }
     {
         const double a = h[K - 2], c = h[K - 3];
-        // d_{K-3} is recomputed from the knots to keep the loop's registers small
-        const double ym3 = load_y(jb, j, K - 3), ym2 = load_y(jb, j, K - 2);
-        const double dkm3 = (ym2 - ym3) * ih[K - 3];
-        r = (a * a * dkm3 + (2.0 * c + 3.0 * a) * c * dprev) / (c + a);
-        rp = r - tr.fac_w[K - 1] * rp;
+        const double r = (a * a * dkm3 + (2.0 * c + 3.0 * a) * c * dprev) / (c + a);
+        rp = r - fw[K - 1] * rp;
     }
-    // back substitution and coefficients in u
-    double s_next = rp * tr.fac_ip[K - 1];  // s_{K-1}
-    double y_next = load_y(jb, j, K - 1);
-    for (int k = K - 2; k >= 0; --k) {
-        double *c = coef + ((size_t)k * J + j) * 4;
-        const double rpk = c[1];
-        const double s = (rpk - tr.fac_up[k] * s_next) * tr.fac_ip[k];
-        const double yk = load_y(jb, j, k);
-        const double D = y_next - yk;
-        const double hk = h[k];
-        const double2 c01 = make_double2(yk, hk * s);
-        const double2 c23 = make_double2(3.0 * D - hk * (2.0 * s + s_next),
-                                         hk * (s + s_next) - 2.0 * D);
-        reinterpret_cast<double2 *>(c)[0] = c01;
-        reinterpret_cast<double2 *>(c)[1] = c23;
-        s_next = s;
-        y_next = yk;
+    // back substitution and coefficients in u, with r'_k and y_k fetched a chunk ahead
+    double s_next = rp * fip[K - 1];  // s_{K-1}
+    double y_next = ycur;             // y_{K-1}
+    for (int k0 = K - 2; k0 >= 0; k0 -= kChunk) {
+        double rv[kChunk], yv[kChunk];
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+            const int k = k0 - q;
+            rv[q] = k >= 0 ? coef[((size_t)k * J + j) * 4 + 1] : 0.0;
+            yv[q] = k >= 0 ? load_y(jb, j, k) : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+            const int k = k0 - q;
+            if (k < 0) break;
+            double *c = coef + ((size_t)k * J + j) * 4;
+            const double s = (rv[q] - fup[k] * s_next) * fip[k];
+            const double yk = yv[q];
+            const double D = y_next - yk;
+            const double hk = h[k];
+            const double2 c01 = make_double2(yk, hk * s);
+            const double2 c23 = make_double2(3.0 * D - hk * (2.0 * s + s_next),
+                                             hk * (s + s_next) - 2.0 * D);
+            reinterpret_cast<double2 *>(c)[0] = c01;
+            reinterpret_cast<double2 *>(c)[1] = c23;
+            s_next = s;
+            y_next = yk;
+        }
     }
     if (!finite) atomicOr(err, ERRBIT_NONFINITE);
 }
 
-cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks, unsigned *err,
-                         cudaStream_t st)
+cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks, int max_knots,
+                         unsigned *err, cudaStream_t st)
 {
+    const int smem_bytes = 5 * max_knots * (int)sizeof(double);
+    if (smem_bytes > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem_bytes);
+        if (e != cudaSuccess) return e;
+    }
     if (total_blocks <= 0) return cudaSuccess;
-    k_build<<<total_blocks, kBuildThreads, 0, st>>>(jobs_dev, n_jobs, err);
+    k_build<<<total_blocks, kBuildThreads, smem_bytes, st>>>(jobs_dev, n_jobs, err);
     return cudaGetLastError();
 }
 

@@ -34,6 +34,11 @@ namespace fewsum {
 
 namespace {
 
+#ifndef FEWSUM_SLOT_UNROLL
+#define FEWSUM_SLOT_UNROLL 2
+#endif
+constexpr int kSlotUnroll = FEWSUM_SLOT_UNROLL;  // slots per iteration of the Horner chain loop
+
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per bounded wait
 constexpr int kWaitMaxIters = 1 << 26;
 constexpr int kBulkChunk = 32768;
@@ -165,16 +170,43 @@ template <> struct Cf<double> {
 __device__ __forceinline__ void sincospi_t(double x, double *s, double *c) { sincospi(x, s, c); }
 __device__ __forceinline__ void sincospi_t(float x, float *s, float *c) { sincospif(x, s, c); }
 
+#ifndef FEWSUM_STAGE_MAJOR
+#define FEWSUM_STAGE_MAJOR 0
+#endif
+
 // acc <- acc * z + K(u) along n consecutive slots (Horner in z = (zr, zi)).
 template <typename T, int R>
 __device__ __forceinline__ void horner_chain(const T *__restrict__ cf, int n, const T (&u)[R],
                                              const T (&zr)[R], const T (&zi)[R], T (&ar)[R],
                                              T (&ai)[R])
 {
-#pragma unroll 2
+#pragma unroll (kSlotUnroll)
     for (int k = 0; k < n; ++k) {
         T c[8];
         Cf<T>::load(cf + 8 * k, c);
+#if FEWSUM_STAGE_MAJOR
+        // one coefficient feeds R consecutive FMAs (operand reuse across samples)
+        T kr[R], ki[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) kr[r] = fma(c[3], u[r], c[2]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) ki[r] = fma(c[7], u[r], c[6]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) kr[r] = fma(kr[r], u[r], c[1]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) ki[r] = fma(ki[r], u[r], c[5]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) kr[r] = fma(kr[r], u[r], c[0]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) ki[r] = fma(ki[r], u[r], c[4]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const T nr = fma(ar[r], zr[r], fma(-ai[r], zi[r], kr[r]));
+            const T ni = fma(ar[r], zi[r], fma(ai[r], zr[r], ki[r]));
+            ar[r] = nr;
+            ai[r] = ni;
+        }
+#else
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const T kr = fma(fma(fma(c[3], u[r], c[2]), u[r], c[1]), u[r], c[0]);
@@ -184,86 +216,212 @@ __device__ __forceinline__ void horner_chain(const T *__restrict__ cf, int n, co
             ar[r] = nr;
             ai[r] = ni;
         }
+#endif
     }
 }
 
+// One pass of the scalar path: R consecutive samples per thread, one value per register.
 template <typename T, int R>
-__device__ __forceinline__ void sum_pass(const WaveDev &W, const T *__restrict__ cf, int p0,
-                                         int i1, const SegPhase &sp)
-{
-    const int tid = threadIdx.x;
-    const int base = p0 + tid * R;
-    T u[R], zr[R], zi[R], fr[R], fi[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int i = min(base + r, i1 - 1);
-        double fphi, frr, ud;
-        sample_phase(sp, W.t0, W.dt, i, fphi, frr, ud);
-        T sp_, cp, sr, cr;
-        sincospi_t((T)(2.0 * fphi), &sp_, &cp);
-        sincospi_t((T)(2.0 * frr), &sr, &cr);
-        u[r] = (T)ud;
-        fr[r] = cp;   // z_phi = e^{-i 2 pi f_phi}
-        fi[r] = -sp_;
-        zr[r] = cr;   // z_r = e^{-i 2 pi f_r}
-        zi[r] = -sr;
-    }
-    T tpr[R], tpi[R], tnr[R], tni[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) tpr[r] = tpi[r] = tnr[r] = tni[r] = (T)0;
-    T nzi[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) nzi[r] = -zi[r];
+struct ScalarPass {
+    static constexpr int kSamples = R;
+    static constexpr int kSlotBytes = 8 * (int)sizeof(T);
 
-    const int2 *__restrict__ rows = W.tr.rows;
-    const int nrp = W.tr.n_rows_pos, nrows = nrp + W.tr.n_rows_neg;
-    int slot = 0;
-    for (int row = 0; row < nrows; ++row) {
-        const int2 rw = __ldg(rows + row);
-        T ar[R], ai[R], br[R], bi[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) ar[r] = ai[r] = br[r] = bi[r] = (T)0;
-        horner_chain<T, R>(cf + 8 * slot, rw.x, u, zr, zi, ar, ai);
-        slot += rw.x;
-        horner_chain<T, R>(cf + 8 * slot, rw.y, u, zr, nzi, br, bi);
-        slot += rw.y;
-        const bool pos = row < nrp;
+    __device__ __forceinline__ static void run(const WaveDev &W, const unsigned char *buf, int p0,
+                                               int i1, const SegPhase &sp)
+    {
+        const T *__restrict__ cf = reinterpret_cast<const T *>(buf);
+        const int tid = threadIdx.x;
+        const int base = p0 + tid * R;
+        T u[R], zr[R], zi[R], fr[R], fi[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            // row value: a + conj(z_r) * b
-            const T vr = ar[r] + fma(br[r], zr[r], bi[r] * zi[r]);
-            const T vi = ai[r] + fma(bi[r], zr[r], -br[r] * zi[r]);
-            // T+ <- T+ z_phi + v   (m >= 0 rows),  T- <- T- conj(z_phi) + v   (m < 0 rows)
-            if (pos) {
-                const T nr = fma(tpr[r], fr[r], fma(-tpi[r], fi[r], vr));
-                const T ni = fma(tpr[r], fi[r], fma(tpi[r], fr[r], vi));
-                tpr[r] = nr;
-                tpi[r] = ni;
-            } else {
-                const T nr = fma(tnr[r], fr[r], fma(tni[r], fi[r], vr));
-                const T ni = fma(tni[r], fr[r], fma(-tnr[r], fi[r], vi));
-                tnr[r] = nr;
-                tni[r] = ni;
+            const int i = min(base + r, i1 - 1);
+            double fphi, frr, ud;
+            sample_phase(sp, W.t0, W.dt, i, fphi, frr, ud);
+            T sp_, cp, sr, cr;
+            sincospi_t((T)(2.0 * fphi), &sp_, &cp);
+            sincospi_t((T)(2.0 * frr), &sr, &cr);
+            u[r] = (T)ud;
+            fr[r] = cp;   // z_phi = e^{-i 2 pi f_phi}
+            fi[r] = -sp_;
+            zr[r] = cr;   // z_r = e^{-i 2 pi f_r}
+            zi[r] = -sr;
+        }
+        T tpr[R], tpi[R], tnr[R], tni[R], nzi[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            tpr[r] = tpi[r] = tnr[r] = tni[r] = (T)0;
+            nzi[r] = -zi[r];
+        }
+        const int2 *__restrict__ rows = W.tr.rows;
+        const int nrp = W.tr.n_rows_pos, nrows = nrp + W.tr.n_rows_neg;
+        int slot = 0;
+        for (int row = 0; row < nrows; ++row) {
+            const int2 rw = __ldg(rows + row);
+            T ar[R], ai[R], br[R], bi[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) ar[r] = ai[r] = br[r] = bi[r] = (T)0;
+            horner_chain<T, R>(cf + 8 * slot, rw.x, u, zr, zi, ar, ai);
+            slot += rw.x;
+            horner_chain<T, R>(cf + 8 * slot, rw.y, u, zr, nzi, br, bi);
+            slot += rw.y;
+            const bool pos = row < nrp;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                // row value: a + conj(z_r) * b
+                const T vr = fma(br[r], zr[r], fma(bi[r], zi[r], ar[r]));
+                const T vi = fma(bi[r], zr[r], fma(br[r], nzi[r], ai[r]));
+                // T+ <- T+ z_phi + v  (m >= 0 rows),  T- <- T- conj(z_phi) + v  (m < 0 rows)
+                if (pos) {
+                    const T nr = fma(tpr[r], fr[r], fma(tpi[r], -fi[r], vr));
+                    const T ni = fma(tpr[r], fi[r], fma(tpi[r], fr[r], vi));
+                    tpr[r] = nr;
+                    tpi[r] = ni;
+                } else {
+                    const T nr = fma(tnr[r], fr[r], fma(tni[r], fi[r], vr));
+                    const T ni = fma(tni[r], fr[r], fma(tnr[r], -fi[r], vi));
+                    tnr[r] = nr;
+                    tni[r] = ni;
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = base + r;
+            if (i >= i1) break;
+            // h = T+ + conj(z_phi) T-
+            const T hr = fma(tnr[r], fr[r], fma(tni[r], fi[r], tpr[r]));
+            const T hi = fma(tni[r], fr[r], fma(tnr[r], -fi[r], tpi[r]));
+            if (W.out_c64)
+                reinterpret_cast<float2 *>(W.out)[i] = make_float2((float)hr, (float)hi);
+            else
+                reinterpret_cast<double2 *>(W.out)[i] = make_double2((double)hr, (double)hi);
+        }
+    }
+};
+
+// Packed FP32x2 path: the thread's 2P samples are held as P pairs, and every multiply-add of the
+// Horner scheme runs on a pair with one packed FMA (__ffma2_rn), halving the instructions
+// issued per FMA.  Each lane of a packed FMA is an IEEE fma, and the operation order equals the
+// scalar path's, so both paths give bit-identical results.  The folded table stores every
+// coefficient twice, (c, c), so a pair operand is one 64-bit shared-memory read.
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+template <int P>
+__device__ __forceinline__ void horner_chain_pk(const float4 *__restrict__ cf, int n,
+                                                const float2 (&U)[P], const float2 (&ZR)[P],
+                                                const float2 (&ZIe)[P], const float2 (&NZIe)[P],
+                                                float2 (&AR)[P], float2 (&AI)[P])
+{
+#pragma unroll (kSlotUnroll)
+    for (int k = 0; k < n; ++k) {
+        const float4 a = cf[4 * k], b = cf[4 * k + 1], c = cf[4 * k + 2], d = cf[4 * k + 3];
+        const float2 c0r = make_float2(a.x, a.y), c1r = make_float2(a.z, a.w);
+        const float2 c2r = make_float2(b.x, b.y), c3r = make_float2(b.z, b.w);
+        const float2 c0i = make_float2(c.x, c.y), c1i = make_float2(c.z, c.w);
+        const float2 c2i = make_float2(d.x, d.y), c3i = make_float2(d.z, d.w);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const float2 kr = f2fma(f2fma(f2fma(c3r, U[p], c2r), U[p], c1r), U[p], c0r);
+            const float2 ki = f2fma(f2fma(f2fma(c3i, U[p], c2i), U[p], c1i), U[p], c0i);
+            const float2 nr = f2fma(AR[p], ZR[p], f2fma(AI[p], NZIe[p], kr));
+            const float2 ni = f2fma(AR[p], ZIe[p], f2fma(AI[p], ZR[p], ki));
+            AR[p] = nr;
+            AI[p] = ni;
+        }
+    }
+}
+
+template <int P>
+struct PackedPass {
+    static constexpr int kSamples = 2 * P;
+    static constexpr int kSlotBytes = 64;
+
+    __device__ __forceinline__ static void run(const WaveDev &W, const unsigned char *buf, int p0,
+                                               int i1, const SegPhase &sp)
+    {
+        const float4 *__restrict__ cf = reinterpret_cast<const float4 *>(buf);
+        const int tid = threadIdx.x;
+        const int base = p0 + tid * 2 * P;
+        float2 U[P], ZR[P], ZI[P], NZI[P], FR[P], FI[P], NFI[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            float uu[2], cpp[2], spp[2], crr[2], srr[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int i = min(base + 2 * p + e, i1 - 1);
+                double fphi, frr, ud;
+                sample_phase(sp, W.t0, W.dt, i, fphi, frr, ud);
+                sincospif((float)(2.0 * fphi), &spp[e], &cpp[e]);
+                sincospif((float)(2.0 * frr), &srr[e], &crr[e]);
+                uu[e] = (float)ud;
+            }
+            U[p] = make_float2(uu[0], uu[1]);
+            FR[p] = make_float2(cpp[0], cpp[1]);
+            FI[p] = make_float2(-spp[0], -spp[1]);
+            NFI[p] = make_float2(spp[0], spp[1]);
+            ZR[p] = make_float2(crr[0], crr[1]);
+            ZI[p] = make_float2(-srr[0], -srr[1]);
+            NZI[p] = make_float2(srr[0], srr[1]);
+        }
+        float2 TPR[P], TPI[P], TNR[P], TNI[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) TPR[p] = TPI[p] = TNR[p] = TNI[p] = make_float2(0.f, 0.f);
+        const int2 *__restrict__ rows = W.tr.rows;
+        const int nrp = W.tr.n_rows_pos, nrows = nrp + W.tr.n_rows_neg;
+        int slot = 0;
+        for (int row = 0; row < nrows; ++row) {
+            const int2 rw = __ldg(rows + row);
+            float2 AR[P], AI[P], BR[P], BI[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) AR[p] = AI[p] = BR[p] = BI[p] = make_float2(0.f, 0.f);
+            // n >= 0 half: Horner in z_r;  n < 0 half: Horner in conj(z_r)
+            horner_chain_pk<P>(cf + 4 * slot, rw.x, U, ZR, ZI, NZI, AR, AI);
+            slot += rw.x;
+            horner_chain_pk<P>(cf + 4 * slot, rw.y, U, ZR, NZI, ZI, BR, BI);
+            slot += rw.y;
+            const bool pos = row < nrp;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const float2 vr = f2fma(BR[p], ZR[p], f2fma(BI[p], ZI[p], AR[p]));
+                const float2 vi = f2fma(BI[p], ZR[p], f2fma(BR[p], NZI[p], AI[p]));
+                if (pos) {
+                    const float2 nr = f2fma(TPR[p], FR[p], f2fma(TPI[p], NFI[p], vr));
+                    const float2 ni = f2fma(TPR[p], FI[p], f2fma(TPI[p], FR[p], vi));
+                    TPR[p] = nr;
+                    TPI[p] = ni;
+                } else {
+                    const float2 nr = f2fma(TNR[p], FR[p], f2fma(TNI[p], FI[p], vr));
+                    const float2 ni = f2fma(TNI[p], FR[p], f2fma(TNR[p], NFI[p], vi));
+                    TNR[p] = nr;
+                    TNI[p] = ni;
+                }
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const float2 hr = f2fma(TNR[p], FR[p], f2fma(TNI[p], FI[p], TPR[p]));
+            const float2 hi = f2fma(TNI[p], FR[p], f2fma(TNR[p], NFI[p], TPI[p]));
+            const float h_r[2] = {hr.x, hr.y}, h_i[2] = {hi.x, hi.y};
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int i = base + 2 * p + e;
+                if (i < i1) {
+                    if (W.out_c64)
+                        reinterpret_cast<float2 *>(W.out)[i] = make_float2(h_r[e], h_i[e]);
+                    else
+                        reinterpret_cast<double2 *>(W.out)[i] =
+                            make_double2((double)h_r[e], (double)h_i[e]);
+                }
             }
         }
     }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int i = base + r;
-        if (i >= i1) break;
-        // h = T+ + conj(z_phi) T-
-        const T hr = tpr[r] + fma(tnr[r], fr[r], tni[r] * fi[r]);
-        const T hi = tpi[r] + fma(tni[r], fr[r], -tnr[r] * fi[r]);
-        if (W.out_c64)
-            reinterpret_cast<float2 *>(W.out)[i] = make_float2((float)hr, (float)hi);
-        else
-            reinterpret_cast<double2 *>(W.out)[i] = make_double2((double)hr, (double)hi);
-    }
-}
+};
 
 }  // namespace
 
-template <typename T, int R>
+template <typename V>
 __global__ void __launch_bounds__(256) k_sum(const PlanHdr *__restrict__ hp)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -271,13 +429,12 @@ __global__ void __launch_bounds__(256) k_sum(const PlanHdr *__restrict__ hp)
     __shared__ int s_abort;
     const PlanHdr h = *hp;
     const int tid = threadIdx.x;
-    const int U = blockDim.x * R;
+    const int U = blockDim.x * V::kSamples;
     const CtaStart beg = h.cta[blockIdx.x];
     const CtaStart end = h.cta[blockIdx.x + 1];
     int w = beg.wave, i = beg.sample;
     if (!normalize(h, w, i, end)) return;  // uniform across the CTA
 
-    const int elem = (int)sizeof(T);
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -292,7 +449,7 @@ __global__ void __launch_bounds__(256) k_sum(const PlanHdr *__restrict__ hp)
     bool prod_more = true;
     auto issue = [&](const Piece &p, int b) {
         const WaveDev &P = h.waves[p.w];
-        const uint32_t bytes = (uint32_t)P.tr.n_slots * 8u * (uint32_t)elem;
+        const uint32_t bytes = (uint32_t)P.tr.n_slots * (uint32_t)V::kSlotBytes;
         const unsigned char *src =
             reinterpret_cast<const unsigned char *>(P.fcoef) + (size_t)p.s * bytes;
         unsigned char *dst = smem + (size_t)b * h.buf_bytes;
@@ -327,12 +484,12 @@ __global__ void __launch_bounds__(256) k_sum(const PlanHdr *__restrict__ hp)
         if (s_abort) break;
 
         const WaveDev &W = h.waves[cur.w];
-        const T *cf = reinterpret_cast<const T *>(smem + (size_t)b * h.buf_bytes);
+        const unsigned char *buf = smem + (size_t)b * h.buf_bytes;
         const SegPhase sp = seg_phase(W.tr, cur.s, W.dphi_phi, W.dphi_r);
-        const int warp_first = (tid & ~31) * R;
+        const int warp_first = (tid & ~31) * V::kSamples;
         for (int p0 = cur.i0; p0 < cur.i1; p0 += U) {
             if (p0 + warp_first >= cur.i1) continue;  // whole warp past the end: idle
-            sum_pass<T, R>(W, cf, p0, cur.i1, sp);
+            V::run(W, buf, p0, cur.i1, sp);
         }
 
         int nw = cur.w, ni = cur.i1;
@@ -383,20 +540,31 @@ cudaError_t launch_phases(const TrajDev &tr, const int *seg_start, double t0, do
 }
 
 namespace {
-template <typename T, int R>
+template <typename V>
 cudaError_t configure_one(int max_dyn)
 {
-    return cudaFuncSetAttribute(k_sum<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
+    return cudaFuncSetAttribute(k_sum<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
 }
-template <typename T, int R>
+template <typename V>
 int occupancy_one(int threads, int smem)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sum<T, R>, threads, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sum<V>, threads, smem) != cudaSuccess)
         return 0;
     return n;
 }
+template <typename V>
+cudaError_t launch_one(const PlanHdr *hdr, int grid, int threads, int smem, cudaStream_t st)
+{
+    k_sum<V><<<grid, threads, smem, st>>>(hdr);
+    return cudaGetLastError();
+}
 }  // namespace
+
+int sum_slot_bytes(int variant)
+{
+    return variant == kVariantFp64 ? 64 : (variant == kVariantPacked ? 64 : 32);
+}
 
 cudaError_t sum_configure()
 {
@@ -406,42 +574,48 @@ cudaError_t sum_configure()
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     const int max_dyn = optin - 1024;  // leaves room for the static mbarriers and flag
-    if ((e = configure_one<double, 1>(max_dyn)) != cudaSuccess) return e;
-    if ((e = configure_one<double, 2>(max_dyn)) != cudaSuccess) return e;
-    if ((e = configure_one<float, 2>(max_dyn)) != cudaSuccess) return e;
-    if ((e = configure_one<float, 4>(max_dyn)) != cudaSuccess) return e;
-    if ((e = configure_one<float, 8>(max_dyn)) != cudaSuccess) return e;
+    if ((e = configure_one<ScalarPass<double, 1>>(max_dyn)) != cudaSuccess) return e;
+    if ((e = configure_one<ScalarPass<double, 2>>(max_dyn)) != cudaSuccess) return e;
+    if ((e = configure_one<ScalarPass<float, 2>>(max_dyn)) != cudaSuccess) return e;
+    if ((e = configure_one<ScalarPass<float, 4>>(max_dyn)) != cudaSuccess) return e;
+    if ((e = configure_one<ScalarPass<float, 8>>(max_dyn)) != cudaSuccess) return e;
+    if ((e = configure_one<PackedPass<2>>(max_dyn)) != cudaSuccess) return e;
+    if ((e = configure_one<PackedPass<4>>(max_dyn)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
-int sum_occupancy(bool fp64, int R, int threads, int smem)
+int sum_occupancy(int variant, int R, int threads, int smem)
 {
-    if (fp64) {
-        if (R == 1) return occupancy_one<double, 1>(threads, smem);
-        if (R == 2) return occupancy_one<double, 2>(threads, smem);
-        return 0;
+    if (variant == kVariantFp64) {
+        if (R == 1) return occupancy_one<ScalarPass<double, 1>>(threads, smem);
+        if (R == 2) return occupancy_one<ScalarPass<double, 2>>(threads, smem);
+    } else if (variant == kVariantScalar) {
+        if (R == 2) return occupancy_one<ScalarPass<float, 2>>(threads, smem);
+        if (R == 4) return occupancy_one<ScalarPass<float, 4>>(threads, smem);
+        if (R == 8) return occupancy_one<ScalarPass<float, 8>>(threads, smem);
+    } else if (variant == kVariantPacked) {
+        if (R == 4) return occupancy_one<PackedPass<2>>(threads, smem);
+        if (R == 8) return occupancy_one<PackedPass<4>>(threads, smem);
     }
-    if (R == 2) return occupancy_one<float, 2>(threads, smem);
-    if (R == 4) return occupancy_one<float, 4>(threads, smem);
-    if (R == 8) return occupancy_one<float, 8>(threads, smem);
     return 0;
 }
 
-cudaError_t launch_sum(const PlanHdr *hdr_dev, int grid, int threads, int R, int smem, bool fp64,
+cudaError_t launch_sum(const PlanHdr *hdr_dev, int grid, int threads, int R, int smem, int variant,
                        cudaStream_t st)
 {
     if (grid <= 0) return cudaSuccess;
-    if (fp64) {
-        if (R == 1) k_sum<double, 1><<<grid, threads, smem, st>>>(hdr_dev);
-        else if (R == 2) k_sum<double, 2><<<grid, threads, smem, st>>>(hdr_dev);
-        else return cudaErrorInvalidValue;
-    } else {
-        if (R == 2) k_sum<float, 2><<<grid, threads, smem, st>>>(hdr_dev);
-        else if (R == 4) k_sum<float, 4><<<grid, threads, smem, st>>>(hdr_dev);
-        else if (R == 8) k_sum<float, 8><<<grid, threads, smem, st>>>(hdr_dev);
-        else return cudaErrorInvalidValue;
+    if (variant == kVariantFp64) {
+        if (R == 1) return launch_one<ScalarPass<double, 1>>(hdr_dev, grid, threads, smem, st);
+        if (R == 2) return launch_one<ScalarPass<double, 2>>(hdr_dev, grid, threads, smem, st);
+    } else if (variant == kVariantScalar) {
+        if (R == 2) return launch_one<ScalarPass<float, 2>>(hdr_dev, grid, threads, smem, st);
+        if (R == 4) return launch_one<ScalarPass<float, 4>>(hdr_dev, grid, threads, smem, st);
+        if (R == 8) return launch_one<ScalarPass<float, 8>>(hdr_dev, grid, threads, smem, st);
+    } else if (variant == kVariantPacked) {
+        if (R == 4) return launch_one<PackedPass<2>>(hdr_dev, grid, threads, smem, st);
+        if (R == 8) return launch_one<PackedPass<4>>(hdr_dev, grid, threads, smem, st);
     }
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace fewsum
