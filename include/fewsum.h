@@ -228,7 +228,8 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
 /* Run a planned batch on `stream` (graph launch or direct launches). Asynchronous. */
 few_status few_batch_run(few_ctx *ctx, few_batch *batch, void *stream);
 
-/* Release a batch plan (after the device is idle on its work). */
+/* Release a batch plan.  The caller must make sure every run of the batch has completed (an
+ * event or stream synchronisation); this call does not wait for the device. */
 few_status few_batch_release(few_ctx *ctx, few_batch *batch);
 
 /*

@@ -968,7 +968,8 @@ few_status few_batch_release(few_ctx *ctx, few_batch *b)
     if (!ctx || !b || b->ctx != ctx) return FEW_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     cudaSetDevice(ctx->device);
-    cudaDeviceSynchronize();
+    // The caller guarantees the batch's work has completed (an event, a stream sync); no device
+    // synchronisation here, so other work in flight keeps running.
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     dev_free(ctx, b->jobs_dev, ctx->internal);

@@ -1,0 +1,306 @@
+"""Serving loop: continuous batching of waveform requests with HBM-budget admission.
+
+Requests arrive as an MCMC sampler emits them (different durations, cadences, mode counts,
+angles and phase offsets of resident trajectories).  The server
+
+* keeps trajectory splines resident on the device (registered once per trajectory key);
+* admits queued requests in arrival order while their device memory (output + plan scratch)
+  fits the HBM budget and a launch slot is free -- requests that arrive while others run are
+  admitted as soon as slots and memory free up;
+* launches each admitted group as one batched persistent summation (one plan, one launch
+  sequence) on one of several worker streams, so the work of successive groups overlaps on the
+  device;
+* resolves each request's Future when its group's completion event fires, releases its memory
+  and records submit-to-result latency (p50/p99) and throughput.
+
+Each result is bit-identical to the same request run alone: every sample is summed by one thread
+in an order fixed by the request's own mode table, whatever else shares the launch.
+
+The execution engine is pluggable: `GpuEngine` drives libfewsum.so; tests of the host logic
+(admission, batching, faults) use a fake engine on the CPU.  Fault injection is host-side only
+(`FaultInjector`): forced admission rejection, forced allocation failure, and cancellation.
+"""
+from __future__ import annotations
+
+import collections
+import concurrent.futures as cf
+import dataclasses
+import threading
+import time
+from typing import Any, Callable, Deque, Dict, List, Optional
+
+from . import fewsum as F
+
+
+class AdmissionError(RuntimeError):
+    """The request can never fit the budget, or admission was refused."""
+
+
+@dataclasses.dataclass
+class Request:
+    traj_key: Any
+    n_samples: int
+    dt: float
+    t0: float = 0.0
+    theta: float = 0.0
+    phi: float = 0.0
+    scale: float = 1.0
+    dphi_phi0: float = 0.0
+    dphi_r0: float = 0.0
+    prec: int = F.FEW_MIXED
+    out_c64: Optional[bool] = None
+
+    def c64(self) -> bool:
+        return self.prec == F.FEW_MIXED if self.out_c64 is None else bool(self.out_c64)
+
+    def out_bytes(self) -> int:
+        return self.n_samples * (8 if self.c64() else 16)
+
+
+@dataclasses.dataclass
+class FaultInjector:
+    """Host-side faults for tests: each hook gets the request and returns True to fire."""
+    reject_admission: Callable[[Request], bool] = lambda r: False
+    fail_allocation: Callable[[Request], bool] = lambda r: False
+
+
+@dataclasses.dataclass
+class _Job:
+    req: Request
+    fut: cf.Future
+    t_submit: float
+    need: int = 0
+    out: Any = None
+
+
+class Server:
+    def __init__(self, engine, hbm_budget_bytes: int, max_batch: int = 32, max_inflight: int = 3,
+                 faults: Optional[FaultInjector] = None):
+        self.engine = engine
+        self.budget = int(hbm_budget_bytes)
+        self.max_batch = int(max_batch)
+        self.max_inflight = int(max_inflight)
+        self.faults = faults or FaultInjector()
+        self._q: Deque[_Job] = collections.deque()
+        self._inflight: Deque[tuple] = collections.deque()  # (handle, [jobs], bytes)
+        self._in_use = 0
+        self._pending = 0  # submitted jobs whose future is not settled yet
+        self._cv = threading.Condition()
+        self._stop = False
+        self.latencies: List[float] = []
+        self.completed = 0
+        self.failed = 0
+        self.max_seen_inflight = 0
+        self.max_seen_bytes = 0
+        self.t_first = None
+        self.t_last = None
+        self._sched = threading.Thread(target=self._schedule_loop, name="fewsum-sched", daemon=True)
+        self._done = threading.Thread(target=self._complete_loop, name="fewsum-done", daemon=True)
+        self._sched.start()
+        self._done.start()
+
+    # ------------------------------------------------------------------ API
+    def submit(self, req: Request) -> cf.Future:
+        fut: cf.Future = cf.Future()
+        need = req.out_bytes() + self.engine.scratch_bytes(req)
+        if need > self.budget:
+            fut.set_exception(AdmissionError(f"request needs {need} bytes > budget {self.budget}"))
+            return fut
+        job = _Job(req, fut, time.perf_counter(), need)
+        with self._cv:
+            if self._stop:
+                raise RuntimeError("server closed")
+            self._q.append(job)
+            self._pending += 1
+            self._cv.notify_all()
+        return fut
+
+    def drain(self, timeout: Optional[float] = None) -> bool:
+        """Wait until the queue is empty and nothing is in flight."""
+        t_end = None if timeout is None else time.perf_counter() + timeout
+        with self._cv:
+            while self._pending > 0:
+                rem = None if t_end is None else t_end - time.perf_counter()
+                if rem is not None and rem <= 0:
+                    return False
+                self._cv.wait(0.05 if rem is None else min(rem, 0.05))
+        return True
+
+    def close(self) -> None:
+        self.drain()
+        with self._cv:
+            self._stop = True
+            self._cv.notify_all()
+        self._sched.join()
+        self._done.join()
+
+    def stats(self) -> Dict[str, float]:
+        lat = sorted(self.latencies)
+
+        def pct(p):
+            if not lat:
+                return float("nan")
+            k = min(len(lat) - 1, max(0, int(round(p / 100.0 * (len(lat) - 1)))))
+            return lat[k]
+        span = (self.t_last - self.t_first) if (self.t_first and self.t_last) else float("nan")
+        return {"completed": self.completed, "failed": self.failed,
+                "p50_ms": 1e3 * pct(50), "p99_ms": 1e3 * pct(99),
+                "mean_ms": 1e3 * (sum(lat) / len(lat)) if lat else float("nan"),
+                "waveforms_per_s": self.completed / span if span and span > 0 else float("nan"),
+                "max_inflight_batches": self.max_seen_inflight,
+                "max_bytes_in_use": self.max_seen_bytes}
+
+    # ------------------------------------------------------------------ internals
+    def _admit(self) -> List[_Job]:
+        """Pop the longest FIFO prefix (same precision) that fits memory and the batch size."""
+        group: List[_Job] = []
+        while self._q and len(group) < self.max_batch:
+            job = self._q[0]
+            if job.fut.cancelled():
+                self._q.popleft()
+                self._pending -= 1
+                self._cv.notify_all()
+                continue
+            if group and job.req.prec != group[0].req.prec:
+                break
+            if self._in_use + job.need > self.budget:
+                break  # head of line waits for memory
+            self._q.popleft()
+            if self.faults.reject_admission(job.req):
+                self.failed += 1
+                self._pending -= 1
+                job.fut.set_exception(AdmissionError("admission refused"))
+                self._cv.notify_all()
+                continue
+            if not job.fut.set_running_or_notify_cancel():
+                self._pending -= 1
+                self._cv.notify_all()
+                continue
+            self._in_use += job.need
+            group.append(job)
+        self.max_seen_bytes = max(self.max_seen_bytes, self._in_use)
+        return group
+
+    def _schedule_loop(self) -> None:
+        while True:
+            with self._cv:
+                while not self._stop and (not self._q or len(self._inflight) >= self.max_inflight):
+                    self._cv.wait(0.05)
+                if self._stop and not self._q:
+                    return
+                group = self._admit()
+            if not group:
+                with self._cv:
+                    self._cv.wait(0.001)
+                continue
+            ok: List[_Job] = []
+            for job in group:
+                try:
+                    if self.faults.fail_allocation(job.req):
+                        raise MemoryError("allocation failed (injected)")
+                    job.out = self.engine.alloc_out(job.req)
+                    ok.append(job)
+                except Exception as e:  # noqa: BLE001 -- reported through the future
+                    self._finish(job, error=e)
+            if not ok:
+                continue
+            try:
+                handle = self.engine.launch([j.req for j in ok], [j.out for j in ok])
+            except Exception as e:  # noqa: BLE001
+                for job in ok:
+                    self._finish(job, error=e)
+                continue
+            with self._cv:
+                if self.t_first is None:
+                    self.t_first = min(j.t_submit for j in ok)
+                self._inflight.append((handle, ok))
+                self.max_seen_inflight = max(self.max_seen_inflight, len(self._inflight))
+                self._cv.notify_all()
+
+    def _complete_loop(self) -> None:
+        while True:
+            with self._cv:
+                while not self._inflight and not (self._stop and not self._q):
+                    self._cv.wait(0.05)
+                if not self._inflight:
+                    if self._stop and not self._q:
+                        return
+                    continue
+                handle, jobs = self._inflight[0]
+            err = None
+            try:
+                self.engine.wait(handle)
+            except Exception as e:  # noqa: BLE001
+                err = e
+            self.engine.release(handle)
+            now = time.perf_counter()
+            with self._cv:
+                self._inflight.popleft()
+                for job in jobs:
+                    self._finish_locked(job, now, err)
+                self.t_last = now
+                self._cv.notify_all()
+
+    def _finish(self, job: _Job, error=None) -> None:
+        with self._cv:
+            self._finish_locked(job, time.perf_counter(), error)
+            self._cv.notify_all()
+
+    def _finish_locked(self, job: _Job, now: float, error) -> None:
+        self._in_use -= job.need
+        self._pending -= 1
+        if error is not None:
+            self.failed += 1
+            if not job.fut.done():
+                job.fut.set_exception(error)
+            return
+        self.completed += 1
+        self.latencies.append(now - job.t_submit)
+        if not job.fut.done():
+            job.fut.set_result(job.out)
+
+
+class GpuEngine:
+    """Executes request groups with libfewsum.so: one batched plan per group, worker streams."""
+
+    def __init__(self, ctx, trajectories: Dict[Any, Any], n_streams: int = 3):
+        import torch
+        self.torch = torch
+        self.ctx = ctx
+        self.trajs = trajectories  # key -> runtime.Trajectory (spline data set)
+        self.streams = [torch.cuda.Stream(device=ctx.device) for _ in range(n_streams)]
+        self._next = 0
+
+    def scratch_bytes(self, req: Request) -> int:
+        tr = self.trajs[req.traj_key]
+        K, N, slots = tr.info
+        elem = 8 if req.prec == F.FEW_FP64 else 4
+        return (K - 1) * slots * 8 * elem + 64 * 1024
+
+    def alloc_out(self, req: Request):
+        torch = self.torch
+        dt = torch.complex64 if req.c64() else torch.complex128
+        s = self.streams[self._next % len(self.streams)]
+        with torch.cuda.stream(s):
+            return torch.empty(req.n_samples, dtype=dt, device=torch.device("cuda", self.ctx.device))
+
+    def launch(self, reqs: List[Request], outs: List[Any]):
+        torch = self.torch
+        s = self.streams[self._next % len(self.streams)]
+        self._next += 1
+        rq = [F.make_request(self.trajs[r.traj_key].handle, o.data_ptr(), r.n_samples, r.t0, r.dt,
+                             r.theta, r.phi, r.scale, r.prec, r.c64(), F.FEW_MEM_DEVICE,
+                             r.dphi_phi0, r.dphi_r0) for r, o in zip(reqs, outs)]
+        b = F.few_batch_plan(self.ctx.handle, rq, F.FEW_BATCH_NO_GRAPH)
+        F.few_batch_run(self.ctx.handle, b, int(s.cuda_stream))
+        ev = torch.cuda.Event()
+        ev.record(s)
+        return (b, ev)
+
+    def wait(self, handle) -> None:
+        b, ev = handle
+        ev.synchronize()
+
+    def release(self, handle) -> None:
+        b, ev = handle
+        F.few_batch_release(self.ctx.handle, b)

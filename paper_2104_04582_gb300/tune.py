@@ -1,0 +1,113 @@
+"""Autotuner for the summation kernel's tile shape.
+
+The summation kernel is tunable in three ways that change speed but never results (every sample
+is summed by one thread in a fixed order, so all choices are bit-identical):
+
+* samples per thread R (the segment tile: one pass covers threads x R consecutive samples),
+* threads per block (128 or 256),
+* the FMA instruction form of the mixed path (scalar FP32 or packed FP32x2).
+
+The mode tile is the per-segment harmonic slot table, staged whole in shared memory; its size is
+set by the mode set, and it decides occupancy together with R and the block size.
+
+`tune()` times every candidate on a representative workload with CUDA events (several runs,
+best of), picks the fastest, installs it in the context, and records it in a JSON cache keyed by
+(precision, slot-count bucket, samples bucket); `apply_cached()` installs a cached choice.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+from typing import Dict, List, Optional, Sequence, Tuple
+
+from . import fewsum as F
+
+CANDIDATES = {
+    F.FEW_FP64: [(1, 256, False), (2, 256, False), (1, 128, False), (2, 128, False)],
+    F.FEW_MIXED: [(r, t, p) for p in (False, True) for r in (2, 4, 8) for t in (128, 256)
+                  if not (p and r == 2)],
+}
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "fewsum_tiles.json")
+
+
+def bucket(prec: int, n_slots: int, n_samples: int) -> str:
+    """Cache key: precision, slots rounded to a power of two, samples to a power of four."""
+    sb = 1 << max(0, math.ceil(math.log2(max(1, n_slots))))
+    nb = 4 ** max(0, math.ceil(math.log(max(1, n_samples), 4)))
+    return f"{'fp64' if prec == F.FEW_FP64 else 'mixed'}:{sb}:{nb}"
+
+
+def _load(path: str) -> Dict[str, dict]:
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh)
+    return {}
+
+
+def _save(path: str, data: Dict[str, dict]) -> None:
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(data, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def install(ctx_handle: int, prec: int, choice: Tuple[int, int, bool]) -> None:
+    R, T, packed = choice
+    F.few_set_tiles(ctx_handle, prec, R, T)
+    if prec == F.FEW_MIXED:
+        F.few_set_packed(ctx_handle, packed)
+
+
+def tune(ctx_handle: int, run, prec: int, n_slots: int, n_samples: int, repeats: int = 3,
+         cache_path: Optional[str] = DEFAULT_CACHE,
+         candidates: Optional[Sequence[Tuple[int, int, bool]]] = None) -> Tuple[Tuple[int, int, bool], Dict[str, float]]:
+    """Time `run()` (which must queue one workload on the current stream) for every candidate.
+
+    Returns the best (R, threads, packed) and the per-candidate best time in ms; installs the
+    winner in the context and stores it in the cache (unless cache_path is None).
+    """
+    import torch
+    cands = list(candidates or CANDIDATES[prec])
+    times: Dict[str, float] = {}
+    best, best_ms = None, float("inf")
+    for c in cands:
+        try:
+            install(ctx_handle, prec, c)
+        except F.FewError:
+            continue
+        run()  # warm-up (plans, occupancy cache)
+        torch.cuda.synchronize()
+        ms = float("inf")
+        for _ in range(repeats):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            run()
+            b.record()
+            b.synchronize()
+            ms = min(ms, a.elapsed_time(b))
+        times[f"R={c[0]} T={c[1]} packed={int(c[2])}"] = ms
+        if ms < best_ms:
+            best, best_ms = c, ms
+    if best is None:
+        raise RuntimeError("no tile candidate ran")
+    install(ctx_handle, prec, best)
+    if cache_path:
+        data = _load(cache_path)
+        data[bucket(prec, n_slots, n_samples)] = {"R": best[0], "threads": best[1],
+                                                  "packed": bool(best[2]), "ms": best_ms}
+        _save(cache_path, data)
+    return best, times
+
+
+def apply_cached(ctx_handle: int, prec: int, n_slots: int, n_samples: int,
+                 cache_path: str = DEFAULT_CACHE) -> Optional[Tuple[int, int, bool]]:
+    """Install the cached choice for this bucket, if any; returns it."""
+    e = _load(cache_path).get(bucket(prec, n_slots, n_samples))
+    if not e:
+        return None
+    choice = (int(e["R"]), int(e["threads"]), bool(e["packed"]))
+    install(ctx_handle, prec, choice)
+    return choice
