@@ -39,9 +39,23 @@ METRIC = "1-yr waveforms/s (3843 modes, dt=10 s) at mismatch<=1e-6; mode-samples
 UNIT = "waveforms/s"
 WORKLOAD = ("1-yr waveform, dt=10 s (3,155,760 samples), K=100 knots, 3843 modes "
             "(l=2..10, m=0..l, n=-30..30), m<0 by symmetry")
+# DRAM bytes (read + write) of one summation launch on this workload, from the ncu capture
+# summarised in profiles/k_sum_mixed_1yr_3843modes.md; used only while the kernel source is the
+# one that was profiled (hash of sum.cu + phase_eval.cuh) and the tile is the profiled one.
+PROFILED_TRAFFIC = {"source_sha256_16": "f0db93fb52c9ad1d", "tile": (4, 256, False), "bytes": 4115200 + 1536}
 N_SMS = 152
 FP32_LANES_PER_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25
+
+
+def _kernel_source_hash() -> str:
+    import hashlib
+    d = os.path.join(ROOT, "paper_2104_04582_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("sum.cu", "phase_eval.cuh"):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def _peaks_file():
@@ -222,6 +236,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
 
     tr = RT.Trajectory(ctx, w.t_knots, w.modes)
     dev_in = tr.upload_inputs(w.phi_phi, w.phi_r, w.amp_re, w.amp_im)
+    tile = tuple(ctx.get_tiles(prec)) + (False,)
     out = RT.alloc_out(w.n_samples, c64, local_rank)
     req = RT.request(tr, out, w.n_samples, w.t0, w.dt, w.theta, w.phi, prec)
     flush = l2_flush_buffer(torch, dev)
@@ -324,6 +339,41 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                "timer": "host wall clock around the two C-ABI calls (the call with host output "
                         "returns after its device-to-host copy)"}
 
+    # batched path: B independent 1-yr 3843-mode waveforms (own trajectories) per step, one
+    # persistent summation launch, the whole sequence (spline rebuild included) as a CUDA graph
+    batched = None
+    if rank == 0 and args.batch > 1:
+        wb = [W.config2(W.SEEDS["C2"] + 1000 + q) for q in range(args.batch)]
+        trb = [RT.from_inputs(ctx, x) for x in wb]
+        outb = [RT.alloc_out(x.n_samples, c64, local_rank) for x in wb]
+        reqb = [RT.request(t_, o_, x.n_samples, x.t0, x.dt, x.theta, x.phi, prec)
+                for t_, o_, x in zip(trb, outb, wb)]
+        bh = F.few_batch_plan(ctx.handle, reqb, F.FEW_BATCH_REBUILD_SPLINES)
+        for _ in range(2):
+            F.few_batch_run(ctx.handle, bh, sh)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(max(3, min(args.steps, 10)))]
+        for a, b_ in evs:
+            flush.zero_()
+            a.record(stream)
+            F.few_batch_run(ctx.handle, bh, sh)
+            b_.record(stream)
+        torch.cuda.synchronize()
+        if ctx.sync_status() != F.FEW_OK:
+            raise RuntimeError("device error in the batched run")
+        msb = sum(a.elapsed_time(b_) for a, b_ in evs) / len(evs)
+        batched = {"waveforms_per_step": args.batch, "ms_per_step": msb,
+                   "value": args.batch * 1000.0 / msb, "unit": UNIT,
+                   "mode_samples_per_s": args.batch * w.N * w.n_samples / (msb * 1e-3),
+                   "launches_per_step": 4, "graph": True,
+                   "step": "spline rebuild of all trajectories + harmonics + fold + one "
+                           "persistent summation launch, replayed as one CUDA graph"}
+        F.few_batch_release(ctx.handle, bh)
+        for t_ in trb:
+            t_.release()
+        del outb
+
     # pipe peaks
     peaks = measure_peaks(local_rank) if rank == 0 and not args.no_probe else {}
 
@@ -332,7 +382,110 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     ctx.close()
     return dict(w=w, ms_local=ms_local, step_ms=step_ms, kernel_ms=kernel_ms, last_t=last_t,
                 clocks=clocks, plain=plain, e2e=e2e, peaks=peaks, slots=slots,
-                h_fast=h_fast, h_plain=h_plain, prec=prec)
+                h_fast=h_fast, h_plain=h_plain, prec=prec, batched=batched, tile=tile)
+
+
+def run_serving(args):
+    """Serving workload: Poisson MCMC-like stream at 50/90/120% of the measured capacity."""
+    import torch
+    from paper_2104_04582_gb300 import _build
+    from paper_2104_04582_gb300 import fewsum as F
+    from paper_2104_04582_gb300 import runtime as RT
+    from paper_2104_04582_gb300.serve import GpuEngine, Request, Server
+
+    _build.build()
+    torch.cuda.set_device(0)
+    n_req = args.serving_requests
+    trajs_in, stream = W.config4_stream(n_req, rate_hz=1.0)
+    ctx = RT.Context(0)
+    trajs = {k: RT.from_inputs(ctx, w) for k, w in trajs_in.items()}
+
+    def reqs_for(prec):
+        out = []
+        for r in stream:
+            w = trajs_in[r.traj_key]
+            out.append(Request(traj_key=r.traj_key, n_samples=w.n_samples, dt=w.dt, t0=w.t0,
+                               theta=r.theta, phi=r.phi, scale=r.scale, dphi_phi0=r.dphi_phi0,
+                               dphi_r0=r.dphi_r0, prec=prec))
+        return out
+
+    def run(reqs, rate_hz=None, seed=0):
+        srv = Server(GpuEngine(ctx, trajs), hbm_budget_bytes=int(args.serving_budget_gb * 2 ** 30),
+                     max_batch=16, max_inflight=3)
+        rng = np.random.default_rng(seed)
+        t0 = time.perf_counter()
+        t_arr = 0.0
+        futs = []
+        for r in reqs:
+            if rate_hz:
+                t_arr += float(rng.exponential(1.0 / rate_hz))
+                d = t_arr - (time.perf_counter() - t0)
+                if d > 0:
+                    time.sleep(d)
+            futs.append(srv.submit(r))
+        srv.drain()
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        for f in futs:
+            f.result()
+        st["wall_s"] = wall
+        st["offered_rate_hz"] = rate_hz
+        return st
+
+    mixed = reqs_for(F.FEW_MIXED)
+    run(mixed[:16])  # warm-up
+    burst = run(mixed)
+    cap = burst["completed"] / burst["wall_s"]
+    loads = {}
+    for f in (0.5, 0.9, 1.2):
+        loads[f"{int(f * 100)}%"] = run(mixed, rate_hz=f * cap, seed=int(f * 100))
+    plain = run(reqs_for(F.FEW_FP64)[:max(8, n_req // 10)])
+    torch.cuda.synchronize()
+    samples = [trajs_in[r.traj_key].n_samples for r in stream]
+    modes = [trajs_in[r.traj_key].N for r in stream]
+    line = {"mode": "serving", "metric": "waveforms/s and p50/p99 latency, Poisson MCMC-like stream",
+            "unit": "waveforms/s", "n_gpus": 1, "requests": n_req,
+            "config": {"workload": "requests of 0.5-4 yr, dt in {5,10,15} s, 10-1000 modes, "
+                                   "perturbed angles/phases/scale of resident trajectories, "
+                                   "10% new trajectories", "seed": W.SEEDS["C4"],
+                       "trajectories": len(trajs), "mean_samples": float(np.mean(samples)),
+                       "mean_modes": float(np.mean(modes)),
+                       "budget_gb": args.serving_budget_gb, "max_batch": 16, "max_inflight": 3},
+            "capacity_mixed": {"value": cap, "p50_ms": burst["p50_ms"], "p99_ms": burst["p99_ms"]},
+            "loads": {k: {"offered_hz": v["offered_rate_hz"], "waveforms_per_s": v["waveforms_per_s"],
+                          "p50_ms": v["p50_ms"], "p99_ms": v["p99_ms"],
+                          "max_inflight_batches": v["max_inflight_batches"]}
+                      for k, v in loads.items()},
+            "plain_fp64_capacity": {"value": plain["completed"] / plain["wall_s"],
+                                    "requests": plain["completed"]}}
+    line["capacity_vs_plain_fp64"] = cap / line["plain_fp64_capacity"]["value"]
+    for tr in trajs.values():
+        tr.release()
+    ctx.close()
+    print(json.dumps(line))
+    return 0
+
+
+def run_profile_case(which: str, repeats: int = 3) -> int:
+    """A short, untimed run of the benchmark workload for profiler captures: the one-year
+    3843-mode waveform computed `repeats` times (the first launch of each kernel is warm-up)."""
+    import torch
+    from paper_2104_04582_gb300 import _build
+    from paper_2104_04582_gb300 import fewsum as F
+    from paper_2104_04582_gb300 import runtime as RT
+    _build.build()
+    prec = F.FEW_FP64 if which == "fp64" else F.FEW_MIXED
+    w = W.config2()
+    with RT.Context(0) as ctx:
+        tr = RT.from_inputs(ctx, w)
+        for _ in range(repeats):
+            RT.waveform_inputs(ctx, tr, w, prec)
+        torch.cuda.synchronize()
+        st = ctx.sync_status()
+        tr.release()
+    print(json.dumps({"profile_case": which, "repeats": repeats, "status": int(st)}))
+    return 0 if st == F.FEW_OK else 1
 
 
 def main():
@@ -346,12 +499,26 @@ def main():
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--profile-case", choices=["mixed", "fp64"], default=None,
+                    help="untimed runs of the benchmark waveform for profiler captures")
+    ap.add_argument("--serving", action="store_true",
+                    help="run the serving workload instead of the single-waveform benchmark")
+    ap.add_argument("--serving-requests", type=int, default=200)
+    ap.add_argument("--serving-budget-gb", type=float, default=16.0)
+    ap.add_argument("--batch", type=int, default=8,
+                    help="waveforms per step of the batched-path measurement (0: skip)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.profile_case:
+        return run_profile_case(args.profile_case)
+
+    if args.serving and args.impl != "reference":
+        return run_serving(args) if rank == 0 else 0
 
     if args.impl == "reference":
         if rank != 0:
@@ -414,8 +581,11 @@ def main():
         peak = FP64_NOMINAL_TFLOPS
         peak_src = "FP64 nominal 1.25 TFLOP/s"
     probe = res["peaks"]
+    traffic = None
+    if fp32 and _kernel_source_hash() == PROFILED_TRAFFIC["source_sha256_16"] and             res.get("tile") == PROFILED_TRAFFIC["tile"]:
+        traffic = PROFILED_TRAFFIC["bytes"]
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
             "kernel": "k_sum<float,R> (mixed)" if fp32 else "k_sum<double,R> (fp64)",
             "kernel_ms": kms, "flops_per_launch": flops,
             "peak_source": peak_src}
@@ -452,6 +622,10 @@ def main():
     if res["plain"]:
         line["plain_fp64"] = res["plain"]
         line["speedup_vs_plain_fp64"] = res["plain"]["ms_per_step"] / ms
+    if res.get("batched"):
+        line["batched"] = res["batched"]
+        if res["plain"]:
+            line["batched"]["speedup_vs_plain_fp64"] = res["batched"]["value"] / res["plain"]["value"]
     if probe:
         line["measured_pipe_peaks"] = {k: v for k, v in probe.items()}
     # accuracy of this run's outputs

@@ -180,7 +180,8 @@ struct SlotPlan {
     int n_slots = 0, n_rows_pos = 0, n_rows_neg = 0;
     std::vector<int2> pair_lm;
     std::vector<int> mode_pair;
-    std::vector<int> slot_ptr, contrib;
+    std::vector<int> slot_ptr;
+    std::vector<int2> contrib;
     std::vector<int2> rows;
 };
 
@@ -249,7 +250,9 @@ few_status plan_slots(const int *l, const int *m, const int *n, int N, SlotPlan 
     for (int s = 0; s < slot; ++s) P.slot_ptr[s + 1] = P.slot_ptr[s] + (int)lists[s].size();
     P.contrib.clear();
     P.contrib.reserve(P.slot_ptr[slot]);
-    for (int s = 0; s < slot; ++s) P.contrib.insert(P.contrib.end(), lists[s].begin(), lists[s].end());
+    for (int s = 0; s < slot; ++s)
+        for (int code : lists[s])
+            P.contrib.push_back(make_int2(code, 2 * P.mode_pair[code >> 1] + (code & 1)));
     return FEW_OK;
 }
 
@@ -622,7 +625,7 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
                  o_coef = take(sizeof(double) * 4 * (size_t)tr->S * tr->J),
                  o_pair = take(sizeof(int2) * P.pair_lm.size()), o_mp = take(sizeof(int) * N),
                  o_sp = take(sizeof(int) * P.slot_ptr.size()),
-                 o_ct = take(sizeof(int) * std::max<size_t>(1, P.contrib.size())),
+                 o_ct = take(sizeof(int2) * std::max<size_t>(1, P.contrib.size())),
                  o_rows = take(sizeof(int2) * P.rows.size()), o_job = take(sizeof(BuildJob));
     if ((st = dev_alloc(ctx, off, ctx->internal, &tr->dmem))) {
         delete tr;
@@ -639,7 +642,7 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
     put(o_pair, P.pair_lm.data(), sizeof(int2) * P.pair_lm.size());
     put(o_mp, P.mode_pair.data(), sizeof(int) * N);
     put(o_sp, P.slot_ptr.data(), sizeof(int) * P.slot_ptr.size());
-    put(o_ct, P.contrib.data(), sizeof(int) * P.contrib.size());
+    put(o_ct, P.contrib.data(), sizeof(int2) * P.contrib.size());
     put(o_rows, P.rows.data(), sizeof(int2) * P.rows.size());
 
     TrajDev &D = tr->dev;
@@ -661,7 +664,7 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
     D.pair_lm = reinterpret_cast<const int2 *>(d + o_pair);
     D.mode_pair = reinterpret_cast<const int *>(d + o_mp);
     D.slot_ptr = reinterpret_cast<const int *>(d + o_sp);
-    D.contrib = reinterpret_cast<const int *>(d + o_ct);
+    D.contrib = reinterpret_cast<const int2 *>(d + o_ct);
     D.rows = reinterpret_cast<const int2 *>(d + o_rows);
     tr->job_dev = reinterpret_cast<BuildJob *>(d + o_job);
 

@@ -31,7 +31,7 @@ enum : int {
     kVariantPacked = 2   // mixed, packed FP32x2 FMA; slot = 8 duplicated float pairs
 };
 constexpr int kFoldThreads = 128;
-constexpr int kYlmThreads = 8;   // few pairs per block: spreads the FP64 work over SMs
+constexpr int kYlmThreads = 16;  // few pairs per block: spreads the FP64 work over SMs
 constexpr int kBuildThreads = 64;
 
 // Trajectory-resident data (one per few_traj).
@@ -53,7 +53,8 @@ struct TrajDev {
     const int2 *pair_lm;   // [n_pairs] (l, m)
     const int *mode_pair;  // [N] pair index of each mode
     const int *slot_ptr;   // [n_slots + 1] CSR into contrib
-    const int *contrib;    // [n_contrib] mode * 2 + kind (0: A Y+, 1: conj(A) Y-)
+    const int2 *contrib;   // [n_contrib] (mode * 2 + kind, 2 * pair + kind); kind 0: A Y+,
+                           //   1: conj(A) Y-
     const int2 *rows;      // [n_rows_pos + n_rows_neg] (np, nn) slots per half row
 };
 

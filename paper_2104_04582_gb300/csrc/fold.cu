@@ -76,11 +76,13 @@ __device__ __forceinline__ int wave_of(const WaveDev *waves, int n, int g, bool 
     return lo;
 }
 
-// One thread per (wave, (l, m) pair).
+// Two threads per (wave, (l, m) pair): one computes Y+, the other Y- (halves the FP64
+// dependency chain each thread waits on).
 __global__ void __launch_bounds__(kYlmThreads) k_ylm(const PlanHdr *__restrict__ hp)
 {
     const PlanHdr h = *hp;
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = t >> 1, which = t & 1;
     if (g >= h.total_pairs) return;
     const int w = wave_of(h.waves, h.n_waves, g, true);
     const WaveDev &W = h.waves[w];
@@ -90,20 +92,21 @@ __global__ void __launch_bounds__(kYlmThreads) k_ylm(const PlanHdr *__restrict__
         return;
     }
     const int2 lm = W.tr.pair_lm[p];
-    const double2 yp = swsh_m2(lm.x, lm.y, W.theta, W.phi);
-    double2 ym = make_double2(0.0, 0.0);
-    if (lm.y > 0) {
-        ym = swsh_m2(lm.x, -lm.y, W.theta, W.phi);
-        if (lm.x & 1) ym = make_double2(-ym.x, -ym.y);
+    double2 y = make_double2(0.0, 0.0);
+    if (which == 0) {
+        y = swsh_m2(lm.x, lm.y, W.theta, W.phi);
+    } else if (lm.y > 0) {
+        y = swsh_m2(lm.x, -lm.y, W.theta, W.phi);
+        if (lm.x & 1) y = make_double2(-y.x, -y.y);
     }
-    W.ylm[2 * p] = yp;
-    W.ylm[2 * p + 1] = ym;
+    W.ylm[2 * p + which] = y;
 }
 
 cudaError_t launch_ylm(const PlanHdr *hdr_dev, int total_pairs, cudaStream_t st)
 {
     if (total_pairs <= 0) return cudaSuccess;
-    k_ylm<<<(total_pairs + kYlmThreads - 1) / kYlmThreads, kYlmThreads, 0, st>>>(hdr_dev);
+    const int threads = 2 * total_pairs;
+    k_ylm<<<(threads + kYlmThreads - 1) / kYlmThreads, kYlmThreads, 0, st>>>(hdr_dev);
     return cudaGetLastError();
 }
 
@@ -156,9 +159,9 @@ __global__ void __launch_bounds__(kFoldThreads) k_fold(const PlanHdr *__restrict
     const int c0 = tr.slot_ptr[slot], c1 = tr.slot_ptr[slot + 1];
     const double *__restrict__ cs = tr.coef + (size_t)s * tr.J * 4;
     for (int c = c0; c < c1; ++c) {
-        const int code = tr.contrib[c];
-        const int i = code >> 1, kind = code & 1;
-        const double2 Yd = W.ylm[2 * tr.mode_pair[i] + kind];
+        const int2 code = tr.contrib[c];  // (mode * 2 + kind, harmonic-table index)
+        const int i = code.x >> 1, kind = code.x & 1;
+        const double2 Yd = W.ylm[code.y];
         const T yr = (T)Yd.x, yi = (T)Yd.y;
         const double2 *ca = reinterpret_cast<const double2 *>(cs + (size_t)(2 + 2 * i) * 4);
         const double2 r01 = ca[0], r23 = ca[1], i01 = ca[2], i23 = ca[3];
