@@ -66,6 +66,9 @@ def _bind(L: ctypes.CDLL) -> ctypes.CDLL:
     L.oracle_phases.argtypes = [_dp, ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double,
                                 i64, i64, _dp]
     L.oracle_phases.restype = ctypes.c_int
+    L.oracle_mode_select.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_double,
+                                     ctypes.POINTER(ctypes.c_ubyte)]
+    L.oracle_mode_select.restype = ctypes.c_int
     L.oracle_max_threads.argtypes = []
     L.oracle_max_threads.restype = ctypes.c_int
     return L
@@ -195,6 +198,17 @@ def phases(t, phi_phi, phi_r, t0, dt, i_begin, count) -> np.ndarray:
     if rc:
         raise OracleError(f"oracle_phases: status {rc}")
     return out.reshape(-1, 2)
+
+
+def mode_select(amp_re, amp_im, modes, eps) -> np.ndarray:
+    """Mode Selector (Sec. 3.D): boolean mask [N] of the modes kept at some knot."""
+    ar, ai = _d(amp_re), _d(amp_im)
+    K, N = ar.shape
+    m = np.ascontiguousarray(np.asarray(modes, dtype=np.int32).reshape(-1, 3)[:, 1])
+    mask = np.zeros(N, dtype=np.uint8)
+    lib().oracle_mode_select(_p(ar), _p(ai), K, N, m.ctypes.data_as(_ip), float(eps),
+                             mask.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+    return mask.astype(bool)
 
 
 def _c(a) -> np.ndarray:

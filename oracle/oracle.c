@@ -495,3 +495,52 @@ int oracle_max_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------ mode selector (Sec. 3.D) */
+
+typedef struct { double p; int i; } pw_entry;
+
+static int pw_desc(const void *a, const void *b)
+{
+    const pw_entry *x = (const pw_entry *)a, *y = (const pw_entry *)b;
+    if (x->p > y->p) return -1;
+    if (x->p < y->p) return 1;
+    return (x->i > y->i) - (x->i < y->i);   /* ties: lower mode index first */
+}
+
+/*
+ * Mode Selector: at every knot the power of each mode, |A(t_k)|^2 (doubled for m > 0, which also
+ * stands for its m < 0 partner of equal power), is sorted in descending order (ties by mode
+ * index) and summed cumulatively; the knot keeps the shortest leading run whose cumulative power
+ * reaches (1 - eps) of that knot's total.  The selection is the union over knots.  A knot with
+ * zero total power keeps nothing.  mask[i] = 1 for selected modes; returns their number.
+ */
+int oracle_mode_select(const double *amp_re, const double *amp_im, int K, int N, const int *m,
+                       double eps, unsigned char *mask)
+{
+    pw_entry *e = malloc(sizeof(pw_entry) * (size_t)N);
+    memset(mask, 0, (size_t)N);
+    for (int k = 0; k < K; ++k) {
+        double total = 0.0;
+        for (int i = 0; i < N; ++i) {
+            double re = amp_re[(size_t)k * N + i], im = amp_im[(size_t)k * N + i];
+            double p = re * re + im * im;
+            if (m[i] > 0) p *= 2.0;
+            e[i].p = p;
+            e[i].i = i;
+        }
+        qsort(e, (size_t)N, sizeof(pw_entry), pw_desc);
+        for (int j = 0; j < N; ++j) total += e[j].p;
+        if (!(total > 0.0)) continue;
+        double target = (1.0 - eps) * total, c = 0.0;
+        for (int j = 0; j < N; ++j) {
+            c += e[j].p;
+            mask[e[j].i] = 1;
+            if (c >= target) break;
+        }
+    }
+    int count = 0;
+    for (int i = 0; i < N; ++i) count += mask[i];
+    free(e);
+    return count;
+}

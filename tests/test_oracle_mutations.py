@@ -37,6 +37,9 @@ MUTATIONS = {
                      "powl(c, (long double)(2 * j - m + mp - 2 * k))"),
     "ylm_norm": ("(2.0L * l + 1.0L) / (4.0L *", "(2.0L * l + 3.0L) / (4.0L *"),
     "scale_dropped": ("out[2 * j] = scale * hr;", "out[2 * j] = hr;"),
+    "select_no_doubling": ("if (m[i] > 0) p *= 2.0;", ""),
+    "select_drops_boundary_mode": [("            mask[e[j].i] = 1;\n            if (c >= target) break;",
+                                    "            if (c >= target) break;\n            mask[e[j].i] = 1;")],
 }
 
 
@@ -94,6 +97,18 @@ def _pins_hold() -> bool:
         want *= 1.7
         if np.max(np.abs(h - want)) > 1e-12 * np.max(np.abs(want)):
             return False
+    # mode selector: geometric closed form and the m > 0 doubling
+    r, N, eps = 0.8, 60, 1e-5
+    pg = r ** np.arange(N)
+    mg = np.stack([np.full(N, 2), np.zeros(N, int), np.arange(N)], axis=1)
+    kept = oracle.mode_select(np.sqrt(pg)[None, :], np.zeros((1, N)), mg, eps)
+    if kept.sum() != math.ceil(math.log(eps + (1 - eps) * r ** N) / math.log(r)):
+        return False
+    md = np.stack([np.full(6, 2), np.array([0, 0, 0, 1, 0, 0]), np.arange(6)], axis=1)
+    re2 = np.array([[1.0, 0.5, 0.0, 0.5, 0.0, 0.0]])
+    if list(oracle.mode_select(re2, np.zeros_like(re2), md, 0.3)) != [True, False, False, True,
+                                                                        False, False]:
+        return False
     # shortcut vs brute force on odd and even l
     w = W.tiny_inputs(3, K=8, n_samples=200)
     a = oracle.waveform_inputs(w)
