@@ -374,6 +374,23 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
             t_.release()
         del outb
 
+    # Mode Selector (Sec. 3.D) on the benchmark's knot amplitudes, eps = 1e-5
+    selector = None
+    if rank == 0:
+        msk = torch.empty(w.N, dtype=torch.uint8, device=dev)
+        mlist = np.ascontiguousarray(w.modes[:, 1])
+        F.few_mode_select(ctx.handle, dev_in[2], dev_in[3], mlist, 1e-5, msk, sh)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(10)]
+        for a, b_ in evs:
+            a.record(stream)
+            F.few_mode_select(ctx.handle, dev_in[2], dev_in[3], mlist, 1e-5, msk, sh)
+            b_.record(stream)
+        torch.cuda.synchronize()
+        selector = {"ms": sum(a.elapsed_time(b_) for a, b_ in evs) / len(evs), "eps": 1e-5,
+                    "knots": w.K, "modes": w.N, "selected": int(msk.sum().item())}
+
     # pipe peaks
     peaks = measure_peaks(local_rank) if rank == 0 and not args.no_probe else {}
 
@@ -382,7 +399,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     ctx.close()
     return dict(w=w, ms_local=ms_local, step_ms=step_ms, kernel_ms=kernel_ms, last_t=last_t,
                 clocks=clocks, plain=plain, e2e=e2e, peaks=peaks, slots=slots,
-                h_fast=h_fast, h_plain=h_plain, prec=prec, batched=batched, tile=tile)
+                h_fast=h_fast, h_plain=h_plain, prec=prec, batched=batched, tile=tile,
+                selector=selector)
 
 
 def run_serving(args):
@@ -622,6 +640,8 @@ def main():
     if res["plain"]:
         line["plain_fp64"] = res["plain"]
         line["speedup_vs_plain_fp64"] = res["plain"]["ms_per_step"] / ms
+    if res.get("selector"):
+        line["mode_selector"] = res["selector"]
     if res.get("batched"):
         line["batched"] = res["batched"]
         if res["plain"]:

@@ -208,6 +208,22 @@ few_status few_phase_samples(few_ctx *ctx, const few_traj *traj, double t0, doub
                              int64_t n_samples, double dphi_phi0, double dphi_r0, double *out_dev,
                              void *stream);
 
+/*
+ * Mode Selector (Sec. 3.D), on the device.  At each knot k the power of mode i is
+ * |A_i(t_k)|^2, doubled for m_i > 0 (the mode also stands for its m < 0 partner); powers are
+ * sorted in descending order (ties: lower mode index first) and summed cumulatively, and the knot
+ * keeps the shortest leading run whose cumulative power reaches (1 - eps) of its total (a knot
+ * with zero total keeps nothing).  mask_dev[i] = 1 for the union of kept modes over all knots,
+ * else 0.
+ *   amp_re_dev, amp_im_dev [K][N]: device arrays, row-major (modes contiguous).
+ *   m [N]: host array of the modes' m (>= 0).  eps >= 0.  N <= 4096.
+ *   mask_dev: N bytes of device memory (overwritten).
+ * Asynchronous on `stream`.  The cumulative sums run in FP64 in a parallel order, so a mode
+ * whose cumulative power lies within rounding of the cut may be decided either way.
+ */
+few_status few_mode_select(few_ctx *ctx, const double *amp_re_dev, const double *amp_im_dev, int K,
+                           int N, const int *m, double eps, unsigned char *mask_dev, void *stream);
+
 /* Flags of few_batch_plan. */
 #define FEW_BATCH_REBUILD_SPLINES 1u  /* each run also rebuilds every distinct trajectory's
                                          splines from its device-resident knot data */

@@ -69,6 +69,11 @@ def _bind(L: ctypes.CDLL) -> ctypes.CDLL:
     L.oracle_mode_select.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_double,
                                      ctypes.POINTER(ctypes.c_ubyte)]
     L.oracle_mode_select.restype = ctypes.c_int
+    L.oracle_frame_angles.argtypes = [ctypes.c_double] * 4 + [_dp, _dp, _dp]
+    L.oracle_frame_angles.restype = ctypes.c_int
+    L.oracle_waveform_ssb.argtypes = [_dp, ctypes.c_int, _dp, _dp, _ip, _ip, _ip, ctypes.c_int, _dp,
+                                      _dp] + [ctypes.c_double] * 7 + [i64, i64, _dp, ctypes.c_int]
+    L.oracle_waveform_ssb.restype = ctypes.c_int
     L.oracle_max_threads.argtypes = []
     L.oracle_max_threads.restype = ctypes.c_int
     return L
@@ -209,6 +214,30 @@ def mode_select(amp_re, amp_im, modes, eps) -> np.ndarray:
     lib().oracle_mode_select(_p(ar), _p(ai), K, N, m.ctypes.data_as(_ip), float(eps),
                              mask.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
     return mask.astype(bool)
+
+
+def frame_angles(theta_S, phi_S, theta_K, phi_K):
+    """(theta_src, phi_src, psi) of the frame transformation (Sec. 2.A)."""
+    th, ph, psi = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    rc = lib().oracle_frame_angles(float(theta_S), float(phi_S), float(theta_K), float(phi_K),
+                                   ctypes.byref(th), ctypes.byref(ph), ctypes.byref(psi))
+    if rc:
+        raise OracleError(f"oracle_frame_angles: status {rc}")
+    return th.value, ph.value, psi.value
+
+
+def waveform_ssb(t, phi_phi, phi_r, modes, amp_re, amp_im, theta_S, phi_S, theta_K, phi_K,
+                 scale=1.0, t0=0.0, dt=10.0, i_begin=0, count=0, nthreads=1) -> np.ndarray:
+    """Detector-frame waveform: source-frame sum at the transformed angles, times -e^{-2i psi}."""
+    keep, args = _wave_args(t, phi_phi, phi_r, modes, amp_re, amp_im)
+    out = np.zeros(2 * int(count))
+    rc = lib().oracle_waveform_ssb(*args, float(theta_S), float(phi_S), float(theta_K),
+                                   float(phi_K), float(scale), float(t0), float(dt), int(i_begin),
+                                   int(count), _p(out), int(nthreads))
+    if rc:
+        raise OracleError(f"oracle_waveform_ssb: status {rc}")
+    del keep
+    return out.view(np.complex128)
 
 
 def _c(a) -> np.ndarray:

@@ -544,3 +544,72 @@ int oracle_mode_select(const double *amp_re, const double *amp_im, int K, int N,
     free(e);
     return count;
 }
+
+/* ------------------------------------------------------------------ frame transformation (Sec. 2.A) */
+
+static void cross3(const double *a, const double *b, double *c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/*
+ * Source-frame viewing angles and polarization angle from the sky position (theta_S, phi_S) and
+ * the MBH spin direction (theta_K, phi_K), Sec. 2.A:
+ *   R = (sin tS cos pS, sin tS sin pS, cos tS),  S = (sin tK cos pK, sin tK sin pK, cos tK),
+ *   source frame x = R x S / |R x S|, y = (R - (R.S) S) / |R x S|, z = S;
+ *   the wave reaches the detector along -R, whose source-frame polar angle gives
+ *   cos theta_src = -R.S and whose azimuth is phi_src = -pi/2;
+ *   tan psi = (cos tS sin tK cos(pS - pK) - sin tS cos tK) / (sin tK sin(pS - pK)).
+ * The azimuth is computed from the projection of -R onto (x, y), not assumed.
+ */
+int oracle_frame_angles(double tS, double pS, double tK, double pK, double *theta_src,
+                        double *phi_src, double *psi)
+{
+    double R[3] = {sin(tS) * cos(pS), sin(tS) * sin(pS), cos(tS)};
+    double S[3] = {sin(tK) * cos(pK), sin(tK) * sin(pK), cos(tK)};
+    double RxS[3];
+    cross3(R, S, RxS);
+    double nrm = sqrt(dot3(RxS, RxS));
+    if (!(nrm > 1e-12)) return OR_ERR_ARG;   /* R parallel to S: frame undefined */
+    double RS = dot3(R, S);
+    double x[3] = {RxS[0] / nrm, RxS[1] / nrm, RxS[2] / nrm};
+    double y[3] = {(R[0] - RS * S[0]) / nrm, (R[1] - RS * S[1]) / nrm, (R[2] - RS * S[2]) / nrm};
+    double v[3] = {-R[0], -R[1], -R[2]};
+    *theta_src = acos(fmax(-1.0, fmin(1.0, dot3(v, S))));
+    *phi_src = atan2(dot3(v, y), dot3(v, x));
+    double num = cos(tS) * sin(tK) * cos(pS - pK) - sin(tS) * cos(tK);
+    double den = sin(tK) * sin(pS - pK);
+    *psi = atan2(num, den);
+    return OR_OK;
+}
+
+/*
+ * Detector-frame (solar-system-barycentre) waveform: the source-frame sum of oracle_waveform at
+ * (theta_src, phi_src), then the pi/2 rotation of the polarization basis -- a phase shift of pi --
+ * and the rotation by twice the polarization angle: h -> -h e^{-2 i psi}
+ * (h_+' = cos 2psi h_+ - sin 2psi h_x, h_x' = sin 2psi h_+ + cos 2psi h_x).
+ */
+int oracle_waveform_ssb(const double *t, int K, const double *phi_phi, const double *phi_r,
+                        const int *l, const int *m, const int *n, int N,
+                        const double *amp_re, const double *amp_im,
+                        double tS, double pS, double tK, double pK, double scale, double t0,
+                        double dt, int64_t i_begin, int64_t count, double *out, int nthreads)
+{
+    double th, ph, psi;
+    int rc = oracle_frame_angles(tS, pS, tK, pK, &th, &ph, &psi);
+    if (rc) return rc;
+    rc = oracle_waveform(t, K, phi_phi, phi_r, l, m, n, N, amp_re, amp_im, th, ph, scale, t0, dt,
+                         i_begin, count, out, nthreads);
+    if (rc) return rc;
+    double fr = -cos(2.0 * psi), fi = sin(2.0 * psi);   /* -e^{-2 i psi} */
+    for (int64_t j = 0; j < count; ++j) {
+        double a = out[2 * j], b = out[2 * j + 1];
+        out[2 * j] = a * fr - b * fi;
+        out[2 * j + 1] = a * fi + b * fr;
+    }
+    return OR_OK;
+}

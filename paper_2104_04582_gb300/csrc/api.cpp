@@ -852,6 +852,33 @@ few_status few_phase_samples(few_ctx *ctx, const few_traj *tr, double t0, double
     return st;
 }
 
+few_status few_mode_select(few_ctx *ctx, const double *amp_re, const double *amp_im, int K, int N,
+                           const int *m, double eps, unsigned char *mask, void *stream)
+{
+    if (!ctx || !amp_re || !amp_im || !m || !mask) return FEW_ERR_INVALID_ARG;
+    if (K < 1 || N < 1 || !is_fin(eps) || eps < 0.0) return FEW_ERR_INVALID_ARG;
+    if (N > mode_select_max_modes()) return FEW_ERR_LIMIT;
+    for (int i = 0; i < N; ++i)
+        if (m[i] < 0) return FEW_ERR_MODES;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *d = nullptr;
+    few_status st = dev_alloc(ctx, sizeof(int) * (size_t)N, s, &d);
+    if (st) return st;
+    st = upload(ctx, d, m, sizeof(int) * (size_t)N, s);
+    if (!st) {
+        cudaError_t e = launch_mode_select(amp_re, amp_im, K, N, static_cast<const int *>(d), eps,
+                                           mask, s);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            st = FEW_ERR_CUDA;
+        }
+    }
+    dev_free(ctx, d, s);
+    return st;
+}
+
 few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned flags, few_batch **out)
 {
     if (!ctx || !reqs || n < 1 || !out) return FEW_ERR_INVALID_ARG;

@@ -119,6 +119,9 @@ cudaError_t launch_sum(const PlanHdr *hdr_dev, int grid, int threads, int sample
 int sum_slot_bytes(int variant);
 cudaError_t launch_phases(const TrajDev &tr, const int *seg_start, double t0, double dt, int n,
                           double dphi_phi, double dphi_r, double *out, cudaStream_t st);
+cudaError_t launch_mode_select(const double *amp_re, const double *amp_im, int K, int N,
+                               const int *m_dev, double eps, unsigned char *mask, cudaStream_t st);
+int mode_select_max_modes();
 // Maximum resident CTAs per SM of the summation kernel for a configuration (0 if invalid).
 int sum_occupancy(int variant, int samples_per_thread, int threads, int smem_bytes);
 // One-time kernel attribute setup (dynamic shared memory opt-in).

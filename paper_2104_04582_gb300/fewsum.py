@@ -42,6 +42,7 @@ EXPORTED = [
     "few_batch_plan", "few_batch_run", "few_batch_release", "few_sync_status", "few_set_tiles",
     "few_get_tiles", "few_plan_segments", "few_mode_slots", "few_ctx_set_timing",
     "few_last_timing", "few_phase_samples", "few_waveform_noalloc", "few_set_packed",
+    "few_mode_select",
 ]
 
 
@@ -116,6 +117,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
             "few_phase_samples": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double,
                                                  ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                                  _vp, _vp]),
+            "few_mode_select": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _ip,
+                                               ctypes.c_double, _vp, _vp]),
             "few_plan_segments": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_int64, _i64p]),
             "few_mode_slots": (ctypes.c_int, [_ip, _ip, _ip, ctypes.c_int, _ip, _ip]),
@@ -284,6 +287,16 @@ def few_phase_samples(ctx: int, traj: int, t0: float, dt: float, n_samples: int,
     st = load().few_phase_samples(ctx, traj, float(t0), float(dt), int(n_samples),
                                   float(dphi_phi0), float(dphi_r0), out_ptr, stream)
     _check("few_phase_samples", st)
+
+
+def few_mode_select(ctx: int, amp_re, amp_im, m, eps: float, mask, stream: int = 0) -> None:
+    """Mode Selector on the device: amp_re/amp_im float64 CUDA tensors [K, N], m host ints [N],
+    mask a uint8 CUDA tensor [N] (overwritten with the union of kept modes)."""
+    K, N = int(amp_re.shape[0]), int(amp_re.shape[1])
+    mm = _i32(m)
+    st = load().few_mode_select(ctx, amp_re.data_ptr(), amp_im.data_ptr(), K, N,
+                                mm.ctypes.data_as(_ip), float(eps), mask.data_ptr(), stream)
+    _check("few_mode_select", st)
 
 
 def few_plan_segments(t_knots, t0: float, dt: float, n_samples: int) -> np.ndarray:

@@ -38,6 +38,10 @@ MUTATIONS = {
     "ylm_norm": ("(2.0L * l + 1.0L) / (4.0L *", "(2.0L * l + 3.0L) / (4.0L *"),
     "scale_dropped": ("out[2 * j] = scale * hr;", "out[2 * j] = hr;"),
     "select_no_doubling": ("if (m[i] > 0) p *= 2.0;", ""),
+    "frame_psi_sign": ("double num = cos(tS) * sin(tK) * cos(pS - pK) - sin(tS) * cos(tK);",
+                       "double num = cos(tS) * sin(tK) * cos(pS - pK) + sin(tS) * cos(tK);"),
+    "frame_no_pi_shift": ("double fr = -cos(2.0 * psi), fi = sin(2.0 * psi);",
+                          "double fr = cos(2.0 * psi), fi = -sin(2.0 * psi);"),
     "select_drops_boundary_mode": [("            mask[e[j].i] = 1;\n            if (c >= target) break;",
                                     "            if (c >= target) break;\n            mask[e[j].i] = 1;")],
 }
@@ -108,6 +112,21 @@ def _pins_hold() -> bool:
     re2 = np.array([[1.0, 0.5, 0.0, 0.5, 0.0, 0.0]])
     if list(oracle.mode_select(re2, np.zeros_like(re2), md, 0.3)) != [True, False, False, True,
                                                                         False, False]:
+        return False
+    # frame transformation: psi against the vector form, and the detector-frame composition
+    R = np.array([math.sin(0.54) * math.cos(5.36), math.sin(0.54) * math.sin(5.36), math.cos(0.54)])
+    S = np.array([math.sin(1.73) * math.cos(3.2), math.sin(1.73) * math.sin(3.2), math.cos(1.73)])
+    z = np.array([0.0, 0.0, 1.0])
+    th, ph, psi = oracle.frame_angles(0.54, 5.36, 1.73, 3.2)
+    want = math.atan2(S @ z - (S @ R) * (z @ R), R @ np.cross(S, z))
+    if abs(np.exp(2j * psi) - np.exp(2j * want)) > 1e-12:
+        return False
+    wt = W.tiny_inputs(5, n_samples=50)
+    src = oracle.waveform(wt.t_knots, wt.phi_phi, wt.phi_r, wt.modes, wt.amp_re, wt.amp_im, th,
+                          ph, 1.0, wt.t0, wt.dt, 0, 50)
+    ssb = oracle.waveform_ssb(wt.t_knots, wt.phi_phi, wt.phi_r, wt.modes, wt.amp_re, wt.amp_im,
+                              0.54, 5.36, 1.73, 3.2, 1.0, wt.t0, wt.dt, 0, 50)
+    if np.max(np.abs(ssb + np.exp(-2j * psi) * src)) > 1e-13 * np.max(np.abs(src)):
         return False
     # shortcut vs brute force on odd and even l
     w = W.tiny_inputs(3, K=8, n_samples=200)
