@@ -52,7 +52,7 @@
 extern "C" {
 #endif
 
-#define FEW_ABI_VERSION 1
+#define FEW_ABI_VERSION 2
 #define FEW_MAX_SLOTS_FP64 1776
 #define FEW_MAX_SLOTS_MIXED 3552
 
@@ -79,6 +79,12 @@ typedef enum few_mem {
     FEW_MEM_HOST = 0,   /* pointer is host memory (pageable or pinned) */
     FEW_MEM_DEVICE = 1  /* pointer is device memory of the context's GPU */
 } few_mem;
+
+typedef enum few_frame {
+    FEW_FRAME_SOURCE = 0,  /* (theta, phi) are the source-frame viewing angles */
+    FEW_FRAME_SSB = 1      /* (theta, phi) = sky position (theta_S, phi_S) and (theta_K, phi_K)
+                              the spin direction; the output is in the detector frame (Sec. 2.A) */
+} few_frame;
 
 typedef struct few_ctx few_ctx;
 typedef struct few_traj few_traj;
@@ -141,7 +147,14 @@ few_status few_traj_info(const few_traj *traj, int *K, int *N, int *n_slots);
 
 /*
  * One waveform request.  Output sample i (0 <= i < n_samples) is h(t0 + i*dt), Sec. 4 sum.
- *   theta, phi: source-frame viewing angles (rad) of -2Y_lm (Sec. 2.A).
+ *   theta, phi: source-frame viewing angles (rad) of -2Y_lm when frame == FEW_FRAME_SOURCE.
+ *   frame == FEW_FRAME_SSB (Sec. 2.A): theta, phi are the sky position (theta_S, phi_S) and
+ *     theta_K, phi_K the spin direction, both in the solar-system-barycentre frame.  The library
+ *     derives the source-frame angles (cos theta_src = -R.S, phi_src = -pi/2, from the paper's
+ *     source-frame basis) and the polarization angle psi (tan psi = (cos tS sin tK cos(pS - pK)
+ *     - sin tS cos tK) / (sin tK sin(pS - pK))), applies the pi/2 basis rotation (a phase shift
+ *     of pi) and the rotation by 2 psi: h_ssb = -e^{-2 i psi} h_src.  R parallel to S is
+ *     rejected (FEW_ERR_INVALID_ARG).
  *   scale: the real prefactor mu/d_L (1 for the dimensionless sum).
  *   dphi_phi0, dphi_r0: constant offsets (rad) added to Phi_phi and Phi_r -- a change of the
  *     initial phases Phi_phi,0 and Phi_r,0 without rebuilding the splines.
@@ -161,8 +174,9 @@ typedef struct few_request {
     int prec;       /* few_precision */
     int out_c64;    /* 1: complex64 output, 0: complex128 output */
     int out_where;  /* few_mem of `out` */
-    int reserved;
+    int frame;      /* few_frame */
     void *out;
+    double theta_K, phi_K;  /* spin direction, used when frame == FEW_FRAME_SSB */
 } few_request;
 
 /*

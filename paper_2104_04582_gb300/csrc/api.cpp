@@ -347,6 +347,18 @@ few_status validate_request(const few_request &r, bool need_device_out)
     if (!is_fin(r.theta) || !is_fin(r.phi) || !is_fin(r.scale) || !is_fin(r.dphi_phi0) ||
         !is_fin(r.dphi_r0))
         return FEW_ERR_INVALID_ARG;
+    if (r.frame != FEW_FRAME_SOURCE && r.frame != FEW_FRAME_SSB) return FEW_ERR_INVALID_ARG;
+    if (r.frame == FEW_FRAME_SSB) {
+        if (!is_fin(r.theta_K) || !is_fin(r.phi_K)) return FEW_ERR_INVALID_ARG;
+        // the source frame needs R x S != 0
+        const double R[3] = {std::sin(r.theta) * std::cos(r.phi), std::sin(r.theta) * std::sin(r.phi),
+                             std::cos(r.theta)};
+        const double S[3] = {std::sin(r.theta_K) * std::cos(r.phi_K),
+                             std::sin(r.theta_K) * std::sin(r.phi_K), std::cos(r.theta_K)};
+        const double x = R[1] * S[2] - R[2] * S[1], y = R[2] * S[0] - R[0] * S[2],
+                     z = R[0] * S[1] - R[1] * S[0];
+        if (!(x * x + y * y + z * z > 1e-24)) return FEW_ERR_INVALID_ARG;
+    }
     if (!is_fin(r.t0) || !is_fin(r.dt) || !(r.dt > 0.0) || r.n_samples < 0 ||
         r.n_samples > 2147483647LL)
         return FEW_ERR_RANGE;
@@ -427,6 +439,9 @@ void fill_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P, unsign
         W.scale = r.scale;
         W.dphi_phi = r.dphi_phi0;
         W.dphi_r = r.dphi_r0;
+        W.frame = r.frame;
+        W.theta_K = r.theta_K;
+        W.phi_K = r.phi_K;
         W.t0 = r.t0;
         W.dt = r.dt;
         W.n_samples = (int)r.n_samples;

@@ -84,7 +84,8 @@ struct WaveDev {
     int pair_begin;       // first global pair index of this wave (ylm kernel)
     int fold_begin;       // first fold block of this wave
     int fold_blocks_per_seg;
-    int pad;
+    int frame;            // few_frame: (theta, phi) source-frame angles, or sky position
+    double theta_K, phi_K;  // spin direction (frame == FEW_FRAME_SSB)
 };
 
 // Start of one CTA's slice of the summation work: (wave, sample).

@@ -76,6 +76,38 @@ __device__ __forceinline__ int wave_of(const WaveDev *waves, int n, int g, bool 
     return lo;
 }
 
+// Frame transformation (Sec. 2.A): from the sky position (tS, pS) and the spin direction
+// (tK, pK) in the barycentre frame, the source-frame viewing angles of the propagation direction
+// -R in the basis x = R x S/|R x S|, y = (R - (R.S) S)/|R x S|, z = S, and the polarization
+// angle psi with tan psi = (cos tS sin tK cos(pS - pK) - sin tS cos tK)/(sin tK sin(pS - pK)).
+// The detector-frame waveform is -e^{-2 i psi} times the source-frame one (a pi phase shift for
+// the pi/2 basis rotation, then the 2 psi rotation), a constant folded into the harmonics.
+__device__ void frame_angles(double tS, double pS, double tK, double pK, double &theta,
+                             double &phi, double &psi)
+{
+    double stS, ctS, spS, cpS, stK, ctK, spK, cpK;
+    sincos(tS, &stS, &ctS);
+    sincos(pS, &spS, &cpS);
+    sincos(tK, &stK, &ctK);
+    sincos(pK, &spK, &cpK);
+    const double R[3] = {stS * cpS, stS * spS, ctS};
+    const double S[3] = {stK * cpK, stK * spK, ctK};
+    const double X[3] = {R[1] * S[2] - R[2] * S[1], R[2] * S[0] - R[0] * S[2],
+                         R[0] * S[1] - R[1] * S[0]};
+    const double nx = sqrt(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
+    const double rs = R[0] * S[0] + R[1] * S[1] + R[2] * S[2];
+    // components of -R: along x (R x S is orthogonal to R), along y, along z = S
+    const double vx = 0.0;
+    const double vy = -((R[0] - rs * S[0]) * R[0] + (R[1] - rs * S[1]) * R[1] +
+                        (R[2] - rs * S[2]) * R[2]) / nx;
+    const double vz = -rs;
+    theta = acos(fmax(-1.0, fmin(1.0, vz)));
+    phi = atan2(vy, vx);
+    double sd, cd;
+    sincos(pS - pK, &sd, &cd);
+    psi = atan2(ctS * stK * cd - stS * ctK, stK * sd);
+}
+
 // Two threads per (wave, (l, m) pair): one computes Y+, the other Y- (halves the FP64
 // dependency chain each thread waits on).
 __global__ void __launch_bounds__(kYlmThreads) k_ylm(const PlanHdr *__restrict__ hp)
@@ -92,12 +124,20 @@ __global__ void __launch_bounds__(kYlmThreads) k_ylm(const PlanHdr *__restrict__
         return;
     }
     const int2 lm = W.tr.pair_lm[p];
+    double theta = W.theta, phi = W.phi, psi = 0.0;
+    if (W.frame == FEW_FRAME_SSB) frame_angles(W.theta, W.phi, W.theta_K, W.phi_K, theta, phi, psi);
     double2 y = make_double2(0.0, 0.0);
     if (which == 0) {
-        y = swsh_m2(lm.x, lm.y, W.theta, W.phi);
+        y = swsh_m2(lm.x, lm.y, theta, phi);
     } else if (lm.y > 0) {
-        y = swsh_m2(lm.x, -lm.y, W.theta, W.phi);
+        y = swsh_m2(lm.x, -lm.y, theta, phi);
         if (lm.x & 1) y = make_double2(-y.x, -y.y);
+    }
+    if (W.frame == FEW_FRAME_SSB) {
+        double s2, c2;
+        sincos(2.0 * psi, &s2, &c2);
+        const double fr = -c2, fi = s2;  // -e^{-2 i psi}
+        y = make_double2(y.x * fr - y.y * fi, y.x * fi + y.y * fr);
     }
     W.ylm[2 * p + which] = y;
 }

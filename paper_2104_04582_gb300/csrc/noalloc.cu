@@ -84,6 +84,7 @@ extern "C" few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req,
     if (!std::isfinite(r.theta) || !std::isfinite(r.phi) || !std::isfinite(r.scale) ||
         !std::isfinite(r.dphi_phi0) || !std::isfinite(r.dphi_r0))
         return FEW_ERR_INVALID_ARG;
+    if (r.frame != FEW_FRAME_SOURCE) return FEW_ERR_INVALID_ARG;  // source-frame requests only
     std::lock_guard<std::recursive_mutex> lk(ctx_mutex(ctx));
     CtxTrajView v;
     if (!ctx_traj_view(ctx, r.traj, &v)) return FEW_ERR_INVALID_ARG;

@@ -32,6 +32,8 @@ FEW_FP64 = 0
 FEW_MIXED = 1
 FEW_MEM_HOST = 0
 FEW_MEM_DEVICE = 1
+FEW_FRAME_SOURCE = 0
+FEW_FRAME_SSB = 1
 FEW_BATCH_REBUILD_SPLINES = 1
 FEW_BATCH_NO_GRAPH = 2
 
@@ -55,8 +57,9 @@ class few_request(ctypes.Structure):
         ("t0", ctypes.c_double), ("dt", ctypes.c_double),
         ("n_samples", ctypes.c_int64),
         ("prec", ctypes.c_int), ("out_c64", ctypes.c_int), ("out_where", ctypes.c_int),
-        ("reserved", ctypes.c_int),
+        ("frame", ctypes.c_int),
         ("out", ctypes.c_void_p),
+        ("theta_K", ctypes.c_double), ("phi_K", ctypes.c_double),
     ]
 
 
@@ -214,12 +217,14 @@ def few_traj_info(traj: int):
 def make_request(traj: int, out_ptr: int, n_samples: int, t0: float, dt: float, theta: float,
                  phi: float, scale: float = 1.0, prec: int = FEW_FP64, out_c64: bool = False,
                  out_where: int = FEW_MEM_DEVICE, dphi_phi0: float = 0.0,
-                 dphi_r0: float = 0.0) -> few_request:
+                 dphi_r0: float = 0.0, frame: int = FEW_FRAME_SOURCE, theta_K: float = 0.0,
+                 phi_K: float = 0.0) -> few_request:
+    """theta, phi: source-frame angles, or the sky position when frame == FEW_FRAME_SSB."""
     return few_request(traj=traj, theta=float(theta), phi=float(phi), scale=float(scale),
                        dphi_phi0=float(dphi_phi0), dphi_r0=float(dphi_r0), t0=float(t0),
                        dt=float(dt), n_samples=int(n_samples), prec=int(prec),
-                       out_c64=1 if out_c64 else 0, out_where=int(out_where), reserved=0,
-                       out=out_ptr)
+                       out_c64=1 if out_c64 else 0, out_where=int(out_where), frame=int(frame),
+                       out=out_ptr, theta_K=float(theta_K), phi_K=float(phi_K))
 
 
 def few_waveform(ctx: int, req: few_request, stream: int = 0) -> None:

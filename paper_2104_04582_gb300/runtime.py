@@ -115,7 +115,8 @@ def alloc_out(n_samples: int, c64: bool, device: int = 0):
 
 def request(tr: Trajectory, out, n_samples: int, t0: float, dt: float, theta: float, phi: float,
             prec: int = F.FEW_FP64, scale: float = 1.0, dphi_phi0: float = 0.0,
-            dphi_r0: float = 0.0, out_where: int = F.FEW_MEM_DEVICE) -> F.few_request:
+            dphi_r0: float = 0.0, out_where: int = F.FEW_MEM_DEVICE, frame: int = F.FEW_FRAME_SOURCE,
+            theta_K: float = 0.0, phi_K: float = 0.0) -> F.few_request:
     if out_where == F.FEW_MEM_DEVICE:
         ptr = out.data_ptr()
         c64 = str(out.dtype) == "torch.complex64"
@@ -123,7 +124,7 @@ def request(tr: Trajectory, out, n_samples: int, t0: float, dt: float, theta: fl
         ptr = out.ctypes.data
         c64 = out.dtype == np.complex64
     return F.make_request(tr.handle, ptr, n_samples, t0, dt, theta, phi, scale, prec, c64,
-                          out_where, dphi_phi0, dphi_r0)
+                          out_where, dphi_phi0, dphi_r0, frame, theta_K, phi_K)
 
 
 def waveform(ctx: Context, tr: Trajectory, n_samples: int, t0: float, dt: float, theta: float,

@@ -279,3 +279,30 @@ def test_phase_step_offsets(gpu_ctx):
     d = g - o
     d -= np.round(d)
     assert np.max(np.abs(d)) * 2 * math.pi <= 1e-9 / 40
+
+
+@pytest.mark.parametrize("prec", [F.FEW_FP64, F.FEW_MIXED])
+def test_detector_frame_output(gpu_ctx, prec):
+    """Frame transformation (Sec. 2.A) fused into the harmonics: against the oracle's SSB sum."""
+    import torch
+    w = W.config1()
+    tS, pS, tK, pK = 0.54, 5.36, 1.73, 3.20  # the angles of the paper's Sec. 6 study
+    tr = RT.from_inputs(gpu_ctx, w)
+    out = RT.alloc_out(w.n_samples, prec == F.FEW_MIXED)
+    req = RT.request(tr, out, w.n_samples, w.t0, w.dt, tS, pS, prec, 1.0, frame=F.FEW_FRAME_SSB,
+                     theta_K=tK, phi_K=pK)
+    F.few_waveform(gpu_ctx.handle, req, RT.current_stream())
+    torch.cuda.synchronize()
+    g = to_host(out)
+    o = oracle.waveform_ssb(w.t_knots, w.phi_phi, w.phi_r, w.modes, w.amp_re, w.amp_im, tS, pS,
+                            tK, pK, 1.0, w.t0, w.dt, 0, w.n_samples, oracle_threads())
+    if prec == F.FEW_FP64:
+        assert rel_l2(g, o) <= FP64_REL_L2
+    else:
+        assert oracle.mismatch(g, o) <= MIXED_MISMATCH
+    # R parallel to S has no source frame
+    bad = RT.request(tr, out, 10, w.t0, w.dt, 0.3, 1.0, prec, frame=F.FEW_FRAME_SSB,
+                     theta_K=0.3, phi_K=1.0)
+    with pytest.raises(F.FewError):
+        F.few_waveform(gpu_ctx.handle, bad, 0)
+    tr.release()
