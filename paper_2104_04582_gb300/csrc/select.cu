@@ -17,9 +17,18 @@ namespace fewsum {
 constexpr int kSelectThreads = 1024;
 constexpr int kSelectMaxModes = 4096;
 
-__device__ __forceinline__ bool sorts_before(double pa, int ia, double pb, int ib)
+// Non-negative doubles order exactly like their IEEE bit patterns read as unsigned integers, so
+// the sort compares 64-bit integer keys (descending power = ascending inverted bits), with the
+// mode index as the tie-break; integer compares avoid GB300's narrow FP64 pipe.
+__device__ __forceinline__ unsigned long long power_key(double p)
 {
-    return pa > pb || (pa == pb && ia < ib);
+    return ~static_cast<unsigned long long>(__double_as_longlong(p));
+}
+
+__device__ __forceinline__ bool sorts_before(unsigned long long ka, int ia, unsigned long long kb,
+                                             int ib)
+{
+    return ka < kb || (ka == kb && ia < ib);
 }
 
 __global__ void __launch_bounds__(kSelectThreads)
@@ -27,7 +36,8 @@ k_mode_select(const double *__restrict__ amp_re, const double *__restrict__ amp_
               const int *__restrict__ m, double eps, int P, unsigned char *__restrict__ mask)
 {
     extern __shared__ double sel_smem[];
-    double *pw = sel_smem;                                  // [P] powers, then prefix sums
+    double *pw = sel_smem;                                  // [P] sort keys, then prefix sums
+    unsigned long long *key = reinterpret_cast<unsigned long long *>(sel_smem);
     int *ix = reinterpret_cast<int *>(sel_smem + P);        // [P] mode indices
     __shared__ double warp_tot[kSelectThreads / 32];
     __shared__ int s_cut;
@@ -37,10 +47,10 @@ k_mode_select(const double *__restrict__ amp_re, const double *__restrict__ amp_
             const double re = amp_re[(size_t)k * N + i], im = amp_im[(size_t)k * N + i];
             double p = re * re + im * im;
             if (m[i] > 0) p *= 2.0;
-            pw[i] = p;
+            key[i] = power_key(p);
             ix[i] = i;
         } else {
-            pw[i] = -1.0;  // padding sorts after every real mode
+            key[i] = ~0ull;  // padding sorts after every real mode
             ix[i] = 0x7fffffff;
         }
     }
@@ -53,11 +63,11 @@ k_mode_select(const double *__restrict__ amp_re, const double *__restrict__ amp_
                 const int j = i ^ stride;
                 if (j > i) {
                     const bool up = (i & size) == 0;
-                    const double pi = pw[i], pj = pw[j];
+                    const unsigned long long ki = key[i], kj = key[j];
                     const int ii = ix[i], ij = ix[j];
-                    const bool swap = up ? sorts_before(pj, ij, pi, ii) : sorts_before(pi, ii, pj, ij);
+                    const bool swap = up ? sorts_before(kj, ij, ki, ii) : sorts_before(ki, ii, kj, ij);
                     if (swap) {
-                        pw[i] = pj; pw[j] = pi;
+                        key[i] = kj; key[j] = ki;
                         ix[i] = ij; ix[j] = ii;
                     }
                 }
@@ -70,7 +80,7 @@ k_mode_select(const double *__restrict__ amp_re, const double *__restrict__ amp_
     const int b0 = tid * chunk, b1 = min(N, b0 + chunk);
     double run = 0.0;
     for (int i = b0; i < b1; ++i) {
-        run += pw[i];
+        run += __longlong_as_double(static_cast<long long>(~key[i]));
         pw[i] = run;
     }
     double incl = run;
