@@ -74,6 +74,10 @@ def _bind(L: ctypes.CDLL) -> ctypes.CDLL:
     L.oracle_waveform_ssb.argtypes = [_dp, ctypes.c_int, _dp, _dp, _ip, _ip, _ip, ctypes.c_int, _dp,
                                       _dp] + [ctypes.c_double] * 7 + [i64, i64, _dp, ctypes.c_int]
     L.oracle_waveform_ssb.restype = ctypes.c_int
+    L.oracle_direct_dense.argtypes = [_dp, _dp, i64, _ip, _ip, _ip, ctypes.c_int, _dp, _dp,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp,
+                                       ctypes.c_int]
+    L.oracle_direct_dense.restype = ctypes.c_int
     L.oracle_max_threads.argtypes = []
     L.oracle_max_threads.restype = ctypes.c_int
     return L
@@ -237,6 +241,24 @@ def waveform_ssb(t, phi_phi, phi_r, modes, amp_re, amp_im, theta_S, phi_S, theta
     if rc:
         raise OracleError(f"oracle_waveform_ssb: status {rc}")
     del keep
+    return out.view(np.complex128)
+
+
+def direct_dense(phi_phi, phi_r, modes, amp_re, amp_im, theta, phi, scale=1.0,
+                 nthreads=1) -> np.ndarray:
+    """Direct summation over arrays given at every sample (Sec. 3.C): complex128 [n_samples]."""
+    pp, pr = _d(phi_phi), _d(phi_r)
+    l, m, n = _modes(modes)
+    ar, ai = _d(amp_re), _d(amp_im)
+    ns = len(pp)
+    if ar.shape != (ns, len(l)) or ai.shape != (ns, len(l)) or len(pr) != ns:
+        raise ValueError("amplitudes must be [n_samples, N]")
+    out = np.zeros(2 * ns)
+    ip = lambda a: a.ctypes.data_as(_ip)
+    rc = lib().oracle_direct_dense(_p(pp), _p(pr), ns, ip(l), ip(m), ip(n), len(l), _p(ar), _p(ai),
+                                   float(theta), float(phi), float(scale), _p(out), int(nthreads))
+    if rc:
+        raise OracleError(f"oracle_direct_dense: status {rc}")
     return out.view(np.complex128)
 
 

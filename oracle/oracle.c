@@ -613,3 +613,62 @@ int oracle_waveform_ssb(const double *t, int K, const double *phi_phi, const dou
     }
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------ direct summation (Sec. 3.C) */
+
+/*
+ * Direct (non-interpolated) summation: the trajectory and amplitudes are given at every output
+ * sample (arrays of the output's density), so no spline is built:
+ *   h_i = scale * sum_modes [ A_i Y+ e^{-i Phi_mn,i} + (m > 0) (-1)^l conj(A_i) -2Y_{l,-m} e^{+i Phi_mn,i} ],
+ * Phi_mn,i = m phi_phi[i] + n phi_r[i]; the phases are reduced modulo 2 pi separately (in long
+ * double, in turns) before the integer combination, as in oracle_waveform.
+ * amp_re, amp_im: [n_samples][N] row-major; out: [n_samples][2].
+ */
+int oracle_direct_dense(const double *phi_phi, const double *phi_r, int64_t n_samples,
+                        const int *l, const int *m, const int *n, int N, const double *amp_re,
+                        const double *amp_im, double theta, double phi, double scale, double *out,
+                        int nthreads)
+{
+    if (N < 1 || n_samples < 0) return OR_ERR_ARG;
+    double *ypr = malloc(sizeof(double) * N), *ypi = malloc(sizeof(double) * N);
+    double *ymr = malloc(sizeof(double) * N), *ymi = malloc(sizeof(double) * N);
+    for (int i = 0; i < N; ++i) {
+        oracle_swsh(-2, l[i], m[i], theta, phi, &ypr[i], &ypi[i]);
+        ymr[i] = ymi[i] = 0.0;
+        if (m[i] > 0) {
+            double a, b;
+            oracle_swsh(-2, l[i], -m[i], theta, phi, &a, &b);
+            double sg = (l[i] & 1) ? -1.0 : 1.0;
+            ymr[i] = sg * a;
+            ymi[i] = sg * b;
+        }
+    }
+    if (nthreads < 1) nthreads = 1;
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+#endif
+    for (int64_t j = 0; j < n_samples; ++j) {
+        long double xp = (long double)phi_phi[j] / two_pi, xr = (long double)phi_r[j] / two_pi;
+        double fphi = (double)(xp - rintl(xp)), fr = (double)(xr - rintl(xr));
+        double hr = 0.0, hi = 0.0;
+        for (int i = 0; i < N; ++i) {
+            double Ar = amp_re[(size_t)j * N + i], Ai = amp_im[(size_t)j * N + i];
+            double ph = (double)m[i] * fphi + (double)n[i] * fr;
+            ph -= rint(ph);
+            double c = cos(TWO_PI * ph), s = sin(TWO_PI * ph);
+            double ayr = Ar * ypr[i] - Ai * ypi[i], ayi = Ar * ypi[i] + Ai * ypr[i];
+            hr += ayr * c + ayi * s;
+            hi += ayi * c - ayr * s;
+            if (m[i] > 0) {
+                double byr = Ar * ymr[i] + Ai * ymi[i], byi = Ar * ymi[i] - Ai * ymr[i];
+                hr += byr * c - byi * s;
+                hi += byi * c + byr * s;
+            }
+        }
+        out[2 * j] = scale * hr;
+        out[2 * j + 1] = scale * hi;
+    }
+    free(ypr); free(ypi); free(ymr); free(ymi);
+    return OR_OK;
+}

@@ -38,6 +38,8 @@ MUTATIONS = {
     "ylm_norm": ("(2.0L * l + 1.0L) / (4.0L *", "(2.0L * l + 3.0L) / (4.0L *"),
     "scale_dropped": ("out[2 * j] = scale * hr;", "out[2 * j] = hr;"),
     "select_no_doubling": ("if (m[i] > 0) p *= 2.0;", ""),
+    "direct_partner_sign": ("double byr = Ar * ymr[i] + Ai * ymi[i], byi = Ar * ymi[i] - Ai * ymr[i];",
+                            "double byr = Ar * ymr[i] - Ai * ymi[i], byi = Ar * ymi[i] + Ai * ymr[i];"),
     "frame_psi_sign": ("double num = cos(tS) * sin(tK) * cos(pS - pK) - sin(tS) * cos(tK);",
                        "double num = cos(tS) * sin(tK) * cos(pS - pK) + sin(tS) * cos(tK);"),
     "frame_no_pi_shift": ("double fr = -cos(2.0 * psi), fi = sin(2.0 * psi);",
@@ -127,6 +129,15 @@ def _pins_hold() -> bool:
     ssb = oracle.waveform_ssb(wt.t_knots, wt.phi_phi, wt.phi_r, wt.modes, wt.amp_re, wt.amp_im,
                               0.54, 5.36, 1.73, 3.2, 1.0, wt.t0, wt.dt, 0, 50)
     if np.max(np.abs(ssb + np.exp(-2j * psi) * src)) > 1e-13 * np.max(np.abs(src)):
+        return False
+    # direct summation: single-mode closed form
+    ts = np.arange(500) * 17.0
+    A = 0.3 + 0.8j
+    hd = oracle.direct_dense(2.1e-3 * ts + 0.4, 1.7e-3 * ts + 2.9, [(2, 1, -2)],
+                             np.full((500, 1), A.real), np.full((500, 1), A.imag), 0.9, 2.2)
+    Phi = 1 * (2.1e-3 * ts + 0.4) - 2 * (1.7e-3 * ts + 2.9)
+    wd = A * _m2y2(1, 0.9, 2.2) * np.exp(-1j * Phi) + np.conj(A) * _m2y2(-1, 0.9, 2.2) * np.exp(1j * Phi)
+    if np.max(np.abs(hd - wd)) > 1e-12 * np.max(np.abs(wd)):
         return False
     # shortcut vs brute force on odd and even l
     w = W.tiny_inputs(3, K=8, n_samples=200)
