@@ -154,7 +154,8 @@ def _build_variant(tmp_path, name, edits):
     if isinstance(edits, tuple):
         edits = [edits]
     for old, new in edits:
-        assert src.count(old) == 1, f"mutation anchor not unique/found: {name}"
+        # a mistake in a line that occurs in several routines is planted in every copy
+        assert src.count(old) >= 1, f"mutation anchor not found: {name}"
         src = src.replace(old, new)
     path = tmp_path / f"{name}.c"
     path.write_text(src)
