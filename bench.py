@@ -391,6 +391,43 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         selector = {"ms": sum(a.elapsed_time(b_) for a, b_ in evs) / len(evs), "eps": 1e-5,
                     "knots": w.K, "modes": w.N, "selected": int(msk.sum().item())}
 
+    # direct (non-interpolated) summation over dense arrays: HBM-bound in mixed precision
+    direct = None
+    if rank == 0 and args.direct_samples > 0:
+        nsd = args.direct_samples
+        tsd = torch.arange(nsd, dtype=torch.float64, device=dev) * w.dt + 1.0e6
+        xd = (tsd / w.T)[:, None]
+        am = w.amp_model
+        ta = lambda a: torch.as_tensor(a, device=dev)[None, :]
+        env = ta(am.a) * (1.0 + ta(am.alpha) * xd + ta(am.beta) * xd * xd)
+        d_re = (env * torch.cos(ta(am.psi))).contiguous()
+        d_im = (env * torch.sin(ta(am.psi))).contiguous()
+        del env
+        d_pp = torch.as_tensor(W.phase_phi(tsd.cpu().numpy(), w.T, w.phi_phi0), device=dev)
+        d_pr = torch.as_tensor(W.phase_r(tsd.cpu().numpy(), w.T, w.phi_r0), device=dev)
+        d_out = torch.empty(nsd, dtype=torch.complex64, device=dev)
+        F.few_direct_sum(ctx.handle, d_pp, d_pr, d_re, d_im, w.modes, w.theta, w.phi, d_out,
+                         1.0, F.FEW_MIXED, sh)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(5)]
+        for a, b_ in evs:
+            a.record(stream)
+            F.few_direct_sum(ctx.handle, d_pp, d_pr, d_re, d_im, w.modes, w.theta, w.phi, d_out,
+                             1.0, F.FEW_MIXED, sh)
+            b_.record(stream)
+        torch.cuda.synchronize()
+        msd = min(a.elapsed_time(b_) for a, b_ in evs)
+        nbytes = nsd * (16 * w.N + 16 + 8)
+        gbs = nbytes / (msd * 1e-3) / 1e9
+        hbm = float(_peaks_file().get("hbm_gbs", 6800.0))
+        direct = {"samples": nsd, "modes": w.N, "ms": msd,
+                  "mode_samples_per_s": nsd * w.N / (msd * 1e-3),
+                  "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                               "frac": gbs / hbm, "bytes_per_launch": nbytes,
+                               "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}}
+        del d_re, d_im, d_pp, d_pr, d_out
+
     # pipe peaks
     peaks = measure_peaks(local_rank) if rank == 0 and not args.no_probe else {}
 
@@ -400,7 +437,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     return dict(w=w, ms_local=ms_local, step_ms=step_ms, kernel_ms=kernel_ms, last_t=last_t,
                 clocks=clocks, plain=plain, e2e=e2e, peaks=peaks, slots=slots,
                 h_fast=h_fast, h_plain=h_plain, prec=prec, batched=batched, tile=tile,
-                selector=selector)
+                selector=selector, direct=direct)
 
 
 def run_serving(args):
@@ -523,6 +560,8 @@ def main():
                     help="run the serving workload instead of the single-waveform benchmark")
     ap.add_argument("--serving-requests", type=int, default=200)
     ap.add_argument("--serving-budget-gb", type=float, default=16.0)
+    ap.add_argument("--direct-samples", type=int, default=100000,
+                    help="samples of the direct-summation measurement (0: skip)")
     ap.add_argument("--batch", type=int, default=8,
                     help="waveforms per step of the batched-path measurement (0: skip)")
     args = ap.parse_args()
@@ -640,6 +679,8 @@ def main():
     if res["plain"]:
         line["plain_fp64"] = res["plain"]
         line["speedup_vs_plain_fp64"] = res["plain"]["ms_per_step"] / ms
+    if res.get("direct"):
+        line["direct_sum"] = res["direct"]
     if res.get("selector"):
         line["mode_selector"] = res["selector"]
     if res.get("batched"):

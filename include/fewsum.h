@@ -238,6 +238,22 @@ few_status few_phase_samples(few_ctx *ctx, const few_traj *traj, double t0, doub
 few_status few_mode_select(few_ctx *ctx, const double *amp_re_dev, const double *amp_im_dev, int K,
                            int N, const int *m, double eps, unsigned char *mask_dev, void *stream);
 
+/*
+ * Direct (non-interpolated) summation (Sec. 3.C, the basic summation module): the phases and the
+ * amplitudes are given at every output sample, so no spline is built:
+ *   out[i] = scale * sum_j [ A_ij Y+_j e^{-i Phi_j,i} + (m_j > 0) conj(A_ij) Y-_j e^{+i Phi_j,i} ],
+ *   Phi_j,i = m_j phi_phi[i] + n_j phi_r[i] (rad), Y+ = -2Y_lm(theta, phi), Y- = (-1)^l -2Y_{l,-m}.
+ *   phi_phi_dev, phi_r_dev [n_samples], amp_re_dev, amp_im_dev [n_samples][N] (modes contiguous):
+ *     device memory.  l, m, n [N]: host arrays (validated as for few_traj_create).
+ *   prec: FEW_MIXED (FP64 phase reduction, FP32 exponentials and sums; bound by HBM bandwidth)
+ *     or FEW_FP64.  out_dev: n_samples complex64 (out_c64) or complex128, device memory.
+ * Asynchronous on `stream`.
+ */
+few_status few_direct_sum(few_ctx *ctx, const double *phi_phi_dev, const double *phi_r_dev,
+                          const double *amp_re_dev, const double *amp_im_dev, int64_t n_samples,
+                          const int *l, const int *m, const int *n, int N, double theta, double phi,
+                          double scale, int prec, void *out_dev, int out_c64, void *stream);
+
 /* Flags of few_batch_plan. */
 #define FEW_BATCH_REBUILD_SPLINES 1u  /* each run also rebuilds every distinct trajectory's
                                          splines from its device-resident knot data */

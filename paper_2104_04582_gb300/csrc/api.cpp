@@ -894,6 +894,46 @@ few_status few_mode_select(few_ctx *ctx, const double *amp_re, const double *amp
     return st;
 }
 
+few_status few_direct_sum(few_ctx *ctx, const double *pphi, const double *pr, const double *are,
+                          const double *aim, int64_t ns, const int *l, const int *m, const int *n,
+                          int N, double theta, double phi, double scale, int prec, void *out,
+                          int out_c64, void *stream)
+{
+    if (!ctx || !pphi || !pr || !are || !aim || !out) return FEW_ERR_INVALID_ARG;
+    if (prec != FEW_FP64 && prec != FEW_MIXED) return FEW_ERR_INVALID_ARG;
+    if (!is_fin(theta) || !is_fin(phi) || !is_fin(scale) || ns < 0) return FEW_ERR_INVALID_ARG;
+    SlotPlan P;
+    few_status st = plan_slots(l, m, n, N, P);  // validates the modes
+    if (st) return st;
+    if (ns == 0) return FEW_OK;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t mc_bytes = align_up(direct_mode_const_bytes(N), 256);
+    const size_t idx_bytes = align_up(sizeof(int) * (size_t)N, 256);
+    void *d = nullptr;
+    if ((st = dev_alloc(ctx, mc_bytes + 3 * idx_bytes, s, &d))) return st;
+    unsigned char *b = static_cast<unsigned char *>(d);
+    std::vector<int> lmn(3 * (idx_bytes / sizeof(int)), 0);
+    const size_t stride = idx_bytes / sizeof(int);
+    std::copy(l, l + N, lmn.begin());
+    std::copy(m, m + N, lmn.begin() + stride);
+    std::copy(n, n + N, lmn.begin() + 2 * stride);
+    st = upload(ctx, b + mc_bytes, lmn.data(), 3 * idx_bytes, s);
+    if (!st) {
+        const int *dl = reinterpret_cast<const int *>(b + mc_bytes);
+        cudaError_t e = launch_direct(pphi, pr, are, aim, (long long)ns, dl, dl + stride,
+                                      dl + 2 * stride, N, theta, phi, scale, prec == FEW_FP64, out,
+                                      out_c64 ? 1 : 0, b, ctx->sm_count, s);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            st = FEW_ERR_CUDA;
+        }
+    }
+    dev_free(ctx, d, s);
+    return st;
+}
+
 few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned flags, few_batch **out)
 {
     if (!ctx || !reqs || n < 1 || !out) return FEW_ERR_INVALID_ARG;

@@ -1,0 +1,163 @@
+// direct.cu -- direct (non-interpolated) mode summation (arXiv:2104.04582 Sec. 3.C).
+//
+// The "more basic" summation of the paper: the phases and every mode's amplitude are given at
+// the output's own sample density, so there is no spline; at each sample i
+//     h_i = scale * sum_modes [ A_i Y+ e^{-i Phi_mn,i} + (m > 0) conj(A_i) Y- e^{+i Phi_mn,i} ],
+// Phi_mn,i = m Phi_phi,i + n Phi_r,i, Y+ = -2Y_lm, Y- = (-1)^l -2Y_{l,-m}  (Eq. amp_symmetry).
+//
+// Each mode-sample reads 16 bytes of FP64 amplitude and nothing is reused across samples, so in
+// mixed precision the kernel is bound by HBM bandwidth (FP64 arithmetic throughout is bound by
+// the FP64 pipe instead).  One warp per sample: lanes stride over the modes (coalesced reads of
+// the [sample][mode] arrays, several loads in flight per lane), each lane forms its modes'
+// exponentials from the sample's reduced phases (FP64 reduction of Phi_phi and Phi_r modulo 2 pi,
+// then the sine and cosine of the reduced integer combination), and the warp reduces its partial
+// sums with shuffles.
+#include "fewsum_internal.h"
+#include "harmonics.cuh"
+#include "phase_eval.cuh"
+
+namespace fewsum {
+
+// Per-mode constants in the arithmetic type of the path: Y+ and Y- of the mode, and m, n.
+template <typename T>
+struct ModeConst {
+    T ypr, ypi, ymr, ymi;
+    T m, n;
+};
+
+template <typename T>
+__global__ void k_mode_consts(const int *__restrict__ l, const int *__restrict__ m,
+                              const int *__restrict__ n, int N, double theta, double phi,
+                              ModeConst<T> *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double2 yp = swsh_m2(l[i], m[i], theta, phi);
+    double2 ym = make_double2(0.0, 0.0);
+    if (m[i] > 0) {
+        ym = swsh_m2(l[i], -m[i], theta, phi);
+        if (l[i] & 1) ym = make_double2(-ym.x, -ym.y);
+    }
+    ModeConst<T> c;
+    c.ypr = (T)yp.x; c.ypi = (T)yp.y; c.ymr = (T)ym.x; c.ymi = (T)ym.y;
+    c.m = (T)m[i]; c.n = (T)n[i];
+    out[i] = c;
+}
+
+// FP64 -> FP32 with round-to-nearest-even, on the integer pipe.  GB300 runs FP64 -> FP32
+// conversions on its narrow FP64 pipe, which would bound this kernel; the bit arithmetic keeps
+// the mixed path on the integer and FP32 pipes.  Magnitudes below 2^-126 flush to zero.
+__device__ __forceinline__ float f64_to_f32(double d)
+{
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+    const unsigned int hi = static_cast<unsigned int>(b >> 32), lo = static_cast<unsigned int>(b);
+    const unsigned int sign = hi & 0x80000000u;
+    const int fe = static_cast<int>((hi >> 20) & 0x7ffu) - 1023 + 127;
+    if (fe <= 0) return __uint_as_float(sign);
+    if (fe >= 255) return __uint_as_float(sign | 0x7f800000u);
+    unsigned int f = sign | (static_cast<unsigned int>(fe) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned int rem = lo & 0x1fffffffu, half = 0x10000000u;
+    if (rem > half || (rem == half && (f & 1u))) f += 1u;  // a carry rounds into the exponent
+    return __uint_as_float(f);
+}
+
+__device__ __forceinline__ double to_t(double v, double) { return v; }
+__device__ __forceinline__ float to_t(double v, float) { return f64_to_f32(v); }
+
+// Nearest integer of |x| < 2^22 by the 1.5 * 2^23 addition (FP32 add pipe); FP64 uses rint.
+__device__ __forceinline__ float round_near(float x)
+{
+    const float k = 12582912.0f;
+    return (x + k) - k;
+}
+__device__ __forceinline__ double round_near(double x) { return rint(x); }
+
+// Exponential of the reduced phase ph (turns, |ph| <= 1/2): FP64 sincospi for the plain path;
+// for the mixed path the SFU sine and cosine of 2 pi ph (|x| <= pi, absolute error below 1e-6).
+__device__ __forceinline__ void expi_turns(double ph, double *s, double *c) { sincospi(2.0 * ph, s, c); }
+__device__ __forceinline__ void expi_turns(float ph, float *s, float *c)
+{
+    __sincosf(6.283185307179586f * ph, s, c);
+}
+
+constexpr int kDirectUnroll = 8;  // amplitude loads in flight per lane before any arithmetic
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_direct(const double *__restrict__ pphi, const double *__restrict__ pr,
+         const double *__restrict__ are, const double *__restrict__ aim, long long ns, int N,
+         const ModeConst<T> *__restrict__ mc, double scale, void *__restrict__ out, int out_c64)
+{
+    const double kInv2Pi = 0.15915494309189533577;
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = warp; i < ns; i += nwarps) {
+        const double xp = reduce_2pi(pphi[i]) * kInv2Pi, xr = reduce_2pi(pr[i]) * kInv2Pi;
+        const T fphi = (T)(xp - rint(xp)), fr = (T)(xr - rint(xr));
+        const double *ar = are + (size_t)i * N, *ai = aim + (size_t)i * N;
+        T hr = 0, hi = 0;
+        for (int j0 = lane; j0 < N; j0 += 32 * kDirectUnroll) {
+            double vr[kDirectUnroll], vi[kDirectUnroll];
+#pragma unroll
+            for (int u = 0; u < kDirectUnroll; ++u) {
+                const int j = j0 + 32 * u;
+                vr[u] = j < N ? __ldcs(ar + j) : 0.0;  // streamed once: evict-first
+                vi[u] = j < N ? __ldcs(ai + j) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < kDirectUnroll; ++u) {
+                const int j = j0 + 32 * u;
+                if (j >= N) break;
+                const ModeConst<T> c = mc[j];
+                const T Ar = to_t(vr[u], T()), Ai = to_t(vi[u], T());
+                T ph = c.m * fphi + c.n * fr;
+                ph -= round_near(ph);
+                T s, co;
+                expi_turns(ph, &s, &co);
+                const T ypr = c.ypr, ypi = c.ypi, ymr = c.ymr, ymi = c.ymi;
+                const T ayr = Ar * ypr - Ai * ypi, ayi = Ar * ypi + Ai * ypr;  // A Y+
+                const T byr = Ar * ymr + Ai * ymi, byi = Ar * ymi - Ai * ymr;  // conj(A) Y-
+                hr += (ayr + byr) * co + (ayi - byi) * s;
+                hi += (ayi + byi) * co - (ayr - byr) * s;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            hr += __shfl_down_sync(0xffffffffu, hr, o);
+            hi += __shfl_down_sync(0xffffffffu, hi, o);
+        }
+        if (lane == 0) {
+            const double vr0 = (double)hr * scale, vi0 = (double)hi * scale;
+            if (out_c64)
+                reinterpret_cast<float2 *>(out)[i] = make_float2((float)vr0, (float)vi0);
+            else
+                reinterpret_cast<double2 *>(out)[i] = make_double2(vr0, vi0);
+        }
+    }
+}
+
+cudaError_t launch_direct(const double *pphi, const double *pr, const double *are,
+                          const double *aim, long long ns, const int *l, const int *m, const int *n,
+                          int N, double theta, double phi, double scale, bool fp64, void *out,
+                          int out_c64, void *mode_consts, int sm_count, cudaStream_t st)
+{
+    const long long want = (ns + 7) / 8;  // 8 warps (samples) per block per round
+    const int grid = (int)(want < (long long)sm_count * 8 ? want : (long long)sm_count * 8);
+    if (fp64) {
+        auto *mc = static_cast<ModeConst<double> *>(mode_consts);
+        k_mode_consts<double><<<(N + 63) / 64, 64, 0, st>>>(l, m, n, N, theta, phi, mc);
+        if (ns > 0)
+            k_direct<double><<<grid, 256, 0, st>>>(pphi, pr, are, aim, ns, N, mc, scale, out, out_c64);
+    } else {
+        auto *mc = static_cast<ModeConst<float> *>(mode_consts);
+        k_mode_consts<float><<<(N + 63) / 64, 64, 0, st>>>(l, m, n, N, theta, phi, mc);
+        if (ns > 0)
+            k_direct<float><<<grid, 256, 0, st>>>(pphi, pr, are, aim, ns, N, mc, scale, out, out_c64);
+    }
+    return cudaGetLastError();
+}
+
+size_t direct_mode_const_bytes(int N) { return sizeof(ModeConst<double>) * (size_t)N; }
+
+}  // namespace fewsum

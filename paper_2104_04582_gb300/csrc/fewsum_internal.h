@@ -123,6 +123,11 @@ cudaError_t launch_phases(const TrajDev &tr, const int *seg_start, double t0, do
 cudaError_t launch_mode_select(const double *amp_re, const double *amp_im, int K, int N,
                                const int *m_dev, double eps, unsigned char *mask, cudaStream_t st);
 int mode_select_max_modes();
+cudaError_t launch_direct(const double *pphi, const double *pr, const double *are,
+                          const double *aim, long long ns, const int *l, const int *m, const int *n,
+                          int N, double theta, double phi, double scale, bool fp64, void *out,
+                          int out_c64, void *mode_consts, int sm_count, cudaStream_t st);
+size_t direct_mode_const_bytes(int N);
 // Maximum resident CTAs per SM of the summation kernel for a configuration (0 if invalid).
 int sum_occupancy(int variant, int samples_per_thread, int threads, int smem_bytes);
 // One-time kernel attribute setup (dynamic shared memory opt-in).

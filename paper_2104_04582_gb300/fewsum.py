@@ -44,7 +44,7 @@ EXPORTED = [
     "few_batch_plan", "few_batch_run", "few_batch_release", "few_sync_status", "few_set_tiles",
     "few_get_tiles", "few_plan_segments", "few_mode_slots", "few_ctx_set_timing",
     "few_last_timing", "few_phase_samples", "few_waveform_noalloc", "few_set_packed",
-    "few_mode_select",
+    "few_mode_select", "few_direct_sum",
 ]
 
 
@@ -122,6 +122,10 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
                                                  _vp, _vp]),
             "few_mode_select": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _ip,
                                                ctypes.c_double, _vp, _vp]),
+            "few_direct_sum": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int64, _ip, _ip, _ip,
+                                              ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_int, _vp, ctypes.c_int,
+                                              _vp]),
             "few_plan_segments": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_int64, _i64p]),
             "few_mode_slots": (ctypes.c_int, [_ip, _ip, _ip, ctypes.c_int, _ip, _ip]),
@@ -302,6 +306,21 @@ def few_mode_select(ctx: int, amp_re, amp_im, m, eps: float, mask, stream: int =
     st = load().few_mode_select(ctx, amp_re.data_ptr(), amp_im.data_ptr(), K, N,
                                 mm.ctypes.data_as(_ip), float(eps), mask.data_ptr(), stream)
     _check("few_mode_select", st)
+
+
+def few_direct_sum(ctx: int, phi_phi, phi_r, amp_re, amp_im, modes, theta: float, phi: float,
+                   out, scale: float = 1.0, prec: int = FEW_MIXED, stream: int = 0) -> None:
+    """Direct summation over dense device arrays (float64 CUDA tensors; amplitudes [Ns, N]) into
+    a complex64/complex128 CUDA tensor `out` [Ns]."""
+    md = _i32(modes).reshape(-1, 3)
+    l, m, n = _i32(md[:, 0]), _i32(md[:, 1]), _i32(md[:, 2])
+    c64 = str(out.dtype) == "torch.complex64"
+    st = load().few_direct_sum(ctx, phi_phi.data_ptr(), phi_r.data_ptr(), amp_re.data_ptr(),
+                               amp_im.data_ptr(), int(phi_phi.shape[0]), l.ctypes.data_as(_ip),
+                               m.ctypes.data_as(_ip), n.ctypes.data_as(_ip), len(l), float(theta),
+                               float(phi), float(scale), int(prec), out.data_ptr(),
+                               1 if c64 else 0, stream)
+    _check("few_direct_sum", st)
 
 
 def few_plan_segments(t_knots, t0: float, dt: float, n_samples: int) -> np.ndarray:
