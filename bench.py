@@ -532,6 +532,21 @@ def run_profile_case(which: str, repeats: int = 3) -> int:
     _build.build()
     prec = F.FEW_FP64 if which == "fp64" else F.FEW_MIXED
     w = W.config2()
+    if which == "direct":
+        # 30,000 samples x 3843 modes of dense FP64 amplitudes (1.8 GB, larger than L2)
+        ts = w.t0 + (np.arange(30000) + 1000000) * w.dt
+        pphi, pr = w.phases_at(ts)
+        A = w.amp_model(ts)
+        dev = [torch.as_tensor(np.ascontiguousarray(a)).cuda() for a in (pphi, pr, A.real, A.imag)]
+        out = torch.empty(len(ts), dtype=torch.complex64, device="cuda")
+        with RT.Context(0) as ctx:
+            for _ in range(repeats):
+                F.few_direct_sum(ctx.handle, *dev, w.modes, w.theta, w.phi, out, 1.0, F.FEW_MIXED,
+                                 RT.current_stream())
+            torch.cuda.synchronize()
+            st = ctx.sync_status()
+        print(json.dumps({"profile_case": which, "repeats": repeats, "status": int(st)}))
+        return 0 if st == F.FEW_OK else 1
     with RT.Context(0) as ctx:
         tr = RT.from_inputs(ctx, w)
         for _ in range(repeats):
@@ -554,7 +569,7 @@ def main():
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--profile-case", choices=["mixed", "fp64"], default=None,
+    ap.add_argument("--profile-case", choices=["mixed", "fp64", "direct"], default=None,
                     help="untimed runs of the benchmark waveform for profiler captures")
     ap.add_argument("--serving", action="store_true",
                     help="run the serving workload instead of the single-waveform benchmark")

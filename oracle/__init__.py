@@ -78,6 +78,8 @@ def _bind(L: ctypes.CDLL) -> ctypes.CDLL:
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp,
                                        ctypes.c_int]
     L.oracle_direct_dense.restype = ctypes.c_int
+    L.oracle_rb_amplitudes.argtypes = [ctypes.c_int] * 3 + [_dp] * 5 + [_dp, _dp, ctypes.c_int]
+    L.oracle_rb_amplitudes.restype = ctypes.c_int
     L.oracle_max_threads.argtypes = []
     L.oracle_max_threads.restype = ctypes.c_int
     return L
@@ -260,6 +262,29 @@ def direct_dense(phi_phi, phi_r, modes, amp_re, amp_im, theta, phi, scale=1.0,
     if rc:
         raise OracleError(f"oracle_direct_dense: status {rc}")
     return out.view(np.complex128)
+
+
+def rb_amplitudes(alpha, basis, norms=None, nthreads=1) -> np.ndarray:
+    """Reduced-basis amplitudes (Sec. 3.E): alpha [M, Nb] complex, basis [Nb, N] complex,
+    optional target norms [M]; returns complex128 [M, N]."""
+    a = np.ascontiguousarray(alpha, dtype=np.complex128)
+    b = np.ascontiguousarray(basis, dtype=np.complex128)
+    if a.ndim != 2 or b.ndim != 2 or a.shape[1] != b.shape[0]:
+        raise ValueError("alpha must be [M, Nb] and basis [Nb, N]")
+    M, Nb = a.shape
+    N = b.shape[1]
+    ar, ai = _d(a.real), _d(a.imag)
+    br, bi = _d(b.real), _d(b.imag)
+    nu = None if norms is None else _d(norms)
+    if nu is not None and nu.shape != (M,):
+        raise ValueError("norms must be [M]")
+    out_re, out_im = np.zeros((M, N)), np.zeros((M, N))
+    rc = lib().oracle_rb_amplitudes(M, Nb, N, _p(ar), _p(ai), _p(br), _p(bi),
+                                    None if nu is None else _p(nu), _p(out_re), _p(out_im),
+                                    int(nthreads))
+    if rc:
+        raise OracleError(f"oracle_rb_amplitudes: status {rc}")
+    return out_re + 1j * out_im
 
 
 def _c(a) -> np.ndarray:

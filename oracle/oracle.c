@@ -16,6 +16,8 @@
  *     given, and the m < 0 partner is added for m > 0 only; the m = 0 modes of the list are
  *     taken literally, since (l,0,n) and (l,0,-n) are separate entries of the 3843-mode grid.
  *   * Sec. 6 overlap/mismatch with S_n = 1 (time-domain form via Parseval).
+ *   * Sec. 3.E (RomanNet): amplitudes from reduced-basis coefficients, A = alpha . B, each
+ *     knot's vector rescaled to a given norm.
  *
  * Spin-weighted spherical harmonics (named a utility in Sec. 3.D; the paper gives no
  * formula): sY_lm(theta,phi) = (-1)^s sqrt((2l+1)/(4 pi)) d^l_{m,-s}(theta) e^{i m phi},
@@ -671,4 +673,59 @@ int oracle_direct_dense(const double *phi_phi, const double *phi_r, int64_t n_sa
     }
     free(ypr); free(ypi); free(ymr); free(ymi);
     return OR_OK;
+}
+
+/*
+ * Reduced-basis amplitudes (Sec. 3.E, RomanNet).  Each knot k carries Nb complex reduced-basis
+ * coefficients alpha_k,j; its N mode amplitudes are the coefficients times the basis,
+ *     A_k,i = sum_j alpha_k,j B_j,i,
+ * and, when target norms nu_k are given, the vector A_k is then rescaled to that Euclidean
+ * norm: A_k <- A_k nu_k / ||A_k||, ||A_k||^2 = sum_i |A_k,i|^2 (a zero vector stays zero).
+ * alpha_re/alpha_im: [M][Nb]; b_re/b_im: [Nb][N]; norms: [M] or NULL; out_re/out_im: [M][N];
+ * all row-major.  Sums are accumulated in long double.
+ */
+int oracle_rb_amplitudes(int M, int Nb, int N, const double *alpha_re, const double *alpha_im,
+                         const double *b_re, const double *b_im, const double *norms,
+                         double *out_re, double *out_im, int nthreads)
+{
+    if (M < 0 || Nb < 1 || N < 1) return OR_ERR_ARG;
+    if (nthreads < 1) nthreads = 1;
+    int rc = OR_OK;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nthreads)
+#endif
+    {
+        long double *rr = malloc(sizeof(long double) * N), *ri = malloc(sizeof(long double) * N);
+        if (!rr || !ri) rc = OR_ERR_ARG;
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+        for (int k = 0; k < M; ++k) {
+            if (!rr || !ri) continue;
+            for (int i = 0; i < N; ++i) {
+                long double sr = 0.0L, si = 0.0L;
+                for (int j = 0; j < Nb; ++j) {
+                    const long double ar = alpha_re[(size_t)k * Nb + j], ai = alpha_im[(size_t)k * Nb + j];
+                    const long double br = b_re[(size_t)j * N + i], bi = b_im[(size_t)j * N + i];
+                    sr += ar * br - ai * bi;
+                    si += ar * bi + ai * br;
+                }
+                rr[i] = sr;
+                ri[i] = si;
+            }
+            long double f = 1.0L;
+            if (norms) {
+                long double nn = 0.0L;
+                for (int i = 0; i < N; ++i) nn += rr[i] * rr[i] + ri[i] * ri[i];
+                f = nn > 0.0L ? (long double)norms[k] / sqrtl(nn) : 0.0L;
+            }
+            for (int i = 0; i < N; ++i) {
+                out_re[(size_t)k * N + i] = (double)(rr[i] * f);
+                out_im[(size_t)k * N + i] = (double)(ri[i] * f);
+            }
+        }
+        free(rr);
+        free(ri);
+    }
+    return rc;
 }

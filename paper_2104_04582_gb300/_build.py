@@ -24,7 +24,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
           f"-I{os.path.join(ROOT, 'include')}", f"-I{CSRC}"]
 SOURCES = ["api.cpp", "spline.cu", "fold.cu", "sum.cu", "noalloc.cu", "select.cu", "direct.cu"]
-HEADERS = ["fewsum_internal.h", "phase_eval.cuh", "harmonics.cuh"]
+HEADERS = ["fewsum_internal.h", "phase_eval.cuh", "harmonics.cuh", "convert.cuh"]
 
 
 def nvcc() -> str:

@@ -15,13 +15,19 @@
 #include "fewsum_internal.h"
 #include "harmonics.cuh"
 #include "phase_eval.cuh"
+#include "convert.cuh"
 
 namespace fewsum {
 
-// Per-mode constants in the arithmetic type of the path: Y+ and Y- of the mode, and m, n.
+// Per-mode constants in the arithmetic type of the path.  With Y+ = -2Y_lm and
+// Y- = (-1)^l -2Y_{l,-m} (zero for m = 0), a mode contributes
+//     A Y+ e^{-i Phi} + conj(A) Y- e^{+i Phi}
+//   = Re A [ (a c + b s) + i (g c - d s) ] + Im A [ (a s - b c) + i (d c + g s) ],
+// c = cos Phi, s = sin Phi, with a = Re(Y+ + Y-), b = Im(Y+ - Y-), g = Im(Y+ + Y-),
+// d = Re(Y+ - Y-).  The record is 16-byte aligned so a lane fetches it in wide loads.
 template <typename T>
-struct ModeConst {
-    T ypr, ypi, ymr, ymi;
+struct alignas(16) ModeConst {
+    T a, b, g, d;
     T m, n;
 };
 
@@ -39,26 +45,10 @@ __global__ void k_mode_consts(const int *__restrict__ l, const int *__restrict__
         if (l[i] & 1) ym = make_double2(-ym.x, -ym.y);
     }
     ModeConst<T> c;
-    c.ypr = (T)yp.x; c.ypi = (T)yp.y; c.ymr = (T)ym.x; c.ymi = (T)ym.y;
+    c.a = (T)(yp.x + ym.x); c.b = (T)(yp.y - ym.y);
+    c.g = (T)(yp.y + ym.y); c.d = (T)(yp.x - ym.x);
     c.m = (T)m[i]; c.n = (T)n[i];
     out[i] = c;
-}
-
-// FP64 -> FP32 with round-to-nearest-even, on the integer pipe.  GB300 runs FP64 -> FP32
-// conversions on its narrow FP64 pipe, which would bound this kernel; the bit arithmetic keeps
-// the mixed path on the integer and FP32 pipes.  Magnitudes below 2^-126 flush to zero.
-__device__ __forceinline__ float f64_to_f32(double d)
-{
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
-    const unsigned int hi = static_cast<unsigned int>(b >> 32), lo = static_cast<unsigned int>(b);
-    const unsigned int sign = hi & 0x80000000u;
-    const int fe = static_cast<int>((hi >> 20) & 0x7ffu) - 1023 + 127;
-    if (fe <= 0) return __uint_as_float(sign);
-    if (fe >= 255) return __uint_as_float(sign | 0x7f800000u);
-    unsigned int f = sign | (static_cast<unsigned int>(fe) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-    const unsigned int rem = lo & 0x1fffffffu, half = 0x10000000u;
-    if (rem > half || (rem == half && (f & 1u))) f += 1u;  // a carry rounds into the exponent
-    return __uint_as_float(f);
 }
 
 __device__ __forceinline__ double to_t(double v, double) { return v; }
@@ -115,11 +105,8 @@ k_direct(const double *__restrict__ pphi, const double *__restrict__ pr,
                 ph -= round_near(ph);
                 T s, co;
                 expi_turns(ph, &s, &co);
-                const T ypr = c.ypr, ypi = c.ypi, ymr = c.ymr, ymi = c.ymi;
-                const T ayr = Ar * ypr - Ai * ypi, ayi = Ar * ypi + Ai * ypr;  // A Y+
-                const T byr = Ar * ymr + Ai * ymi, byi = Ar * ymi - Ai * ymr;  // conj(A) Y-
-                hr += (ayr + byr) * co + (ayi - byi) * s;
-                hi += (ayi + byi) * co - (ayr - byr) * s;
+                hr += Ar * (c.a * co + c.b * s) + Ai * (c.a * s - c.b * co);
+                hi += Ar * (c.g * co - c.d * s) + Ai * (c.d * co + c.g * s);
             }
         }
 #pragma unroll
@@ -142,8 +129,19 @@ cudaError_t launch_direct(const double *pphi, const double *pr, const double *ar
                           int N, double theta, double phi, double scale, bool fp64, void *out,
                           int out_c64, void *mode_consts, int sm_count, cudaStream_t st)
 {
-    const long long want = (ns + 7) / 8;  // 8 warps (samples) per block per round
-    const int grid = (int)(want < (long long)sm_count * 8 ? want : (long long)sm_count * 8);
+    // one wave of resident blocks (8 warps, i.e. 8 samples, per block per round)
+    static int resident[2] = {0, 0};
+    int &rb = resident[fp64 ? 1 : 0];
+    if (rb == 0) {
+        const cudaError_t e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                         &rb, k_direct<double>, 256, 0)
+                                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                         &rb, k_direct<float>, 256, 0);
+        if (e != cudaSuccess) return e;
+        if (rb < 1) rb = 1;
+    }
+    const long long want = (ns + 7) / 8, cap = (long long)sm_count * rb;
+    const int grid = (int)(want < cap ? want : cap);
     if (fp64) {
         auto *mc = static_cast<ModeConst<double> *>(mode_consts);
         k_mode_consts<double><<<(N + 63) / 64, 64, 0, st>>>(l, m, n, N, theta, phi, mc);

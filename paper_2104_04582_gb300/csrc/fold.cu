@@ -20,6 +20,7 @@
 // and the Jacobi polynomial by its three-term recurrence in the degree.
 #include "fewsum_internal.h"
 #include "harmonics.cuh"
+#include "convert.cuh"
 
 namespace fewsum {
 
@@ -108,6 +109,9 @@ cudaError_t launch_ylm(const PlanHdr *hdr_dev, int total_pairs, cudaStream_t st)
     return cudaGetLastError();
 }
 
+__device__ __forceinline__ double cvt(double v, double) { return v; }
+__device__ __forceinline__ float cvt(double v, float) { return f64_to_f32(v); }
+
 template <typename T> struct Slot8;
 template <> struct Slot8<double> {
     __device__ static void store(double *dst, const double (&re)[4], const double (&im)[4])
@@ -160,11 +164,11 @@ __global__ void __launch_bounds__(kFoldThreads) k_fold(const PlanHdr *__restrict
         const int2 code = tr.contrib[c];  // (mode * 2 + kind, harmonic-table index)
         const int i = code.x >> 1, kind = code.x & 1;
         const double2 Yd = W.ylm[code.y];
-        const T yr = (T)Yd.x, yi = (T)Yd.y;
+        const T yr = cvt(Yd.x, T()), yi = cvt(Yd.y, T());
         const double2 *ca = reinterpret_cast<const double2 *>(cs + (size_t)(2 + 2 * i) * 4);
         const double2 r01 = ca[0], r23 = ca[1], i01 = ca[2], i23 = ca[3];
-        const T ar[4] = {(T)r01.x, (T)r01.y, (T)r23.x, (T)r23.y};
-        T ai[4] = {(T)i01.x, (T)i01.y, (T)i23.x, (T)i23.y};
+        const T ar[4] = {cvt(r01.x, T()), cvt(r01.y, T()), cvt(r23.x, T()), cvt(r23.y, T())};
+        T ai[4] = {cvt(i01.x, T()), cvt(i01.y, T()), cvt(i23.x, T()), cvt(i23.y, T())};
         if (kind) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) ai[q] = -ai[q];
@@ -175,7 +179,7 @@ __global__ void __launch_bounds__(kFoldThreads) k_fold(const PlanHdr *__restrict
             im[q] += ar[q] * yi + ai[q] * yr;
         }
     }
-    const T sc = (T)W.scale;
+    const T sc = cvt(W.scale, T());
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         re[q] *= sc;

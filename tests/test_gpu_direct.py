@@ -51,3 +51,28 @@ def test_direct_ragged_sizes(gpu_ctx, N, ns):
     g = _gpu_direct(gpu_ctx, pphi, pr, are[:, idx], aim[:, idx], modes, 0.7, 1.9, F.FEW_FP64)
     o = oracle.direct_dense(pphi, pr, modes, are[:, idx], aim[:, idx], 0.7, 1.9)
     assert rel_l2(g, o) <= FP64_REL_L2
+
+
+def test_direct_mixed_amplitude_range(gpu_ctx):
+    """The mixed path converts FP64 amplitudes to FP32 on the integer pipe (round to nearest
+    even, magnitudes below 2^-126 flushed to zero).  One m = 0 mode at zero phase makes every output
+    sample a single product A_i * -2Y_20, so each conversion branch (zero, below the normal
+    range, boundary magnitudes, exact rounding ties, the whole normal range) is checked sample
+    by sample against the oracle: within FP32 rounding, plus the flush's absolute 2^-126."""
+    rng = np.random.default_rng(20240417)
+    ns = 4096
+    amp = (rng.standard_normal(ns) + 1j * rng.standard_normal(ns)) * 10.0 ** rng.uniform(-37, 37, ns)
+    special = np.array([0.0, -0.0, 1e-39, -3e-42, 2.0 ** -126, -(2.0 ** -126) * (1 - 2.0 ** -30),
+                        2.0 ** -149, 1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24, -(1.0 + 2.0 ** -24),
+                        3.0e38, -2.0 ** 127])
+    amp[:len(special)] = special * (1 + 1j)           # both parts special, same sample
+    amp[len(special):2 * len(special)] = special      # real part special, imaginary part zero
+    are = np.ascontiguousarray(amp.real.reshape(ns, 1))
+    aim = np.ascontiguousarray(amp.imag.reshape(ns, 1))
+    modes = np.array([[2, 0, 0]], dtype=np.int32)
+    zeros = np.zeros(ns)
+    g = _gpu_direct(gpu_ctx, zeros, zeros, are, aim, modes, 0.7, 0.0, F.FEW_MIXED)
+    o = oracle.direct_dense(zeros, zeros, modes, are, aim, 0.7, 0.0)
+    err = np.abs(g.astype(np.complex128) - o)
+    assert np.all(err <= 1e-6 * np.abs(o) + 2.0 ** -126), np.max(err / (np.abs(o) + 1e-300))
+    assert np.all(g[o == 0] == 0)

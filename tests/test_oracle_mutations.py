@@ -44,6 +44,11 @@ MUTATIONS = {
                        "double num = cos(tS) * sin(tK) * cos(pS - pK) + sin(tS) * cos(tK);"),
     "frame_no_pi_shift": ("double fr = -cos(2.0 * psi), fi = sin(2.0 * psi);",
                           "double fr = cos(2.0 * psi), fi = -sin(2.0 * psi);"),
+    "rb_cross_term_sign": ("si += ar * bi + ai * br;", "si += ar * bi - ai * br;"),
+    "rb_conjugated_basis": ("sr += ar * br - ai * bi;", "sr += ar * br + ai * bi;"),
+    "rb_norm_not_rooted": ("(long double)norms[k] / sqrtl(nn)", "(long double)norms[k] / nn"),
+    "rb_basis_row_fixed": ("b_re[(size_t)j * N + i], bi = b_im[(size_t)j * N + i];",
+                           "b_re[(size_t)i], bi = b_im[(size_t)i];"),
     "select_drops_boundary_mode": [("            mask[e[j].i] = 1;\n            if (c >= target) break;",
                                     "            if (c >= target) break;\n            mask[e[j].i] = 1;")],
 }
@@ -138,6 +143,19 @@ def _pins_hold() -> bool:
     Phi = 1 * (2.1e-3 * ts + 0.4) - 2 * (1.7e-3 * ts + 2.9)
     wd = A * _m2y2(1, 0.9, 2.2) * np.exp(-1j * Phi) + np.conj(A) * _m2y2(-1, 0.9, 2.2) * np.exp(1j * Phi)
     if np.max(np.abs(hd - wd)) > 1e-12 * np.max(np.abs(wd)):
+        return False
+    # reduced-basis amplitudes: the hand-worked product, its renormalisation, the Fourier basis
+    ab = np.array([[1 + 2j, 3 - 1j]])
+    Bh = np.array([[1, 1j, 0], [2, 0, -1]], dtype=complex)
+    if not np.array_equal(oracle.rb_amplitudes(ab, Bh), np.array([[7, -2 + 1j, -3 + 1j]])):
+        return False
+    if not np.array_equal(oracle.rb_amplitudes(ab, Bh, norms=[2.0]),
+                          np.array([[1.75, -0.5 + 0.25j, -0.75 + 0.25j]])):
+        return False
+    jj, ii = np.meshgrid(np.arange(5), np.arange(16), indexing="ij")
+    af = rng.normal(size=(2, 5)) + 1j * rng.normal(size=(2, 5))
+    if np.max(np.abs(oracle.rb_amplitudes(af, np.exp(-2j * np.pi * jj * ii / 16))
+                     - np.fft.fft(af, n=16, axis=1))) > 1e-12:
         return False
     # shortcut vs brute force on odd and even l
     w = W.tiny_inputs(3, K=8, n_samples=200)
