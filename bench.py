@@ -52,7 +52,7 @@ def _kernel_source_hash() -> str:
     import hashlib
     d = os.path.join(ROOT, "paper_2104_04582_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("sum.cu", "phase_eval.cuh"):
+    for f in ("sum.cu", "phase_eval.cuh", "async.cuh"):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -52,7 +52,7 @@
 extern "C" {
 #endif
 
-#define FEW_ABI_VERSION 2
+#define FEW_ABI_VERSION 3
 #define FEW_MAX_SLOTS_FP64 1776
 #define FEW_MAX_SLOTS_MIXED 3552
 
@@ -89,6 +89,7 @@ typedef enum few_frame {
 typedef struct few_ctx few_ctx;
 typedef struct few_traj few_traj;
 typedef struct few_batch few_batch;
+typedef struct few_basis few_basis;
 
 /* Human-readable name of a status code (static string, never NULL). */
 const char *few_strerror(few_status s);
@@ -208,6 +209,7 @@ few_status few_waveform(few_ctx *ctx, const few_request *req, void *stream);
  *   (one stream, or events).  Asynchronous on `stream`.
  */
 #define FEW_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define FEW_MAX_BASIS 256  /* reduced-basis size limit of few_basis_create */
 few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req, void *stream);
 
 /*
@@ -253,6 +255,42 @@ few_status few_direct_sum(few_ctx *ctx, const double *phi_phi_dev, const double 
                           const double *amp_re_dev, const double *amp_im_dev, int64_t n_samples,
                           const int *l, const int *m, const int *n, int N, double theta, double phi,
                           double scale, int prec, void *out_dev, int out_c64, void *stream);
+
+/*
+ * Reduced basis of the mode amplitudes (Sec. 3.E, RomanNet): Nb complex vectors B_j over the N
+ * modes of a mode list, so that a knot's amplitudes are A_i = sum_j alpha_j B_j,i.
+ *   b_re, b_im [Nb][N]: row-major (modes contiguous), host (where = FEW_MEM_HOST; copied before
+ *     the call returns) or device memory (FEW_MEM_DEVICE; read on `stream`, must stay valid
+ *     until that work completes).  1 <= Nb <= FEW_MAX_BASIS, N >= 1.
+ * The library keeps an FP64 copy of B, the Gram matrix B B^H (for the renormalisation) and the
+ * split, packed bf16 operand of the tensor-core product, about 16 x Nb x N + 24 x Nb x N bytes.
+ * Asynchronous on `stream`; the handle is usable on any stream ordered after it.
+ * Errors: FEW_ERR_INVALID_ARG, FEW_ERR_LIMIT (Nb too large), FEW_ERR_BUDGET, FEW_ERR_NOMEM,
+ * FEW_ERR_CUDA.
+ */
+few_status few_basis_create(few_ctx *ctx, const double *b_re, const double *b_im, int Nb, int N,
+                            few_mem where, void *stream, few_basis **out);
+
+/* Release a basis (after the device is idle on the work that uses it). */
+few_status few_basis_release(few_ctx *ctx, few_basis *basis);
+
+/*
+ * Mode amplitudes from reduced-basis coefficients (Sec. 3.E): for each of M knots,
+ *   A_k,i = s_k sum_j alpha_k,j B_j,i,  s_k = nu_k / ||alpha_k B|| if norms_dev, else 1,
+ * the renormalisation of the network output to the trajectory's norm (a zero vector stays zero).
+ *   alpha_re_dev, alpha_im_dev [M][Nb], norms_dev [M] (or NULL): device memory.  Target norms
+ *     must be finite and >= 0; others latch FEW_ERR_INVALID_ARG (see few_sync_status).
+ *   amp_re_dev, amp_im_dev [M][N]: device memory, overwritten; the layout few_traj_set_data
+ *     reads (FEW_MEM_DEVICE), so a trajectory's amplitudes can be produced in place.
+ *   prec: FEW_FP64 (complex GEMM on the FP64 pipe) or FEW_MIXED (one real GEMM on the tensor
+ *     cores: bf16 operands split three ways, six partial products, FP32 accumulation; relative
+ *     error near FP32 rounding of the row's largest terms).
+ * Asynchronous on `stream`; scratch (M x 8 bytes, plus about 2.4 x M x Nb x 12 bytes for
+ * FEW_MIXED) comes from the context's pool.  M = 0 is a no-op.
+ */
+few_status few_rb_amplitudes(few_ctx *ctx, const few_basis *basis, const double *alpha_re_dev,
+                             const double *alpha_im_dev, int M, const double *norms_dev, int prec,
+                             double *amp_re_dev, double *amp_im_dev, void *stream);
 
 /* Flags of few_batch_plan. */
 #define FEW_BATCH_REBUILD_SPLINES 1u  /* each run also rebuilds every distinct trajectory's

@@ -102,6 +102,7 @@ struct few_ctx {
     std::unordered_map<void *, size_t> sizes;
     std::set<few_traj *> trajs;
     std::set<few_batch *> batches;
+    std::set<few_basis *> bases;
     PinnedPool pinned;
     int tile_R[2] = {1, 4};
     int tile_T[2] = {256, 256};
@@ -571,6 +572,7 @@ few_status few_ctx_create(few_ctx **out, int device, size_t hbm_budget_bytes)
 
 few_status few_batch_release(few_ctx *ctx, few_batch *b);
 few_status few_traj_release(few_ctx *ctx, few_traj *t);
+few_status few_basis_release(few_ctx *ctx, few_basis *b);
 
 few_status few_ctx_destroy(few_ctx *ctx)
 {
@@ -583,6 +585,8 @@ few_status few_ctx_destroy(few_ctx *ctx)
         for (few_batch *b : bs) few_batch_release(ctx, b);
         auto ts = ctx->trajs;
         for (few_traj *t : ts) few_traj_release(ctx, t);
+        auto rbs = ctx->bases;
+        for (few_basis *b : rbs) few_basis_release(ctx, b);
         cudaStreamSynchronize(ctx->internal);
         for (auto &e : ctx->tev)
             if (e) cudaEventDestroy(e);
@@ -929,6 +933,115 @@ few_status few_direct_sum(few_ctx *ctx, const double *pphi, const double *pr, co
             (void)cudaGetLastError();
             st = FEW_ERR_CUDA;
         }
+    }
+    dev_free(ctx, d, s);
+    return st;
+}
+
+// Reduced basis (Sec. 3.E): FP64 B, its transposed Gram matrix in FP64 and FP32, and the split
+// bf16 operand of the tensor-core product, in one device allocation.
+struct few_basis {
+    few_ctx *ctx = nullptr;
+    int Nb = 0, N = 0;
+    void *dmem = nullptr;
+    const double *bre = nullptr, *bim = nullptr;
+    const double2 *gt64 = nullptr;
+    const float2 *gt32 = nullptr;
+    const unsigned char *bpack = nullptr;
+};
+
+few_status few_basis_create(few_ctx *ctx, const double *b_re, const double *b_im, int Nb, int N,
+                            few_mem where, void *stream, few_basis **out)
+{
+    if (!ctx || !b_re || !b_im || !out || Nb < 1 || N < 1) return FEW_ERR_INVALID_ARG;
+    if (where != FEW_MEM_HOST && where != FEW_MEM_DEVICE) return FEW_ERR_INVALID_ARG;
+    if (Nb > FEW_MAX_BASIS) return FEW_ERR_LIMIT;
+    *out = nullptr;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const RbLayout L = rb_layout(Nb, N, 0);
+    const size_t b_bytes = align_up(sizeof(double) * (size_t)Nb * N, 256);
+    const size_t g64 = align_up(sizeof(double2) * (size_t)Nb * Nb, 256);
+    const size_t g32 = align_up(sizeof(float2) * (size_t)Nb * Nb, 256);
+    void *d = nullptr;
+    few_status st = dev_alloc(ctx, 2 * b_bytes + g64 + g32 + L.bpack_bytes, s, &d);
+    if (st) return st;
+    unsigned char *p = static_cast<unsigned char *>(d);
+    double *bre = reinterpret_cast<double *>(p), *bim = reinterpret_cast<double *>(p + b_bytes);
+    const size_t bytes = sizeof(double) * (size_t)Nb * N;
+    if (where == FEW_MEM_HOST) {
+        st = upload(ctx, bre, b_re, bytes, s);
+        if (!st) st = upload(ctx, bim, b_im, bytes, s);
+    } else if (cudaMemcpyAsync(bre, b_re, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+               cudaMemcpyAsync(bim, b_im, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        st = FEW_ERR_CUDA;
+    }
+    auto *gt64 = reinterpret_cast<double2 *>(p + 2 * b_bytes);
+    auto *gt32 = reinterpret_cast<float2 *>(p + 2 * b_bytes + g64);
+    unsigned char *bpack = p + 2 * b_bytes + g64 + g32;
+    if (!st && launch_rb_basis(bre, bim, Nb, N, gt64, gt32, bpack, ctx->sm_count, s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        st = FEW_ERR_CUDA;
+    }
+    if (st) {
+        dev_free(ctx, d, s);
+        return st;
+    }
+    auto *b = new few_basis;
+    b->ctx = ctx;
+    b->Nb = Nb;
+    b->N = N;
+    b->dmem = d;
+    b->bre = bre;
+    b->bim = bim;
+    b->gt64 = gt64;
+    b->gt32 = gt32;
+    b->bpack = bpack;
+    ctx->bases.insert(b);
+    *out = b;
+    return FEW_OK;
+}
+
+few_status few_basis_release(few_ctx *ctx, few_basis *b)
+{
+    if (!ctx || !b || b->ctx != ctx) return FEW_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    dev_free(ctx, b->dmem, ctx->internal);
+    cudaStreamSynchronize(ctx->internal);
+    (void)cudaGetLastError();
+    ctx->bases.erase(b);
+    delete b;
+    return FEW_OK;
+}
+
+few_status few_rb_amplitudes(few_ctx *ctx, const few_basis *b, const double *are,
+                             const double *aim, int M, const double *nu, int prec, double *ore,
+                             double *oim, void *stream)
+{
+    if (!ctx || !b || b->ctx != ctx || M < 0) return FEW_ERR_INVALID_ARG;
+    if (prec != FEW_FP64 && prec != FEW_MIXED) return FEW_ERR_INVALID_ARG;
+    if (M == 0) return FEW_OK;
+    if (!are || !aim || !ore || !oim) return FEW_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool fp64 = prec == FEW_FP64;
+    const RbLayout L = rb_layout(b->Nb, b->N, M);
+    const size_t sc_bytes = align_up(sizeof(double) * (size_t)M, 256);
+    void *d = nullptr;
+    few_status st = dev_alloc(ctx, sc_bytes + (fp64 ? 0 : L.apack_bytes), s, &d);
+    if (st) return st;
+    unsigned char *p = static_cast<unsigned char *>(d);
+    cudaError_t e = launch_rb(are, aim, M, b->Nb, b->N, nu, fp64, b->bre, b->bim, b->gt64, b->gt32,
+                              b->bpack, reinterpret_cast<double *>(p), p + sc_bytes, ore, oim,
+                              ctx->d_err, ctx->sm_count, s);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        st = FEW_ERR_CUDA;
     }
     dev_free(ctx, d, s);
     return st;

@@ -44,7 +44,8 @@ EXPORTED = [
     "few_batch_plan", "few_batch_run", "few_batch_release", "few_sync_status", "few_set_tiles",
     "few_get_tiles", "few_plan_segments", "few_mode_slots", "few_ctx_set_timing",
     "few_last_timing", "few_phase_samples", "few_waveform_noalloc", "few_set_packed",
-    "few_mode_select", "few_direct_sum",
+    "few_mode_select", "few_direct_sum", "few_basis_create", "few_basis_release",
+    "few_rb_amplitudes",
 ]
 
 
@@ -126,6 +127,11 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
                                               ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_int, _vp, ctypes.c_int,
                                               _vp]),
+            "few_basis_create": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+            "few_basis_release": (ctypes.c_int, [_vp, _vp]),
+            "few_rb_amplitudes": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int,
+                                                 _vp, _vp, _vp]),
             "few_plan_segments": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_int64, _i64p]),
             "few_mode_slots": (ctypes.c_int, [_ip, _ip, _ip, ctypes.c_int, _ip, _ip]),
@@ -321,6 +327,43 @@ def few_direct_sum(ctx: int, phi_phi, phi_r, amp_re, amp_im, modes, theta: float
                                float(phi), float(scale), int(prec), out.data_ptr(),
                                1 if c64 else 0, stream)
     _check("few_direct_sum", st)
+
+
+def few_basis_create(ctx: int, b_re, b_im, stream: int = 0) -> int:
+    """Reduced basis [Nb, N] (real and imaginary parts) from host arrays (copied) or contiguous
+    float64 CUDA tensors (read on `stream`)."""
+    arrs = (b_re, b_im)
+    if all(hasattr(a, "data_ptr") and getattr(a, "is_cuda", False) for a in arrs):
+        for a in arrs:
+            if not a.is_contiguous() or str(a.dtype) != "torch.float64":
+                raise ValueError("device inputs must be contiguous float64 tensors")
+        keep, ptrs, where = arrs, [a.data_ptr() for a in arrs], FEW_MEM_DEVICE
+    else:
+        keep = [_f64(a) for a in arrs]
+        ptrs, where = [a.ctypes.data for a in keep], FEW_MEM_HOST
+    if keep[0].shape != keep[1].shape or len(keep[0].shape) != 2:
+        raise ValueError("basis parts must both be [Nb, N]")
+    Nb, N = int(keep[0].shape[0]), int(keep[0].shape[1])
+    h = _vp()
+    st = load().few_basis_create(ctx, ptrs[0], ptrs[1], Nb, N, where, stream, ctypes.byref(h))
+    del keep
+    _check("few_basis_create", st)
+    return h.value
+
+
+def few_basis_release(ctx: int, basis: int) -> None:
+    _check("few_basis_release", load().few_basis_release(ctx, basis))
+
+
+def few_rb_amplitudes(ctx: int, basis: int, alpha_re, alpha_im, amp_re, amp_im, norms=None,
+                      prec: int = FEW_MIXED, stream: int = 0) -> None:
+    """Amplitudes [M, N] from reduced-basis coefficients [M, Nb] (float64 CUDA tensors), with
+    optional target norms [M]; amp_re/amp_im are overwritten."""
+    M = int(alpha_re.shape[0])
+    st = load().few_rb_amplitudes(ctx, basis, alpha_re.data_ptr(), alpha_im.data_ptr(), M,
+                                  None if norms is None else norms.data_ptr(), int(prec),
+                                  amp_re.data_ptr(), amp_im.data_ptr(), stream)
+    _check("few_rb_amplitudes", st)
 
 
 def few_plan_segments(t_knots, t0: float, dt: float, n_samples: int) -> np.ndarray:

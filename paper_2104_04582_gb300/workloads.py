@@ -306,3 +306,31 @@ def tiny_inputs(seed: int, K: int = 6, n_samples: int = 200, modes: Optional[np.
     if dt is None:
         dt = T / n_samples
     return make_inputs(T, K, dt, modes, seed, name="tiny", n_samples=n_samples)
+
+
+SEEDS["RB"] = 20210414
+
+
+def rb_inputs(M: int, Nb: int = 99, N: int = 3843, seed: int = SEEDS["RB"], n_traj: int = 1):
+    """Reduced-basis amplitude inputs (Sec. 3.E shapes: 99 complex coefficients per knot, 3843
+    modes).  The basis has orthonormal rows (a greedy reduced basis is orthonormalised as it is
+    built); coefficient j has weight exp(-j/20) (the decay of a reduced basis' projections) and
+    drifts smoothly along each of `n_traj` trajectories of M / n_traj knots; the target norms
+    are the coefficient norms times 1 + 1e-3 sin(...), standing in for the fit error between
+    the network output and the trajectory's norm spline.
+    Returns (alpha [M, Nb] complex, basis [Nb, N] complex, norms [M])."""
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal((N, Nb)) + 1j * rng.standard_normal((N, Nb))
+    q, _ = np.linalg.qr(g)
+    basis = np.ascontiguousarray(q.T)
+    w = np.exp(-np.arange(Nb) / 20.0)
+    per = max(1, -(-M // n_traj))
+    x = (np.arange(M) % per) / max(per - 1, 1)  # position along each trajectory, 0..1
+    ph0 = rng.uniform(0.0, 2.0 * math.pi, Nb)
+    rate = rng.uniform(0.5, 3.0, Nb)
+    traj = np.arange(M) // per
+    off = rng.uniform(0.0, 2.0 * math.pi, (n_traj, Nb))[traj]
+    alpha = w * (1.0 + 0.3 * np.sin(2 * math.pi * rate * x[:, None] + off)) \
+        * np.exp(1j * (ph0 + 4.0 * rate * x[:, None]))
+    norms = np.linalg.norm(alpha, axis=1) * (1.0 + 1e-3 * np.sin(7.0 * x + traj))
+    return np.ascontiguousarray(alpha), basis, norms
