@@ -178,6 +178,64 @@ def l2_flush_buffer(torch, dev):
     return torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
 
+def _rb_device_inputs(M, N, n_traj, dev):
+    import torch
+    alpha, basis, nu = W.rb_inputs(M, 99, N, n_traj=n_traj)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev)
+    return (t(alpha.real), t(alpha.imag)), (t(basis.real), t(basis.imag)), t(nu)
+
+
+def bench_rb(ctx, M, N, stream, sh):
+    """Reduced-basis amplitudes for M knots (64 trajectories' worth by default), mixed precision
+    with renormalisation, timed over the whole call; FP64 timed on one trajectory's knots."""
+    import torch
+    from paper_2104_04582_gb300 import fewsum as F
+    dev = torch.device("cuda", torch.cuda.current_device())
+    (are, aim), (bre, bim), nu = _rb_device_inputs(M, N, max(1, M // 100), dev)
+    Nb = int(are.shape[1])
+    h = F.few_basis_create(ctx.handle, bre, bim, sh)
+    ore = torch.empty((M, N), dtype=torch.float64, device=dev)
+    oim = torch.empty_like(ore)
+
+    def timed(m, prec, reps):
+        F.few_rb_amplitudes(ctx.handle, h, are[:m], aim[:m], ore[:m], oim[:m], nu[:m], prec, sh)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(reps)]
+        for a, b_ in evs:
+            a.record(stream)
+            F.few_rb_amplitudes(ctx.handle, h, are[:m], aim[:m], ore[:m], oim[:m], nu[:m], prec, sh)
+            b_.record(stream)
+        torch.cuda.synchronize()
+        return min(a.elapsed_time(b_) for a, b_ in evs)
+
+    ms = timed(M, F.FEW_MIXED, 5)
+    m64 = min(M, 100)
+    ms64 = timed(m64, F.FEW_FP64, 3)
+    if ctx.sync_status() != F.FEW_OK:
+        raise RuntimeError("reduced-basis amplitudes latched an error")
+    F.few_basis_release(ctx.handle, h)
+    peaks = _peaks_file()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    nbytes = 16 * M * N + 16 * M * Nb + 16 * Nb * N + 8 * M  # out, alpha, basis, norms
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    alg_flops = 8.0 * M * Nb * N  # complex product: 4 real multiply-adds per term
+    n_kb = -(-(12 * Nb) // 64)
+    exec_flops = 2.0 * (-(-M // 128) * 128) * (-(-(2 * N) // 256) * 256) * (n_kb * 64)
+    return {"knots": M, "basis": Nb, "modes": N, "prec": "mixed (split bf16 on tcgen05)",
+            "ms": ms, "amplitudes_per_s": M * N / (ms * 1e-3),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": gbs / hbm, "bytes_per_launch": nbytes,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"},
+            "tensor": {"algorithmic_tflops": alg_flops / (ms * 1e-3) / 1e12,
+                       "executed_tflops": exec_flops / (ms * 1e-3) / 1e12,
+                       "executed_flops_per_launch": exec_flops, "peak": bf16,
+                       "frac_executed": exec_flops / (ms * 1e-3) / 1e12 / bf16,
+                       "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)"},
+            "fp64": {"knots": m64, "ms": ms64}}
+
+
 def measure_peaks(dev_index: int):
     """FP32 FMA, FP64 FMA and SFU rates from the probe library (ops/s, FMA = 1 op)."""
     import ctypes
@@ -428,6 +486,13 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                                "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}}
         del d_re, d_im, d_pp, d_pr, d_out
 
+    # reduced-basis amplitudes (Sec. 3.E): 99 coefficients per knot -> 3843 modes, for the knots
+    # of many trajectories at once, renormalised; the output (FP64 amplitudes) is what the
+    # spline build reads
+    rb = None
+    if rank == 0 and args.rb_knots > 0:
+        rb = bench_rb(ctx, args.rb_knots, w.N, stream, sh)
+
     # pipe peaks
     peaks = measure_peaks(local_rank) if rank == 0 and not args.no_probe else {}
 
@@ -437,7 +502,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     return dict(w=w, ms_local=ms_local, step_ms=step_ms, kernel_ms=kernel_ms, last_t=last_t,
                 clocks=clocks, plain=plain, e2e=e2e, peaks=peaks, slots=slots,
                 h_fast=h_fast, h_plain=h_plain, prec=prec, batched=batched, tile=tile,
-                selector=selector, direct=direct)
+                selector=selector, direct=direct, rb=rb)
 
 
 def run_serving(args):
@@ -532,6 +597,22 @@ def run_profile_case(which: str, repeats: int = 3) -> int:
     _build.build()
     prec = F.FEW_FP64 if which == "fp64" else F.FEW_MIXED
     w = W.config2()
+    if which == "rb":
+        # 6400 knots (64 trajectories x 100), 99 coefficients, 3843 modes, mixed, renormalised
+        dev = torch.device("cuda", 0)
+        (are, aim), (bre, bim), nu = _rb_device_inputs(6400, w.N, 64, dev)
+        ore = torch.empty((6400, w.N), dtype=torch.float64, device=dev)
+        oim = torch.empty_like(ore)
+        with RT.Context(0) as ctx:
+            h = F.few_basis_create(ctx.handle, bre, bim, RT.current_stream())
+            for _ in range(repeats):
+                F.few_rb_amplitudes(ctx.handle, h, are, aim, ore, oim, nu, F.FEW_MIXED,
+                                    RT.current_stream())
+            torch.cuda.synchronize()
+            st = ctx.sync_status()
+            F.few_basis_release(ctx.handle, h)
+        print(json.dumps({"profile_case": which, "repeats": repeats, "status": int(st)}))
+        return 0 if st == F.FEW_OK else 1
     if which == "direct":
         # 30,000 samples x 3843 modes of dense FP64 amplitudes (1.8 GB, larger than L2)
         ts = w.t0 + (np.arange(30000) + 1000000) * w.dt
@@ -569,7 +650,9 @@ def main():
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--profile-case", choices=["mixed", "fp64", "direct"], default=None,
+    ap.add_argument("--rb-knots", type=int, default=6400,
+                    help="knots of the reduced-basis amplitude measurement (0: skip)")
+    ap.add_argument("--profile-case", choices=["mixed", "fp64", "direct", "rb"], default=None,
                     help="untimed runs of the benchmark waveform for profiler captures")
     ap.add_argument("--serving", action="store_true",
                     help="run the serving workload instead of the single-waveform benchmark")
@@ -696,6 +779,8 @@ def main():
         line["speedup_vs_plain_fp64"] = res["plain"]["ms_per_step"] / ms
     if res.get("direct"):
         line["direct_sum"] = res["direct"]
+    if res.get("rb"):
+        line["rb_amplitudes"] = res["rb"]
     if res.get("selector"):
         line["mode_selector"] = res["selector"]
     if res.get("batched"):

@@ -1031,7 +1031,7 @@ few_status few_rb_amplitudes(few_ctx *ctx, const few_basis *b, const double *are
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool fp64 = prec == FEW_FP64;
     const RbLayout L = rb_layout(b->Nb, b->N, M);
-    const size_t sc_bytes = align_up(sizeof(double) * (size_t)M, 256);
+    const size_t sc_bytes = align_up(2 * sizeof(double) * (size_t)M, 256);  // scale, then q
     void *d = nullptr;
     few_status st = dev_alloc(ctx, sc_bytes + (fp64 ? 0 : L.apack_bytes), s, &d);
     if (st) return st;

@@ -23,4 +23,16 @@ __device__ __forceinline__ float f64_to_f32(double d)
     return __uint_as_float(f);
 }
 
+// FP32 -> FP64 on the integer pipe: exact for normal floats (rebias the exponent 127 -> 1023,
+// widen the significand); zero and subnormal inputs give a signed zero, inf and nan stay so.
+__device__ __forceinline__ double f32_to_f64(float x)
+{
+    const unsigned int u = __float_as_uint(x), sign = u & 0x80000000u;
+    const unsigned int e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    unsigned int hi = sign | ((e + 896u) << 20) | (m >> 3), lo = m << 29;
+    if (e == 0u) hi = sign, lo = 0u;
+    if (e == 255u) hi = sign | 0x7ff00000u | (m >> 3);
+    return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
+}
+
 }  // namespace fewsum

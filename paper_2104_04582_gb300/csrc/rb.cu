@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 
 #include "async.cuh"
+#include "convert.cuh"
 #include "fewsum_internal.h"
 
 namespace fewsum {
@@ -134,78 +135,114 @@ __global__ void k_rb_pack_b(const double *__restrict__ bre, const double *__rest
 
 // ---- per call -----------------------------------------------------------------------------
 
-// s_k = nu_k / sqrt(sum_j alpha_j sum_l G_jl conj(alpha_l)), one warp per knot, in the
-// arithmetic type T of the path.  A non-finite or negative target norm latches
-// ERRBIT_NONFINITE; a zero quadratic form (alpha_k B = 0) gives s_k = 0.
+// Quadratic form q_k = ||alpha_k B||^2 = sum_j Re(alpha_j t_j), t_j = sum_l G_jl conj(alpha_l), in
+// the arithmetic type T of the path, as a small register-blocked product: a block takes 32 knots
+// and 64 values of j; a thread owns one j for 8 knots, so each Gram entry read from shared memory
+// feeds 8 complex multiply-adds.  Partial sums over j are reduced per warp and added to q (FP64,
+// zeroed beforehand).
+constexpr int kQRows = 32, kQJ = 64, kQL = 16, kQThreads = 256, kQPer = kQRows / (kQThreads / kQJ);
+
 template <typename T, typename C>
-__global__ void k_rb_scale(const double *__restrict__ are, const double *__restrict__ aim, int M,
-                           int Nb, const C *__restrict__ gt, const double *__restrict__ nu,
-                           double *__restrict__ scale, unsigned *__restrict__ err)
+__global__ void __launch_bounds__(kQThreads)
+k_rb_quad(const double *__restrict__ are, const double *__restrict__ aim, int M, int Nb,
+          const C *__restrict__ gt, double *__restrict__ q)
 {
-    extern __shared__ unsigned char rb_scale_smem[];
-    const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T *al = reinterpret_cast<T *>(rb_scale_smem) + (size_t)w * 2 * Nb;  // [re | im] of alpha_k
-    for (int k = blockIdx.x * warps + w; k < M; k += gridDim.x * warps) {
-        for (int j = lane; j < Nb; j += 32) {
-            al[j] = (T)are[(size_t)k * Nb + j];
-            al[Nb + j] = (T)aim[(size_t)k * Nb + j];
+    __shared__ C sg[kQL][kQJ];     // G_jl for a chunk of l, stored [l][j]
+    __shared__ C sa[kQRows][kQL];  // alpha_k,l for the block's knots
+    const int tid = threadIdx.x, jj = tid % kQJ, rg = tid / kQJ;
+    const int j = blockIdx.x * kQJ + jj, k0 = blockIdx.y * kQRows;
+    T tr[kQPer], ti[kQPer];
+#pragma unroll
+    for (int i = 0; i < kQPer; ++i) tr[i] = ti[i] = 0;
+    for (int l0 = 0; l0 < Nb; l0 += kQL) {
+        __syncthreads();
+        for (int e = tid; e < kQL * kQJ; e += kQThreads) {
+            const int l = l0 + e / kQJ, jx = blockIdx.x * kQJ + e % kQJ;
+            sg[e / kQJ][e % kQJ] = (l < Nb && jx < Nb) ? gt[(size_t)l * Nb + jx] : C{};
         }
-        __syncwarp();
-        T q = 0;
-        for (int j = lane; j < Nb; j += 32) {
-            T tr = 0, ti = 0;  // sum_l G_jl conj(alpha_l)
-            for (int l = 0; l < Nb; ++l) {
-                const C g = gt[(size_t)l * Nb + j];
-                const T xr = al[l], xi = al[Nb + l];
-                tr += (T)g.x * xr + (T)g.y * xi;
-                ti += (T)g.y * xr - (T)g.x * xi;
+        for (int e = tid; e < kQRows * kQL; e += kQThreads) {
+            const int r = e / kQL, l = l0 + e % kQL, k = k0 + r;
+            C v{};
+            if (k < M && l < Nb) {
+                v.x = (T)are[(size_t)k * Nb + l];
+                v.y = (T)aim[(size_t)k * Nb + l];
             }
-            q += al[j] * tr - al[Nb + j] * ti;  // Re(alpha_j t_j)
+            sa[r][e % kQL] = v;
         }
-        for (int o = 16; o > 0; o >>= 1) q += __shfl_down_sync(0xffffffffu, q, o);
-        if (lane == 0) {
-            const double v = nu[k];
-            if (!(v >= 0.0) || !isfinite(v)) atomicOr(err, ERRBIT_NONFINITE);
-            scale[k] = q > (T)0 ? v / sqrt((double)q) : 0.0;
+        __syncthreads();
+#pragma unroll 4
+        for (int l = 0; l < kQL; ++l) {
+            const C g = sg[l][jj];
+#pragma unroll
+            for (int i = 0; i < kQPer; ++i) {
+                const C x = sa[rg * kQPer + i][l];
+                tr[i] += g.x * x.x + g.y * x.y;  // G_jl conj(alpha_l)
+                ti[i] += g.y * x.x - g.x * x.y;
+            }
         }
-        __syncwarp();
+    }
+#pragma unroll
+    for (int i = 0; i < kQPer; ++i) {
+        const int k = k0 + rg * kQPer + i;
+        T c = 0;
+        if (k < M && j < Nb) c = (T)are[(size_t)k * Nb + j] * tr[i] - (T)aim[(size_t)k * Nb + j] * ti[i];
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+        if ((tid & 31) == 0 && k < M) atomicAdd(q + k, (double)c);
     }
 }
 
-// Coefficient operand: row k of tile k/128, column c = g * 2Nb + q holds part kPartA[g] of
-// s_k alpha_k,q (real parts for q < Nb, imaginary parts after).  Rows past M are zero.
-__global__ void k_rb_pack_a(const double *__restrict__ are, const double *__restrict__ aim, int M,
-                            int Nb, int n_kb, int m_tiles, const double *__restrict__ scale,
-                            unsigned char *__restrict__ apack)
+// s_k = nu_k / sqrt(q_k) (0 when q_k = 0, i.e. alpha_k B = 0).  A non-finite or negative target
+// norm latches ERRBIT_NONFINITE.
+__global__ void k_rb_norm(const double *__restrict__ q, const double *__restrict__ nu, int M,
+                          double *__restrict__ scale, unsigned *__restrict__ err)
 {
-    const long long chunks = (long long)m_tiles * kRbTileM * n_kb * (kRbTileK / 8);
-    const int Kr = 2 * Nb;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < chunks;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int q8 = (int)(t % (n_kb * (kRbTileK / 8)));
-        const int row = (int)(t / (n_kb * (kRbTileK / 8)));
-        const int c0 = q8 * 8;
-        const double s = (scale && row < M) ? scale[row] : 1.0;
-        uint32_t w[4];
-        for (int e = 0; e < 8; e += 2) {
-            __nv_bfloat16 v[2];
-            for (int h = 0; h < 2; ++h) {
-                const int c = c0 + e + h, g = c / Kr, q = c % Kr;
-                float x = 0.0f;
-                int part = 0;
-                if (g < kRbParts && row < M) {
-                    const double a = q < Nb ? are[(size_t)row * Nb + q] : aim[(size_t)row * Nb + q - Nb];
-                    x = (float)(s * a);
-                    part = kPartA[g];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M) return;
+    const double v = nu[k], qk = q[k];
+    if (!(v >= 0.0) || !isfinite(v)) atomicOr(err, ERRBIT_NONFINITE);
+    scale[k] = qk > 0.0 ? v / sqrt(qk) : 0.0;
+}
+
+// Coefficient operand, one warp per row: row k of tile k/128, column c = g * 2Nb + q holds part
+// kPartA[g] of x_q = s_k alpha_k,q (real parts for q < Nb, imaginary parts after).  The row's
+// x_q are formed once (one FP64 product each, converted on the integer pipe) in shared memory,
+// then the lanes write its 16-byte chunks.  Rows past M are zero.
+constexpr int kRbPackWarps = 8;
+
+__global__ void __launch_bounds__(kRbPackWarps * 32)
+k_rb_pack_a(const double *__restrict__ are, const double *__restrict__ aim, int M, int Nb, int n_kb,
+            int m_tiles, const double *__restrict__ scale, unsigned char *__restrict__ apack)
+{
+    __shared__ float xs[kRbPackWarps][2 * FEW_MAX_BASIS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, Kr = 2 * Nb;
+    float *x = xs[w];
+    const int rows = m_tiles * kRbTileM, chunks = n_kb * (kRbTileK / 8);
+    for (int row = blockIdx.x * kRbPackWarps + w; row < rows; row += gridDim.x * kRbPackWarps) {
+        const bool live = row < M;
+        const double s = (live && scale) ? scale[row] : 1.0;
+        for (int q = lane; q < Kr; q += 32)
+            x[q] = live ? f64_to_f32(s * (q < Nb ? are[(size_t)row * Nb + q] : aim[(size_t)row * Nb + q - Nb]))
+                        : 0.0f;
+        __syncwarp();
+        unsigned char *tile = apack + (size_t)(row / kRbTileM) * n_kb * kRbABytes;
+        for (int q8 = lane; q8 < chunks; q8 += 32) {
+            const int c0 = q8 * 8;
+            uint32_t wv[4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                __nv_bfloat16 v[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = c0 + e + h, g = c / Kr;
+                    v[h] = g < kRbParts ? split_part(x[c - g * Kr], kPartA[g]) : __float2bfloat16_rn(0.0f);
                 }
-                v[h] = split_part(x, part);
+                wv[e / 2] = pack2(v[0], v[1]);
             }
-            w[e / 2] = pack2(v[0], v[1]);
+            *reinterpret_cast<uint4 *>(tile + (size_t)(c0 / kRbTileK) * kRbABytes +
+                                       core_offset(row % kRbTileM, c0 % kRbTileK)) =
+                make_uint4(wv[0], wv[1], wv[2], wv[3]);
         }
-        const int tile = row / kRbTileM, kb = c0 / kRbTileK;
-        unsigned char *blk = apack + ((size_t)tile * n_kb + kb) * kRbABytes;
-        *reinterpret_cast<uint4 *>(blk + core_offset(row % kRbTileM, c0 % kRbTileK)) =
-            make_uint4(w[0], w[1], w[2], w[3]);
+        __syncwarp();
     }
 }
 
@@ -266,29 +303,47 @@ struct RbMmaArgs {
     const unsigned char *apack;  // [m_tiles][n_kb] blocks of kRbABytes
     const unsigned char *bpack;  // [n_tiles][n_kb] blocks of kRbBBytes
     double *out_re, *out_im;     // [M][N]
-    int M, N, n_kb;
+    int M, N, n_kb, m_tiles, n_tiles;
     unsigned *err;
 };
 
-// One CTA per (basis tile, knot tile): thread 0 streams the k-blocks through a kRbStages ring
-// of shared-memory stages and issues the MMAs; then the four warps read the 128 x 256 FP32
-// accumulator from tensor memory (warp w owns lanes 32w..32w+31, i.e. knots) and store FP64.
-__global__ void __launch_bounds__(128, 1) k_rb_mma(RbMmaArgs a)
+constexpr int kRbEpiWarps = 4;
+constexpr int kRbMmaThreads = 64 + 32 * kRbEpiWarps;  // producer warp, MMA warp, epilogue warps
+constexpr int kRbStgPad = 17;                          // staging row pitch (floats)
+constexpr uint32_t kRbStgBytes = kRbEpiWarps * 2 * 32 * kRbStgPad * 4;
+constexpr uint32_t kRbTmemCols = 2 * kRbTileN;         // two accumulator buffers
+
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity)
+{
+    return __all_sync(0xffffffffu, mbar_wait_bounded(bar, parity));
+}
+
+// Persistent: CTA b takes tiles b, b + grid, ... (tile t = knot tile t / n_tiles, basis tile
+// t % n_tiles).  Warp 0 (one lane) streams each tile's k-blocks through a kRbStages ring of
+// shared-memory stages with bulk copies; warp 1 (one lane) issues the MMAs of a tile into one of
+// two tensor-memory accumulators of 256 columns and commits; warps 2-5 drain the other
+// accumulator meanwhile: each reads its 32 lanes (knots) 32 columns at a time, transposes them
+// through shared memory and stores rows of 16 modes as FP64 (two full 128-byte segments per
+// store instruction).  Every wait is bounded; a timeout latches ERRBIT_TIMEOUT and the CTA waits
+// for its copies and MMAs in flight before it frees tensor memory.
+__global__ void __launch_bounds__(kRbMmaThreads, 1) k_rb_mma(RbMmaArgs a)
 {
     extern __shared__ unsigned char rb_mma_smem[];
-    __shared__ __align__(8) uint64_t full[kRbStages], empty[kRbStages], done;
+    __shared__ __align__(8) uint64_t full[kRbStages], empty[kRbStages], tfull[2], tempty[2], drain;
     __shared__ uint32_t tmem_slot;
-    __shared__ int s_abort;
+    __shared__ volatile int s_abort;
+    __shared__ uint32_t s_issued, s_consumed;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nt = blockIdx.x, mt = blockIdx.y;
+    const int total = a.m_tiles * a.n_tiles;
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(rb_mma_smem) + 1023) & ~(uintptr_t)1023);
     unsigned char *sA = base, *sB = base + kRbStages * kRbABytes;
+    float *stg = reinterpret_cast<float *>(base + kRbStages * kRbStageBytes);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_slot)),
-                     "r"((uint32_t)kRbTileN)
+                     "r"(kRbTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -297,85 +352,116 @@ __global__ void __launch_bounds__(128, 1) k_rb_mma(RbMmaArgs a)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(&done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], kRbEpiWarps);
+        }
+        mbar_init(&drain, 1);
         fence_mbar_init();
         s_abort = 0;
+        s_issued = s_consumed = 0;
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    if (tid == 0) {
-        const unsigned char *ga = a.apack + (size_t)mt * a.n_kb * kRbABytes;
-        const unsigned char *gb = a.bpack + (size_t)nt * a.n_kb * kRbBBytes;
-        const int pre = a.n_kb < kRbStages ? a.n_kb : kRbStages;
-        for (int s = 0; s < pre; ++s) {
-            mbar_arrive_expect_tx(&full[s], kRbStageBytes);
-            bulk_g2s(sA + s * kRbABytes, ga + (size_t)s * kRbABytes, kRbABytes, &full[s]);
-            bulk_g2s(sB + s * kRbBBytes, gb + (size_t)s * kRbBBytes, kRbBBytes, &full[s]);
+    if (warp == 0) {
+        if (lane == 0) {  // producer
+            const uint64_t keep = l2_evict_last_policy();  // operands are re-read by other CTAs
+            uint32_t g = 0;
+            for (int t = blockIdx.x; t < total && !s_abort; t += gridDim.x) {
+                const unsigned char *ga = a.apack + (size_t)(t / a.n_tiles) * a.n_kb * kRbABytes;
+                const unsigned char *gb = a.bpack + (size_t)(t % a.n_tiles) * a.n_kb * kRbBBytes;
+                for (int kb = 0; kb < a.n_kb; ++kb, ++g) {
+                    const int s = g % kRbStages;
+                    if (!mbar_wait_bounded(&empty[s], ((g / kRbStages) & 1) ^ 1)) { s_abort = 1; break; }
+                    mbar_arrive_expect_tx(&full[s], kRbStageBytes);
+                    bulk_g2s_hint(sA + s * kRbABytes, ga + (size_t)kb * kRbABytes, kRbABytes, &full[s], keep);
+                    bulk_g2s_hint(sB + s * kRbBBytes, gb + (size_t)kb * kRbBBytes, kRbBBytes, &full[s], keep);
+                }
+            }
+            s_issued = g;
         }
-        int issued = pre, consumed = 0;
-        bool ok = true;
-        for (int kb = 0; kb < a.n_kb; ++kb) {
-            const int s = kb % kRbStages;
-            if (!mbar_wait_bounded(&full[s], (uint32_t)((kb / kRbStages) & 1))) { ok = false; break; }
-            consumed = kb + 1;
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            uint32_t g = 0;
+            int u = 0;
+            for (int t = blockIdx.x; t < total && !s_abort; t += gridDim.x, ++u) {
+                const int b = u & 1;
+                if (!mbar_wait_bounded(&tempty[b], ((u >> 1) & 1) ^ 1)) { s_abort = 1; break; }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * kRbTileN);
+                bool ok = true;
+                for (int kb = 0; kb < a.n_kb; ++kb, ++g) {
+                    const int s = g % kRbStages;
+                    if (!mbar_wait_bounded(&full[s], (g / kRbStages) & 1)) { s_abort = 1; ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(sA + s * kRbABytes), b0 = smem_u32(sB + s * kRbBBytes);
+#pragma unroll
+                    for (int k = 0; k < kRbTileK / 16; ++k)  // K = 16 per MMA: two core matrices
+                        tc_mma(d, smem_desc(a0 + k * 256, 128, 1024), smem_desc(b0 + k * 256, 128, 1024),
+                               kRbIdesc, (uint32_t)((kb | k) != 0));
+                    tc_commit(&empty[s]);
+                }
+                if (!ok) break;
+                tc_commit(&tfull[b]);
+            }
+            s_consumed = g;
+            tc_commit(&drain);  // arrives once every MMA issued above has completed
+        }
+        __syncwarp();
+    } else {  // epilogue
+        const int e = warp - 2, qd = warp & 3;  // a warp reads tensor-memory lanes 32 (warp % 4) ..
+        float *sre = stg + (size_t)e * 2 * 32 * kRbStgPad, *sim = sre + 32 * kRbStgPad;
+        int u = 0;
+        for (int t = blockIdx.x; t < total && !__any_sync(0xffffffffu, s_abort != 0); t += gridDim.x, ++u) {
+            const int b = u & 1;
+            if (!warp_wait(&tfull[b], (u >> 1) & 1)) { s_abort = 1; break; }
             tc_fence_after();
-            const uint32_t a0 = smem_u32(sA + s * kRbABytes), b0 = smem_u32(sB + s * kRbBBytes);
+            const int r0 = (t / a.n_tiles) * kRbTileM + 32 * qd;
+            const int m0 = (t % a.n_tiles) * (kRbTileN / 2);
+            for (int c = 0; c < kRbTileN / 32; ++c) {
+                uint32_t v[32];
+                tc_ld32(tmem + (uint32_t)(b * kRbTileN) + ((uint32_t)(32 * qd) << 16) + (uint32_t)(32 * c), v);
 #pragma unroll
-            for (int k = 0; k < kRbTileK / 16; ++k)  // K = 16 per MMA: two core matrices
-                tc_mma(tmem, smem_desc(a0 + k * 256, 128, 1024), smem_desc(b0 + k * 256, 128, 1024),
-                       kRbIdesc, (uint32_t)((kb | k) != 0));
-            tc_commit(&empty[s]);
-            // refill the stage of the previous k-block once its MMAs have drained
-            const int kp = kb - 1, nk = kp + kRbStages;
-            if (kp >= 0 && nk < a.n_kb) {
-                const int sp = kp % kRbStages;
-                if (!mbar_wait_bounded(&empty[sp], (uint32_t)((kp / kRbStages) & 1))) { ok = false; break; }
-                mbar_arrive_expect_tx(&full[sp], kRbStageBytes);
-                bulk_g2s(sA + sp * kRbABytes, ga + (size_t)nk * kRbABytes, kRbABytes, &full[sp]);
-                bulk_g2s(sB + sp * kRbBBytes, gb + (size_t)nk * kRbBBytes, kRbBBytes, &full[sp]);
-                issued = nk + 1;
-            }
-        }
-        if (!ok) {
-            // let copies already in flight land before the CTA can exit
-            for (int kb = consumed; kb < issued; ++kb)
-                mbar_wait_bounded(&full[kb % kRbStages], (uint32_t)((kb / kRbStages) & 1));
-            s_abort = 1;
-        }
-        tc_commit(&done);
-    }
-    __syncthreads();
-    if (!mbar_wait_bounded(&done, 0)) s_abort = 1;
-    tc_fence_after();
-    __syncthreads();
-    if (!s_abort) {
-        const int row = mt * kRbTileM + warp * 32 + lane;
-        for (int c = 0; c < kRbTileN / 32; ++c) {
-            uint32_t v[32];
-            tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
-            if (row < a.M) {
-                const int i0 = nt * (kRbTileN / 2) + c * 16;
-                double *ore = a.out_re + (size_t)row * a.N, *oim = a.out_im + (size_t)row * a.N;
-#pragma unroll
-                for (int t = 0; t < 16; ++t)
-                    if (i0 + t < a.N) {
-                        ore[i0 + t] = (double)__uint_as_float(v[2 * t]);
-                        oim[i0 + t] = (double)__uint_as_float(v[2 * t + 1]);
+                for (int j = 0; j < 16; ++j) {
+                    sre[lane * kRbStgPad + j] = __uint_as_float(v[2 * j]);
+                    sim[lane * kRbStgPad + j] = __uint_as_float(v[2 * j + 1]);
+                }
+                __syncwarp();
+                const int col = m0 + 16 * c + (lane & 15);
+#pragma unroll 4
+                for (int rr = 0; rr < 16; ++rr) {
+                    const int row = 2 * rr + (lane >> 4), gr = r0 + row;
+                    if (gr < a.M && col < a.N) {
+                        // streamed once: evict-first, so the output does not push the operands out of L2
+                        __stcs(a.out_re + (size_t)gr * a.N + col, f32_to_f64(sre[row * kRbStgPad + (lane & 15)]));
+                        __stcs(a.out_im + (size_t)gr * a.N + col, f32_to_f64(sim[row * kRbStgPad + (lane & 15)]));
                     }
+                }
+                __syncwarp();
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
         }
-    } else if (tid == 0) {
+    }
+
+    __syncthreads();
+    if (!warp_wait(&drain, 0)) s_abort = 1;  // no MMA of this CTA still running
+    if (tid == 0 && s_abort) {
         atomicOr(a.err, ERRBIT_TIMEOUT);
+        for (uint32_t g = s_consumed; g < s_issued; ++g)  // let copies in flight land
+            mbar_wait_bounded(&full[g % kRbStages], (g / kRbStages) & 1);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"((uint32_t)kRbTileN)
+                     "r"(kRbTmemCols)
                      : "memory");
 }
 
@@ -469,16 +555,17 @@ cudaError_t launch_rb(const double *are, const double *aim, int M, int Nb, int N
 {
     if (M == 0) return cudaSuccess;
     const RbLayout L = rb_layout(Nb, N, M);
+    cudaError_t e;
     if (nu) {
-        const int warps = 8;
-        const int blocks = (M + warps - 1) / warps;
-        const int grid = blocks < sm_count * 8 ? blocks : sm_count * 8;
+        double *q = scale + M;  // the caller's scratch holds scale [M] then q [M]
+        e = cudaMemsetAsync(q, 0, sizeof(double) * (size_t)M, st);
+        if (e != cudaSuccess) return e;
+        const dim3 grid((Nb + kQJ - 1) / kQJ, (M + kQRows - 1) / kQRows);
         if (fp64)
-            k_rb_scale<double, double2><<<grid, warps * 32, warps * 2 * Nb * sizeof(double), st>>>(
-                are, aim, M, Nb, gt64, nu, scale, err);
+            k_rb_quad<double, double2><<<grid, kQThreads, 0, st>>>(are, aim, M, Nb, gt64, q);
         else
-            k_rb_scale<float, float2><<<grid, warps * 32, warps * 2 * Nb * sizeof(float), st>>>(
-                are, aim, M, Nb, gt32, nu, scale, err);
+            k_rb_quad<float, float2><<<grid, kQThreads, 0, st>>>(are, aim, M, Nb, gt32, q);
+        k_rb_norm<<<(M + 255) / 256, 256, 0, st>>>(q, nu, M, scale, err);
     }
     const double *sc = nu ? scale : nullptr;
     if (fp64) {
@@ -486,12 +573,16 @@ cudaError_t launch_rb(const double *are, const double *aim, int M, int Nb, int N
         k_rb_fp64<<<grid, 256, 0, st>>>(are, aim, bre, bim, M, Nb, N, sc, ore, oim);
         return cudaGetLastError();
     }
-    k_rb_pack_a<<<sm_count * 8, 256, 0, st>>>(are, aim, M, Nb, L.n_kb, L.m_tiles, sc, apack);
-    const int smem = kRbStages * (int)kRbStageBytes + 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_rb_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int rows = L.m_tiles * kRbTileM;
+    const int pgrid = (rows + kRbPackWarps - 1) / kRbPackWarps;
+    k_rb_pack_a<<<pgrid < sm_count * 8 ? pgrid : sm_count * 8, kRbPackWarps * 32, 0, st>>>(
+        are, aim, M, Nb, L.n_kb, L.m_tiles, sc, apack);
+    const int smem = kRbStages * (int)kRbStageBytes + (int)kRbStgBytes + 1024;
+    e = cudaFuncSetAttribute(k_rb_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    RbMmaArgs args{apack, bpack, ore, oim, M, N, L.n_kb, err};
-    k_rb_mma<<<dim3(L.n_tiles, L.m_tiles), 128, smem, st>>>(args);
+    const int tiles = L.m_tiles * L.n_tiles;
+    RbMmaArgs args{apack, bpack, ore, oim, M, N, L.n_kb, L.m_tiles, L.n_tiles, err};
+    k_rb_mma<<<tiles < sm_count ? tiles : sm_count, kRbMmaThreads, smem, st>>>(args);
     return cudaGetLastError();
 }
 
