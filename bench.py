@@ -41,8 +41,9 @@ WORKLOAD = ("1-yr waveform, dt=10 s (3,155,760 samples), K=100 knots, 3843 modes
             "(l=2..10, m=0..l, n=-30..30), m<0 by symmetry")
 # DRAM bytes (read + write) of one summation launch on this workload, from the ncu capture
 # summarised in profiles/k_sum_mixed_1yr_3843modes.md; used only while the kernel source is the
-# one that was profiled (hash of sum.cu + phase_eval.cuh) and the tile is the profiled one.
-PROFILED_TRAFFIC = {"source_sha256_16": "f0db93fb52c9ad1d", "tile": (4, 256, False), "bytes": 4115200 + 1536}
+# one that was profiled (hash of sum.cu + phase_eval.cuh + async.cuh) and the tile is the
+# profiled one.
+PROFILED_TRAFFIC = {"source_sha256_16": "ea83547a100f196d", "tile": (4, 256, False), "bytes": 4113920 + 256}
 N_SMS = 152
 FP32_LANES_PER_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25
@@ -221,9 +222,9 @@ def bench_rb(ctx, M, N, stream, sh):
     nbytes = 16 * M * N + 16 * M * Nb + 16 * Nb * N + 8 * M  # out, alpha, basis, norms
     gbs = nbytes / (ms * 1e-3) / 1e9
     alg_flops = 8.0 * M * Nb * N  # complex product: 4 real multiply-adds per term
-    n_kb = -(-(12 * Nb) // 64)
+    n_kb = -(-(6 * Nb) // 64)  # three split products of depth 2 Nb
     exec_flops = 2.0 * (-(-M // 128) * 128) * (-(-(2 * N) // 256) * 256) * (n_kb * 64)
-    return {"knots": M, "basis": Nb, "modes": N, "prec": "mixed (split bf16 on tcgen05)",
+    return {"knots": M, "basis": Nb, "modes": N, "prec": "mixed (split fp16 on tcgen05)",
             "ms": ms, "amplitudes_per_s": M * N / (ms * 1e-3),
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                          "frac": gbs / hbm, "bytes_per_launch": nbytes,

@@ -263,7 +263,8 @@ few_status few_direct_sum(few_ctx *ctx, const double *phi_phi_dev, const double 
  *     the call returns) or device memory (FEW_MEM_DEVICE; read on `stream`, must stay valid
  *     until that work completes).  1 <= Nb <= FEW_MAX_BASIS, N >= 1.
  * The library keeps an FP64 copy of B, the Gram matrix B B^H (for the renormalisation) and the
- * split, packed bf16 operand of the tensor-core product, about 16 x Nb x N + 24 x Nb x N bytes.
+ * scaled, split, packed fp16 operand of the tensor-core product, about 16 x Nb x N + 12 x Nb x N
+ * bytes.
  * Asynchronous on `stream`; the handle is usable on any stream ordered after it.
  * Errors: FEW_ERR_INVALID_ARG, FEW_ERR_LIMIT (Nb too large), FEW_ERR_BUDGET, FEW_ERR_NOMEM,
  * FEW_ERR_CUDA.
@@ -283,10 +284,11 @@ few_status few_basis_release(few_ctx *ctx, few_basis *basis);
  *   amp_re_dev, amp_im_dev [M][N]: device memory, overwritten; the layout few_traj_set_data
  *     reads (FEW_MEM_DEVICE), so a trajectory's amplitudes can be produced in place.
  *   prec: FEW_FP64 (complex GEMM on the FP64 pipe) or FEW_MIXED (one real GEMM on the tensor
- *     cores: bf16 operands split three ways, six partial products, FP32 accumulation; relative
- *     error near FP32 rounding of the row's largest terms).
- * Asynchronous on `stream`; scratch (M x 8 bytes, plus about 2.4 x M x Nb x 12 bytes for
- * FEW_MIXED) comes from the context's pool.  M = 0 is a no-op.
+ *     cores: fp16 operands split two ways after exact power-of-two scaling of each knot's row and
+ *     each mode's column, three partial products, FP32 accumulation; error near FP32 rounding of
+ *     the row's and column's largest terms).
+ * Asynchronous on `stream`; scratch (M x 16 bytes, plus about M x Nb x 12 bytes for FEW_MIXED)
+ * comes from the context's pool.  M = 0 is a no-op.
  */
 few_status few_rb_amplitudes(few_ctx *ctx, const few_basis *basis, const double *alpha_re_dev,
                              const double *alpha_im_dev, int M, const double *norms_dev, int prec,

@@ -947,6 +947,7 @@ struct few_basis {
     const double *bre = nullptr, *bim = nullptr;
     const double2 *gt64 = nullptr;
     const float2 *gt32 = nullptr;
+    const int *bexp = nullptr;
     const unsigned char *bpack = nullptr;
 };
 
@@ -964,8 +965,9 @@ few_status few_basis_create(few_ctx *ctx, const double *b_re, const double *b_im
     const size_t b_bytes = align_up(sizeof(double) * (size_t)Nb * N, 256);
     const size_t g64 = align_up(sizeof(double2) * (size_t)Nb * Nb, 256);
     const size_t g32 = align_up(sizeof(float2) * (size_t)Nb * Nb, 256);
+    const size_t ex = align_up(sizeof(int) * (size_t)L.modes_padded, 256);
     void *d = nullptr;
-    few_status st = dev_alloc(ctx, 2 * b_bytes + g64 + g32 + L.bpack_bytes, s, &d);
+    few_status st = dev_alloc(ctx, 2 * b_bytes + g64 + g32 + ex + L.bpack_bytes, s, &d);
     if (st) return st;
     unsigned char *p = static_cast<unsigned char *>(d);
     double *bre = reinterpret_cast<double *>(p), *bim = reinterpret_cast<double *>(p + b_bytes);
@@ -980,8 +982,9 @@ few_status few_basis_create(few_ctx *ctx, const double *b_re, const double *b_im
     }
     auto *gt64 = reinterpret_cast<double2 *>(p + 2 * b_bytes);
     auto *gt32 = reinterpret_cast<float2 *>(p + 2 * b_bytes + g64);
-    unsigned char *bpack = p + 2 * b_bytes + g64 + g32;
-    if (!st && launch_rb_basis(bre, bim, Nb, N, gt64, gt32, bpack, ctx->sm_count, s) != cudaSuccess) {
+    int *bexp = reinterpret_cast<int *>(p + 2 * b_bytes + g64 + g32);
+    unsigned char *bpack = p + 2 * b_bytes + g64 + g32 + ex;
+    if (!st && launch_rb_basis(bre, bim, Nb, N, gt64, gt32, bexp, bpack, ctx->sm_count, s) != cudaSuccess) {
         (void)cudaGetLastError();
         st = FEW_ERR_CUDA;
     }
@@ -998,6 +1001,7 @@ few_status few_basis_create(few_ctx *ctx, const double *b_re, const double *b_im
     b->bim = bim;
     b->gt64 = gt64;
     b->gt32 = gt32;
+    b->bexp = bexp;
     b->bpack = bpack;
     ctx->bases.insert(b);
     *out = b;
@@ -1032,13 +1036,15 @@ few_status few_rb_amplitudes(few_ctx *ctx, const few_basis *b, const double *are
     const bool fp64 = prec == FEW_FP64;
     const RbLayout L = rb_layout(b->Nb, b->N, M);
     const size_t sc_bytes = align_up(2 * sizeof(double) * (size_t)M, 256);  // scale, then q
+    const size_t ex_bytes = fp64 ? 0 : align_up(sizeof(int) * (size_t)L.rows_padded, 256);
     void *d = nullptr;
-    few_status st = dev_alloc(ctx, sc_bytes + (fp64 ? 0 : L.apack_bytes), s, &d);
+    few_status st = dev_alloc(ctx, sc_bytes + ex_bytes + (fp64 ? 0 : L.apack_bytes), s, &d);
     if (st) return st;
     unsigned char *p = static_cast<unsigned char *>(d);
     cudaError_t e = launch_rb(are, aim, M, b->Nb, b->N, nu, fp64, b->bre, b->bim, b->gt64, b->gt32,
-                              b->bpack, reinterpret_cast<double *>(p), p + sc_bytes, ore, oim,
-                              ctx->d_err, ctx->sm_count, s);
+                              b->bexp, b->bpack, reinterpret_cast<double *>(p),
+                              reinterpret_cast<int *>(p + sc_bytes), p + sc_bytes + ex_bytes, ore,
+                              oim, ctx->d_err, ctx->sm_count, s);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         st = FEW_ERR_CUDA;

@@ -130,17 +130,17 @@ cudaError_t launch_direct(const double *pphi, const double *pr, const double *ar
 size_t direct_mode_const_bytes(int N);
 // Reduced-basis amplitudes (rb.cu): tile counts of the packed tensor-core operands.
 struct RbLayout {
-    int n_kb = 0, n_tiles = 0, m_tiles = 0;
+    int n_kb = 0, n_tiles = 0, m_tiles = 0, modes_padded = 0, rows_padded = 0;
     size_t bpack_bytes = 0, apack_bytes = 0;
 };
 RbLayout rb_layout(int Nb, int N, int M);
 cudaError_t launch_rb_basis(const double *bre, const double *bim, int Nb, int N, double2 *gt64,
-                            float2 *gt32, unsigned char *bpack, int sm_count, cudaStream_t st);
+                            float2 *gt32, int *bexp, unsigned char *bpack, int sm_count, cudaStream_t st);
 cudaError_t launch_rb(const double *are, const double *aim, int M, int Nb, int N, const double *nu,
                       bool fp64, const double *bre, const double *bim, const double2 *gt64,
-                      const float2 *gt32, const unsigned char *bpack, double *scale,
-                      unsigned char *apack, double *ore, double *oim, unsigned *err, int sm_count,
-                      cudaStream_t st);
+                      const float2 *gt32, const int *bexp, const unsigned char *bpack, double *scale,
+                      int *aexp, unsigned char *apack, double *ore, double *oim, unsigned *err,
+                      int sm_count, cudaStream_t st);
 // Maximum resident CTAs per SM of the summation kernel for a configuration (0 if invalid).
 int sum_occupancy(int variant, int samples_per_thread, int threads, int smem_bytes);
 // One-time kernel attribute setup (dynamic shared memory opt-in).

@@ -11,17 +11,21 @@
 // Mixed path: the complex product as one real GEMM on the tcgen05 tensor cores,
 //     [Re A_i, Im A_i] = sum_q a_q Bhat_q,(2i, 2i+1),  a = [Re(s alpha) | Im(s alpha)] (2 Nb),
 //     Bhat_q,2i = (Re B_qi | -Im B_qi),  Bhat_q,2i+1 = (Im B_qi | Re B_qi),
-// in bf16 with FP32 accumulation in tensor memory.  To keep FP32 accuracy every operand is split
-// into three bf16 parts x = hi + mid + lo (8 significant bits each) and the six products of
-// order <= 2^-16 (hi.hi, hi.mid, mid.hi, hi.lo, mid.mid, lo.hi) are laid side by side along K,
-// so one GEMM of depth 6 x 2 Nb sums them all.
+// in fp16 with FP32 accumulation in tensor memory.  To keep near-FP32 accuracy every operand is
+// split into two fp16 parts x = hi + lo (11 significant bits each) and the three products of
+// order <= 2^-11 (hi.hi, hi.lo, lo.hi) are laid side by side along K, so one GEMM of depth
+// 3 x 2 Nb sums them all.  fp16's narrow exponent range is handled by exact power-of-two
+// scaling: each knot's coefficient row and each mode's basis column are scaled so that their
+// largest magnitude lies in [2^14, 2^15) before the split, and the epilogue multiplies the
+// accumulator back by both inverse powers.  An entry far below its row or column maximum keeps
+// an absolute error near 2^-24 of that maximum.
 //
 // Operands are packed once into the canonical K-major layout without swizzle that the tensor
-// core's shared-memory descriptors read: 8 x 8 bf16 "core matrices" of 16-byte rows, core
+// core's shared-memory descriptors read: 8 x 8 fp16 "core matrices" of 16-byte rows, core
 // matrices adjacent in K 128 bytes apart, 8-row groups 1024 bytes apart.  A k-block of 64
 // columns of a 128-row (A) or 256-row (B) tile is one contiguous 16 / 32 KB block in global
 // memory, so each pipeline stage is filled by two bulk asynchronous copies.
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "async.cuh"
 #include "convert.cuh"
@@ -31,17 +35,18 @@ namespace fewsum {
 
 constexpr int kRbTileM = 128;   // knots per tile: tensor-memory lanes
 constexpr int kRbTileN = 256;   // real output columns per tile: 128 modes, re/im interleaved
-constexpr int kRbTileK = 64;    // bf16 columns per k-block: 128 bytes per row
-constexpr int kRbStages = 4;    // shared-memory pipeline depth
-constexpr int kRbParts = 6;     // split products laid along K
+constexpr int kRbTileK = 64;    // fp16 columns per k-block: 128 bytes per row
+constexpr int kRbStages = 3;    // shared-memory pipeline depth
+constexpr int kRbParts = 3;     // split products laid along K
 constexpr uint32_t kRbABytes = kRbTileM * kRbTileK * 2;  // 16 KB
 constexpr uint32_t kRbBBytes = kRbTileN * kRbTileK * 2;  // 32 KB
 constexpr uint32_t kRbStageBytes = kRbABytes + kRbBBytes;
 
-// Which bf16 part of the A (coefficient) and B (basis) operand each K segment holds, so that
-// segment g multiplies A part kPartA[g] by B part kPartB[g] (0 = hi, 1 = mid, 2 = lo).
-__constant__ int kPartA[kRbParts] = {0, 0, 1, 0, 1, 2};
-__constant__ int kPartB[kRbParts] = {0, 1, 0, 2, 1, 0};
+// Which fp16 part of the A (coefficient) and B (basis) operand each K segment holds, so that
+// segment g multiplies A part kPartA[g] by B part kPartB[g] (0 = hi, 1 = lo).
+__constant__ int kPartA[kRbParts] = {0, 0, 1};
+__constant__ int kPartB[kRbParts] = {0, 1, 0};
+constexpr int kRbMaxExp = 100;  // bound on the power-of-two scaling exponents
 
 __host__ __device__ constexpr uint32_t core_offset(int r, int c)
 {
@@ -49,19 +54,27 @@ __host__ __device__ constexpr uint32_t core_offset(int r, int c)
            (uint32_t)(c & 7) * 2u;
 }
 
-__device__ __forceinline__ __nv_bfloat16 split_part(float x, int part)
+__device__ __forceinline__ __half split_part(float x, int part)
 {
-    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+    const __half hi = __float2half_rn(x);
     if (part == 0) return hi;
-    const float r1 = x - __bfloat162float(hi);  // exact: x and hi share the leading bits
-    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-    if (part == 1) return mid;
-    return __float2bfloat16_rn(r1 - __bfloat162float(mid));
+    return __float2half_rn(x - __half2float(hi));  // the difference is exact in FP32
 }
 
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b)
+__device__ __forceinline__ uint32_t pack2(__half a, __half b)
 {
-    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+    return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+
+// 2^e as a float, |e| <= kRbMaxExp.
+__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(127 + e) << 23); }
+
+// Exponent e with m 2^e in [2^14, 2^15) for m > 0 (0 for m = 0), clamped to +-kRbMaxExp.
+__device__ __forceinline__ int scale_exp(float m)
+{
+    if (!(m > 0.0f)) return 0;
+    const int e = 14 - (int)((__float_as_uint(m) >> 23) & 0xffu) + 127;
+    return e > kRbMaxExp ? kRbMaxExp : (e < -kRbMaxExp ? -kRbMaxExp : e);
 }
 
 // ---- basis set-up -------------------------------------------------------------------------
@@ -95,11 +108,26 @@ __global__ void k_rb_gram(const double *__restrict__ bre, const double *__restri
     }
 }
 
-// Basis operand of the real GEMM, split and packed: row n' of tile n'/256 is real output column
-// n' (mode n'/2, real part for even n', imaginary for odd); column c = g * 2Nb + q holds part
-// kPartB[g] of Bhat_q,n'.  Rows past 2N and columns past 6 x 2Nb are zero.
+// Scaling exponent of each mode's basis column: bexp[i] puts max_j max(|Re B_ji|, |Im B_ji|)
+// into [2^14, 2^15); padded modes get 0.
+__global__ void k_rb_bexp(const double *__restrict__ bre, const double *__restrict__ bim, int Nb,
+                          int N, int n_modes_padded, int *__restrict__ bexp)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_modes_padded) return;
+    double m = 0.0;
+    if (i < N)
+        for (int j = 0; j < Nb; ++j)
+            m = fmax(m, fmax(fabs(bre[(size_t)j * N + i]), fabs(bim[(size_t)j * N + i])));
+    bexp[i] = scale_exp((float)m);
+}
+
+// Basis operand of the real GEMM, scaled, split and packed: row n' of tile n'/256 is real output
+// column n' (mode n'/2, real part for even n', imaginary for odd); column c = g * 2Nb + q holds
+// part kPartB[g] of 2^bexp[n'/2] Bhat_q,n'.  Rows past 2N and columns past 3 x 2Nb are zero.
 __global__ void k_rb_pack_b(const double *__restrict__ bre, const double *__restrict__ bim, int Nb,
-                            int N, int n_kb, int n_tiles, unsigned char *__restrict__ bpack)
+                            int N, int n_kb, int n_tiles, const int *__restrict__ bexp,
+                            unsigned char *__restrict__ bpack)
 {
     const long long chunks = (long long)n_tiles * kRbTileN * n_kb * (kRbTileK / 8);
     const int Kr = 2 * Nb;
@@ -110,7 +138,7 @@ __global__ void k_rb_pack_b(const double *__restrict__ bre, const double *__rest
         const int c0 = q8 * 8;
         uint32_t w[4];
         for (int e = 0; e < 8; e += 2) {
-            __nv_bfloat16 v[2];
+            __half v[2];
             for (int h = 0; h < 2; ++h) {
                 const int c = c0 + e + h, g = c / Kr, q = c % Kr;
                 float x = 0.0f;
@@ -119,7 +147,8 @@ __global__ void k_rb_pack_b(const double *__restrict__ bre, const double *__rest
                     const int i = row >> 1, j = q % Nb;
                     const bool imag_out = row & 1, from_im = q >= Nb;
                     const double br = bre[(size_t)j * N + i], bi = bim[(size_t)j * N + i];
-                    x = (float)(imag_out ? (from_im ? br : bi) : (from_im ? -bi : br));
+                    const double v = imag_out ? (from_im ? br : bi) : (from_im ? -bi : br);
+                    x = (float)ldexp(v, bexp[i]);
                     part = kPartB[g];
                 }
                 v[h] = split_part(x, part);
@@ -137,47 +166,54 @@ __global__ void k_rb_pack_b(const double *__restrict__ bre, const double *__rest
 
 // Quadratic form q_k = ||alpha_k B||^2 = sum_j Re(alpha_j t_j), t_j = sum_l G_jl conj(alpha_l), in
 // the arithmetic type T of the path, as a small register-blocked product: a block takes 32 knots
-// and 64 values of j; a thread owns one j for 8 knots, so each Gram entry read from shared memory
-// feeds 8 complex multiply-adds.  Partial sums over j are reduced per warp and added to q (FP64,
-// zeroed beforehand).
-constexpr int kQRows = 32, kQJ = 64, kQL = 16, kQThreads = 256, kQPer = kQRows / (kQThreads / kQJ);
+// and 64 values of j, l advancing in chunks of 64 staged in (dynamic) shared memory; a thread owns
+// 4 knots x 2 values of j (j and j + 32), so 6 shared-memory reads feed 16 complex multiply-adds.
+// Partial sums over j are reduced per warp and added to q (FP64, zeroed beforehand).
+constexpr int kQRows = 32, kQJ = 64, kQL = 64, kQThreads = 256, kQPer = 4;
+
+template <typename C>
+constexpr int rb_quad_smem() { return (kQL * kQJ + kQRows * kQL) * (int)sizeof(C); }
 
 template <typename T, typename C>
 __global__ void __launch_bounds__(kQThreads)
 k_rb_quad(const double *__restrict__ are, const double *__restrict__ aim, int M, int Nb,
           const C *__restrict__ gt, double *__restrict__ q)
 {
-    __shared__ C sg[kQL][kQJ];     // G_jl for a chunk of l, stored [l][j]
-    __shared__ C sa[kQRows][kQL];  // alpha_k,l for the block's knots
-    const int tid = threadIdx.x, jj = tid % kQJ, rg = tid / kQJ;
-    const int j = blockIdx.x * kQJ + jj, k0 = blockIdx.y * kQRows;
-    T tr[kQPer], ti[kQPer];
+    extern __shared__ __align__(16) unsigned char rb_quad_smem_raw[];
+    C(*sg)[kQJ] = reinterpret_cast<C(*)[kQJ]>(rb_quad_smem_raw);                       // G_jl [l][j]
+    C(*sa)[kQL] = reinterpret_cast<C(*)[kQL]>(rb_quad_smem_raw + kQL * kQJ * sizeof(C));  // alpha
+    const int tid = threadIdx.x, jl = tid & 31, rg = tid >> 5;  // rg: knots 4 rg .. 4 rg + 3
+    const int j0 = blockIdx.x * kQJ + jl, k0 = blockIdx.y * kQRows;
+    T tr[kQPer][2], ti[kQPer][2];
 #pragma unroll
-    for (int i = 0; i < kQPer; ++i) tr[i] = ti[i] = 0;
+    for (int i = 0; i < kQPer; ++i) tr[i][0] = tr[i][1] = ti[i][0] = ti[i][1] = 0;
     for (int l0 = 0; l0 < Nb; l0 += kQL) {
+        const int lc = Nb - l0 < kQL ? Nb - l0 : kQL;
         __syncthreads();
-        for (int e = tid; e < kQL * kQJ; e += kQThreads) {
+        for (int e = tid; e < lc * kQJ; e += kQThreads) {
             const int l = l0 + e / kQJ, jx = blockIdx.x * kQJ + e % kQJ;
-            sg[e / kQJ][e % kQJ] = (l < Nb && jx < Nb) ? gt[(size_t)l * Nb + jx] : C{};
+            sg[e / kQJ][e % kQJ] = jx < Nb ? gt[(size_t)l * Nb + jx] : C{};
         }
-        for (int e = tid; e < kQRows * kQL; e += kQThreads) {
-            const int r = e / kQL, l = l0 + e % kQL, k = k0 + r;
+        for (int e = tid; e < kQRows * lc; e += kQThreads) {
+            const int r = e / lc, l = l0 + e % lc, k = k0 + r;
             C v{};
-            if (k < M && l < Nb) {
+            if (k < M) {
                 v.x = (T)are[(size_t)k * Nb + l];
                 v.y = (T)aim[(size_t)k * Nb + l];
             }
-            sa[r][e % kQL] = v;
+            sa[r][e % lc] = v;
         }
         __syncthreads();
-#pragma unroll 4
-        for (int l = 0; l < kQL; ++l) {
-            const C g = sg[l][jj];
+#pragma unroll 2
+        for (int l = 0; l < lc; ++l) {
+            const C g0 = sg[l][jl], g1 = sg[l][jl + 32];
 #pragma unroll
             for (int i = 0; i < kQPer; ++i) {
                 const C x = sa[rg * kQPer + i][l];
-                tr[i] += g.x * x.x + g.y * x.y;  // G_jl conj(alpha_l)
-                ti[i] += g.y * x.x - g.x * x.y;
+                tr[i][0] += g0.x * x.x + g0.y * x.y;  // G_jl conj(alpha_l)
+                ti[i][0] += g0.y * x.x - g0.x * x.y;
+                tr[i][1] += g1.x * x.x + g1.y * x.y;
+                ti[i][1] += g1.y * x.x - g1.x * x.y;
             }
         }
     }
@@ -185,9 +221,14 @@ k_rb_quad(const double *__restrict__ are, const double *__restrict__ aim, int M,
     for (int i = 0; i < kQPer; ++i) {
         const int k = k0 + rg * kQPer + i;
         T c = 0;
-        if (k < M && j < Nb) c = (T)are[(size_t)k * Nb + j] * tr[i] - (T)aim[(size_t)k * Nb + j] * ti[i];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = j0 + 32 * h;
+            if (k < M && j < Nb)
+                c += (T)are[(size_t)k * Nb + j] * tr[i][h] - (T)aim[(size_t)k * Nb + j] * ti[i][h];
+        }
         for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-        if ((tid & 31) == 0 && k < M) atomicAdd(q + k, (double)c);
+        if (jl == 0 && k < M) atomicAdd(q + k, (double)c);
     }
 }
 
@@ -204,14 +245,16 @@ __global__ void k_rb_norm(const double *__restrict__ q, const double *__restrict
 }
 
 // Coefficient operand, one warp per row: row k of tile k/128, column c = g * 2Nb + q holds part
-// kPartA[g] of x_q = s_k alpha_k,q (real parts for q < Nb, imaginary parts after).  The row's
-// x_q are formed once (one FP64 product each, converted on the integer pipe) in shared memory,
-// then the lanes write its 16-byte chunks.  Rows past M are zero.
+// kPartA[g] of 2^aexp[k] x_q, x_q = s_k alpha_k,q (real parts for q < Nb, imaginary parts after).
+// The row's x_q are formed once (one FP64 product each, converted on the integer pipe) in shared
+// memory, its largest magnitude sets aexp[k], then the lanes write its 16-byte chunks.  Rows past
+// M are zero.
 constexpr int kRbPackWarps = 8;
 
 __global__ void __launch_bounds__(kRbPackWarps * 32)
 k_rb_pack_a(const double *__restrict__ are, const double *__restrict__ aim, int M, int Nb, int n_kb,
-            int m_tiles, const double *__restrict__ scale, unsigned char *__restrict__ apack)
+            int m_tiles, const double *__restrict__ scale, unsigned char *__restrict__ apack,
+            int *__restrict__ aexp)
 {
     __shared__ float xs[kRbPackWarps][2 * FEW_MAX_BASIS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, Kr = 2 * Nb;
@@ -220,23 +263,30 @@ k_rb_pack_a(const double *__restrict__ are, const double *__restrict__ aim, int 
     for (int row = blockIdx.x * kRbPackWarps + w; row < rows; row += gridDim.x * kRbPackWarps) {
         const bool live = row < M;
         const double s = (live && scale) ? scale[row] : 1.0;
-        for (int q = lane; q < Kr; q += 32)
+        float mx = 0.0f;
+        for (int q = lane; q < Kr; q += 32) {
             x[q] = live ? f64_to_f32(s * (q < Nb ? are[(size_t)row * Nb + q] : aim[(size_t)row * Nb + q - Nb]))
                         : 0.0f;
+            mx = fmaxf(mx, fabsf(x[q]));
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const int e = scale_exp(mx);
+        const float f = pow2f(e);
+        if (lane == 0) aexp[row] = e;
         __syncwarp();
         unsigned char *tile = apack + (size_t)(row / kRbTileM) * n_kb * kRbABytes;
         for (int q8 = lane; q8 < chunks; q8 += 32) {
             const int c0 = q8 * 8;
             uint32_t wv[4];
 #pragma unroll
-            for (int e = 0; e < 8; e += 2) {
-                __nv_bfloat16 v[2];
+            for (int e2 = 0; e2 < 8; e2 += 2) {
+                __half v[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int c = c0 + e + h, g = c / Kr;
-                    v[h] = g < kRbParts ? split_part(x[c - g * Kr], kPartA[g]) : __float2bfloat16_rn(0.0f);
+                    const int c = c0 + e2 + h, g = c / Kr;
+                    v[h] = g < kRbParts ? split_part(x[c - g * Kr] * f, kPartA[g]) : __float2half_rn(0.0f);
                 }
-                wv[e / 2] = pack2(v[0], v[1]);
+                wv[e2 / 2] = pack2(v[0], v[1]);
             }
             *reinterpret_cast<uint4 *>(tile + (size_t)(c0 / kRbTileK) * kRbABytes +
                                        core_offset(row % kRbTileM, c0 % kRbTileK)) =
@@ -257,10 +307,9 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), bf16 A and B (bits 7-9
-// and 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-constexpr uint32_t kRbIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kRbTileN >> 3) << 17) |
-                              ((uint32_t)(kRbTileM >> 4) << 24);
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), fp16 A and B (bits 7-9
+// and 10-12 = 0), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kRbIdesc = (1u << 4) | ((uint32_t)(kRbTileN >> 3) << 17) | ((uint32_t)(kRbTileM >> 4) << 24);
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -303,11 +352,13 @@ struct RbMmaArgs {
     const unsigned char *apack;  // [m_tiles][n_kb] blocks of kRbABytes
     const unsigned char *bpack;  // [n_tiles][n_kb] blocks of kRbBBytes
     double *out_re, *out_im;     // [M][N]
+    const int *aexp, *bexp;      // scaling exponents of the coefficient rows and basis columns
     int M, N, n_kb, m_tiles, n_tiles;
     unsigned *err;
 };
 
-constexpr int kRbEpiWarps = 4;
+constexpr int kRbEpiWarps = 16;  // four per tensor-memory lane quarter, every fourth 32-column chunk
+constexpr int kRbEpiPerQuarter = kRbEpiWarps / 4;
 constexpr int kRbMmaThreads = 64 + 32 * kRbEpiWarps;  // producer warp, MMA warp, epilogue warps
 constexpr int kRbStgPad = 17;                          // staging row pitch (floats)
 constexpr uint32_t kRbStgBytes = kRbEpiWarps * 2 * 32 * kRbStgPad * 4;
@@ -321,10 +372,10 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity)
 // Persistent: CTA b takes tiles b, b + grid, ... (tile t = knot tile t / n_tiles, basis tile
 // t % n_tiles).  Warp 0 (one lane) streams each tile's k-blocks through a kRbStages ring of
 // shared-memory stages with bulk copies; warp 1 (one lane) issues the MMAs of a tile into one of
-// two tensor-memory accumulators of 256 columns and commits; warps 2-5 drain the other
-// accumulator meanwhile: each reads its 32 lanes (knots) 32 columns at a time, transposes them
-// through shared memory and stores rows of 16 modes as FP64 (two full 128-byte segments per
-// store instruction).  Every wait is bounded; a timeout latches ERRBIT_TIMEOUT and the CTA waits
+// two tensor-memory accumulators of 256 columns and commits; warps 2.. drain the other
+// accumulator meanwhile: warp w reads lanes (knots) 32 (w % 4) .. + 31 and one in
+// kRbEpiPerQuarter chunks of 32 columns, transposes them through shared memory and stores rows of 16 modes as FP64 (two full
+// 128-byte segments per store instruction).  Every wait is bounded; a timeout latches ERRBIT_TIMEOUT and the CTA waits
 // for its copies and MMAs in flight before it frees tensor memory.
 __global__ void __launch_bounds__(kRbMmaThreads, 1) k_rb_mma(RbMmaArgs a)
 {
@@ -336,7 +387,7 @@ __global__ void __launch_bounds__(kRbMmaThreads, 1) k_rb_mma(RbMmaArgs a)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int total = a.m_tiles * a.n_tiles;
     unsigned char *base = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(rb_mma_smem) + 1023) & ~(uintptr_t)1023);
+        (reinterpret_cast<uintptr_t>(rb_mma_smem) + 127) & ~(uintptr_t)127);
     unsigned char *sA = base, *sB = base + kRbStages * kRbABytes;
     float *stg = reinterpret_cast<float *>(base + kRbStages * kRbStageBytes);
 
@@ -414,6 +465,7 @@ __global__ void __launch_bounds__(kRbMmaThreads, 1) k_rb_mma(RbMmaArgs a)
         __syncwarp();
     } else {  // epilogue
         const int e = warp - 2, qd = warp & 3;  // a warp reads tensor-memory lanes 32 (warp % 4) ..
+        const int c_first = e / 4;              // and chunks c_first + kRbEpiPerQuarter i
         float *sre = stg + (size_t)e * 2 * 32 * kRbStgPad, *sim = sre + 32 * kRbStgPad;
         int u = 0;
         for (int t = blockIdx.x; t < total && !__any_sync(0xffffffffu, s_abort != 0); t += gridDim.x, ++u) {
@@ -422,23 +474,25 @@ __global__ void __launch_bounds__(kRbMmaThreads, 1) k_rb_mma(RbMmaArgs a)
             tc_fence_after();
             const int r0 = (t / a.n_tiles) * kRbTileM + 32 * qd;
             const int m0 = (t % a.n_tiles) * (kRbTileN / 2);
-            for (int c = 0; c < kRbTileN / 32; ++c) {
+            const float fa = pow2f(-a.aexp[r0 + lane]);  // undo the row scaling (exact)
+            for (int c = c_first; c < kRbTileN / 32; c += kRbEpiPerQuarter) {
                 uint32_t v[32];
                 tc_ld32(tmem + (uint32_t)(b * kRbTileN) + ((uint32_t)(32 * qd) << 16) + (uint32_t)(32 * c), v);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    sre[lane * kRbStgPad + j] = __uint_as_float(v[2 * j]);
-                    sim[lane * kRbStgPad + j] = __uint_as_float(v[2 * j + 1]);
+                    sre[lane * kRbStgPad + j] = __uint_as_float(v[2 * j]) * fa;
+                    sim[lane * kRbStgPad + j] = __uint_as_float(v[2 * j + 1]) * fa;
                 }
                 __syncwarp();
                 const int col = m0 + 16 * c + (lane & 15);
+                const float fb = pow2f(-a.bexp[col]);  // undo the column scaling (exact)
 #pragma unroll 4
                 for (int rr = 0; rr < 16; ++rr) {
                     const int row = 2 * rr + (lane >> 4), gr = r0 + row;
                     if (gr < a.M && col < a.N) {
                         // streamed once: evict-first, so the output does not push the operands out of L2
-                        __stcs(a.out_re + (size_t)gr * a.N + col, f32_to_f64(sre[row * kRbStgPad + (lane & 15)]));
-                        __stcs(a.out_im + (size_t)gr * a.N + col, f32_to_f64(sim[row * kRbStgPad + (lane & 15)]));
+                        __stcs(a.out_re + (size_t)gr * a.N + col, f32_to_f64(sre[row * kRbStgPad + (lane & 15)] * fb));
+                        __stcs(a.out_im + (size_t)gr * a.N + col, f32_to_f64(sim[row * kRbStgPad + (lane & 15)] * fb));
                     }
                 }
                 __syncwarp();
@@ -533,41 +587,52 @@ RbLayout rb_layout(int Nb, int N, int M)
     L.n_kb = (kRbParts * 2 * Nb + kRbTileK - 1) / kRbTileK;
     L.n_tiles = (2 * N + kRbTileN - 1) / kRbTileN;
     L.m_tiles = (M + kRbTileM - 1) / kRbTileM;
+    L.modes_padded = L.n_tiles * (kRbTileN / 2);
+    L.rows_padded = L.m_tiles * kRbTileM;
     L.bpack_bytes = (size_t)L.n_tiles * L.n_kb * kRbBBytes;
     L.apack_bytes = (size_t)L.m_tiles * L.n_kb * kRbABytes;
     return L;
 }
 
 cudaError_t launch_rb_basis(const double *bre, const double *bim, int Nb, int N, double2 *gt64,
-                            float2 *gt32, unsigned char *bpack, int sm_count, cudaStream_t st)
+                            float2 *gt32, int *bexp, unsigned char *bpack, int sm_count, cudaStream_t st)
 {
     const RbLayout L = rb_layout(Nb, N, 0);
     k_rb_gram<<<Nb * Nb, 128, 0, st>>>(bre, bim, Nb, N, gt64, gt32);
-    k_rb_pack_b<<<sm_count * 8, 256, 0, st>>>(bre, bim, Nb, N, L.n_kb, L.n_tiles, bpack);
+    k_rb_bexp<<<(L.modes_padded + 127) / 128, 128, 0, st>>>(bre, bim, Nb, N, L.modes_padded, bexp);
+    k_rb_pack_b<<<sm_count * 8, 256, 0, st>>>(bre, bim, Nb, N, L.n_kb, L.n_tiles, bexp, bpack);
     return cudaGetLastError();
 }
 
 cudaError_t launch_rb(const double *are, const double *aim, int M, int Nb, int N, const double *nu,
                       bool fp64, const double *bre, const double *bim, const double2 *gt64,
-                      const float2 *gt32, const unsigned char *bpack, double *scale,
-                      unsigned char *apack, double *ore, double *oim, unsigned *err, int sm_count,
-                      cudaStream_t st)
+                      const float2 *gt32, const int *bexp, const unsigned char *bpack, double *scale,
+                      int *aexp, unsigned char *apack, double *ore, double *oim, unsigned *err,
+                      int sm_count, cudaStream_t st)
 {
     if (M == 0) return cudaSuccess;
     const RbLayout L = rb_layout(Nb, N, M);
     cudaError_t e;
+    const double *sc = nullptr;
     if (nu) {
         double *q = scale + M;  // the caller's scratch holds scale [M] then q [M]
         e = cudaMemsetAsync(q, 0, sizeof(double) * (size_t)M, st);
         if (e != cudaSuccess) return e;
         const dim3 grid((Nb + kQJ - 1) / kQJ, (M + kQRows - 1) / kQRows);
-        if (fp64)
-            k_rb_quad<double, double2><<<grid, kQThreads, 0, st>>>(are, aim, M, Nb, gt64, q);
-        else
-            k_rb_quad<float, float2><<<grid, kQThreads, 0, st>>>(are, aim, M, Nb, gt32, q);
+        if (fp64) {
+            e = cudaFuncSetAttribute(k_rb_quad<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     rb_quad_smem<double2>());
+            if (e != cudaSuccess) return e;
+            k_rb_quad<double, double2><<<grid, kQThreads, rb_quad_smem<double2>(), st>>>(are, aim, M, Nb, gt64, q);
+        } else {
+            e = cudaFuncSetAttribute(k_rb_quad<float, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     rb_quad_smem<float2>());
+            if (e != cudaSuccess) return e;
+            k_rb_quad<float, float2><<<grid, kQThreads, rb_quad_smem<float2>(), st>>>(are, aim, M, Nb, gt32, q);
+        }
         k_rb_norm<<<(M + 255) / 256, 256, 0, st>>>(q, nu, M, scale, err);
+        sc = scale;
     }
-    const double *sc = nu ? scale : nullptr;
     if (fp64) {
         dim3 grid((N + kRb64Modes - 1) / kRb64Modes, (M + kRb64Rows - 1) / kRb64Rows);
         k_rb_fp64<<<grid, 256, 0, st>>>(are, aim, bre, bim, M, Nb, N, sc, ore, oim);
@@ -576,12 +641,12 @@ cudaError_t launch_rb(const double *are, const double *aim, int M, int Nb, int N
     const int rows = L.m_tiles * kRbTileM;
     const int pgrid = (rows + kRbPackWarps - 1) / kRbPackWarps;
     k_rb_pack_a<<<pgrid < sm_count * 8 ? pgrid : sm_count * 8, kRbPackWarps * 32, 0, st>>>(
-        are, aim, M, Nb, L.n_kb, L.m_tiles, sc, apack);
-    const int smem = kRbStages * (int)kRbStageBytes + (int)kRbStgBytes + 1024;
+        are, aim, M, Nb, L.n_kb, L.m_tiles, sc, apack, aexp);
+    const int smem = kRbStages * (int)kRbStageBytes + (int)kRbStgBytes + 128;
     e = cudaFuncSetAttribute(k_rb_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int tiles = L.m_tiles * L.n_tiles;
-    RbMmaArgs args{apack, bpack, ore, oim, M, N, L.n_kb, L.m_tiles, L.n_tiles, err};
+    RbMmaArgs args{apack, bpack, ore, oim, aexp, bexp, M, N, L.n_kb, L.m_tiles, L.n_tiles, err};
     k_rb_mma<<<tiles < sm_count ? tiles : sm_count, kRbMmaThreads, smem, st>>>(args);
     return cudaGetLastError();
 }
