@@ -67,8 +67,10 @@ __device__ void frame_angles(double tS, double pS, double tK, double pK, double 
     psi = atan2(ctS * stK * cd - stS * ctK, stK * sd);
 }
 
-// Two threads per (wave, (l, m) pair): one computes Y+, the other Y- (halves the FP64
-// dependency chain each thread waits on).
+// Two threads per (wave, (l, m) pair): one computes Y+, the other Y- (halves the dependency
+// chain each thread waits on).  FP64 plans evaluate the harmonics in FP64; mixed plans, whose
+// folded coefficients are FP32, evaluate them in FP32 (relative error near 1e-7, far below the
+// path's 1e-6 mismatch budget) and stay off GB300's narrow FP64 pipe.  The frame angles are FP64.
 __global__ void __launch_bounds__(kYlmThreads) k_ylm(const PlanHdr *__restrict__ hp)
 {
     const PlanHdr h = *hp;
@@ -86,11 +88,12 @@ __global__ void __launch_bounds__(kYlmThreads) k_ylm(const PlanHdr *__restrict__
     double theta = W.theta, phi = W.phi, psi = 0.0;
     if (W.frame == FEW_FRAME_SSB) frame_angles(W.theta, W.phi, W.theta_K, W.phi_K, theta, phi, psi);
     double2 y = make_double2(0.0, 0.0);
-    if (which == 0) {
-        y = swsh_m2(lm.x, lm.y, theta, phi);
-    } else if (lm.y > 0) {
-        y = swsh_m2(lm.x, -lm.y, theta, phi);
-        if (lm.x & 1) y = make_double2(-y.x, -y.y);
+    const bool fp64 = h.variant == kVariantFp64;
+    const int mm = which == 0 ? lm.y : -lm.y;
+    if (which == 0 || lm.y > 0) {
+        y = fp64 ? swsh_m2_t<double>(lm.x, mm, theta, phi)
+                 : swsh_m2_t<float>(lm.x, mm, (float)theta, (float)phi);
+        if (which == 1 && (lm.x & 1)) y = make_double2(-y.x, -y.y);
     }
     if (W.frame == FEW_FRAME_SSB) {
         double s2, c2;
