@@ -753,7 +753,7 @@ few_status few_traj_set_data(few_ctx *ctx, few_traj *tr, const double *phi_phi, 
     job.block_begin = 0;
     few_status s = upload(ctx, tr->job_dev, &job, sizeof(job), st);
     if (s) return s;
-    const int blocks = (tr->J + kBuildThreads - 1) / kBuildThreads;
+    const int blocks = (tr->J + kBuildSplines - 1) / kBuildSplines;
     tmark(ctx, 0, false, st);
     FEW_CUDA_TRY(launch_build(tr->job_dev, 1, blocks, tr->K, ctx->d_err, st));
     tmark(ctx, 0, true, st);
@@ -1106,7 +1106,7 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
             j.amp_re = tr->src_re;
             j.amp_im = tr->src_im;
             j.block_begin = blocks;
-            blocks += (tr->J + kBuildThreads - 1) / kBuildThreads;
+            blocks += (tr->J + kBuildSplines - 1) / kBuildSplines;
             b->max_knots = std::max(b->max_knots, tr->K);
             jobs.push_back(j);
         }

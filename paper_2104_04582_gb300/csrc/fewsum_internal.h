@@ -33,6 +33,7 @@ enum : int {
 constexpr int kFoldThreads = 128;
 constexpr int kYlmThreads = 16;  // few pairs per block: spreads the FP64 work over SMs
 constexpr int kBuildThreads = 64;
+constexpr int kBuildSplines = kBuildThreads / 2;  // two threads (top and bottom sweep) per spline
 
 // Trajectory-resident data (one per few_traj).
 struct TrajDev {
@@ -44,9 +45,9 @@ struct TrajDev {
     const double *t;       // [K] knot times
     const double *inv_h;   // [S] 1/(t_{k+1}-t_k)
     const double *h;       // [S] t_{k+1}-t_k
-    const double *fac_w;   // [K] forward multipliers of the shared tridiagonal factorization
-    const double *fac_ip;  // [K] inverse pivots
-    const double *fac_up;  // [K] super-diagonal
+    const double *fac_w;   // [K] top-down multipliers w_k (rows 2..m) of the shared twisted factorization
+    const double *fac_ip;  // [K] inverse pivots: top rows < m, bottom rows > m, twist pivot at m
+    const double *fac_up;  // [K] bottom-up multipliers v_k (rows m..K-3)
     double *coef;          // [S][J][4] spline coefficients in u = (t - t_k)/h_k;
                            //   columns 0,1 = Phi_phi, Phi_r (rad),
                            //   column 2+2i / 3+2i = Re / Im A_i

@@ -9,10 +9,19 @@
 //     h_1 s_0 + (h_0 + h_1) s_1 = ((2 h_1 + 3 h_0) h_1 d_0 + h_0^2 d_1) / (h_0 + h_1)
 //     (h_{K-2} + h_{K-3}) s_{K-2} + h_{K-3} s_{K-1}
 //         = (h_{K-2}^2 d_{K-3} + (2 h_{K-3} + 3 h_{K-2}) h_{K-3} d_{K-2}) / (h_{K-3} + h_{K-2}).
-// The matrix depends only on the knots, so it is factorised once per trajectory (k_factor,
-// Thomas elimination without pivoting) and every spline reuses that factorisation: one thread
-// per spline does the forward sweep and back substitution on its own right-hand side.
-// Coefficients are stored in the normalised local variable u = (t - t_k)/h_k in [0, 1]:
+// Substituting the end rows' s_0 and s_{K-1} into rows 1 and K-2 leaves a strictly diagonally
+// dominant tridiagonal system for s_1 .. s_{K-2}:
+//     row 1:    (h_0 + h_1) s_1 + h_0 s_2 = r_1 - R_0,
+//     row K-2:  h_{K-2} s_{K-3} + (h_{K-3} + h_{K-2}) s_{K-2} = r_{K-2} - R_L,
+// (R_0, R_L the end rows' right-hand sides), interior rows as above.  Its matrix depends only on
+// the knots, so it is factorised once per trajectory (k_factor) in twisted form: top-down
+// elimination of rows 1..m and bottom-up elimination of rows K-2..m, m = (K-1)/2, both stable
+// by diagonal dominance.  Every spline reuses that factorisation with two threads: the top one
+// sweeps rows 1..m, the bottom one rows K-2..m, they combine at row m
+//     s_m = (y_m + z_m - rhs_m) / (p_m + q_m - d_m),
+// and substitute away from m in opposite directions, each writing the segments on its side;
+// s_0 and s_{K-1} follow from the end rows.  Coefficients are stored in the normalised local
+// variable u = (t - t_k)/h_k in [0, 1]:
 //     p(u) = y_k + h_k s_k u + (3 D - h_k (2 s_k + s_{k+1})) u^2 + (h_k (s_k + s_{k+1}) - 2 D) u^3,
 // D = y_{k+1} - y_k.  The two phase arrays are fitted in radians as given (their reduction
 // modulo 2 pi happens per segment and per sample in the summation kernel).
@@ -20,34 +29,42 @@
 
 namespace fewsum {
 
-// Shared factorisation of the not-a-knot matrix of one knot grid (single thread; O(K)).
+// Shared twisted factorisation of the reduced not-a-knot matrix of one knot grid (single
+// thread; O(K)).  fac_w[k] = w_k (top rows 2..m), fac_up[k] = v_k (bottom rows m..K-3),
+// fac_ip[k] = 1/p_k (k < m), 1/q_k (k > m), 1/(p_m + q_m - d_m) (k = m).
 __global__ void k_factor(const double *__restrict__ t, int K, double *h, double *inv_h,
                          double *fac_w, double *fac_ip, double *fac_up)
 {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    const int S = K - 1;
+    const int S = K - 1, m = (K - 1) / 2;
     for (int k = 0; k < S; ++k) {
         h[k] = t[k + 1] - t[k];
         inv_h[k] = 1.0 / h[k];
     }
-    // row k: lo_k * s_{k-1} + dg_k * s_k + up_k * s_{k+1}
-    double piv = 0.0;
-    for (int k = 0; k < K; ++k) {
-        double lo, dg, up;
-        if (k == 0) {
-            lo = 0.0; dg = h[1]; up = h[0] + h[1];
-        } else if (k == K - 1) {
-            lo = h[K - 2] + h[K - 3]; dg = h[K - 3]; up = 0.0;
-        } else {
-            lo = h[k]; dg = 2.0 * (h[k - 1] + h[k]); up = h[k - 1];
-        }
-        double w = (k == 0) ? 0.0 : lo / piv;
-        double prev_up = (k == 0) ? 0.0 : fac_up[k - 1];
-        piv = dg - w * prev_up;
+    for (int k = 0; k < K; ++k) fac_w[k] = fac_ip[k] = fac_up[k] = 0.0;
+    // reduced rows 1..K-2: lo_k = h_k (k >= 2), up_k = h_{k-1} (k <= K-3), diagonal dg(k)
+    auto dg = [&](int k) {
+        if (k == 1) return h[0] + h[1];
+        if (k == K - 2) return h[K - 3] + h[K - 2];
+        return 2.0 * (h[k - 1] + h[k]);
+    };
+    double p = dg(1);
+    fac_ip[1] = 1.0 / p;
+    for (int k = 2; k <= m; ++k) {
+        const double w = h[k] / p;
+        p = dg(k) - w * h[k - 2];
         fac_w[k] = w;
-        fac_ip[k] = 1.0 / piv;
-        fac_up[k] = up;
+        fac_ip[k] = 1.0 / p;
     }
+    double q = dg(K - 2);
+    if (K - 2 > m) fac_ip[K - 2] = 1.0 / q;
+    for (int k = K - 3; k >= m; --k) {
+        const double v = h[k - 1] / q;
+        q = dg(k) - v * h[k + 1];
+        fac_up[k] = v;
+        if (k > m) fac_ip[k] = 1.0 / q;
+    }
+    fac_ip[m] = 1.0 / (p + q - dg(m));
 }
 
 cudaError_t launch_factor(const double *t, int K, double *h, double *inv_h, double *fac_w,
@@ -66,16 +83,17 @@ __device__ __forceinline__ double load_y(const BuildJob &jb, int j, int k)
     return ((j - 2) & 1) ? jb.amp_im[idx] : jb.amp_re[idx];
 }
 
-// One thread per spline column.  Jobs are laid out in a flattened grid of column blocks.
-// The sweeps are sequential in k, so each step would wait on its own global load; instead the
-// knot-only arrays (h, 1/h, factorisation) are staged in shared memory and the column values
-// are fetched kChunk knots ahead into registers, so kChunk loads are in flight at once.
+// Two threads per spline column: lane l (< 16) of a warp runs the top sweep and lane l + 16 the
+// bottom sweep of the same column, in one instruction stream (direction and coefficients are
+// per-lane data), so the pair meets at row m without divergence and exchanges its reduced
+// right-hand side with one shuffle.  The knot-only arrays are staged in shared memory and the
+// column values are fetched kChunk rows ahead into registers, so kChunk loads are in flight.
 constexpr int kChunk = 8;
 
 __global__ void __launch_bounds__(kBuildThreads)
 k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
 {
-    extern __shared__ double sk[];  // [5][K]: h, 1/h, w, 1/pivot, up
+    extern __shared__ double sk[];  // [5][K]: h, 1/h, top multipliers, inverse pivots, bottom multipliers
     // job of this block: largest q with jobs[q].block_begin <= blockIdx.x
     int lo = 0, hi = n_jobs - 1;
     const int b = blockIdx.x;
@@ -86,83 +104,107 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
     const BuildJob &jb = jobs[lo];
     const TrajDev &tr = jb.tr;
     const int K = tr.K, J = tr.J;
-    double *h = sk, *ih = sk + K, *fw = sk + 2 * K, *fip = sk + 3 * K, *fup = sk + 4 * K;
+    double *h = sk, *ih = sk + K, *fw = sk + 2 * K, *fip = sk + 3 * K, *fv = sk + 4 * K;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         h[k] = k < K - 1 ? tr.h[k] : 0.0;
         ih[k] = k < K - 1 ? tr.inv_h[k] : 0.0;
         fw[k] = tr.fac_w[k];
         fip[k] = tr.fac_ip[k];
-        fup[k] = tr.fac_up[k];
+        fv[k] = tr.fac_up[k];
     }
     __syncthreads();
-    const int j = (b - jb.block_begin) * kBuildThreads + threadIdx.x;
-    if (j >= J) return;
+    const int lane = threadIdx.x & 31;
+    const bool top = lane < 16;
+    const int j = (b - jb.block_begin) * kBuildSplines + (threadIdx.x >> 5) * 16 + (lane & 15);
+    const bool live = j < J;
+    const int jj = live ? j : 0;  // a column past J computes on column 0 and stores nothing
     double *__restrict__ coef = tr.coef;
     bool finite = true;
+    const int m = (K - 1) / 2;
+    const int dir = top ? 1 : -1, k0 = top ? 1 : K - 2;
+    const int steps = top ? m : K - 1 - m, steps_max = K - 1 - m;
 
-    // forward sweep: r'_k = r_k - w_k r'_{k-1}; r'_k is parked in coef[k][j][1] (k < K-1)
-    double y0 = load_y(jb, j, 0), y1 = load_y(jb, j, 1), y2 = load_y(jb, j, 2);
-    finite &= isfinite(y0) && isfinite(y1) && isfinite(y2);
-    const double d0 = (y1 - y0) * ih[0], d1 = (y2 - y1) * ih[1];
-    double rp = ((2.0 * h[1] + 3.0 * h[0]) * h[1] * d0 + h[0] * h[0] * d1) / (h[0] + h[1]);
-    coef[(size_t)j * 4 + 1] = rp;
-    double dprev = d0;  // d_{k-1}
-    double ycur = y1;   // y_k
-    double dkm3 = d0;   // d_{K-3}, kept for the last row
-    for (int k0 = 1; k0 <= K - 2; k0 += kChunk) {
-        double yn[kChunk];
+    // elimination: acc = rhs_k - mult_k acc along rows k0, k0 + dir, ..., m; the window holds
+    // y_{k - dir} (yb) and y_k (yc)
+    double yb = load_y(jb, jj, k0 - dir), yc = load_y(jb, jj, k0);
+    finite &= isfinite(yb) && isfinite(yc);
+    double acc = 0.0, rend = 0.0, rm = 0.0;
+    for (int i0 = 0; i0 < steps_max; i0 += kChunk) {
+        double ya[kChunk];  // y_{k + dir} for the chunk's rows
 #pragma unroll
         for (int q = 0; q < kChunk; ++q)
-            yn[q] = (k0 + q <= K - 2) ? load_y(jb, j, k0 + q + 1) : 0.0;
+            ya[q] = (i0 + q < steps) ? load_y(jb, jj, k0 + dir * (i0 + q + 1)) : 0.0;
 #pragma unroll
         for (int q = 0; q < kChunk; ++q) {
-            const int k = k0 + q;
-            if (k > K - 2) break;
-            finite &= isfinite(yn[q]);
-            const double dk = (yn[q] - ycur) * ih[k];
-            const double r = 3.0 * (h[k] * dprev + h[k - 1] * dk);
-            rp = r - fw[k] * rp;
-            coef[((size_t)k * J + j) * 4 + 1] = rp;
-            if (k == K - 3) dkm3 = dk;
-            dprev = dk;
-            ycur = yn[q];
+            const int i = i0 + q;
+            if (i >= steps) break;
+            const int k = k0 + dir * i;
+            finite &= isfinite(ya[q]);
+            const double ylo = top ? yb : ya[q], yhi = top ? ya[q] : yb;  // y_{k-1}, y_{k+1}
+            const double dl = (yc - ylo) * ih[k - 1], dr = (yhi - yc) * ih[k];
+            double r = 3.0 * (h[k] * dl + h[k - 1] * dr);
+            if (k == 1) {
+                const double R0 = ((2.0 * h[1] + 3.0 * h[0]) * h[1] * dl + h[0] * h[0] * dr) / (h[0] + h[1]);
+                r -= R0;
+                if (top) rend = R0;
+            }
+            if (k == K - 2) {
+                const double a = h[K - 2], c = h[K - 3];
+                const double RL = (a * a * dl + (2.0 * c + 3.0 * a) * c * dr) / (c + a);
+                r -= RL;
+                if (!top) rend = RL;
+            }
+            if (k == m) rm = r;
+            acc = r - (i == 0 ? 0.0 : (top ? fw[k] : fv[k])) * acc;
+            if (k != m && live) coef[((size_t)k * J + j) * 4 + 1] = acc;  // parked for the substitution
+            yb = yc;
+            yc = ya[q];
         }
     }
-    {
-        const double a = h[K - 2], c = h[K - 3];
-        const double r = (a * a * dkm3 + (2.0 * c + 3.0 * a) * c * dprev) / (c + a);
-        rp = r - fw[K - 1] * rp;
-    }
-    // back substitution and coefficients in u, with r'_k and y_k fetched a chunk ahead
-    double s_next = rp * fip[K - 1];  // s_{K-1}
-    double y_next = ycur;             // y_{K-1}
-    for (int k0 = K - 2; k0 >= 0; k0 -= kChunk) {
-        double rv[kChunk], yv[kChunk];
+    // row m: both threads hold rhs_m and their own reduced value; yb = y_m for both
+    const double other = __shfl_xor_sync(0xffffffffu, acc, 16);
+    double s_prev = (acc + other - rm) * fip[m];
+    double y_prev = yb;
+
+    // substitution away from m: rows m - 1, ..., 0 (top) or m + 1, ..., K - 1 (bottom)
+    const int ds = -dir;
+    for (int i0 = 0; i0 < steps_max; i0 += kChunk) {
+        double pv[kChunk], yv[kChunk];
 #pragma unroll
         for (int q = 0; q < kChunk; ++q) {
-            const int k = k0 - q;
-            rv[q] = k >= 0 ? coef[((size_t)k * J + j) * 4 + 1] : 0.0;
-            yv[q] = k >= 0 ? load_y(jb, j, k) : 0.0;
+            const int i = i0 + q, k = m + ds * (1 + i);
+            const bool act = i < steps;
+            pv[q] = (act && k >= 1 && k <= K - 2) ? coef[((size_t)k * J + jj) * 4 + 1] : 0.0;
+            yv[q] = act ? load_y(jb, jj, k) : 0.0;
         }
 #pragma unroll
         for (int q = 0; q < kChunk; ++q) {
-            const int k = k0 - q;
-            if (k < 0) break;
-            double *c = coef + ((size_t)k * J + j) * 4;
-            const double s = (rv[q] - fup[k] * s_next) * fip[k];
-            const double yk = yv[q];
-            const double D = y_next - yk;
-            const double hk = h[k];
-            const double2 c01 = make_double2(yk, hk * s);
-            const double2 c23 = make_double2(3.0 * D - hk * (2.0 * s + s_next),
-                                             hk * (s + s_next) - 2.0 * D);
-            reinterpret_cast<double2 *>(c)[0] = c01;
-            reinterpret_cast<double2 *>(c)[1] = c23;
-            s_next = s;
-            y_next = yk;
+            const int i = i0 + q;
+            if (i >= steps) break;
+            const int k = m + ds * (1 + i);
+            double par, c, ipv;
+            if (k == 0) {  // end row 0: h_1 s_0 + (h_0 + h_1) s_1 = R_0
+                par = rend; c = h[0] + h[1]; ipv = ih[1];
+            } else if (k == K - 1) {  // end row K-1: (h_{K-2} + h_{K-3}) s_{K-2} + h_{K-3} s_{K-1} = R_L
+                par = rend; c = h[K - 2] + h[K - 3]; ipv = ih[K - 3];
+            } else {  // s_k = (y_k - up_k s_{k+1}) / p_k  or  (z_k - lo_k s_{k-1}) / q_k
+                par = pv[q]; c = top ? h[k - 1] : h[k]; ipv = fip[k];
+            }
+            const double s = (par - c * s_prev) * ipv;
+            const int seg = top ? k : k - 1;  // the segment between rows k and k - ds
+            const double yl = top ? yv[q] : y_prev, yr = top ? y_prev : yv[q];
+            const double sl = top ? s : s_prev, sr = top ? s_prev : s;
+            const double D = yr - yl, hk = h[seg];
+            if (live) {
+                double2 *cc = reinterpret_cast<double2 *>(coef + ((size_t)seg * J + j) * 4);
+                cc[0] = make_double2(yl, hk * sl);
+                cc[1] = make_double2(3.0 * D - hk * (2.0 * sl + sr), hk * (sl + sr) - 2.0 * D);
+            }
+            s_prev = s;
+            y_prev = yv[q];
         }
     }
-    if (!finite) atomicOr(err, ERRBIT_NONFINITE);
+    if (!finite && live) atomicOr(err, ERRBIT_NONFINITE);
 }
 
 cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks, int max_knots,
