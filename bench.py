@@ -326,13 +326,19 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         starts[k].record(stream)
         step()
         ends[k].record(stream)
-        kt = F.few_last_timing(ctx.handle)
-        sum_ms.append(kt[3])
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop() if sampler else None
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    # the summation kernel's own duration (CUDA events the library records around it on the
+    # same stream), read after each of a few more flushed steps; reading waits for the step, so
+    # this runs after the timed loop rather than inside it
+    for k in range(min(args.steps, 5)):
+        flush.zero_()
+        step()
+        kt = F.few_last_timing(ctx.handle)
+        sum_ms.append(kt[3])
     ms_local = sum(step_ms) / len(step_ms)
     if ctx.sync_status() != F.FEW_OK:
         raise RuntimeError("device error during the timed region")
