@@ -23,6 +23,24 @@ __device__ __forceinline__ float f64_to_f32(double d)
     return __uint_as_float(f);
 }
 
+// Branchless FP64 -> FP32 for streaming kernels: round to nearest with ties away from zero (a
+// 64-bit add of half a float ulp, then truncation; it differs from the even-tie cast only on exact
+// ties), exponent rebiased and shifted into place by one funnel shift.  Classified on the
+// unrounded bits: magnitudes below 2^-126 give a signed zero (also the few just below that would
+// round up to it), magnitudes from 2^128 up, inf and nan give a signed infinity.
+__device__ __forceinline__ float f64_to_f32_fast(double d)
+{
+    const unsigned long long raw = static_cast<unsigned long long>(__double_as_longlong(d));
+    const unsigned int rhi = static_cast<unsigned int>(raw >> 32), rmag = rhi & 0x7fffffffu;
+    const unsigned int sign = rhi & 0x80000000u;
+    const unsigned long long b = raw + 0x10000000ull;
+    const unsigned int hi = static_cast<unsigned int>(b >> 32), lo = static_cast<unsigned int>(b);
+    unsigned int f = __funnelshift_l(lo, hi - (896u << 20), 3) | sign;
+    f = rmag < (897u << 20) ? sign : f;
+    f = rmag >= (1151u << 20) ? (sign | 0x7f800000u) : f;
+    return __uint_as_float(f);
+}
+
 // FP32 -> FP64 on the integer pipe: exact for normal floats (rebias the exponent 127 -> 1023,
 // widen the significand); zero and subnormal inputs give a signed zero, inf and nan stay so.
 __device__ __forceinline__ double f32_to_f64(float x)

@@ -51,8 +51,11 @@ __global__ void k_mode_consts(const int *__restrict__ l, const int *__restrict__
     out[i] = c;
 }
 
+// Amplitude conversion of the arithmetic path: the mixed path uses the branchless integer-pipe
+// conversion (ties away from zero, below 2^-126 flushed, from 2^128 up given as infinity): the
+// exact even-tie conversion costs about 15 integer operations per value and bounded this kernel.
 __device__ __forceinline__ double to_t(double v, double) { return v; }
-__device__ __forceinline__ float to_t(double v, float) { return f64_to_f32(v); }
+__device__ __forceinline__ float to_t(double v, float) { return f64_to_f32_fast(v); }
 
 // Nearest integer of |x| < 2^22 by the 1.5 * 2^23 addition (FP32 add pipe); FP64 uses rint.
 __device__ __forceinline__ float round_near(float x)

@@ -54,8 +54,8 @@ def test_direct_ragged_sizes(gpu_ctx, N, ns):
 
 
 def test_direct_mixed_amplitude_range(gpu_ctx):
-    """The mixed path converts FP64 amplitudes to FP32 on the integer pipe (round to nearest
-    even, magnitudes below 2^-126 flushed to zero).  One m = 0 mode at zero phase makes every output
+    """The mixed path converts FP64 amplitudes to FP32 on the integer pipe (round to nearest,
+    ties away from zero, magnitudes below 2^-126 flushed to zero).  One m = 0 mode at zero phase makes every output
     sample a single product A_i * -2Y_20, so each conversion branch (zero, below the normal
     range, boundary magnitudes, exact rounding ties, the whole normal range) is checked sample
     by sample against the oracle: within FP32 rounding, plus the flush's absolute 2^-126."""
@@ -76,3 +76,41 @@ def test_direct_mixed_amplitude_range(gpu_ctx):
     err = np.abs(g.astype(np.complex128) - o)
     assert np.all(err <= 1e-6 * np.abs(o) + 2.0 ** -126), np.max(err / (np.abs(o) + 1e-300))
     assert np.all(g[o == 0] == 0)
+
+
+@pytest.mark.parametrize("N,ns", [(64, 3), (97, 777), (513, 152), (3843, 301)])
+def test_direct_mixed_sizes(gpu_ctx, N, ns):
+    """Mixed path at mode counts from 64 to the full grid, sample counts below and above the
+    number of warps in flight, and odd N (rows that start 8 bytes past a 16-byte boundary)."""
+    w = W.config2()
+    idx = np.arange(N)
+    modes = w.modes[idx]
+    pphi, pr, are, aim = _dense(w, ns, 2000000)
+    are, aim = np.ascontiguousarray(are[:, idx]), np.ascontiguousarray(aim[:, idx])
+    g = _gpu_direct(gpu_ctx, pphi, pr, are, aim, modes, w.theta, w.phi, F.FEW_MIXED)
+    o = oracle.direct_dense(pphi, pr, modes, are, aim, w.theta, w.phi, 1.0, oracle_threads())
+    assert oracle.mismatch(g, o) <= MIXED_MISMATCH
+
+
+def test_direct_mixed_unaligned_amplitudes(gpu_ctx):
+    """Amplitude arrays that start 8 bytes past a 16-byte boundary (a sliced view) give the
+    oracle's result."""
+    import torch
+    w = W.config1()
+    ns = 3001
+    pphi, pr, are, aim = _dense(w, ns)
+    N = are.shape[1]
+    d = [torch.as_tensor(np.ascontiguousarray(a)).cuda() for a in (pphi, pr)]
+    views = []
+    for a in (are, aim):
+        buf = torch.zeros(ns * N + 1, dtype=torch.float64, device="cuda")
+        buf[1:] = torch.as_tensor(a.ravel()).cuda()
+        views.append(buf[1:])
+    assert views[0].data_ptr() % 16 == 8
+    out = torch.empty(ns, dtype=torch.complex64, device="cuda")
+    F.few_direct_sum(gpu_ctx.handle, d[0], d[1], views[0], views[1], w.modes, w.theta, w.phi, out,
+                     1.0, F.FEW_MIXED, RT.current_stream())
+    torch.cuda.synchronize()
+    assert gpu_ctx.sync_status() == F.FEW_OK
+    o = oracle.direct_dense(pphi, pr, w.modes, are, aim, w.theta, w.phi, 1.0, oracle_threads())
+    assert oracle.mismatch(to_host(out), o) <= MIXED_MISMATCH
