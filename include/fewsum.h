@@ -162,8 +162,10 @@ few_status few_traj_info(const few_traj *traj, int *K, int *N, int *n_slots);
  *   t0, dt: first sample time and cadence (s); every sample must lie in [t_0, t_{K-1}].
  *   prec: FEW_FP64 or FEW_MIXED.
  *   out: n_samples complex values, complex64 if out_c64 else complex128; device memory if
- *     out_where == FEW_MEM_DEVICE, else host memory (the library stages the result on the
- *     device and copies it back on `stream`).
+ *     out_where == FEW_MEM_DEVICE, else host memory: page-locked host memory (cudaHostAlloc,
+ *     cudaHostRegister) is written directly by the summation kernel, pageable memory is staged
+ *     on the device and copied back on `stream`; either way few_waveform returns once the
+ *     result is in host memory.
  */
 typedef struct few_request {
     const few_traj *traj;

@@ -810,12 +810,22 @@ few_status few_waveform(few_ctx *ctx, const few_request *req, void *stream)
     }
     void *out_dev = req->out;
     if (req->out_where == FEW_MEM_HOST) {
-        if ((st = dev_alloc(ctx, out_bytes, s, &dout))) {
-            dev_free(ctx, scratch, s);
-            dev_free(ctx, blob, s);
-            return st;
+        // page-locked host memory is addressable from the device (over NVLink-C2C on a Grace
+        // host): the summation kernel stores into it directly and the transfer overlaps the
+        // compute; pageable memory is staged on the device and copied back
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, req->out) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer != nullptr) {
+            out_dev = pa.devicePointer;
+        } else {
+            (void)cudaGetLastError();
+            if ((st = dev_alloc(ctx, out_bytes, s, &dout))) {
+                dev_free(ctx, scratch, s);
+                dev_free(ctx, blob, s);
+                return st;
+            }
+            out_dev = dout;
         }
-        out_dev = dout;
     }
     fill_image(ctx, req, 1, P, static_cast<unsigned char *>(blob),
                static_cast<unsigned char *>(scratch), &out_dev);
@@ -823,7 +833,7 @@ few_status few_waveform(few_ctx *ctx, const few_request *req, void *stream)
     if (!st)
         st = launch_kernels(ctx, static_cast<const PlanHdr *>(blob), P.total_pairs, P.total_fold,
                             P.grid, P.threads, P.R, P.smem, P.variant, s);
-    if (!st && req->out_where == FEW_MEM_HOST) {
+    if (!st && dout) {
         cudaError_t e = cudaMemcpyAsync(req->out, dout, out_bytes, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();

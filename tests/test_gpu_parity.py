@@ -173,6 +173,26 @@ def test_host_buffers_match_device_path(gpu_ctx):
     np.testing.assert_array_equal(host, g_dev)
 
 
+def test_pinned_host_output_matches_device_path(gpu_ctx):
+    """Page-locked host output is stored directly by the summation kernel: same bits as a
+    device-resident output, in both precisions."""
+    import torch
+    w = W.config1()
+    tr = RT.from_inputs(gpu_ctx, w)
+    for prec, dt in ((F.FEW_FP64, torch.complex128), (F.FEW_MIXED, torch.complex64)):
+        dev = RT.alloc_out(w.n_samples, dt == torch.complex64)
+        RT.waveform(gpu_ctx, tr, w.n_samples, w.t0, w.dt, w.theta, w.phi, prec, scale=w.scale,
+                    out=dev)
+        host = torch.zeros(w.n_samples, dtype=dt).pin_memory().numpy()
+        req = RT.request(tr, host, w.n_samples, w.t0, w.dt, w.theta, w.phi, prec, scale=w.scale,
+                         out_where=F.FEW_MEM_HOST)
+        F.few_waveform(gpu_ctx.handle, req, RT.current_stream())
+        torch.cuda.synchronize()
+        assert gpu_ctx.sync_status() == F.FEW_OK
+        np.testing.assert_array_equal(host, dev.cpu().numpy())
+    tr.release()
+
+
 def test_tiles_and_variants_are_bit_identical(gpu_ctx):
     """Every tile shape, and the scalar and packed FP32x2 kernels, give the same bits."""
     w = W.config1()
