@@ -405,7 +405,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": 1000.0 * statistics.mean(t_e), "steps": e_steps,
                "timer": "host wall clock around the two C-ABI calls (the call with host output "
-                        "returns after its device-to-host copy)"}
+                        "returns once the result is in host memory; page-locked output is "
+                        "stored by the summation kernel directly)"}
 
     # batched path: B independent 1-yr 3843-mode waveforms (own trajectories) per step, one
     # persistent summation launch, the whole sequence (spline rebuild included) as a CUDA graph
