@@ -608,6 +608,19 @@ def run_profile_case(which: str, repeats: int = 3) -> int:
     _build.build()
     prec = F.FEW_FP64 if which == "fp64" else F.FEW_MIXED
     w = W.config2()
+    if which == "select":
+        # Mode Selector over the one-year workload's knots: 100 knots x 3843 modes, eps = 1e-5
+        dev = torch.device("cuda", 0)
+        are = torch.as_tensor(np.ascontiguousarray(w.amp_re)).to(dev)
+        aim = torch.as_tensor(np.ascontiguousarray(w.amp_im)).to(dev)
+        mask = torch.empty(w.N, dtype=torch.uint8, device=dev)
+        with RT.Context(0) as ctx:
+            for _ in range(repeats):
+                F.few_mode_select(ctx.handle, are, aim, w.modes[:, 1], 1e-5, mask, RT.current_stream())
+            torch.cuda.synchronize()
+            st = ctx.sync_status()
+        print(json.dumps({"profile_case": which, "repeats": repeats, "status": int(st)}))
+        return 0 if st == F.FEW_OK else 1
     if which == "rb":
         # 6400 knots (64 trajectories x 100), 99 coefficients, 3843 modes, mixed, renormalised
         dev = torch.device("cuda", 0)
@@ -663,7 +676,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--rb-knots", type=int, default=6400,
                     help="knots of the reduced-basis amplitude measurement (0: skip)")
-    ap.add_argument("--profile-case", choices=["mixed", "fp64", "direct", "rb"], default=None,
+    ap.add_argument("--profile-case", choices=["mixed", "fp64", "direct", "rb", "select"], default=None,
                     help="untimed runs of the benchmark waveform for profiler captures")
     ap.add_argument("--serving", action="store_true",
                     help="run the serving workload instead of the single-waveform benchmark")
