@@ -640,7 +640,7 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
     };
     const size_t o_t = take(sizeof(double) * K), o_h = take(sizeof(double) * K),
                  o_ih = take(sizeof(double) * K), o_w = take(sizeof(double) * K),
-                 o_ip = take(sizeof(double) * K), o_up = take(sizeof(double) * K),
+                 o_ip = take(sizeof(double) * K), o_v = take(sizeof(double) * K),
                  o_coef = take(sizeof(double) * 4 * (size_t)tr->S * tr->J),
                  o_pair = take(sizeof(int2) * P.pair_lm.size()), o_mp = take(sizeof(int) * N),
                  o_sp = take(sizeof(int) * P.slot_ptr.size()),
@@ -678,7 +678,7 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
     D.inv_h = reinterpret_cast<const double *>(d + o_ih);
     D.fac_w = reinterpret_cast<const double *>(d + o_w);
     D.fac_ip = reinterpret_cast<const double *>(d + o_ip);
-    D.fac_up = reinterpret_cast<const double *>(d + o_up);
+    D.fac_v = reinterpret_cast<const double *>(d + o_v);
     D.coef = reinterpret_cast<double *>(d + o_coef);
     D.pair_lm = reinterpret_cast<const int2 *>(d + o_pair);
     D.mode_pair = reinterpret_cast<const int *>(d + o_mp);
@@ -693,7 +693,7 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
     cudaError_t e = cudaSuccess;
     if (!us) e = launch_factor(D.t, K, const_cast<double *>(D.h), const_cast<double *>(D.inv_h),
                                const_cast<double *>(D.fac_w), const_cast<double *>(D.fac_ip),
-                               const_cast<double *>(D.fac_up), s);
+                               const_cast<double *>(D.fac_v), s);
     cudaError_t e2 = cudaStreamSynchronize(s);
     if (us || e != cudaSuccess || e2 != cudaSuccess) {
         (void)cudaGetLastError();

@@ -47,7 +47,7 @@ struct TrajDev {
     const double *h;       // [S] t_{k+1}-t_k
     const double *fac_w;   // [K] top-down multipliers w_k (rows 2..m) of the shared twisted factorization
     const double *fac_ip;  // [K] inverse pivots: top rows < m, bottom rows > m, twist pivot at m
-    const double *fac_up;  // [K] bottom-up multipliers v_k (rows m..K-3)
+    const double *fac_v;  // [K] bottom-up multipliers v_k (rows m..K-3)
     double *coef;          // [S][J][4] spline coefficients in u = (t - t_k)/h_k;
                            //   columns 0,1 = Phi_phi, Phi_r (rad),
                            //   column 2+2i / 3+2i = Re / Im A_i
@@ -110,7 +110,7 @@ struct PlanHdr {
 
 // Kernel launchers (defined in the .cu files; every launcher returns the launch error).
 cudaError_t launch_factor(const double *t, int K, double *h, double *inv_h, double *fac_w,
-                          double *fac_ip, double *fac_up, cudaStream_t st);
+                          double *fac_ip, double *fac_v, cudaStream_t st);
 cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks, int max_knots,
                          unsigned *err, cudaStream_t st);
 cudaError_t launch_ylm(const PlanHdr *hdr_dev, int total_pairs, cudaStream_t st);

@@ -30,10 +30,10 @@
 namespace fewsum {
 
 // Shared twisted factorisation of the reduced not-a-knot matrix of one knot grid (single
-// thread; O(K)).  fac_w[k] = w_k (top rows 2..m), fac_up[k] = v_k (bottom rows m..K-3),
+// thread; O(K)).  fac_w[k] = w_k (top rows 2..m), fac_v[k] = v_k (bottom rows m..K-3),
 // fac_ip[k] = 1/p_k (k < m), 1/q_k (k > m), 1/(p_m + q_m - d_m) (k = m).
 __global__ void k_factor(const double *__restrict__ t, int K, double *h, double *inv_h,
-                         double *fac_w, double *fac_ip, double *fac_up)
+                         double *fac_w, double *fac_ip, double *fac_v)
 {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     const int S = K - 1, m = (K - 1) / 2;
@@ -41,7 +41,7 @@ __global__ void k_factor(const double *__restrict__ t, int K, double *h, double 
         h[k] = t[k + 1] - t[k];
         inv_h[k] = 1.0 / h[k];
     }
-    for (int k = 0; k < K; ++k) fac_w[k] = fac_ip[k] = fac_up[k] = 0.0;
+    for (int k = 0; k < K; ++k) fac_w[k] = fac_ip[k] = fac_v[k] = 0.0;
     // reduced rows 1..K-2: lo_k = h_k (k >= 2), up_k = h_{k-1} (k <= K-3), diagonal dg(k)
     auto dg = [&](int k) {
         if (k == 1) return h[0] + h[1];
@@ -61,16 +61,16 @@ __global__ void k_factor(const double *__restrict__ t, int K, double *h, double 
     for (int k = K - 3; k >= m; --k) {
         const double v = h[k - 1] / q;
         q = dg(k) - v * h[k + 1];
-        fac_up[k] = v;
+        fac_v[k] = v;
         if (k > m) fac_ip[k] = 1.0 / q;
     }
     fac_ip[m] = 1.0 / (p + q - dg(m));
 }
 
 cudaError_t launch_factor(const double *t, int K, double *h, double *inv_h, double *fac_w,
-                          double *fac_ip, double *fac_up, cudaStream_t st)
+                          double *fac_ip, double *fac_v, cudaStream_t st)
 {
-    k_factor<<<1, 32, 0, st>>>(t, K, h, inv_h, fac_w, fac_ip, fac_up);
+    k_factor<<<1, 32, 0, st>>>(t, K, h, inv_h, fac_w, fac_ip, fac_v);
     return cudaGetLastError();
 }
 
@@ -110,7 +110,7 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
         ih[k] = k < K - 1 ? tr.inv_h[k] : 0.0;
         fw[k] = tr.fac_w[k];
         fip[k] = tr.fac_ip[k];
-        fv[k] = tr.fac_up[k];
+        fv[k] = tr.fac_v[k];
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
