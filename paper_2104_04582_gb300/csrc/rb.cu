@@ -232,6 +232,96 @@ k_rb_quad(const double *__restrict__ are, const double *__restrict__ aim, int M,
     }
 }
 
+// Mixed path, Nb <= 128: the renormalisation scale in one kernel, one wave.  A block takes
+// kTRows knots; their FP32 coefficients and the whole FP32 Gram matrix (j padded to 128) sit in
+// shared memory, and thread (rg, jg) owns knots 4 rg .. 4 rg + 3 and j = jg + 16 t, t < 8, so 12
+// shared-memory reads (half of them broadcasts) feed 128 multiply-adds per l.  The 16 threads of
+// a knot group share a half-warp: q_k is reduced by shuffles and s_k = nu_k / sqrt(q_k) written
+// directly (0 for q_k = 0; a non-finite or negative nu_k latches ERRBIT_NONFINITE).
+constexpr int kTRows = 48, kTJ = 128, kTThreads = (kTRows / 4) * 16;
+constexpr int kTMaxBasis = kTJ;
+
+__global__ void __launch_bounds__(kTThreads)
+k_rb_scale_tile(const double *__restrict__ are, const double *__restrict__ aim, int M, int Nb,
+                const float2 *__restrict__ gt, const double *__restrict__ nu,
+                double *__restrict__ scale, unsigned *__restrict__ err)
+{
+    extern __shared__ __align__(16) float2 rb_tile_smem[];
+    float2 *as = rb_tile_smem;                 // [kTRows][Nb] alpha
+    float2 *gs = rb_tile_smem + kTRows * Nb;   // [Nb][kTJ] G_jl stored [l][j], zero for j >= Nb
+    const int tid = threadIdx.x, jg = tid & 15, rg = tid >> 4;
+    const int k0 = blockIdx.x * kTRows;
+    // staging: 8 independent loads in flight per thread per round trip
+    constexpr int kU = 8;
+    for (int e0 = tid; e0 < kTRows * Nb; e0 += kTThreads * kU) {
+        double vr[kU], vi[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int e = e0 + u * kTThreads, k = k0 + e / (Nb > 0 ? Nb : 1);
+            const bool ok = e < kTRows * Nb && k < M;
+            vr[u] = ok ? are[(size_t)k0 * Nb + e] : 0.0;  // rows k0.. are contiguous: index k0*Nb + e
+            vi[u] = ok ? aim[(size_t)k0 * Nb + e] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int e = e0 + u * kTThreads;
+            if (e < kTRows * Nb) as[e] = make_float2(f64_to_f32(vr[u]), f64_to_f32(vi[u]));
+        }
+    }
+    for (int e0 = tid; e0 < Nb * kTJ; e0 += kTThreads * kU) {
+        float2 v[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int e = e0 + u * kTThreads, l = e / kTJ, j = e % kTJ;
+            v[u] = (e < Nb * kTJ && j < Nb) ? gt[(size_t)l * Nb + j] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int e = e0 + u * kTThreads;
+            if (e < Nb * kTJ) gs[e] = v[u];
+        }
+    }
+    __syncthreads();
+    float tr[4][8], ti[4][8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int t = 0; t < 8; ++t) tr[r][t] = ti[r][t] = 0.f;
+    for (int l = 0; l < Nb; ++l) {
+        float2 x[4], g[8];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) x[r] = as[(rg * 4 + r) * Nb + l];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) g[t] = gs[l * kTJ + jg + 16 * t];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                tr[r][t] += g[t].x * x[r].x + g[t].y * x[r].y;  // G_jl conj(alpha_l)
+                ti[r][t] += g[t].y * x[r].x - g[t].x * x[r].y;
+            }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int row = rg * 4 + r, k = k0 + row;
+        float q = 0.f;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int j = jg + 16 * t;
+            if (j < Nb) {
+                const float2 a = as[row * Nb + j];
+                q += a.x * tr[r][t] - a.y * ti[r][t];  // Re(alpha_j t_j)
+            }
+        }
+        for (int o = 8; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+        if (jg == 0 && k < M) {
+            const double v = nu[k];
+            if (!(v >= 0.0) || !isfinite(v)) atomicOr(err, ERRBIT_NONFINITE);
+            scale[k] = q > 0.f ? v / sqrt((double)q) : 0.0;
+        }
+    }
+}
+
 // s_k = nu_k / sqrt(q_k) (0 when q_k = 0, i.e. alpha_k B = 0).  A non-finite or negative target
 // norm latches ERRBIT_NONFINITE.
 __global__ void k_rb_norm(const double *__restrict__ q, const double *__restrict__ nu, int M,
@@ -614,7 +704,14 @@ cudaError_t launch_rb(const double *are, const double *aim, int M, int Nb, int N
     const RbLayout L = rb_layout(Nb, N, M);
     cudaError_t e;
     const double *sc = nullptr;
-    if (nu) {
+    if (nu && !fp64 && Nb <= kTMaxBasis) {
+        const int smem = (kTRows * Nb + Nb * kTJ) * (int)sizeof(float2);
+        e = cudaFuncSetAttribute(k_rb_scale_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        k_rb_scale_tile<<<(M + kTRows - 1) / kTRows, kTThreads, smem, st>>>(are, aim, M, Nb, gt32, nu,
+                                                                             scale, err);
+        sc = scale;
+    } else if (nu) {
         double *q = scale + M;  // the caller's scratch holds scale [M] then q [M]
         e = cudaMemsetAsync(q, 0, sizeof(double) * (size_t)M, st);
         if (e != cudaSuccess) return e;
