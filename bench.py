@@ -774,6 +774,12 @@ def main():
             pm = 2 * probe[key] / 1e12
             roof["peak_probe_tflops"] = pm
             roof["frac_of_probe"] = achieved / pm
+        if fp32 and "fp32_fma_3reg_per_s" in probe:
+            # the Horner loop's FMAs take three register operands: the measured rate of that
+            # instruction form is the ceiling the kernel can reach
+            p3 = 2 * probe["fp32_fma_3reg_per_s"] / 1e12
+            roof["peak_register_operand_tflops"] = p3
+            roof["frac_of_register_operand_rate"] = achieved / p3
     if clocks.get("sm_mhz"):
         roof["frac_at_measured_clock"] = achieved / (peak * clocks["sm_mhz"] / sm_max)
 
