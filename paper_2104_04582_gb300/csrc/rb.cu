@@ -168,7 +168,8 @@ __global__ void k_rb_pack_b(const double *__restrict__ bre, const double *__rest
 // the arithmetic type T of the path, as a small register-blocked product: a block takes 32 knots
 // and 64 values of j, l advancing in chunks of 64 staged in (dynamic) shared memory; a thread owns
 // 4 knots x 2 values of j (j and j + 32), so 6 shared-memory reads feed 16 complex multiply-adds.
-// Partial sums over j are reduced per warp and added to q (FP64, zeroed beforehand).
+// Partial sums over j are reduced per warp and added to q (FP64, zeroed beforehand); k_rb_norm
+// then forms s_k.  Used by the FP64 path and, in FP32, for bases of more than 128 vectors.
 constexpr int kQRows = 32, kQJ = 64, kQL = 64, kQThreads = 256, kQPer = 4;
 
 template <typename C>
