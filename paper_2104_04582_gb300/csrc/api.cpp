@@ -496,7 +496,7 @@ few_status launch_kernels(few_ctx *c, const PlanHdr *hdr_dev, int total_pairs, i
                           int grid, int threads, int R, int smem, int variant, cudaStream_t st)
 {
     tmark(c, 1, false, st);
-    FEW_CUDA_TRY(launch_ylm(hdr_dev, total_pairs, st));
+    FEW_CUDA_TRY(launch_ylm(hdr_dev, total_pairs, variant == kVariantFp64, st));
     tmark(c, 1, true, st);
     tmark(c, 2, false, st);
     FEW_CUDA_TRY(launch_fold(hdr_dev, total_fold, variant == kVariantFp64, st));
@@ -1142,7 +1142,7 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
             if (b->n_jobs)
                 launch_build(static_cast<const BuildJob *>(b->jobs_dev), b->n_jobs, b->build_blocks,
                              b->max_knots, ctx->d_err, cap);
-            launch_ylm(hd, b->total_pairs, cap);
+            launch_ylm(hd, b->total_pairs, b->fp64, cap);
             launch_fold(hd, b->total_fold, b->fp64, cap);
             launch_sum(hd, b->grid, b->threads, b->R, b->smem, b->variant, cap);
             e = cudaStreamEndCapture(cap, &b->graph);

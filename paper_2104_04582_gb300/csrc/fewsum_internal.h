@@ -113,7 +113,7 @@ cudaError_t launch_factor(const double *t, int K, double *h, double *inv_h, doub
                           double *fac_ip, double *fac_v, cudaStream_t st);
 cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks, int max_knots,
                          unsigned *err, cudaStream_t st);
-cudaError_t launch_ylm(const PlanHdr *hdr_dev, int total_pairs, cudaStream_t st);
+cudaError_t launch_ylm(const PlanHdr *hdr_dev, int total_pairs, bool fp64, cudaStream_t st);
 cudaError_t launch_fold(const PlanHdr *hdr_dev, int total_fold_blocks, bool fp64, cudaStream_t st);
 cudaError_t launch_sum(const PlanHdr *hdr_dev, int grid, int threads, int samples_per_thread,
                        int smem_bytes, int variant, cudaStream_t st);

@@ -71,6 +71,8 @@ __device__ void frame_angles(double tS, double pS, double tK, double pK, double 
 // chain each thread waits on).  FP64 plans evaluate the harmonics in FP64; mixed plans, whose
 // folded coefficients are FP32, evaluate them in FP32 (relative error near 1e-7, far below the
 // path's 1e-6 mismatch budget) and stay off GB300's narrow FP64 pipe.  The frame angles are FP64.
+// One instantiation per arithmetic type keeps each kernel's code small (it runs cold, once).
+template <bool FP64>
 __global__ void __launch_bounds__(kYlmThreads) k_ylm(const PlanHdr *__restrict__ hp)
 {
     const PlanHdr h = *hp;
@@ -88,10 +90,9 @@ __global__ void __launch_bounds__(kYlmThreads) k_ylm(const PlanHdr *__restrict__
     double theta = W.theta, phi = W.phi, psi = 0.0;
     if (W.frame == FEW_FRAME_SSB) frame_angles(W.theta, W.phi, W.theta_K, W.phi_K, theta, phi, psi);
     double2 y = make_double2(0.0, 0.0);
-    const bool fp64 = h.variant == kVariantFp64;
     const int mm = which == 0 ? lm.y : -lm.y;
     if (which == 0 || lm.y > 0) {
-        y = fp64 ? swsh_m2_t<double>(lm.x, mm, theta, phi)
+        y = FP64 ? swsh_m2_t<double>(lm.x, mm, theta, phi)
                  : swsh_m2_t<float>(lm.x, mm, (float)theta, (float)phi);
         if (which == 1 && (lm.x & 1)) y = make_double2(-y.x, -y.y);
     }
@@ -104,11 +105,14 @@ __global__ void __launch_bounds__(kYlmThreads) k_ylm(const PlanHdr *__restrict__
     W.ylm[2 * p + which] = y;
 }
 
-cudaError_t launch_ylm(const PlanHdr *hdr_dev, int total_pairs, cudaStream_t st)
+cudaError_t launch_ylm(const PlanHdr *hdr_dev, int total_pairs, bool fp64, cudaStream_t st)
 {
     if (total_pairs <= 0) return cudaSuccess;
-    const int threads = 2 * total_pairs;
-    k_ylm<<<(threads + kYlmThreads - 1) / kYlmThreads, kYlmThreads, 0, st>>>(hdr_dev);
+    const int threads = 2 * total_pairs, grid = (threads + kYlmThreads - 1) / kYlmThreads;
+    if (fp64)
+        k_ylm<true><<<grid, kYlmThreads, 0, st>>>(hdr_dev);
+    else
+        k_ylm<false><<<grid, kYlmThreads, 0, st>>>(hdr_dev);
     return cudaGetLastError();
 }
 

@@ -195,7 +195,7 @@ extern "C" few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req,
     }
     if (cudaGetLastError() != cudaSuccess) return FEW_ERR_CUDA;
     const PlanHdr *hd = reinterpret_cast<const PlanHdr *>(base);
-    if (launch_ylm(hd, v.n_pairs, s) != cudaSuccess ||
+    if (launch_ylm(hd, v.n_pairs, fp64, s) != cudaSuccess ||
         launch_fold(hd, hdr->total_fold_blocks, fp64, s) != cudaSuccess ||
         launch_sum(hd, grid, T, R, smem, variant, s) != cudaSuccess) {
         (void)cudaGetLastError();
