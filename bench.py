@@ -249,7 +249,9 @@ def measure_peaks(dev_index: int):
     out = {}
     for which, name, it0 in ((0, "fp32_fma_per_s", 20000), (1, "fp64_fma_per_s", 400),
                              (2, "sfu_sin_per_s", 4000), (3, "fp32_fma_3reg_per_s", 20000),
-                             (4, "fp32x2_fma_3reg_per_s", 10000)):
+                             (4, "fp32x2_fma_3reg_per_s", 10000),
+                             (5, "fp32_fma_shared_addend_per_s", 20000),
+                             (6, "fp32_fma_summation_block_per_s", 4000)):
         r, ms = ctypes.c_double(), ctypes.c_float()
         if L.fewprobe_measure(dev_index, which, it0, ctypes.byref(r), ctypes.byref(ms)):
             continue
@@ -780,6 +782,12 @@ def main():
             p3 = 2 * probe["fp32_fma_3reg_per_s"] / 1e12
             roof["peak_register_operand_tflops"] = p3
             roof["frac_of_register_operand_rate"] = achieved / p3
+        if fp32 and "fp32_fma_summation_block_per_s" in probe:
+            # the kernel's own per-slot block (coefficients from shared memory, two cubics, the
+            # complex step) run in isolation: what the inner loop can reach on this chip
+            pb = 2 * probe["fp32_fma_summation_block_per_s"] / 1e12
+            roof["peak_summation_block_tflops"] = pb
+            roof["frac_of_summation_block_rate"] = achieved / pb
     if clocks.get("sm_mhz"):
         roof["frac_at_measured_clock"] = achieved / (peak * clocks["sm_mhz"] / sm_max)
 
