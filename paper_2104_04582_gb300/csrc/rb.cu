@@ -20,11 +20,16 @@
 // accumulator back by both inverse powers.  An entry far below its row or column maximum keeps
 // an absolute error near 2^-24 of that maximum.
 //
-// Operands are packed once into the canonical K-major layout without swizzle that the tensor
-// core's shared-memory descriptors read: 8 x 8 fp16 "core matrices" of 16-byte rows, core
-// matrices adjacent in K 128 bytes apart, 8-row groups 1024 bytes apart.  A k-block of 64
-// columns of a 128-row (A) or 256-row (B) tile is one contiguous 16 / 32 KB block in global
-// memory, so each pipeline stage is filled by two bulk asynchronous copies.
+// The product is computed transposed, A^T = Bhat^T a^T: the MMA's M side (tensor-memory lanes)
+// is 128 real output columns of 64 modes (rows 0-63 the real parts, 64-127 the imaginary parts)
+// and its N side (tensor-memory columns) 256 knots.  A lane of the accumulator then holds one
+// output column for consecutive knots, so for each knot a warp stores 32 consecutive modes (256
+// contiguous bytes) straight from registers.  Operands are packed once into the canonical K-major
+// layout without swizzle that the tensor core's shared-memory descriptors read: 8 x 8 fp16 "core
+// matrices" of 16-byte rows, core matrices adjacent in K 128 bytes apart, 8-row groups 1024
+// bytes apart.  A k-block of 64 columns of a 128-row basis tile or a 256-row coefficient tile is
+// one contiguous 16 / 32 KB block in global memory, so each pipeline stage is filled by two bulk
+// asynchronous copies.
 #include <cuda_fp16.h>
 
 #include "async.cuh"
@@ -33,13 +38,14 @@
 
 namespace fewsum {
 
-constexpr int kRbTileM = 128;   // knots per tile: tensor-memory lanes
-constexpr int kRbTileN = 256;   // real output columns per tile: 128 modes, re/im interleaved
+constexpr int kRbTileM = 128;   // MMA M, tensor-memory lanes: real output columns of 64 modes
+constexpr int kRbModes = kRbTileM / 2;  // modes per basis tile
+constexpr int kRbTileN = 256;   // MMA N, tensor-memory columns: knots per coefficient tile
 constexpr int kRbTileK = 64;    // fp16 columns per k-block: 128 bytes per row
-constexpr int kRbStages = 3;    // shared-memory pipeline depth
+constexpr int kRbStages = 4;    // shared-memory pipeline depth
 constexpr int kRbParts = 3;     // split products laid along K
-constexpr uint32_t kRbABytes = kRbTileM * kRbTileK * 2;  // 16 KB
-constexpr uint32_t kRbBBytes = kRbTileN * kRbTileK * 2;  // 32 KB
+constexpr uint32_t kRbABytes = kRbTileM * kRbTileK * 2;  // 16 KB: basis (A operand)
+constexpr uint32_t kRbBBytes = kRbTileN * kRbTileK * 2;  // 32 KB: coefficients (B operand)
 constexpr uint32_t kRbStageBytes = kRbABytes + kRbBBytes;
 
 // Which fp16 part of the A (coefficient) and B (basis) operand each K segment holds, so that
@@ -122,20 +128,23 @@ __global__ void k_rb_bexp(const double *__restrict__ bre, const double *__restri
     bexp[i] = scale_exp((float)m);
 }
 
-// Basis operand of the real GEMM, scaled, split and packed: row n' of tile n'/256 is real output
-// column n' (mode n'/2, real part for even n', imaginary for odd); column c = g * 2Nb + q holds
-// part kPartB[g] of 2^bexp[n'/2] Bhat_q,n'.  Rows past 2N and columns past 3 x 2Nb are zero.
+// Basis operand (the MMA's A side), scaled, split and packed: row r of basis tile b is the real
+// (r < 64) or imaginary (r >= 64) output column of mode 64 b + (r mod 64); column c = g 2Nb + q
+// holds part kPartB[g] of 2^bexp[mode] Bhat for that column.  Modes past N and columns past
+// 3 x 2Nb are zero.
 __global__ void k_rb_pack_b(const double *__restrict__ bre, const double *__restrict__ bim, int Nb,
                             int N, int n_kb, int n_tiles, const int *__restrict__ bexp,
                             unsigned char *__restrict__ bpack)
 {
-    const long long chunks = (long long)n_tiles * kRbTileN * n_kb * (kRbTileK / 8);
+    const long long chunks = (long long)n_tiles * kRbTileM * n_kb * (kRbTileK / 8);
     const int Kr = 2 * Nb;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < chunks;
          t += (long long)gridDim.x * blockDim.x) {
         const int q8 = (int)(t % (n_kb * (kRbTileK / 8)));
         const int row = (int)(t / (n_kb * (kRbTileK / 8)));
         const int c0 = q8 * 8;
+        const int rr = row % kRbTileM, i = (row / kRbTileM) * kRbModes + (rr % kRbModes);
+        const bool imag_out = rr >= kRbModes;
         uint32_t w[4];
         for (int e = 0; e < 8; e += 2) {
             __half v[2];
@@ -143,9 +152,9 @@ __global__ void k_rb_pack_b(const double *__restrict__ bre, const double *__rest
                 const int c = c0 + e + h, g = c / Kr, q = c % Kr;
                 float x = 0.0f;
                 int part = 0;
-                if (g < kRbParts && row < 2 * N) {
-                    const int i = row >> 1, j = q % Nb;
-                    const bool imag_out = row & 1, from_im = q >= Nb;
+                if (g < kRbParts && i < N) {
+                    const int j = q % Nb;
+                    const bool from_im = q >= Nb;
                     const double br = bre[(size_t)j * N + i], bi = bim[(size_t)j * N + i];
                     const double v = imag_out ? (from_im ? br : bi) : (from_im ? -bi : br);
                     x = (float)ldexp(v, bexp[i]);
@@ -155,10 +164,9 @@ __global__ void k_rb_pack_b(const double *__restrict__ bre, const double *__rest
             }
             w[e / 2] = pack2(v[0], v[1]);
         }
-        const int tile = row / kRbTileN, kb = c0 / kRbTileK;
-        unsigned char *blk = bpack + ((size_t)tile * n_kb + kb) * kRbBBytes;
-        *reinterpret_cast<uint4 *>(blk + core_offset(row % kRbTileN, c0 % kRbTileK)) =
-            make_uint4(w[0], w[1], w[2], w[3]);
+        const int tile = row / kRbTileM, kb = c0 / kRbTileK;
+        unsigned char *blk = bpack + ((size_t)tile * n_kb + kb) * kRbABytes;
+        *reinterpret_cast<uint4 *>(blk + core_offset(rr, c0 % kRbTileK)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 
@@ -335,7 +343,8 @@ __global__ void k_rb_norm(const double *__restrict__ q, const double *__restrict
     scale[k] = qk > 0.0 ? v / sqrt(qk) : 0.0;
 }
 
-// Coefficient operand, one warp per row: row k of tile k/128, column c = g * 2Nb + q holds part
+// Coefficient operand (the MMA's B side), one warp per row: row k of tile k/256, column
+// c = g * 2Nb + q holds part
 // kPartA[g] of 2^aexp[k] x_q, x_q = s_k alpha_k,q (real parts for q < Nb, imaginary parts after).
 // The row's x_q are formed once (one FP64 product each, converted on the integer pipe) in shared
 // memory, its largest magnitude sets aexp[k], then the lanes write its 16-byte chunks.  Rows past
@@ -350,7 +359,7 @@ k_rb_pack_a(const double *__restrict__ are, const double *__restrict__ aim, int 
     __shared__ float xs[kRbPackWarps][2 * FEW_MAX_BASIS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, Kr = 2 * Nb;
     float *x = xs[w];
-    const int rows = m_tiles * kRbTileM, chunks = n_kb * (kRbTileK / 8);
+    const int rows = m_tiles * kRbTileN, chunks = n_kb * (kRbTileK / 8);
     for (int row = blockIdx.x * kRbPackWarps + w; row < rows; row += gridDim.x * kRbPackWarps) {
         const bool live = row < M;
         const double s = (live && scale) ? scale[row] : 1.0;
@@ -365,7 +374,7 @@ k_rb_pack_a(const double *__restrict__ are, const double *__restrict__ aim, int 
         const float f = pow2f(e);
         if (lane == 0) aexp[row] = e;
         __syncwarp();
-        unsigned char *tile = apack + (size_t)(row / kRbTileM) * n_kb * kRbABytes;
+        unsigned char *tile = apack + (size_t)(row / kRbTileN) * n_kb * kRbBBytes;
         for (int q8 = lane; q8 < chunks; q8 += 32) {
             const int c0 = q8 * 8;
             uint32_t wv[4];
@@ -379,8 +388,8 @@ k_rb_pack_a(const double *__restrict__ are, const double *__restrict__ aim, int 
                 }
                 wv[e2 / 2] = pack2(v[0], v[1]);
             }
-            *reinterpret_cast<uint4 *>(tile + (size_t)(c0 / kRbTileK) * kRbABytes +
-                                       core_offset(row % kRbTileM, c0 % kRbTileK)) =
+            *reinterpret_cast<uint4 *>(tile + (size_t)(c0 / kRbTileK) * kRbBBytes +
+                                       core_offset(row % kRbTileN, c0 % kRbTileK)) =
                 make_uint4(wv[0], wv[1], wv[2], wv[3]);
         }
         __syncwarp();
@@ -440,8 +449,8 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32])
 }
 
 struct RbMmaArgs {
-    const unsigned char *apack;  // [m_tiles][n_kb] blocks of kRbABytes
-    const unsigned char *bpack;  // [n_tiles][n_kb] blocks of kRbBBytes
+    const unsigned char *apack;  // coefficients: [m_tiles][n_kb] blocks of kRbBBytes (B operand)
+    const unsigned char *bpack;  // basis: [n_tiles][n_kb] blocks of kRbABytes (A operand)
     double *out_re, *out_im;     // [M][N]
     const int *aexp, *bexp;      // scaling exponents of the coefficient rows and basis columns
     int M, N, n_kb, m_tiles, n_tiles;
@@ -451,8 +460,6 @@ struct RbMmaArgs {
 constexpr int kRbEpiWarps = 16;  // four per tensor-memory lane quarter, every fourth 32-column chunk
 constexpr int kRbEpiPerQuarter = kRbEpiWarps / 4;
 constexpr int kRbMmaThreads = 64 + 32 * kRbEpiWarps;  // producer warp, MMA warp, epilogue warps
-constexpr int kRbStgPad = 17;                          // staging row pitch (floats)
-constexpr uint32_t kRbStgBytes = kRbEpiWarps * 2 * 32 * kRbStgPad * 4;
 constexpr uint32_t kRbTmemCols = 2 * kRbTileN;         // two accumulator buffers
 
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity)
@@ -464,9 +471,9 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity)
 // t % n_tiles).  Warp 0 (one lane) streams each tile's k-blocks through a kRbStages ring of
 // shared-memory stages with bulk copies; warp 1 (one lane) issues the MMAs of a tile into one of
 // two tensor-memory accumulators of 256 columns and commits; warps 2.. drain the other
-// accumulator meanwhile: warp w reads lanes (knots) 32 (w % 4) .. + 31 and one in
-// kRbEpiPerQuarter chunks of 32 columns, transposes them through shared memory and stores rows of 16 modes as FP64 (two full
-// 128-byte segments per store instruction).  Every wait is bounded; a timeout latches ERRBIT_TIMEOUT and the CTA waits
+// accumulator meanwhile: warp w reads lanes 32 (w % 4) .. + 31 (32 output columns: real parts
+// for w % 4 < 2, imaginary parts otherwise) and one in kRbEpiPerQuarter chunks of 32 knots, and
+// for each knot stores the 32 columns' FP64 values, 256 contiguous bytes, from registers.  Every wait is bounded; a timeout latches ERRBIT_TIMEOUT and the CTA waits
 // for its copies and MMAs in flight before it frees tensor memory.
 __global__ void __launch_bounds__(kRbMmaThreads, 1) k_rb_mma(RbMmaArgs a)
 {
@@ -480,7 +487,6 @@ __global__ void __launch_bounds__(kRbMmaThreads, 1) k_rb_mma(RbMmaArgs a)
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(rb_mma_smem) + 127) & ~(uintptr_t)127);
     unsigned char *sA = base, *sB = base + kRbStages * kRbABytes;
-    float *stg = reinterpret_cast<float *>(base + kRbStages * kRbStageBytes);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -513,8 +519,8 @@ __global__ void __launch_bounds__(kRbMmaThreads, 1) k_rb_mma(RbMmaArgs a)
             const uint64_t keep = l2_evict_last_policy();  // operands are re-read by other CTAs
             uint32_t g = 0;
             for (int t = blockIdx.x; t < total && !s_abort; t += gridDim.x) {
-                const unsigned char *ga = a.apack + (size_t)(t / a.n_tiles) * a.n_kb * kRbABytes;
-                const unsigned char *gb = a.bpack + (size_t)(t % a.n_tiles) * a.n_kb * kRbBBytes;
+                const unsigned char *ga = a.bpack + (size_t)(t % a.n_tiles) * a.n_kb * kRbABytes;  // basis
+                const unsigned char *gb = a.apack + (size_t)(t / a.n_tiles) * a.n_kb * kRbBBytes;  // coefficients
                 for (int kb = 0; kb < a.n_kb; ++kb, ++g) {
                     const int s = g % kRbStages;
                     if (!mbar_wait_bounded(&empty[s], ((g / kRbStages) & 1) ^ 1)) { s_abort = 1; break; }
@@ -557,36 +563,26 @@ __global__ void __launch_bounds__(kRbMmaThreads, 1) k_rb_mma(RbMmaArgs a)
     } else {  // epilogue
         const int e = warp - 2, qd = warp & 3;  // a warp reads tensor-memory lanes 32 (warp % 4) ..
         const int c_first = e / 4;              // and chunks c_first + kRbEpiPerQuarter i
-        float *sre = stg + (size_t)e * 2 * 32 * kRbStgPad, *sim = sre + 32 * kRbStgPad;
         int u = 0;
         for (int t = blockIdx.x; t < total && !__any_sync(0xffffffffu, s_abort != 0); t += gridDim.x, ++u) {
             const int b = u & 1;
             if (!warp_wait(&tfull[b], (u >> 1) & 1)) { s_abort = 1; break; }
             tc_fence_after();
-            const int r0 = (t / a.n_tiles) * kRbTileM + 32 * qd;
-            const int m0 = (t % a.n_tiles) * (kRbTileN / 2);
-            const float fa = pow2f(-a.aexp[r0 + lane]);  // undo the row scaling (exact)
+            const int mode = (t % a.n_tiles) * kRbModes + (qd & 1) * 32 + lane;  // this lane's column
+            double *dst = qd < 2 ? a.out_re : a.out_im;
+            const float fb = pow2f(-a.bexp[mode]);  // undo the column scaling (exact)
+            const int k0 = (t / a.n_tiles) * kRbTileN;
             for (int c = c_first; c < kRbTileN / 32; c += kRbEpiPerQuarter) {
                 uint32_t v[32];
                 tc_ld32(tmem + (uint32_t)(b * kRbTileN) + ((uint32_t)(32 * qd) << 16) + (uint32_t)(32 * c), v);
+                const int kc = k0 + 32 * c;
+                const float fa_lane = pow2f(-a.aexp[kc + lane]);  // knot kc + lane's row scaling
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    sre[lane * kRbStgPad + j] = __uint_as_float(v[2 * j]) * fa;
-                    sim[lane * kRbStgPad + j] = __uint_as_float(v[2 * j + 1]) * fa;
+                for (int j = 0; j < 32; ++j) {
+                    const float fa = __shfl_sync(0xffffffffu, fa_lane, j);
+                    if (kc + j < a.M && mode < a.N)  // streamed once: evict-first
+                        __stcs(dst + (size_t)(kc + j) * a.N + mode, f32_to_f64(__uint_as_float(v[j]) * fb * fa));
                 }
-                __syncwarp();
-                const int col = m0 + 16 * c + (lane & 15);
-                const float fb = pow2f(-a.bexp[col]);  // undo the column scaling (exact)
-#pragma unroll 4
-                for (int rr = 0; rr < 16; ++rr) {
-                    const int row = 2 * rr + (lane >> 4), gr = r0 + row;
-                    if (gr < a.M && col < a.N) {
-                        // streamed once: evict-first, so the output does not push the operands out of L2
-                        __stcs(a.out_re + (size_t)gr * a.N + col, f32_to_f64(sre[row * kRbStgPad + (lane & 15)] * fb));
-                        __stcs(a.out_im + (size_t)gr * a.N + col, f32_to_f64(sim[row * kRbStgPad + (lane & 15)] * fb));
-                    }
-                }
-                __syncwarp();
             }
             tc_fence_before();
             __syncwarp();
@@ -676,12 +672,12 @@ RbLayout rb_layout(int Nb, int N, int M)
 {
     RbLayout L;
     L.n_kb = (kRbParts * 2 * Nb + kRbTileK - 1) / kRbTileK;
-    L.n_tiles = (2 * N + kRbTileN - 1) / kRbTileN;
-    L.m_tiles = (M + kRbTileM - 1) / kRbTileM;
-    L.modes_padded = L.n_tiles * (kRbTileN / 2);
-    L.rows_padded = L.m_tiles * kRbTileM;
-    L.bpack_bytes = (size_t)L.n_tiles * L.n_kb * kRbBBytes;
-    L.apack_bytes = (size_t)L.m_tiles * L.n_kb * kRbABytes;
+    L.n_tiles = (N + kRbModes - 1) / kRbModes;
+    L.m_tiles = (M + kRbTileN - 1) / kRbTileN;
+    L.modes_padded = L.n_tiles * kRbModes;
+    L.rows_padded = L.m_tiles * kRbTileN;
+    L.bpack_bytes = (size_t)L.n_tiles * L.n_kb * kRbABytes;
+    L.apack_bytes = (size_t)L.m_tiles * L.n_kb * kRbBBytes;
     return L;
 }
 
@@ -736,11 +732,11 @@ cudaError_t launch_rb(const double *are, const double *aim, int M, int Nb, int N
         k_rb_fp64<<<grid, 256, 0, st>>>(are, aim, bre, bim, M, Nb, N, sc, ore, oim);
         return cudaGetLastError();
     }
-    const int rows = L.m_tiles * kRbTileM;
+    const int rows = L.m_tiles * kRbTileN;
     const int pgrid = (rows + kRbPackWarps - 1) / kRbPackWarps;
     k_rb_pack_a<<<pgrid < sm_count * 8 ? pgrid : sm_count * 8, kRbPackWarps * 32, 0, st>>>(
         are, aim, M, Nb, L.n_kb, L.m_tiles, sc, apack, aexp);
-    const int smem = kRbStages * (int)kRbStageBytes + (int)kRbStgBytes + 128;
+    const int smem = kRbStages * (int)kRbStageBytes + 128;
     e = cudaFuncSetAttribute(k_rb_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int tiles = L.m_tiles * L.n_tiles;
