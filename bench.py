@@ -223,7 +223,8 @@ def bench_rb(ctx, M, N, stream, sh):
     gbs = nbytes / (ms * 1e-3) / 1e9
     alg_flops = 8.0 * M * Nb * N  # complex product: 4 real multiply-adds per term
     n_kb = -(-(6 * Nb) // 64)  # three split products of depth 2 Nb
-    exec_flops = 2.0 * (-(-M // 128) * 128) * (-(-(2 * N) // 256) * 256) * (n_kb * 64)
+    # transposed tiles: 256 knots x 128 output columns (64 modes, real and imaginary)
+    exec_flops = 2.0 * (-(-M // 256) * 256) * (-(-N // 64) * 128) * (n_kb * 64)
     return {"knots": M, "basis": Nb, "modes": N, "prec": "mixed (split fp16 on tcgen05)",
             "ms": ms, "amplitudes_per_s": M * N / (ms * 1e-3),
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
