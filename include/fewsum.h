@@ -119,7 +119,8 @@ few_status few_ctx_memory(few_ctx *ctx, size_t *bytes_in_use, size_t *budget_byt
  *   l, m, n [N]: mode indices, host memory, copied.
  * Plans the shared tridiagonal factorization on the device (one launch on an internal stream)
  * and waits for it.  Spline data are set with few_traj_set_data before first use.
- * Errors: FEW_ERR_KNOTS, FEW_ERR_MODES, FEW_ERR_BUDGET, FEW_ERR_NOMEM, FEW_ERR_CUDA.
+ * Errors: FEW_ERR_KNOTS, FEW_ERR_MODES, FEW_ERR_LIMIT (K > FEW_MAX_KNOTS), FEW_ERR_BUDGET,
+ * FEW_ERR_NOMEM, FEW_ERR_CUDA.
  */
 few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int *l, const int *m,
                            const int *n, int N, few_traj **out);
@@ -212,6 +213,7 @@ few_status few_waveform(few_ctx *ctx, const few_request *req, void *stream);
  */
 #define FEW_NOALLOC_SCRATCH_BYTES (16u << 20)
 #define FEW_MAX_BASIS 256  /* reduced-basis size limit of few_basis_create */
+#define FEW_MAX_KNOTS 4096 /* knots per trajectory (the spline build stages 48 bytes per knot) */
 few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req, void *stream);
 
 /*

@@ -616,6 +616,7 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
     *out = nullptr;
     few_status st = check_knots(t_knots, K);
     if (st) return st;
+    if (K > FEW_MAX_KNOTS) return FEW_ERR_LIMIT;
     SlotPlan plan;
     if ((st = plan_slots(l, m, n, N, plan))) return st;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);

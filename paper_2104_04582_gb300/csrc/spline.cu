@@ -93,7 +93,7 @@ constexpr int kChunk = 8;
 __global__ void __launch_bounds__(kBuildThreads)
 k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
 {
-    extern __shared__ double sk[];  // [5][K]: h, 1/h, top multipliers, inverse pivots, bottom multipliers
+    extern __shared__ double sk[];  // [6][K]: h, ra, rb, top multipliers, inverse pivots, bottom multipliers
     // job of this block: largest q with jobs[q].block_begin <= blockIdx.x
     int lo = 0, hi = n_jobs - 1;
     const int b = blockIdx.x;
@@ -104,10 +104,14 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
     const BuildJob &jb = jobs[lo];
     const TrajDev &tr = jb.tr;
     const int K = tr.K, J = tr.J;
-    double *h = sk, *ih = sk + K, *fw = sk + 2 * K, *fip = sk + 3 * K, *fv = sk + 4 * K;
+    // ra_k = 3 h_k / h_{k-1}, rb_k = 3 h_{k-1} / h_k: the interior right-hand side
+    // 3 (h_k d_{k-1} + h_{k-1} d_k) becomes ra_k (y_k - y_{k-1}) + rb_k (y_{k+1} - y_k)
+    double *h = sk, *ra = sk + K, *rb = sk + 2 * K, *fw = sk + 3 * K, *fip = sk + 4 * K, *fv = sk + 5 * K;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         h[k] = k < K - 1 ? tr.h[k] : 0.0;
-        ih[k] = k < K - 1 ? tr.inv_h[k] : 0.0;
+        const bool in = k >= 1 && k <= K - 2;
+        ra[k] = in ? 3.0 * tr.h[k] * tr.inv_h[k - 1] : 0.0;
+        rb[k] = in ? 3.0 * tr.h[k - 1] * tr.inv_h[k] : 0.0;
         fw[k] = tr.fac_w[k];
         fip[k] = tr.fac_ip[k];
         fv[k] = tr.fac_v[k];
@@ -141,18 +145,21 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
             const int k = k0 + dir * i;
             finite &= isfinite(ya[q]);
             const double ylo = top ? yb : ya[q], yhi = top ? ya[q] : yb;  // y_{k-1}, y_{k+1}
-            const double dl = (yc - ylo) * ih[k - 1], dr = (yhi - yc) * ih[k];
-            double r = 3.0 * (h[k] * dl + h[k - 1] * dr);
-            if (k == 1) {
-                const double R0 = ((2.0 * h[1] + 3.0 * h[0]) * h[1] * dl + h[0] * h[0] * dr) / (h[0] + h[1]);
-                r -= R0;
-                if (top) rend = R0;
-            }
-            if (k == K - 2) {
-                const double a = h[K - 2], c = h[K - 3];
-                const double RL = (a * a * dl + (2.0 * c + 3.0 * a) * c * dr) / (c + a);
-                r -= RL;
-                if (!top) rend = RL;
+            const double el = yc - ylo, er = yhi - yc;
+            double r = fma(ra[k], el, rb[k] * er);
+            if (k == 1 || k == K - 2) {
+                const double dl = el / h[k - 1], dr = er / h[k];
+                if (k == 1) {
+                    const double R0 = ((2.0 * h[1] + 3.0 * h[0]) * h[1] * dl + h[0] * h[0] * dr) / (h[0] + h[1]);
+                    r -= R0;
+                    if (top) rend = R0;
+                }
+                if (k == K - 2) {
+                    const double a = h[K - 2], c = h[K - 3];
+                    const double RL = (a * a * dl + (2.0 * c + 3.0 * a) * c * dr) / (c + a);
+                    r -= RL;
+                    if (!top) rend = RL;
+                }
             }
             if (k == m) rm = r;
             acc = r - (i == 0 ? 0.0 : (top ? fw[k] : fv[k])) * acc;
@@ -184,9 +191,9 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
             const int k = m + ds * (1 + i);
             double par, c, ipv;
             if (k == 0) {  // end row 0: h_1 s_0 + (h_0 + h_1) s_1 = R_0
-                par = rend; c = h[0] + h[1]; ipv = ih[1];
+                par = rend; c = h[0] + h[1]; ipv = 1.0 / h[1];
             } else if (k == K - 1) {  // end row K-1: (h_{K-2} + h_{K-3}) s_{K-2} + h_{K-3} s_{K-1} = R_L
-                par = rend; c = h[K - 2] + h[K - 3]; ipv = ih[K - 3];
+                par = rend; c = h[K - 2] + h[K - 3]; ipv = 1.0 / h[K - 3];
             } else {  // s_k = (y_k - up_k s_{k+1}) / p_k  or  (z_k - lo_k s_{k-1}) / q_k
                 par = pv[q]; c = top ? h[k - 1] : h[k]; ipv = fip[k];
             }
@@ -210,7 +217,7 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
 cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks, int max_knots,
                          unsigned *err, cudaStream_t st)
 {
-    const int smem_bytes = 5 * max_knots * (int)sizeof(double);
+    const int smem_bytes = 6 * max_knots * (int)sizeof(double);
     if (smem_bytes > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              smem_bytes);

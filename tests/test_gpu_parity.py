@@ -340,3 +340,10 @@ def test_strongly_nonuniform_knots(gpu_ctx):
     o = _oracle(w)
     assert rel_l2(_gpu(gpu_ctx, w, F.FEW_FP64), o) <= FP64_REL_L2
     assert oracle.mismatch(_gpu(gpu_ctx, w, F.FEW_MIXED), o) <= MIXED_MISMATCH
+
+
+def test_knot_count_limit(gpu_ctx):
+    t = np.arange(4097, dtype=np.float64)  # one knot more than FEW_MAX_KNOTS
+    with pytest.raises(F.FewError) as e:
+        F.few_traj_create(gpu_ctx.handle, t, np.array([[2, 2, 0]], dtype=np.int32))
+    assert e.value.status == F.FEW_ERR_LIMIT
