@@ -117,7 +117,7 @@ cudaError_t launch_ylm(const PlanHdr *hdr_dev, int total_pairs, bool fp64, cudaS
 }
 
 __device__ __forceinline__ double cvt(double v, double) { return v; }
-__device__ __forceinline__ float cvt(double v, float) { return f64_to_f32(v); }
+__device__ __forceinline__ float cvt(double v, float) { return f64_to_f32_fast(v); }
 
 template <typename T> struct Slot8;
 template <> struct Slot8<double> {
