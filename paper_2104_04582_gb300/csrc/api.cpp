@@ -720,6 +720,7 @@ few_status few_traj_set_data(few_ctx *ctx, few_traj *tr, const double *phi_phi, 
     const size_t K = tr->K, N = tr->N;
     BuildJob job{};
     job.tr = tr->dev;
+    cudaEvent_t copied = nullptr;  // host inputs: completion of their copies
     if (where == FEW_MEM_HOST) {
         if (!tr->ybuf) {
             void *p = nullptr;
@@ -734,13 +735,14 @@ few_status few_traj_set_data(few_ctx *ctx, few_traj *tr, const double *phi_phi, 
         FEW_CUDA_TRY(cudaMemcpyAsync(y + 2 * K, amp_re, sizeof(double) * K * N, cudaMemcpyHostToDevice, st));
         FEW_CUDA_TRY(cudaMemcpyAsync(y + 2 * K + K * N, amp_im, sizeof(double) * K * N,
                                      cudaMemcpyHostToDevice, st));
-        // the caller may reuse its host arrays on return: wait for these copies only
-        cudaEvent_t ev = nullptr;
-        FEW_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        cudaError_t e1 = cudaEventRecord(ev, st);
-        cudaError_t e2 = e1 == cudaSuccess ? cudaEventSynchronize(ev) : e1;
-        cudaEventDestroy(ev);
-        FEW_CUDA_TRY(e2);
+        // the caller may reuse its host arrays on return: the copies' completion is waited for
+        // after the build is queued behind them, so the device does not idle on the host
+        FEW_CUDA_TRY(cudaEventCreateWithFlags(&copied, cudaEventDisableTiming));
+        if (cudaEventRecord(copied, st) != cudaSuccess) {
+            (void)cudaGetLastError();
+            cudaEventDestroy(copied);
+            return FEW_ERR_CUDA;
+        }
         job.phi_phi = y;
         job.phi_r = y + K;
         job.amp_re = y + 2 * K;
@@ -753,11 +755,23 @@ few_status few_traj_set_data(few_ctx *ctx, few_traj *tr, const double *phi_phi, 
     }
     job.block_begin = 0;
     few_status s = upload(ctx, tr->job_dev, &job, sizeof(job), st);
-    if (s) return s;
     const int blocks = (tr->J + kBuildSplines - 1) / kBuildSplines;
-    tmark(ctx, 0, false, st);
-    FEW_CUDA_TRY(launch_build(tr->job_dev, 1, blocks, tr->K, ctx->d_err, st));
-    tmark(ctx, 0, true, st);
+    if (!s) {
+        tmark(ctx, 0, false, st);
+        if (launch_build(tr->job_dev, 1, blocks, tr->K, ctx->d_err, st) != cudaSuccess) {
+            (void)cudaGetLastError();
+            s = FEW_ERR_CUDA;
+        }
+        tmark(ctx, 0, true, st);
+    }
+    if (copied) {
+        if (cudaEventSynchronize(copied) != cudaSuccess && !s) {
+            (void)cudaGetLastError();
+            s = FEW_ERR_CUDA;
+        }
+        cudaEventDestroy(copied);
+    }
+    if (s) return s;
     tr->src_phi_phi = job.phi_phi;
     tr->src_phi_r = job.phi_r;
     tr->src_re = job.amp_re;
