@@ -69,3 +69,32 @@ def test_mode_select_edge_cases(gpu_ctx):
                                   [True])
     with pytest.raises(F.FewError):
         _gpu_select(gpu_ctx, re, im, modes, -1.0)
+
+
+@pytest.mark.parametrize("N", [1, 2, 31, 127, 128, 129, 255, 257, 1000, 2049, 4096])
+def test_mode_select_ragged_exact(gpu_ctx, N):
+    # integer powers with many exact ties: every prefix sum is exact in FP64, so the cut and the
+    # tie order (lower mode index first) are unique and the masks must agree bit for bit
+    rng = np.random.default_rng(1000 + N)
+    modes = np.stack([np.full(N, 2), rng.integers(0, 3, N), np.zeros(N, int)], axis=1)
+    re = rng.integers(0, 4, (5, N)).astype(np.float64)
+    im = rng.integers(0, 3, (5, N)).astype(np.float64)
+    for eps in (0.5, 0.1, 1e-3, 0.0):
+        g = _gpu_select(gpu_ctx, re, im, modes, eps)
+        o = oracle.mode_select(re, im, modes, eps)
+        np.testing.assert_array_equal(g, o, err_msg=f"N={N} eps={eps}")
+
+
+@pytest.mark.parametrize("N", [129, 2049, 4096])
+def test_mode_select_ragged_random(gpu_ctx, N):
+    rng = np.random.default_rng(2000 + N)
+    modes = np.stack([np.full(N, 2), rng.integers(0, 3, N), np.zeros(N, int)], axis=1)
+    re = rng.standard_normal((7, N)) * np.exp(-3.0 * rng.random(N))
+    im = rng.standard_normal((7, N)) * np.exp(-3.0 * rng.random(N))
+    eps = 1e-4
+    g = _gpu_select(gpu_ctx, re, im, modes, eps)
+    o = oracle.mode_select(re, im, modes, eps)
+    diff = np.where(g != o)[0]
+    assert len(diff) <= 2
+    for i in diff:
+        assert _near_cut(re, im, modes, eps, i), i
