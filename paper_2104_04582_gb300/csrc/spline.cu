@@ -83,6 +83,14 @@ __device__ __forceinline__ double load_y(const BuildJob &jb, int j, int k)
     return ((j - 2) & 1) ? jb.amp_im[idx] : jb.amp_re[idx];
 }
 
+// Bit 31 of the result is set iff x is infinite or NaN (exponent field all ones): the exponent
+// field plus one carries into the sign position only from 0x7ff.  Integer pipe only, so the
+// finiteness screen of the build takes nothing from the narrow FP64 pipe.
+__device__ __forceinline__ unsigned nonfinite_bit(double x)
+{
+    return ((unsigned)__double2hiint(x) & 0x7ff00000u) + 0x00100000u;
+}
+
 // Two threads per spline column: lane l (< 16) of a warp runs the top sweep and lane l + 16 the
 // bottom sweep of the same column, in one instruction stream (direction and coefficients are
 // per-lane data), so the pair meets at row m without divergence and exchanges its reduced
@@ -123,7 +131,7 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
     const bool live = j < J;
     const int jj = live ? j : 0;  // a column past J computes on column 0 and stores nothing
     double *__restrict__ coef = tr.coef;
-    bool finite = true;
+    unsigned bad = 0u;  // bit 31: some column value was not finite
     const int m = (K - 1) / 2;
     const int dir = top ? 1 : -1, k0 = top ? 1 : K - 2;
     const int steps = top ? m : K - 1 - m, steps_max = K - 1 - m;
@@ -131,7 +139,7 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
     // elimination: acc = rhs_k - mult_k acc along rows k0, k0 + dir, ..., m; the window holds
     // y_{k - dir} (yb) and y_k (yc)
     double yb = load_y(jb, jj, k0 - dir), yc = load_y(jb, jj, k0);
-    finite &= isfinite(yb) && isfinite(yc);
+    bad |= nonfinite_bit(yb) | nonfinite_bit(yc);
     double acc = 0.0, rend = 0.0, rm = 0.0;
     for (int i0 = 0; i0 < steps_max; i0 += kChunk) {
         double ya[kChunk];  // y_{k + dir} for the chunk's rows
@@ -143,7 +151,7 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
             const int i = i0 + q;
             if (i >= steps) break;
             const int k = k0 + dir * i;
-            finite &= isfinite(ya[q]);
+            bad |= nonfinite_bit(ya[q]);
             const double ylo = top ? yb : ya[q], yhi = top ? ya[q] : yb;  // y_{k-1}, y_{k+1}
             const double el = yc - ylo, er = yhi - yc;
             double r = fma(ra[k], el, rb[k] * er);
@@ -201,17 +209,19 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
             const int seg = top ? k : k - 1;  // the segment between rows k and k - ds
             const double yl = top ? yv[q] : y_prev, yr = top ? y_prev : yv[q];
             const double sl = top ? s : s_prev, sr = top ? s_prev : s;
+            // power basis in u = (t - t_seg) / h: y_l, h s_l, 3 D - 2 h s_l - h s_r, h s_l + h s_r - 2 D
             const double D = yr - yl, hk = h[seg];
+            const double a = hk * sl, b = hk * sr;
             if (live) {
                 double2 *cc = reinterpret_cast<double2 *>(coef + ((size_t)seg * J + j) * 4);
-                cc[0] = make_double2(yl, hk * sl);
-                cc[1] = make_double2(3.0 * D - hk * (2.0 * sl + sr), hk * (sl + sr) - 2.0 * D);
+                cc[0] = make_double2(yl, a);
+                cc[1] = make_double2(fma(-2.0, a, fma(3.0, D, -b)), fma(-2.0, D, a + b));
             }
             s_prev = s;
             y_prev = yv[q];
         }
     }
-    if (!finite && live) atomicOr(err, ERRBIT_NONFINITE);
+    if ((bad & 0x80000000u) && live) atomicOr(err, ERRBIT_NONFINITE);
 }
 
 cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks, int max_knots,

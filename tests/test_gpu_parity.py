@@ -243,6 +243,21 @@ def test_errors_and_noop(gpu_ctx):
     tr.set_data_host(w.phi_phi, w.phi_r, bad, w.amp_im)
     assert gpu_ctx.sync_status() == F.FEW_ERR_INVALID_ARG
     assert gpu_ctx.sync_status() == F.FEW_OK  # latch cleared
+    # infinities at the end rows (the first values each sweep loads) and a NaN in a phase
+    K = w.phi_phi.shape[0]
+    for which, row, col, val in [("amp_re", 0, 0, np.inf), ("amp_im", K - 1, 5, -np.inf),
+                                 ("phi_r", K // 2, None, np.nan), ("phi_phi", K - 1, None, np.inf)]:
+        arrs = {"phi_phi": w.phi_phi.copy(), "phi_r": w.phi_r.copy(),
+                "amp_re": w.amp_re.copy(), "amp_im": w.amp_im.copy()}
+        if col is None:
+            arrs[which][row] = val
+        else:
+            arrs[which][row, col] = val
+        tr.set_data_host(arrs["phi_phi"], arrs["phi_r"], arrs["amp_re"], arrs["amp_im"])
+        assert gpu_ctx.sync_status() == F.FEW_ERR_INVALID_ARG, which
+        assert gpu_ctx.sync_status() == F.FEW_OK
+    tr.set_data_host(w.phi_phi, w.phi_r, w.amp_re, w.amp_im)
+    assert gpu_ctx.sync_status() == F.FEW_OK
     tr.release()
     with pytest.raises(F.FewError) as e:
         RT.Trajectory(gpu_ctx, [0.0, 1.0, 2.0], w.modes)
