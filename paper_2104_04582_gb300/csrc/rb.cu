@@ -243,11 +243,14 @@ k_rb_quad(const double *__restrict__ are, const double *__restrict__ aim, int M,
 
 // Mixed path, Nb <= 128: the renormalisation scale in one kernel, one wave.  A block takes
 // kTRows knots; their FP32 coefficients and the whole FP32 Gram matrix (j padded to 128) sit in
-// shared memory, and thread (rg, jg) owns knots 4 rg .. 4 rg + 3 and j = jg + 16 t, t < 8, so 12
+// shared memory.  The sum over l is split among kTParts thread groups (l = part mod kTParts);
+// within a group thread (rg, jg) owns knots 4 rg .. 4 rg + 3 and j = jg + 16 t, t < 8, so 12
 // shared-memory reads (half of them broadcasts) feed 128 multiply-adds per l.  The 16 threads of
-// a knot group share a half-warp: q_k is reduced by shuffles and s_k = nu_k / sqrt(q_k) written
-// directly (0 for q_k = 0; a non-finite or negative nu_k latches ERRBIT_NONFINITE).
-constexpr int kTRows = 48, kTJ = 128, kTThreads = (kTRows / 4) * 16;
+// a knot group share a half-warp and reduce their partial q_k by shuffles; the groups' partials
+// are added in group order and s_k = nu_k / sqrt(q_k) written directly (0 for q_k = 0; a
+// non-finite or negative nu_k latches ERRBIT_NONFINITE).
+constexpr int kTRows = 48, kTJ = 128, kTGroup = (kTRows / 4) * 16, kTParts = 3;
+constexpr int kTThreads = kTGroup * kTParts;
 constexpr int kTMaxBasis = kTJ;
 
 __global__ void __launch_bounds__(kTThreads)
@@ -258,7 +261,9 @@ k_rb_scale_tile(const double *__restrict__ are, const double *__restrict__ aim, 
     extern __shared__ __align__(16) float2 rb_tile_smem[];
     float2 *as = rb_tile_smem;                 // [kTRows][Nb] alpha
     float2 *gs = rb_tile_smem + kTRows * Nb;   // [Nb][kTJ] G_jl stored [l][j], zero for j >= Nb
-    const int tid = threadIdx.x, jg = tid & 15, rg = tid >> 4;
+    __shared__ float q_part[kTParts][kTRows];
+    const int tid = threadIdx.x, part = tid / kTGroup, local = tid - part * kTGroup;
+    const int jg = local & 15, rg = local >> 4;
     const int k0 = blockIdx.x * kTRows;
     // staging: 8 independent loads in flight per thread per round trip
     constexpr int kU = 8;
@@ -296,7 +301,7 @@ k_rb_scale_tile(const double *__restrict__ are, const double *__restrict__ aim, 
     for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int t = 0; t < 8; ++t) tr[r][t] = ti[r][t] = 0.f;
-    for (int l = 0; l < Nb; ++l) {
+    for (int l = part; l < Nb; l += kTParts) {
         float2 x[4], g[8];
 #pragma unroll
         for (int r = 0; r < 4; ++r) x[r] = as[(rg * 4 + r) * Nb + l];
@@ -312,7 +317,7 @@ k_rb_scale_tile(const double *__restrict__ are, const double *__restrict__ aim, 
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        const int row = rg * 4 + r, k = k0 + row;
+        const int row = rg * 4 + r;
         float q = 0.f;
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
@@ -323,11 +328,17 @@ k_rb_scale_tile(const double *__restrict__ are, const double *__restrict__ aim, 
             }
         }
         for (int o = 8; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-        if (jg == 0 && k < M) {
-            const double v = nu[k];
-            if (!(v >= 0.0) || !isfinite(v)) atomicOr(err, ERRBIT_NONFINITE);
-            scale[k] = q > 0.f ? v / sqrt((double)q) : 0.0;
-        }
+        if (jg == 0) q_part[part][row] = q;
+    }
+    __syncthreads();
+    if (tid < kTRows && k0 + tid < M) {
+        const int k = k0 + tid;
+        float q = q_part[0][tid];
+#pragma unroll
+        for (int p = 1; p < kTParts; ++p) q += q_part[p][tid];
+        const double v = nu[k];
+        if (!(v >= 0.0) || !isfinite(v)) atomicOr(err, ERRBIT_NONFINITE);
+        scale[k] = q > 0.f ? v / sqrt((double)q) : 0.0;
     }
 }
 
