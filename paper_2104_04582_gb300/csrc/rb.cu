@@ -48,10 +48,11 @@ constexpr uint32_t kRbABytes = kRbTileM * kRbTileK * 2;  // 16 KB: basis (A oper
 constexpr uint32_t kRbBBytes = kRbTileN * kRbTileK * 2;  // 32 KB: coefficients (B operand)
 constexpr uint32_t kRbStageBytes = kRbABytes + kRbBBytes;
 
-// Which fp16 part of the A (coefficient) and B (basis) operand each K segment holds, so that
-// segment g multiplies A part kPartA[g] by B part kPartB[g] (0 = hi, 1 = lo).
-__constant__ int kPartA[kRbParts] = {0, 0, 1};
-__constant__ int kPartB[kRbParts] = {0, 1, 0};
+// Which fp16 part of the A (coefficient) and B (basis) operand each K segment g < kRbParts
+// holds (0 = hi, 1 = lo): the segments multiply hi x hi, hi x lo and lo x hi.  Arithmetic, not a
+// table, so lanes at different segments need no divergent constant-memory reads.
+__host__ __device__ constexpr int part_a(int g) { return g == 2 ? 1 : 0; }
+__host__ __device__ constexpr int part_b(int g) { return g == 1 ? 1 : 0; }
 constexpr int kRbMaxExp = 100;  // bound on the power-of-two scaling exponents
 
 __host__ __device__ constexpr uint32_t core_offset(int r, int c)
@@ -130,7 +131,7 @@ __global__ void k_rb_bexp(const double *__restrict__ bre, const double *__restri
 
 // Basis operand (the MMA's A side), scaled, split and packed: row r of basis tile b is the real
 // (r < 64) or imaginary (r >= 64) output column of mode 64 b + (r mod 64); column c = g 2Nb + q
-// holds part kPartB[g] of 2^bexp[mode] Bhat for that column.  Modes past N and columns past
+// holds part part_b(g) of 2^bexp[mode] Bhat for that column.  Modes past N and columns past
 // 3 x 2Nb are zero.
 __global__ void k_rb_pack_b(const double *__restrict__ bre, const double *__restrict__ bim, int Nb,
                             int N, int n_kb, int n_tiles, const int *__restrict__ bexp,
@@ -158,7 +159,7 @@ __global__ void k_rb_pack_b(const double *__restrict__ bre, const double *__rest
                     const double br = bre[(size_t)j * N + i], bi = bim[(size_t)j * N + i];
                     const double v = imag_out ? (from_im ? br : bi) : (from_im ? -bi : br);
                     x = (float)ldexp(v, bexp[i]);
-                    part = kPartB[g];
+                    part = part_b(g);
                 }
                 v[h] = split_part(x, part);
             }
@@ -356,7 +357,7 @@ __global__ void k_rb_norm(const double *__restrict__ q, const double *__restrict
 
 // Coefficient operand (the MMA's B side), one warp per row: row k of tile k/256, column
 // c = g * 2Nb + q holds part
-// kPartA[g] of 2^aexp[k] x_q, x_q = s_k alpha_k,q (real parts for q < Nb, imaginary parts after).
+// part_a(g) of 2^aexp[k] x_q, x_q = s_k alpha_k,q (real parts for q < Nb, imaginary parts after).
 // The row's x_q are formed once (one FP64 product each, converted on the integer pipe) in shared
 // memory, its largest magnitude sets aexp[k], then the lanes write its 16-byte chunks.  Rows past
 // M are zero.
@@ -388,14 +389,15 @@ k_rb_pack_a(const double *__restrict__ are, const double *__restrict__ aim, int 
         unsigned char *tile = apack + (size_t)(row / kRbTileN) * n_kb * kRbBBytes;
         for (int q8 = lane; q8 < chunks; q8 += 32) {
             const int c0 = q8 * 8;
+            int g = c0 / Kr, q = c0 - g * Kr;  // segment and column of c0, then stepped
             uint32_t wv[4];
 #pragma unroll
             for (int e2 = 0; e2 < 8; e2 += 2) {
                 __half v[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int c = c0 + e2 + h, g = c / Kr;
-                    v[h] = g < kRbParts ? split_part(x[c - g * Kr] * f, kPartA[g]) : __float2half_rn(0.0f);
+                    v[h] = g < kRbParts ? split_part(x[q] * f, part_a(g)) : __float2half_rn(0.0f);
+                    if (++q == Kr) { q = 0; ++g; }
                 }
                 wv[e2 / 2] = pack2(v[0], v[1]);
             }
