@@ -902,25 +902,19 @@ few_status few_mode_select(few_ctx *ctx, const double *amp_re, const double *amp
     if (!ctx || !amp_re || !amp_im || !m || !mask) return FEW_ERR_INVALID_ARG;
     if (K < 1 || N < 1 || !is_fin(eps) || eps < 0.0) return FEW_ERR_INVALID_ARG;
     if (N > mode_select_max_modes()) return FEW_ERR_LIMIT;
-    for (int i = 0; i < N; ++i)
+    ModeDoubling dbl{};
+    for (int i = 0; i < N; ++i) {
         if (m[i] < 0) return FEW_ERR_MODES;
+        if (m[i] > 0) dbl.w[i >> 5] |= 1u << (i & 31);
+    }
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    void *d = nullptr;
-    few_status st = dev_alloc(ctx, sizeof(int) * (size_t)N, s, &d);
-    if (st) return st;
-    st = upload(ctx, d, m, sizeof(int) * (size_t)N, s);
-    if (!st) {
-        cudaError_t e = launch_mode_select(amp_re, amp_im, K, N, static_cast<const int *>(d), eps,
-                                           mask, s);
-        if (e != cudaSuccess) {
-            (void)cudaGetLastError();
-            st = FEW_ERR_CUDA;
-        }
+    if (launch_mode_select(amp_re, amp_im, K, N, dbl, eps, mask, s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return FEW_ERR_CUDA;
     }
-    dev_free(ctx, d, s);
-    return st;
+    return FEW_OK;
 }
 
 few_status few_direct_sum(few_ctx *ctx, const double *pphi, const double *pr, const double *are,

@@ -121,8 +121,16 @@ cudaError_t launch_sum(const PlanHdr *hdr_dev, int grid, int threads, int sample
 int sum_slot_bytes(int variant);
 cudaError_t launch_phases(const TrajDev &tr, const int *seg_start, double t0, double dt, int n,
                           double dphi_phi, double dphi_r, double *out, cudaStream_t st);
+// Mode Selector: at most kSelectMaxModes modes; which of them stand for an m < 0 partner too
+// (m > 0, power doubled) travels as one bit per mode (bit i % 32 of word i / 32) in the launch
+// parameters, so a call needs no device allocation or copy.
+constexpr int kSelectMaxModes = 4096;
+struct ModeDoubling {
+    unsigned w[kSelectMaxModes / 32];
+};
 cudaError_t launch_mode_select(const double *amp_re, const double *amp_im, int K, int N,
-                               const int *m_dev, double eps, unsigned char *mask, cudaStream_t st);
+                               const ModeDoubling &dbl, double eps, unsigned char *mask,
+                               cudaStream_t st);
 int mode_select_max_modes();
 cudaError_t launch_direct(const double *pphi, const double *pr, const double *are,
                           const double *aim, long long ns, const int *l, const int *m, const int *n,

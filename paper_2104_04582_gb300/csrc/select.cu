@@ -19,7 +19,6 @@
 namespace fewsum {
 
 constexpr int kSelectMaxThreads = 1024;
-constexpr int kSelectMaxModes = 4096;
 constexpr int kSelectPerThread = 4;  // consecutive sort slots per thread
 constexpr int kSelectWarpSlots = 32 * kSelectPerThread;
 
@@ -64,7 +63,8 @@ __device__ __forceinline__ void cx_keep(unsigned long long &k, int &i, unsigned 
 
 __global__ void __launch_bounds__(kSelectMaxThreads)
 k_mode_select(const double *__restrict__ amp_re, const double *__restrict__ amp_im, int N,
-              const int *__restrict__ m, double eps, int P, unsigned char *__restrict__ mask)
+              const __grid_constant__ ModeDoubling dbl, double eps, int P,
+              unsigned char *__restrict__ mask)
 {
     extern __shared__ __align__(16) unsigned long long sel_key[];  // [P] keys, then [P] indices
     int *sel_ix = reinterpret_cast<int *>(sel_key + P);
@@ -83,7 +83,7 @@ k_mode_select(const double *__restrict__ amp_re, const double *__restrict__ amp_
         if (i < N) {
             const double re = amp_re[(size_t)k * N + i], im = amp_im[(size_t)k * N + i];
             double p = re * re + im * im;
-            if (m[i] > 0) p *= 2.0;
+            if ((dbl.w[i >> 5] >> (i & 31)) & 1u) p *= 2.0;  // m > 0
             key[r] = power_key(p);
             ix[r] = i;
         } else {
@@ -197,7 +197,8 @@ k_mode_select(const double *__restrict__ amp_re, const double *__restrict__ amp_
 }
 
 cudaError_t launch_mode_select(const double *amp_re, const double *amp_im, int K, int N,
-                               const int *m_dev, double eps, unsigned char *mask, cudaStream_t st)
+                               const ModeDoubling &dbl, double eps, unsigned char *mask,
+                               cudaStream_t st)
 {
     int P = kSelectWarpSlots;
     while (P < N) P <<= 1;
@@ -208,7 +209,7 @@ cudaError_t launch_mode_select(const double *amp_re, const double *amp_im, int K
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(mask, 0, (size_t)N, st);
     if (e != cudaSuccess) return e;
-    k_mode_select<<<K, threads, smem, st>>>(amp_re, amp_im, N, m_dev, eps, P, mask);
+    k_mode_select<<<K, threads, smem, st>>>(amp_re, amp_im, N, dbl, eps, P, mask);
     return cudaGetLastError();
 }
 
