@@ -238,8 +238,10 @@ few_status few_phase_samples(few_ctx *ctx, const few_traj *traj, double t0, doub
  *   amp_re_dev, amp_im_dev [K][N]: device arrays, row-major (modes contiguous).
  *   m [N]: host array of the modes' m (>= 0).  eps >= 0.  N <= 4096.
  *   mask_dev: N bytes of device memory (overwritten).
- * Asynchronous on `stream`.  The cumulative sums run in FP64 in a parallel order, so a mode
- * whose cumulative power lies within rounding of the cut may be decided either way.
+ * Asynchronous on `stream`.  The result is exact with respect to this definition evaluated in
+ * FP64: each power is fl(fl(re^2) + fl(im^2)) (no fused multiply-add) and each cumulative sum is
+ * the left-to-right FP64 sum over the sorted powers, the total being the last of them, so the
+ * mask does not depend on the GPU's scheduling.
  */
 few_status few_mode_select(few_ctx *ctx, const double *amp_re_dev, const double *amp_im_dev, int K,
                            int N, const int *m, double eps, unsigned char *mask_dev, void *stream);

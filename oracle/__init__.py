@@ -31,13 +31,18 @@ _ip = ctypes.POINTER(ctypes.c_int)
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c with gcc (OpenMP, -O2, no target-specific flags)."""
+    """Compile oracle.c with gcc (OpenMP, -O2, no target-specific flags).
+
+    Expressions are evaluated as written (no contraction of a*b + c into a fused multiply-add,
+    on x86-64 and on aarch64 alike), so every rounding step is the one the source shows.
+    """
     os.makedirs(_LIBDIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-fopenmp", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
+    cmd = ["gcc", "-O2", "-fopenmp", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", _SRC,
+           "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH

@@ -6,14 +6,21 @@
 // leading run whose cumulative power reaches (1 - eps) of the knot's total.  The selection is the
 // union of the kept sets over all knots.
 //
+// The selection is index output, so it is decided exactly as the plain definition computes it:
+// the power is fl(fl(re^2) + fl(im^2)) (no fused multiply-add), and the cumulative sums are the
+// left-to-right FP64 sums over the sorted powers, c_j = fl(c_{j-1} + p_j), with the total equal
+// to the last of them.  Any other summation order can round differently and move the cut.
+//
 // One CTA per knot, P = max(128, next power of two >= N) sort slots, P/4 threads holding four
 // consecutive slots each in registers.  Bitonic sort of (power, index) pairs: the exchanges at
 // distances 1 and 2 stay inside a thread, distances 4..64 are warp shuffles (a warp holds 128
 // consecutive slots), and only distances >= 128 pass through shared memory.  The sorted powers
-// are then scanned in FP64 straight from the registers (thread, warp, block), the first rank whose
-// prefix reaches the target is found with an atomic minimum, and the kept modes are marked with
-// plain byte stores of 1 into a mask zeroed beforehand (every writer stores the same value, so
-// the union needs no atomics).
+// then go to shared memory and one thread runs the sequential sum.  The powers are non-negative
+// and sorted in descending order, so once an addition leaves the running sum unchanged every
+// later one does too (rounding is monotone): the chain stops there and the sums that follow all
+// equal the total.  The first rank whose sum reaches the target is found by all threads with an
+// atomic minimum, and the kept modes are marked with plain byte stores of 1 into a mask zeroed
+// beforehand (every writer stores the same value, so the union needs no atomics).
 #include "fewsum_internal.h"
 
 namespace fewsum {
@@ -21,6 +28,7 @@ namespace fewsum {
 constexpr int kSelectMaxThreads = 1024;
 constexpr int kSelectPerThread = 4;  // consecutive sort slots per thread
 constexpr int kSelectWarpSlots = 32 * kSelectPerThread;
+constexpr int kChainChunk = 8;  // powers loaded ahead of the sequential sum's additions
 
 // Non-negative doubles order exactly like their IEEE bit patterns read as unsigned integers, so
 // the sort compares 64-bit integer keys (descending power = ascending inverted bits), with the
@@ -68,11 +76,10 @@ k_mode_select(const double *__restrict__ amp_re, const double *__restrict__ amp_
 {
     extern __shared__ __align__(16) unsigned long long sel_key[];  // [P] keys, then [P] indices
     int *sel_ix = reinterpret_cast<int *>(sel_key + P);
-    __shared__ double warp_tot[kSelectMaxThreads / 32];
     __shared__ double s_total;
+    __shared__ int s_conv;
     __shared__ int s_cut;
     const int k = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, wid = tid >> 5;
     const int p0 = kSelectPerThread * tid;  // first slot of this thread
 
     unsigned long long key[kSelectPerThread];
@@ -82,7 +89,7 @@ k_mode_select(const double *__restrict__ amp_re, const double *__restrict__ amp_
         const int i = p0 + r;
         if (i < N) {
             const double re = amp_re[(size_t)k * N + i], im = amp_im[(size_t)k * N + i];
-            double p = re * re + im * im;
+            double p = __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
             if ((dbl.w[i >> 5] >> (i & 31)) & 1u) p *= 2.0;  // m > 0
             key[r] = power_key(p);
             ix[r] = i;
@@ -142,58 +149,64 @@ k_mode_select(const double *__restrict__ amp_re, const double *__restrict__ amp_
         cx_pair(key[2], ix[2], key[3], ix[3], ((p0 + 2) & size) == 0);
     }
 
-    // inclusive prefix sums of the sorted powers (padding adds +0): thread, warp, block
-    double pre[kSelectPerThread];
-    double run = 0.0;
+    // sorted powers to shared memory (slot j = rank j; padding holds +0)
+    double *s_pw = reinterpret_cast<double *>(sel_key);
+    __syncthreads();  // the last shared-memory exchange stage may still be read
 #pragma unroll
-    for (int r = 0; r < kSelectPerThread; ++r) {
-        run += key_power(key[r]);
-        pre[r] = run;
-    }
-    double incl = run;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    double excl = __shfl_up_sync(0xffffffffu, incl, 1);
-    if (lane == 0) excl = 0.0;
-    if (lane == 31) warp_tot[wid] = incl;
+    for (int r = 0; r < kSelectPerThread; ++r) s_pw[p0 + r] = key_power(key[r]);
     __syncthreads();
-    if (wid == 0) {
-        double w = lane < nt / 32 ? warp_tot[lane] : 0.0;
+
+    // the sequential cumulative sum, c_j = fl(c_{j-1} + p_j), in place: s_pw[j] <- c_j for
+    // j < s_conv; every c_j with j >= s_conv equals the total
+    if (tid == 0) {
+        double c = 0.0;
+        int conv = N;
+        double v[kChainChunk], nv[kChainChunk];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const double v = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += v;
+        for (int q = 0; q < kChainChunk; ++q) v[q] = s_pw[q];
+        for (int j0 = 0; j0 < N; j0 += kChainChunk) {
+            // next chunk's loads ahead of this chunk's additions (P is a multiple of the chunk)
+            const int jn = j0 + kChainChunk < P ? j0 + kChainChunk : j0;
+#pragma unroll
+            for (int q = 0; q < kChainChunk; ++q) nv[q] = s_pw[jn + q];
+            const double c_start = c;
+#pragma unroll
+            for (int q = 0; q < kChainChunk; ++q) {
+                c = __dadd_rn(c, v[q]);
+                s_pw[j0 + q] = c;
+            }
+            // c never decreases: unchanged across the chunk means no addition changed it, so
+            // neither does any later (smaller) power
+            if (c == c_start) {
+                conv = j0;
+                break;
+            }
+#pragma unroll
+            for (int q = 0; q < kChainChunk; ++q) v[q] = nv[q];
         }
-        double we = __shfl_up_sync(0xffffffffu, w, 1);
-        if (lane == 0) we = 0.0;
-        if (lane < nt / 32) warp_tot[lane] = we;  // exclusive over warps
-    }
-    __syncthreads();
-    const double offset = excl + warp_tot[wid];
-#pragma unroll
-    for (int r = 0; r < kSelectPerThread; ++r) {
-        pre[r] += offset;
-        if (p0 + r == N - 1) s_total = pre[r];  // the knot's total is the last real prefix
+        s_conv = conv;
+        s_total = c;
     }
     __syncthreads();
     const double total = s_total;
+    const int conv = s_conv;
     if (!(total > 0.0)) return;  // uniform: nothing kept at a knot without power
-    const double target = (1.0 - eps) * total;  // <= total, so some rank below N reaches it
+    const double target = (1.0 - eps) * total;
 #pragma unroll
     for (int r = 0; r < kSelectPerThread; ++r) {
-        if (p0 + r < N && pre[r] >= target) {
-            atomicMin(&s_cut, p0 + r);
+        const int j = p0 + r;
+        if (j >= N) break;
+        const double cj = j < conv ? s_pw[j] : total;
+        if (cj >= target) {
+            atomicMin(&s_cut, j);
             break;
         }
     }
     __syncthreads();
-    const int cut = s_cut;
+    const int cut = s_cut;  // no rank reaching the target keeps every mode
 #pragma unroll
     for (int r = 0; r < kSelectPerThread; ++r)
-        if (p0 + r <= cut) mask[ix[r]] = 1;
+        if (p0 + r < N && p0 + r <= cut) mask[ix[r]] = 1;
 }
 
 cudaError_t launch_mode_select(const double *amp_re, const double *amp_im, int K, int N,
