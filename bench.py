@@ -43,7 +43,7 @@ WORKLOAD = ("1-yr waveform, dt=10 s (3,155,760 samples), K=100 knots, 3843 modes
 # summarised in profiles/k_sum_mixed_1yr_3843modes.md; used only while the kernel source is the
 # one that was profiled (hash of sum.cu + phase_eval.cuh + async.cuh) and the tile is the
 # profiled one.
-PROFILED_TRAFFIC = {"source_sha256_16": "ea83547a100f196d", "tile": (4, 256, False), "bytes": 4113920 + 256}
+PROFILED_TRAFFIC = {"source_sha256_16": "ea83547a100f196d", "tile": (4, 256), "bytes": 4113920 + 256}
 N_SMS = 152
 FP32_LANES_PER_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25
@@ -298,7 +298,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
 
     tr = RT.Trajectory(ctx, w.t_knots, w.modes)
     dev_in = tr.upload_inputs(w.phi_phi, w.phi_r, w.amp_re, w.amp_im)
-    tile = tuple(ctx.get_tiles(prec)) + (False,)
+    tile = tuple(ctx.get_tiles(prec))
     out = RT.alloc_out(w.n_samples, c64, local_rank)
     req = RT.request(tr, out, w.n_samples, w.t0, w.dt, w.theta, w.phi, prec)
     flush = l2_flush_buffer(torch, dev)

@@ -52,7 +52,7 @@
 extern "C" {
 #endif
 
-#define FEW_ABI_VERSION 3
+#define FEW_ABI_VERSION 4
 #define FEW_MAX_SLOTS_FP64 1776
 #define FEW_MAX_SLOTS_MIXED 3552
 
@@ -196,20 +196,22 @@ few_status few_waveform(few_ctx *ctx, const few_request *req, void *stream);
  * for callers that must not allocate memory once they are running -- e.g. a sampler or a
  * real-time pipeline that reserves all device memory at start-up, or code under a policy that
  * forbids cudaMalloc (and the synchronisation it can imply) on the call path.  It computes
- * exactly what few_waveform computes for the same request, but keeps its scratch (plan,
- * harmonic table, folded coefficients) in one fixed device array of FEW_NOALLOC_SCRATCH_BYTES
- * that is part of the library image (reserved on every GPU that loads the library, until the
- * process exits) and calls no allocator of any kind.
+ * what few_waveform computes for the same request (either frame), but keeps its scratch (plan,
+ * harmonic table, folded coefficients and, for FEW_MIXED, the phase anchors) in one fixed device
+ * array of FEW_NOALLOC_SCRATCH_BYTES that is part of the library image (reserved on every GPU
+ * that loads the library, until the process exits) and calls no allocator of any kind.
  *   req->out_where must be FEW_MEM_DEVICE; the trajectory and the output buffer are the
  *   caller's, as for few_waveform.
- * Limits: the request's scratch (about 8 x slots x K x 4 bytes for FEW_MIXED, twice that for
- *   FEW_FP64, plus a few KB) must fit in FEW_NOALLOC_SCRATCH_BYTES and K <= 4096; otherwise it
- *   returns FEW_ERR_LIMIT without queuing work.  The one-year 3843-mode waveform fits in both
- *   precisions; the four-year one (K = 300) fits only for FEW_MIXED.
+ * Limits: the request's scratch must fit in FEW_NOALLOC_SCRATCH_BYTES and K <= 4096; otherwise
+ *   it returns FEW_ERR_LIMIT without queuing work.  The scratch is about 64 x slots x (K - 1)
+ *   bytes for FEW_FP64; for FEW_MIXED 32 x slots x (K - 1) bytes plus 2 bytes per output sample
+ *   (the phase anchors), plus a few KB.  The one-year 3843-mode waveform (K = 100,
+ *   3,155,760 samples) fits in both precisions; the four-year one at dt = 2 s does not.
  * The first call made on a device looks up the array's device address (once per device);
  *   make that first call before any stream capture.  All calls share the array: every call
  *   rewrites what it uses, but calls whose work overlaps on the GPU race on it -- order them
- *   (one stream, or events).  Asynchronous on `stream`.
+ *   (one stream, or events).  Asynchronous on `stream`; the caller's current device is
+ *   restored on return.
  */
 #define FEW_NOALLOC_SCRATCH_BYTES (16u << 20)
 #define FEW_MAX_BASIS 256  /* reduced-basis size limit of few_basis_create */
@@ -338,13 +340,6 @@ few_status few_sync_status(few_ctx *ctx);
  */
 few_status few_set_tiles(few_ctx *ctx, int prec, int samples_per_thread, int threads_per_block);
 few_status few_get_tiles(few_ctx *ctx, int prec, int *samples_per_thread, int *threads_per_block);
-
-/*
- * FEW_MIXED summation instruction set: packed FP32x2 FMA (enable = 1; used when the tile has
- * R in {4, 8} and the per-segment table has at most FEW_MAX_SLOTS_FP64 slots) or scalar FP32
- * FMA (enable = 0, the default).  Speed only: both give bit-identical results.
- */
-few_status few_set_packed(few_ctx *ctx, int enable);
 
 /*
  * Per-kernel device timing.  With timing enabled, the library records a CUDA event pair on the

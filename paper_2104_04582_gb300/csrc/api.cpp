@@ -106,7 +106,6 @@ struct few_ctx {
     PinnedPool pinned;
     int tile_R[2] = {1, 4};
     int tile_T[2] = {256, 256};
-    bool packed = false;  // packed FP32x2 summation for FEW_MIXED when the slot table fits
     std::map<std::tuple<int, int, int, int>, int> occ_cache;
     bool timing = false;
     cudaEvent_t tev[8] = {};
@@ -302,6 +301,7 @@ struct few_batch {
     void *jobs_dev = nullptr;
     int n_jobs = 0, build_blocks = 0, max_knots = 0;
     int grid = 0, threads = 0, R = 0, smem = 0, total_pairs = 0, total_fold = 0;
+    int total_anchors = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -311,22 +311,15 @@ namespace {
 // Host image of a plan (the blob) plus its scratch requirements.
 struct PlanImage {
     std::vector<unsigned char> blob;
-    size_t off_waves = 0, off_cta = 0, off_seg = 0;
+    size_t off_waves = 0, off_cta = 0, off_seg = 0, off_anc = 0;
     size_t scratch_bytes = 0;
-    std::vector<size_t> fcoef_off, ylm_off;
+    std::vector<size_t> fcoef_off, ylm_off, anchor_off;
+    std::vector<std::vector<int64_t>> seg;  // per wave: segment sample ranges [K]
     bool fp64 = false;
     int variant = kVariantFp64;
     int grid = 0, threads = 0, R = 0, smem = 0, buf_bytes = 0, total_pairs = 0, total_fold = 0;
+    int total_anchors = 0;
 };
-
-// Summation variant of a plan: FP64, or for the mixed path the packed FP32x2 kernel when the
-// largest slot table fits its (duplicated) layout and the tile has R in {4, 8}, else scalar FP32.
-int pick_variant(bool fp64, bool packed_ok, int R, int max_slots)
-{
-    if (fp64) return kVariantFp64;
-    if (packed_ok && (R == 4 || R == 8) && max_slots <= kMaxSlotsPacked) return kVariantPacked;
-    return kVariantScalar;
-}
 
 int occupancy(few_ctx *c, int variant, int R, int T, int smem)
 {
@@ -382,7 +375,7 @@ few_status build_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P)
     P.threads = c->tile_T[pi];
     int max_slots = 1;
     for (int q = 0; q < n; ++q) max_slots = std::max(max_slots, reqs[q].traj->plan.n_slots);
-    P.variant = pick_variant(P.fp64, c->packed, P.R, max_slots);
+    P.variant = P.fp64 ? kVariantFp64 : kVariantScalar;
     const size_t slot_bytes = (size_t)sum_slot_bytes(P.variant);
     P.buf_bytes = (int)align_up((size_t)max_slots * slot_bytes, 128);
     P.smem = 2 * P.buf_bytes;
@@ -399,19 +392,36 @@ few_status build_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P)
     P.off_seg = off;
     size_t seg_ints = 0;
     for (int q = 0; q < n; ++q) seg_ints += reqs[q].traj->K;
-    off = align_up(off + sizeof(int) * seg_ints, 256);
+    off = align_up(off + sizeof(int) * seg_ints, 64);
+    P.off_anc = off;  // per wave: first anchor of each segment, then the wave's total
+    if (!P.fp64) off += sizeof(int) * seg_ints;
+    off = align_up(off, 256);
     P.blob.assign(off, 0);
+    P.seg.resize(n);
+    for (int q = 0; q < n; ++q) {
+        const few_request &r = reqs[q];
+        P.seg[q].resize(r.traj->K);
+        segments(r.traj->t_host.data(), r.traj->K, r.t0, r.dt, r.n_samples, P.seg[q].data());
+    }
 
     // scratch: folded coefficients and harmonic tables per wave
     size_t s_off = 0;
     P.fcoef_off.resize(n);
     P.ylm_off.resize(n);
+    P.anchor_off.resize(n);
     for (int q = 0; q < n; ++q) {
         const few_traj *tr = reqs[q].traj;
         P.fcoef_off[q] = s_off;
         s_off = align_up(s_off + (size_t)tr->S * tr->plan.n_slots * slot_bytes, 256);
         P.ylm_off[q] = s_off;
         s_off = align_up(s_off + (size_t)tr->plan.pair_lm.size() * 2 * sizeof(double2), 256);
+        P.anchor_off[q] = s_off;
+        if (!P.fp64) {
+            int na = 0;
+            for (int k = 0; k + 1 < tr->K; ++k)
+                na += anchors_in_segment((int)P.seg[q][k], (int)P.seg[q][k + 1]);
+            s_off = align_up(s_off + sizeof(Anchor) * (size_t)na, 256);
+        }
     }
     P.scratch_bytes = s_off;
     return FEW_OK;
@@ -425,9 +435,9 @@ void fill_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P, unsign
     WaveDev *wv = reinterpret_cast<WaveDev *>(P.blob.data() + P.off_waves);
     CtaStart *cta = reinterpret_cast<CtaStart *>(P.blob.data() + P.off_cta);
     int *seg = reinterpret_cast<int *>(P.blob.data() + P.off_seg);
+    int *anc = reinterpret_cast<int *>(P.blob.data() + P.off_anc);
     size_t seg_pos = 0;
-    int pair_begin = 0, fold_begin = 0;
-    std::vector<int64_t> tmp;
+    int pair_begin = 0, fold_begin = 0, anchor_begin = 0;
     std::vector<long double> cum(n + 1, 0.0L);
     for (int q = 0; q < n; ++q) {
         const few_request &r = reqs[q];
@@ -450,10 +460,21 @@ void fill_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P, unsign
         W.out = outs[q];
         W.fcoef = scratch_dev + P.fcoef_off[q];
         W.ylm = reinterpret_cast<double2 *>(scratch_dev + P.ylm_off[q]);
-        tmp.resize(tr->K);
-        segments(tr->t_host.data(), tr->K, r.t0, r.dt, r.n_samples, tmp.data());
-        for (int k = 0; k < tr->K; ++k) seg[seg_pos + k] = (int)tmp[k];
+        const std::vector<int64_t> &ss = P.seg[q];
+        for (int k = 0; k < tr->K; ++k) seg[seg_pos + k] = (int)ss[k];
         W.seg_start = reinterpret_cast<const int *>(blob_dev + P.off_seg) + seg_pos;
+        if (!P.fp64) {
+            int a = 0;
+            for (int k = 0; k + 1 < tr->K; ++k) {
+                anc[seg_pos + k] = a;
+                a += anchors_in_segment((int)ss[k], (int)ss[k + 1]);
+            }
+            anc[seg_pos + tr->K - 1] = a;
+            W.anchors = reinterpret_cast<Anchor *>(scratch_dev + P.anchor_off[q]);
+            W.anchor_off = reinterpret_cast<const int *>(blob_dev + P.off_anc) + seg_pos;
+            W.anchor_begin = anchor_begin;
+            anchor_begin += a;
+        }
         seg_pos += tr->K;
         W.pair_begin = pair_begin;
         pair_begin += (int)tr->plan.pair_lm.size();
@@ -465,6 +486,7 @@ void fill_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P, unsign
     }
     P.total_pairs = pair_begin;
     P.total_fold = fold_begin;
+    P.total_anchors = anchor_begin;
     // equal-cost CTA slices of the concatenated (wave, sample) space
     const long double total = cum[n];
     int q = 0;
@@ -484,6 +506,7 @@ void fill_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P, unsign
     hdr->n_waves = n;
     hdr->total_pairs = P.total_pairs;
     hdr->total_fold_blocks = P.total_fold;
+    hdr->total_anchors = P.total_anchors;
     hdr->grid_sum = P.grid;
     hdr->buf_bytes = P.buf_bytes;
     hdr->variant = P.variant;
@@ -493,13 +516,15 @@ void fill_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P, unsign
 }
 
 few_status launch_kernels(few_ctx *c, const PlanHdr *hdr_dev, int total_pairs, int total_fold,
-                          int grid, int threads, int R, int smem, int variant, cudaStream_t st)
+                          int total_anchors, int grid, int threads, int R, int smem, int variant,
+                          cudaStream_t st)
 {
     tmark(c, 1, false, st);
     FEW_CUDA_TRY(launch_ylm(hdr_dev, total_pairs, variant == kVariantFp64, st));
     tmark(c, 1, true, st);
     tmark(c, 2, false, st);
     FEW_CUDA_TRY(launch_fold(hdr_dev, total_fold, variant == kVariantFp64, st));
+    FEW_CUDA_TRY(launch_anchor(hdr_dev, total_anchors, st));
     tmark(c, 2, true, st);
     tmark(c, 3, false, st);
     FEW_CUDA_TRY(launch_sum(hdr_dev, grid, threads, R, smem, variant, st));
@@ -549,7 +574,8 @@ few_status few_ctx_create(few_ctx **out, int device, size_t hbm_budget_bytes)
         delete c;
         return s;
     };
-    if (cudaSetDevice(device) != cudaSuccess) return fail(FEW_ERR_CUDA);
+    DeviceScope dev_scope(device);
+    if (!dev_scope.ok) return fail(FEW_ERR_CUDA);
     if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return fail(FEW_ERR_CUDA);
     cudaMemPoolProps props{};
@@ -579,7 +605,7 @@ few_status few_ctx_destroy(few_ctx *ctx)
     if (!ctx) return FEW_OK;
     {
         std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-        cudaSetDevice(ctx->device);
+        DeviceScope dev_scope(ctx->device);
         cudaDeviceSynchronize();
         auto bs = ctx->batches;
         for (few_batch *b : bs) few_batch_release(ctx, b);
@@ -620,7 +646,8 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
     SlotPlan plan;
     if ((st = plan_slots(l, m, n, N, plan))) return st;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    DeviceScope dev_scope(ctx->device);
+    if (!dev_scope.ok) return FEW_ERR_CUDA;
     few_traj *tr = new (std::nothrow) few_traj();
     if (!tr) return FEW_ERR_NOMEM;
     tr->ctx = ctx;
@@ -715,7 +742,8 @@ few_status few_traj_set_data(few_ctx *ctx, few_traj *tr, const double *phi_phi, 
     if (!phi_phi || !phi_r || !amp_re || !amp_im) return FEW_ERR_INVALID_ARG;
     if (where != FEW_MEM_HOST && where != FEW_MEM_DEVICE) return FEW_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    DeviceScope dev_scope(ctx->device);
+    if (!dev_scope.ok) return FEW_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t K = tr->K, N = tr->N;
     BuildJob job{};
@@ -784,7 +812,7 @@ few_status few_traj_release(few_ctx *ctx, few_traj *tr)
 {
     if (!ctx || !tr || tr->ctx != ctx) return FEW_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    cudaSetDevice(ctx->device);
+    DeviceScope dev_scope(ctx->device);
     cudaDeviceSynchronize();
     dev_free(ctx, tr->ybuf, ctx->internal);
     dev_free(ctx, tr->dmem, ctx->internal);
@@ -812,7 +840,8 @@ few_status few_waveform(few_ctx *ctx, const few_request *req, void *stream)
     if (req->traj->ctx != ctx) return FEW_ERR_INVALID_ARG;
     if (req->n_samples == 0) return FEW_OK;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    DeviceScope dev_scope(ctx->device);
+    if (!dev_scope.ok) return FEW_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     PlanImage P;
     if ((st = build_image(ctx, req, 1, P))) return st;
@@ -847,7 +876,7 @@ few_status few_waveform(few_ctx *ctx, const few_request *req, void *stream)
     st = upload(ctx, blob, P.blob.data(), P.blob.size(), s);
     if (!st)
         st = launch_kernels(ctx, static_cast<const PlanHdr *>(blob), P.total_pairs, P.total_fold,
-                            P.grid, P.threads, P.R, P.smem, P.variant, s);
+                            P.total_anchors, P.grid, P.threads, P.R, P.smem, P.variant, s);
     if (!st && dout) {
         cudaError_t e = cudaMemcpyAsync(req->out, dout, out_bytes, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) {
@@ -878,7 +907,8 @@ few_status few_phase_samples(few_ctx *ctx, const few_traj *tr, double t0, double
     if (st) return st;
     if (n == 0) return FEW_OK;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    DeviceScope dev_scope(ctx->device);
+    if (!dev_scope.ok) return FEW_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     std::vector<int> seg32(seg.begin(), seg.end());
     void *d = nullptr;
@@ -908,7 +938,8 @@ few_status few_mode_select(few_ctx *ctx, const double *amp_re, const double *amp
         if (m[i] > 0) dbl.w[i >> 5] |= 1u << (i & 31);
     }
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    DeviceScope dev_scope(ctx->device);
+    if (!dev_scope.ok) return FEW_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (launch_mode_select(amp_re, amp_im, K, N, dbl, eps, mask, s) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -930,7 +961,8 @@ few_status few_direct_sum(few_ctx *ctx, const double *pphi, const double *pr, co
     if (st) return st;
     if (ns == 0) return FEW_OK;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    DeviceScope dev_scope(ctx->device);
+    if (!dev_scope.ok) return FEW_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t mc_bytes = align_up(direct_mode_const_bytes(N), 256);
     const size_t idx_bytes = align_up(sizeof(int) * (size_t)N, 256);
@@ -978,7 +1010,8 @@ few_status few_basis_create(few_ctx *ctx, const double *b_re, const double *b_im
     if (Nb > FEW_MAX_BASIS) return FEW_ERR_LIMIT;
     *out = nullptr;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    DeviceScope dev_scope(ctx->device);
+    if (!dev_scope.ok) return FEW_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const RbLayout L = rb_layout(Nb, N, 0);
     const size_t b_bytes = align_up(sizeof(double) * (size_t)Nb * N, 256);
@@ -1031,7 +1064,7 @@ few_status few_basis_release(few_ctx *ctx, few_basis *b)
 {
     if (!ctx || !b || b->ctx != ctx) return FEW_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    cudaSetDevice(ctx->device);
+    DeviceScope dev_scope(ctx->device);
     cudaDeviceSynchronize();
     dev_free(ctx, b->dmem, ctx->internal);
     cudaStreamSynchronize(ctx->internal);
@@ -1050,7 +1083,8 @@ few_status few_rb_amplitudes(few_ctx *ctx, const few_basis *b, const double *are
     if (M == 0) return FEW_OK;
     if (!are || !aim || !ore || !oim) return FEW_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    DeviceScope dev_scope(ctx->device);
+    if (!dev_scope.ok) return FEW_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool fp64 = prec == FEW_FP64;
     const RbLayout L = rb_layout(b->Nb, b->N, M);
@@ -1082,7 +1116,8 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
         if (reqs[q].traj->ctx != ctx || reqs[q].prec != reqs[0].prec) return FEW_ERR_INVALID_ARG;
     }
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    DeviceScope dev_scope(ctx->device);
+    if (!dev_scope.ok) return FEW_ERR_CUDA;
     PlanImage P;
     few_status st = build_image(ctx, reqs, n, P);
     if (st) return st;
@@ -1141,6 +1176,7 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
     b->smem = P.smem;
     b->total_pairs = P.total_pairs;
     b->total_fold = P.total_fold;
+    b->total_anchors = P.total_anchors;
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(FEW_ERR_CUDA);
     if (!(flags & FEW_BATCH_NO_GRAPH)) {
         cudaStream_t cap = nullptr;
@@ -1153,6 +1189,7 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
                              b->max_knots, ctx->d_err, cap);
             launch_ylm(hd, b->total_pairs, b->fp64, cap);
             launch_fold(hd, b->total_fold, b->fp64, cap);
+            launch_anchor(hd, b->total_anchors, cap);
             launch_sum(hd, b->grid, b->threads, b->R, b->smem, b->variant, cap);
             e = cudaStreamEndCapture(cap, &b->graph);
         }
@@ -1169,7 +1206,8 @@ few_status few_batch_run(few_ctx *ctx, few_batch *b, void *stream)
 {
     if (!ctx || !b || b->ctx != ctx) return FEW_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    DeviceScope dev_scope(ctx->device);
+    if (!dev_scope.ok) return FEW_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (b->exec) {
         FEW_CUDA_TRY(cudaGraphLaunch(b->exec, s));
@@ -1182,15 +1220,15 @@ few_status few_batch_run(few_ctx *ctx, few_batch *b, void *stream)
                                   b->build_blocks, b->max_knots, ctx->d_err, s));
         tmark(ctx, 0, true, s);
     }
-    return launch_kernels(ctx, hd, b->total_pairs, b->total_fold, b->grid, b->threads, b->R,
-                          b->smem, b->variant, s);
+    return launch_kernels(ctx, hd, b->total_pairs, b->total_fold, b->total_anchors, b->grid,
+                          b->threads, b->R, b->smem, b->variant, s);
 }
 
 few_status few_batch_release(few_ctx *ctx, few_batch *b)
 {
     if (!ctx || !b || b->ctx != ctx) return FEW_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    cudaSetDevice(ctx->device);
+    DeviceScope dev_scope(ctx->device);
     // The caller guarantees the batch's work has completed (an event, a stream sync); no device
     // synchronisation here, so other work in flight keeps running.
     if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -1209,7 +1247,8 @@ few_status few_sync_status(few_ctx *ctx)
 {
     if (!ctx) return FEW_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    DeviceScope dev_scope(ctx->device);
+    if (!dev_scope.ok) return FEW_ERR_CUDA;
     if (cudaDeviceSynchronize() != cudaSuccess) {
         (void)cudaGetLastError();
         return FEW_ERR_CUDA;
@@ -1237,7 +1276,8 @@ few_status few_last_timing(few_ctx *ctx, float *ms)
 {
     if (!ctx || !ms) return FEW_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEW_ERR_CUDA;
+    DeviceScope dev_scope(ctx->device);
+    if (!dev_scope.ok) return FEW_ERR_CUDA;
     for (int i = 0; i < 4; ++i) {
         ms[i] = -1.0f;
         if (!ctx->trec[i]) continue;
@@ -1261,14 +1301,6 @@ few_status few_set_tiles(few_ctx *ctx, int prec, int R, int threads)
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     ctx->tile_R[prec] = R;
     ctx->tile_T[prec] = threads;
-    return FEW_OK;
-}
-
-few_status few_set_packed(few_ctx *ctx, int enable)
-{
-    if (!ctx) return FEW_ERR_INVALID_ARG;
-    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    ctx->packed = enable != 0;
     return FEW_OK;
 }
 
@@ -1310,7 +1342,6 @@ bool ctx_traj_view(few_ctx *ctx, const few_traj *tr, CtxTrajView *v)
     if (!ctx || !tr || !v || tr->ctx != ctx) return false;
     v->device = ctx->device;
     v->sm_count = ctx->sm_count;
-    v->packed = ctx->packed;
     v->d_err = ctx->d_err;
     v->tile_R[0] = ctx->tile_R[0];
     v->tile_R[1] = ctx->tile_R[1];
@@ -1326,5 +1357,10 @@ bool ctx_traj_view(few_ctx *ctx, const few_traj *tr, CtxTrajView *v)
 }
 
 std::recursive_mutex &ctx_mutex(few_ctx *ctx) { return ctx->mu; }
+
+few_status check_request(const few_request &r, bool need_device_out)
+{
+    return validate_request(r, need_device_out);
+}
 
 }  // namespace fewsum

@@ -22,13 +22,21 @@ constexpr int kMaxL = 32;
 constexpr int kMaxAbsN = 1024;
 constexpr int kMaxSlotsFp64 = 1776;   // 2 buffers x slots x 64 B <= 227 KB
 constexpr int kMaxSlotsMixed = 3552;  // 2 buffers x slots x 32 B <= 227 KB
-constexpr int kMaxSlotsPacked = 1776; // 2 buffers x slots x 64 B (duplicated FP32 pairs)
 
 // Summation kernel variants (and the folded-coefficient layout each reads).
 enum : int {
-    kVariantFp64 = 0,    // FP64 throughout; slot = 8 doubles
-    kVariantScalar = 1,  // mixed, scalar FP32 FMA; slot = 8 floats
-    kVariantPacked = 2   // mixed, packed FP32x2 FMA; slot = 8 duplicated float pairs
+    kVariantFp64 = 0,   // FP64 throughout; slot = 8 doubles
+    kVariantScalar = 1  // mixed: FP64 phases at anchors, FP32 everything else; slot = 8 floats
+};
+
+// Phase anchors of the mixed path: the FP64 phase splines are evaluated and reduced modulo one
+// turn at every kAnchorGroup-th sample (absolute sample index a = kAnchorGroup * q), together
+// with the exact Taylor coefficients of the phase cubic about that sample in sample units; the
+// summation kernel adds the increment to the following samples of the group in FP32.
+constexpr int kAnchorGroup = 16;
+struct Anchor {
+    float4 phi;  // (f0, d1, d2, d3): reduced phase (turns) and increment coefficients (turns / sample^k)
+    float4 r;
 };
 constexpr int kFoldThreads = 128;
 constexpr int kYlmThreads = 16;  // few pairs per block: spreads the FP64 work over SMs
@@ -80,6 +88,9 @@ struct WaveDev {
     int out_c64;
     void *out;
     void *fcoef;          // [S][n_slots][8] folded coefficients (float or double)
+    Anchor *anchors;      // mixed plans: [n_anchors] phase anchors (segment by segment)
+    const int *anchor_off;  // mixed plans: [K] first anchor of each segment, then the total
+    int anchor_begin;     // first global anchor index of this wave (anchor kernel)
     double2 *ylm;         // [n_pairs][2]: Y+ = -2Y_{l,m}, Y- = (-1)^l -2Y_{l,-m} (0 if m = 0)
     const int *seg_start; // [K] sample range of each segment
     int pair_begin;       // first global pair index of this wave (ylm kernel)
@@ -101,6 +112,7 @@ struct PlanHdr {
     int total_pairs;
     int total_fold_blocks;
     int grid_sum;
+    int total_anchors;  // anchors over all waves (mixed plans; 0 for FP64 plans)
     int buf_bytes;   // bytes of one shared-memory coefficient buffer (max slots x slot bytes)
     int variant;     // kVariant* of the summation kernel and the folded layout
     const WaveDev *waves;
@@ -115,6 +127,13 @@ cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks,
                          unsigned *err, cudaStream_t st);
 cudaError_t launch_ylm(const PlanHdr *hdr_dev, int total_pairs, bool fp64, cudaStream_t st);
 cudaError_t launch_fold(const PlanHdr *hdr_dev, int total_fold_blocks, bool fp64, cudaStream_t st);
+cudaError_t launch_anchor(const PlanHdr *hdr_dev, int total_anchors, cudaStream_t st);
+// Anchors of one segment's samples [s_begin, s_end): groups floor(s_begin / G) ..
+// floor((s_end - 1) / G); none for an empty segment.
+inline int anchors_in_segment(int s_begin, int s_end)
+{
+    return s_end > s_begin ? (s_end - 1) / kAnchorGroup - s_begin / kAnchorGroup + 1 : 0;
+}
 cudaError_t launch_sum(const PlanHdr *hdr_dev, int grid, int threads, int samples_per_thread,
                        int smem_bytes, int variant, cudaStream_t st);
 // Bytes of one folded slot in the layout a variant reads.
@@ -155,10 +174,35 @@ int sum_occupancy(int variant, int samples_per_thread, int threads, int smem_byt
 // One-time kernel attribute setup (dynamic shared memory opt-in).
 cudaError_t sum_configure();
 
+// Makes `device` current for the lifetime of the object and then restores the caller's current
+// device, so a library call never leaves a different device current behind.
+struct DeviceScope {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceScope(int device)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            prev = -1;
+            (void)cudaGetLastError();
+        }
+        ok = cudaSetDevice(device) == cudaSuccess;
+        if (!ok) (void)cudaGetLastError();
+    }
+    ~DeviceScope()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DeviceScope(const DeviceScope &) = delete;
+    DeviceScope &operator=(const DeviceScope &) = delete;
+};
+
+// Host validation of one request (few_waveform's checks; need_device_out additionally requires
+// out_where == FEW_MEM_DEVICE).
+few_status check_request(const few_request &r, bool need_device_out);
+
 // Read-only snapshot of a context and one of its trajectories (filled by api.cpp).
 struct CtxTrajView {
     int device, sm_count;
-    bool packed;
     unsigned *d_err;
     int tile_R[2], tile_T[2];
     bool has_data;

@@ -137,21 +137,11 @@ template <> struct Slot8<float> {
         d[0] = make_float4(re[0], re[1], re[2], re[3]);
         d[1] = make_float4(im[0], im[1], im[2], im[3]);
     }
-    // layout of the packed FP32x2 kernel: every coefficient twice, (c, c)
-    __device__ static void store_pairs(float *dst, const float (&re)[4], const float (&im)[4])
-    {
-        float4 *d = reinterpret_cast<float4 *>(dst);
-        d[0] = make_float4(re[0], re[0], re[1], re[1]);
-        d[1] = make_float4(re[2], re[2], re[3], re[3]);
-        d[2] = make_float4(im[0], im[0], im[1], im[1]);
-        d[3] = make_float4(im[2], im[2], im[3], im[3]);
-    }
 };
 
 // One thread per (wave, segment, slot): K_slot = scale * sum of its contributions.
 // T is the arithmetic and storage type of the folded coefficients (double for FEW_FP64,
-// float for FEW_MIXED, whose amplitudes are FP32 by design); the FP32 table is written compact
-// or with every coefficient duplicated, as the plan's summation variant reads it.
+// float for FEW_MIXED, whose amplitudes are FP32 by design).
 template <typename T>
 __global__ void __launch_bounds__(kFoldThreads) k_fold(const PlanHdr *__restrict__ hp)
 {
@@ -191,13 +181,6 @@ __global__ void __launch_bounds__(kFoldThreads) k_fold(const PlanHdr *__restrict
     for (int q = 0; q < 4; ++q) {
         re[q] *= sc;
         im[q] *= sc;
-    }
-    if constexpr (sizeof(T) == 4) {
-        if (h.variant == kVariantPacked) {
-            float *dst = reinterpret_cast<float *>(W.fcoef) + ((size_t)s * tr.n_slots + slot) * 16;
-            Slot8<float>::store_pairs(dst, re, im);
-            return;
-        }
     }
     T *dst = reinterpret_cast<T *>(W.fcoef) + ((size_t)s * tr.n_slots + slot) * 8;
     Slot8<T>::store(dst, re, im);

@@ -79,40 +79,24 @@ extern "C" few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req,
 {
     if (!ctx || !req || !req->traj || !req->out) return FEW_ERR_INVALID_ARG;
     const few_request &r = *req;
-    if (r.prec != FEW_FP64 && r.prec != FEW_MIXED) return FEW_ERR_INVALID_ARG;
-    if (r.out_where != FEW_MEM_DEVICE) return FEW_ERR_INVALID_ARG;
-    if (!std::isfinite(r.theta) || !std::isfinite(r.phi) || !std::isfinite(r.scale) ||
-        !std::isfinite(r.dphi_phi0) || !std::isfinite(r.dphi_r0))
-        return FEW_ERR_INVALID_ARG;
-    if (r.frame != FEW_FRAME_SOURCE) return FEW_ERR_INVALID_ARG;  // source-frame requests only
     std::lock_guard<std::recursive_mutex> lk(ctx_mutex(ctx));
     CtxTrajView v;
     if (!ctx_traj_view(ctx, r.traj, &v)) return FEW_ERR_INVALID_ARG;
-    if (!v.has_data) return FEW_ERR_STATE;
-    if (!std::isfinite(r.t0) || !std::isfinite(r.dt) || !(r.dt > 0.0) || r.n_samples < 0 ||
-        r.n_samples > 2147483647LL)
-        return FEW_ERR_RANGE;
+    few_status st = check_request(r, true);  // as few_waveform; device output only
+    if (st) return st;
     const int K = v.K, S = K - 1;
-    if (r.n_samples > 0) {
-        const double last = std::fma((double)(r.n_samples - 1), r.dt, r.t0);
-        if (r.t0 < v.t_host[0] || last > v.t_host[K - 1]) return FEW_ERR_RANGE;
-    }
     const bool fp64 = r.prec == FEW_FP64;
-    if (v.n_slots > (fp64 ? kMaxSlotsFp64 : kMaxSlotsMixed)) return FEW_ERR_LIMIT;
     if (K > kMaxKnots) return FEW_ERR_LIMIT;
     if (r.n_samples == 0) return FEW_OK;
-    if (cudaSetDevice(v.device) != cudaSuccess) return FEW_ERR_CUDA;
+    DeviceScope dev_scope(v.device);
+    if (!dev_scope.ok) return FEW_ERR_CUDA;
     unsigned char *base = nullptr;
-    few_status st = scratch_address(v.device, &base);
-    if (st) return st;
+    if ((st = scratch_address(v.device, &base))) return st;
 
     // tile shape and grid as in few_waveform
     const int pi = fp64 ? 0 : 1;
     const int R = v.tile_R[pi], T = v.tile_T[pi];
-    const int variant = fp64 ? kVariantFp64
-                             : ((v.packed && (R == 4 || R == 8) && v.n_slots <= kMaxSlotsPacked)
-                                    ? kVariantPacked
-                                    : kVariantScalar);
+    const int variant = fp64 ? kVariantFp64 : kVariantScalar;
     const size_t slot_bytes = (size_t)sum_slot_bytes(variant);
     const int buf_bytes = (int)up((size_t)v.n_slots * slot_bytes, 128);
     const int smem = 2 * buf_bytes;
@@ -121,17 +105,13 @@ extern "C" few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req,
     const int grid = v.sm_count * occ;
     if (grid > kMaxGrid) return FEW_ERR_LIMIT;
 
-    // layout inside the fixed array: [plan | folded coefficients | harmonic table]
+    // layout inside the fixed array: [plan | folded coefficients | harmonic table | anchors]
     const size_t off_waves = up(sizeof(PlanHdr), 64);
     const size_t off_cta = up(off_waves + sizeof(WaveDev), 64);
     const size_t off_seg = up(off_cta + sizeof(CtaStart) * (grid + 1), 64);
-    const size_t blob_bytes = up(off_seg + sizeof(int) * K, 256);
-    const size_t fcoef_bytes = up((size_t)S * v.n_slots * slot_bytes, 256);
-    const size_t ylm_bytes = up((size_t)v.n_pairs * 2 * sizeof(double2), 256);
-    if (blob_bytes > kBlobMax || blob_bytes + fcoef_bytes + ylm_bytes > kScratchBytes)
-        return FEW_ERR_LIMIT;
-    unsigned char *d_fcoef = base + blob_bytes;
-    unsigned char *d_ylm = d_fcoef + fcoef_bytes;
+    const size_t off_anc = up(off_seg + sizeof(int) * K, 64);
+    const size_t blob_bytes = up(off_anc + (fp64 ? 0 : sizeof(int) * K), 256);
+    if (blob_bytes > kBlobMax) return FEW_ERR_LIMIT;
 
     std::lock_guard<std::mutex> blk(g_blob_mu);
     std::memset(g_blob, 0, blob_bytes);
@@ -139,6 +119,7 @@ extern "C" few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req,
     WaveDev *W = reinterpret_cast<WaveDev *>(g_blob + off_waves);
     CtaStart *cta = reinterpret_cast<CtaStart *>(g_blob + off_cta);
     int *seg = reinterpret_cast<int *>(g_blob + off_seg);
+    int *anc = reinterpret_cast<int *>(g_blob + off_anc);
 
     // segment sample ranges: seg[k] = clamp(ceil((t_k - t0)/dt), 0, n)
     const int64_t ns = r.n_samples;
@@ -150,6 +131,22 @@ extern "C" few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req,
         seg[k] = (int)val;
     }
     seg[K - 1] = (int)ns;
+    // mixed path: first phase anchor of each segment, then the total
+    int n_anchors = 0;
+    if (!fp64) {
+        for (int k = 0; k + 1 < K; ++k) {
+            anc[k] = n_anchors;
+            n_anchors += anchors_in_segment(seg[k], seg[k + 1]);
+        }
+        anc[K - 1] = n_anchors;
+    }
+    const size_t fcoef_bytes = up((size_t)S * v.n_slots * slot_bytes, 256);
+    const size_t ylm_bytes = up((size_t)v.n_pairs * 2 * sizeof(double2), 256);
+    const size_t anc_bytes = up(sizeof(Anchor) * (size_t)n_anchors, 256);
+    if (blob_bytes + fcoef_bytes + ylm_bytes + anc_bytes > kScratchBytes) return FEW_ERR_LIMIT;
+    unsigned char *d_fcoef = base + blob_bytes;
+    unsigned char *d_ylm = d_fcoef + fcoef_bytes;
+    unsigned char *d_anc = d_ylm + ylm_bytes;
 
     W->tr = v.dev;
     W->theta = r.theta;
@@ -162,12 +159,20 @@ extern "C" few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req,
     W->n_samples = (int)ns;
     W->out_c64 = r.out_c64 ? 1 : 0;
     W->out = r.out;
+    W->frame = r.frame;
+    W->theta_K = r.theta_K;
+    W->phi_K = r.phi_K;
     W->fcoef = d_fcoef;
     W->ylm = reinterpret_cast<double2 *>(d_ylm);
     W->seg_start = reinterpret_cast<const int *>(base + off_seg);
     W->pair_begin = 0;
     W->fold_begin = 0;
     W->fold_blocks_per_seg = (v.n_slots + kFoldThreads - 1) / kFoldThreads;
+    if (!fp64) {
+        W->anchors = reinterpret_cast<Anchor *>(d_anc);
+        W->anchor_off = reinterpret_cast<const int *>(base + off_anc);
+        W->anchor_begin = 0;
+    }
 
     // equal slices of the samples (one waveform: equal cost per sample)
     for (int g = 0; g < grid; ++g) {
@@ -179,6 +184,7 @@ extern "C" few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req,
     hdr->n_waves = 1;
     hdr->total_pairs = v.n_pairs;
     hdr->total_fold_blocks = S * W->fold_blocks_per_seg;
+    hdr->total_anchors = n_anchors;
     hdr->grid_sum = grid;
     hdr->buf_bytes = buf_bytes;
     hdr->variant = variant;
@@ -197,6 +203,7 @@ extern "C" few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req,
     const PlanHdr *hd = reinterpret_cast<const PlanHdr *>(base);
     if (launch_ylm(hd, v.n_pairs, fp64, s) != cudaSuccess ||
         launch_fold(hd, hdr->total_fold_blocks, fp64, s) != cudaSuccess ||
+        launch_anchor(hd, n_anchors, s) != cudaSuccess ||
         launch_sum(hd, grid, T, R, smem, variant, s) != cudaSuccess) {
         (void)cudaGetLastError();
         return FEW_ERR_CUDA;

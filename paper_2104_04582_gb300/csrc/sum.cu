@@ -11,9 +11,15 @@
 // m < 0 in conj(z_phi).  Per (slot, sample) that is one complex cubic (6 FMA) and one complex
 // multiply-add (4 FMA) -- no transcendental per mode.
 //
-// Phases: the phase splines (in turns) are evaluated in FP64 for every sample and each phase
-// is reduced modulo one turn, x - rint(x), in FP64; the reduced phases give z_phi and z_r
-// (sincospi).  The integer combination m Phi_phi + n Phi_r is then carried exactly by the
+// Phases: FEW_FP64 evaluates the phase splines (in rad) in FP64 for every sample and reduces
+// each phase modulo one turn, x - rint(x), in FP64; the reduced phases give z_phi and z_r
+// (sincospi).  FEW_MIXED reads the phases from anchors written by k_anchor: at every
+// kAnchorGroup-th sample the FP64 splines are evaluated and reduced modulo one turn, and the
+// phase cubic's exact Taylor coefficients about that sample (in turns per sample^k) are stored;
+// the kernel adds the in-group increment r (d1 + r (d2 + r d3)), r < kAnchorGroup (at most a
+// few tenths of a turn), in FP32.  So every large phase value and every reduction is FP64,
+// and the mixed kernel itself issues no FP64 instruction per sample (FP64 issue is scarce on
+// this chip).  The integer combination m Phi_phi + n Phi_r is then carried exactly by the
 // unit-modulus powers, so (m Phi_phi + n Phi_r) mod 2 pi never has to be formed explicitly.
 // FEW_FP64 does everything else in FP64; FEW_MIXED evaluates amplitudes, exponential powers
 // and the accumulation in FP32.
@@ -35,11 +41,7 @@ namespace fewsum {
 
 namespace {
 
-#ifndef FEWSUM_SLOT_UNROLL
-#define FEWSUM_SLOT_UNROLL 2
-#endif
-constexpr int kSlotUnroll = FEWSUM_SLOT_UNROLL;  // slots per iteration of the Horner chain loop
-
+constexpr int kSlotUnroll = 2;  // slots per iteration of the Horner chain loop
 constexpr int kBulkChunk = 32768;
 
 struct Piece {
@@ -97,12 +99,58 @@ template <> struct Cf<double> {
     }
 };
 
-__device__ __forceinline__ void sincospi_t(double x, double *s, double *c) { sincospi(x, s, c); }
-__device__ __forceinline__ void sincospi_t(float x, float *s, float *c) { sincospif(x, s, c); }
+// Per-sample local coordinate u and the powers' bases (cos, sin of 2 pi f) of one segment.
+template <typename T> struct PhaseSrc;
 
-#ifndef FEWSUM_STAGE_MAJOR
-#define FEWSUM_STAGE_MAJOR 0
-#endif
+// FP64: both phase splines evaluated and reduced for every sample.
+template <> struct PhaseSrc<double> {
+    SegPhase sp;
+    double t0, dt;
+    __device__ __forceinline__ void init(const WaveDev &W, int s)
+    {
+        sp = seg_phase(W.tr, s, W.dphi_phi, W.dphi_r);
+        t0 = W.t0;
+        dt = W.dt;
+    }
+    __device__ __forceinline__ void at(int i, double &u, double &cphi, double &sphi, double &cr,
+                                       double &sr) const
+    {
+        double fphi, fr;
+        sample_phase(sp, t0, dt, i, fphi, fr, u);
+        sincospi(2.0 * fphi, &sphi, &cphi);
+        sincospi(2.0 * fr, &sr, &cr);
+    }
+};
+
+// FP32: the anchor of the sample's group plus the in-group increment; u from the segment's
+// first sample.
+template <> struct PhaseSrc<float> {
+    const Anchor *anc;
+    int aidx;  // anc[aidx + (i / kAnchorGroup)] is sample i's anchor
+    int i0;    // first sample of the segment
+    float u0, du;
+    __device__ __forceinline__ void init(const WaveDev &W, int s)
+    {
+        i0 = W.seg_start[s];
+        anc = W.anchors;
+        aidx = W.anchor_off[s] - i0 / kAnchorGroup;
+        const double ih = W.tr.inv_h[s];
+        u0 = (float)((fma((double)i0, W.dt, W.t0) - W.tr.t[s]) * ih);
+        du = (float)(W.dt * ih);
+    }
+    __device__ __forceinline__ void at(int i, float &u, float &cphi, float &sphi, float &cr,
+                                       float &sr) const
+    {
+        const float4 *a = reinterpret_cast<const float4 *>(anc + aidx + i / kAnchorGroup);
+        const float4 ap = __ldg(a), ar = __ldg(a + 1);
+        const float x = (float)(i % kAnchorGroup);
+        const float fphi = fmaf(fmaf(fmaf(ap.w, x, ap.z), x, ap.y), x, ap.x);
+        const float fr = fmaf(fmaf(fmaf(ar.w, x, ar.z), x, ar.y), x, ar.x);
+        sincospif(2.0f * fphi, &sphi, &cphi);
+        sincospif(2.0f * fr, &sr, &cr);
+        u = fmaf((float)(i - i0), du, u0);
+    }
+};
 
 // acc <- acc * z + K(u) along n consecutive slots (Horner in z = (zr, zi)).
 template <typename T, int R>
@@ -114,29 +162,6 @@ __device__ __forceinline__ void horner_chain(const T *__restrict__ cf, int n, co
     for (int k = 0; k < n; ++k) {
         T c[8];
         Cf<T>::load(cf + 8 * k, c);
-#if FEWSUM_STAGE_MAJOR
-        // one coefficient feeds R consecutive FMAs (operand reuse across samples)
-        T kr[R], ki[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) kr[r] = fma(c[3], u[r], c[2]);
-#pragma unroll
-        for (int r = 0; r < R; ++r) ki[r] = fma(c[7], u[r], c[6]);
-#pragma unroll
-        for (int r = 0; r < R; ++r) kr[r] = fma(kr[r], u[r], c[1]);
-#pragma unroll
-        for (int r = 0; r < R; ++r) ki[r] = fma(ki[r], u[r], c[5]);
-#pragma unroll
-        for (int r = 0; r < R; ++r) kr[r] = fma(kr[r], u[r], c[0]);
-#pragma unroll
-        for (int r = 0; r < R; ++r) ki[r] = fma(ki[r], u[r], c[4]);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const T nr = fma(ar[r], zr[r], fma(-ai[r], zi[r], kr[r]));
-            const T ni = fma(ar[r], zi[r], fma(ai[r], zr[r], ki[r]));
-            ar[r] = nr;
-            ai[r] = ni;
-        }
-#else
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const T kr = fma(fma(fma(c[3], u[r], c[2]), u[r], c[1]), u[r], c[0]);
@@ -146,18 +171,18 @@ __device__ __forceinline__ void horner_chain(const T *__restrict__ cf, int n, co
             ar[r] = nr;
             ai[r] = ni;
         }
-#endif
     }
 }
 
 // One pass of the scalar path: R consecutive samples per thread, one value per register.
 template <typename T, int R>
 struct ScalarPass {
+    using Scalar = T;
     static constexpr int kSamples = R;
     static constexpr int kSlotBytes = 8 * (int)sizeof(T);
 
     __device__ __forceinline__ static void run(const WaveDev &W, const unsigned char *buf, int p0,
-                                               int i1, const SegPhase &sp)
+                                               int i1, const PhaseSrc<T> &ps)
     {
         const T *__restrict__ cf = reinterpret_cast<const T *>(buf);
         const int tid = threadIdx.x;
@@ -166,12 +191,8 @@ struct ScalarPass {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int i = min(base + r, i1 - 1);
-            double fphi, frr, ud;
-            sample_phase(sp, W.t0, W.dt, i, fphi, frr, ud);
             T sp_, cp, sr, cr;
-            sincospi_t((T)(2.0 * fphi), &sp_, &cp);
-            sincospi_t((T)(2.0 * frr), &sr, &cr);
-            u[r] = (T)ud;
+            ps.at(i, u[r], cp, sp_, cr, sr);
             fr[r] = cp;   // z_phi = e^{-i 2 pi f_phi}
             fi[r] = -sp_;
             zr[r] = cr;   // z_r = e^{-i 2 pi f_r}
@@ -226,125 +247,6 @@ struct ScalarPass {
                 reinterpret_cast<float2 *>(W.out)[i] = make_float2((float)hr, (float)hi);
             else
                 reinterpret_cast<double2 *>(W.out)[i] = make_double2((double)hr, (double)hi);
-        }
-    }
-};
-
-// Packed FP32x2 path: the thread's 2P samples are held as P pairs, and every multiply-add of the
-// Horner scheme runs on a pair with one packed FMA (__ffma2_rn), halving the instructions
-// issued per FMA.  Each lane of a packed FMA is an IEEE fma, and the operation order equals the
-// scalar path's, so both paths give bit-identical results.  The folded table stores every
-// coefficient twice, (c, c), so a pair operand is one 64-bit shared-memory read.
-__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
-
-template <int P>
-__device__ __forceinline__ void horner_chain_pk(const float4 *__restrict__ cf, int n,
-                                                const float2 (&U)[P], const float2 (&ZR)[P],
-                                                const float2 (&ZIe)[P], const float2 (&NZIe)[P],
-                                                float2 (&AR)[P], float2 (&AI)[P])
-{
-#pragma unroll (kSlotUnroll)
-    for (int k = 0; k < n; ++k) {
-        const float4 a = cf[4 * k], b = cf[4 * k + 1], c = cf[4 * k + 2], d = cf[4 * k + 3];
-        const float2 c0r = make_float2(a.x, a.y), c1r = make_float2(a.z, a.w);
-        const float2 c2r = make_float2(b.x, b.y), c3r = make_float2(b.z, b.w);
-        const float2 c0i = make_float2(c.x, c.y), c1i = make_float2(c.z, c.w);
-        const float2 c2i = make_float2(d.x, d.y), c3i = make_float2(d.z, d.w);
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const float2 kr = f2fma(f2fma(f2fma(c3r, U[p], c2r), U[p], c1r), U[p], c0r);
-            const float2 ki = f2fma(f2fma(f2fma(c3i, U[p], c2i), U[p], c1i), U[p], c0i);
-            const float2 nr = f2fma(AR[p], ZR[p], f2fma(AI[p], NZIe[p], kr));
-            const float2 ni = f2fma(AR[p], ZIe[p], f2fma(AI[p], ZR[p], ki));
-            AR[p] = nr;
-            AI[p] = ni;
-        }
-    }
-}
-
-template <int P>
-struct PackedPass {
-    static constexpr int kSamples = 2 * P;
-    static constexpr int kSlotBytes = 64;
-
-    __device__ __forceinline__ static void run(const WaveDev &W, const unsigned char *buf, int p0,
-                                               int i1, const SegPhase &sp)
-    {
-        const float4 *__restrict__ cf = reinterpret_cast<const float4 *>(buf);
-        const int tid = threadIdx.x;
-        const int base = p0 + tid * 2 * P;
-        float2 U[P], ZR[P], ZI[P], NZI[P], FR[P], FI[P], NFI[P];
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            float uu[2], cpp[2], spp[2], crr[2], srr[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int i = min(base + 2 * p + e, i1 - 1);
-                double fphi, frr, ud;
-                sample_phase(sp, W.t0, W.dt, i, fphi, frr, ud);
-                sincospif((float)(2.0 * fphi), &spp[e], &cpp[e]);
-                sincospif((float)(2.0 * frr), &srr[e], &crr[e]);
-                uu[e] = (float)ud;
-            }
-            U[p] = make_float2(uu[0], uu[1]);
-            FR[p] = make_float2(cpp[0], cpp[1]);
-            FI[p] = make_float2(-spp[0], -spp[1]);
-            NFI[p] = make_float2(spp[0], spp[1]);
-            ZR[p] = make_float2(crr[0], crr[1]);
-            ZI[p] = make_float2(-srr[0], -srr[1]);
-            NZI[p] = make_float2(srr[0], srr[1]);
-        }
-        float2 TPR[P], TPI[P], TNR[P], TNI[P];
-#pragma unroll
-        for (int p = 0; p < P; ++p) TPR[p] = TPI[p] = TNR[p] = TNI[p] = make_float2(0.f, 0.f);
-        const int2 *__restrict__ rows = W.tr.rows;
-        const int nrp = W.tr.n_rows_pos, nrows = nrp + W.tr.n_rows_neg;
-        int slot = 0;
-        for (int row = 0; row < nrows; ++row) {
-            const int2 rw = __ldg(rows + row);
-            float2 AR[P], AI[P], BR[P], BI[P];
-#pragma unroll
-            for (int p = 0; p < P; ++p) AR[p] = AI[p] = BR[p] = BI[p] = make_float2(0.f, 0.f);
-            // n >= 0 half: Horner in z_r;  n < 0 half: Horner in conj(z_r)
-            horner_chain_pk<P>(cf + 4 * slot, rw.x, U, ZR, ZI, NZI, AR, AI);
-            slot += rw.x;
-            horner_chain_pk<P>(cf + 4 * slot, rw.y, U, ZR, NZI, ZI, BR, BI);
-            slot += rw.y;
-            const bool pos = row < nrp;
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                const float2 vr = f2fma(BR[p], ZR[p], f2fma(BI[p], ZI[p], AR[p]));
-                const float2 vi = f2fma(BI[p], ZR[p], f2fma(BR[p], NZI[p], AI[p]));
-                if (pos) {
-                    const float2 nr = f2fma(TPR[p], FR[p], f2fma(TPI[p], NFI[p], vr));
-                    const float2 ni = f2fma(TPR[p], FI[p], f2fma(TPI[p], FR[p], vi));
-                    TPR[p] = nr;
-                    TPI[p] = ni;
-                } else {
-                    const float2 nr = f2fma(TNR[p], FR[p], f2fma(TNI[p], FI[p], vr));
-                    const float2 ni = f2fma(TNI[p], FR[p], f2fma(TNR[p], NFI[p], vi));
-                    TNR[p] = nr;
-                    TNI[p] = ni;
-                }
-            }
-        }
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const float2 hr = f2fma(TNR[p], FR[p], f2fma(TNI[p], FI[p], TPR[p]));
-            const float2 hi = f2fma(TNI[p], FR[p], f2fma(TNR[p], NFI[p], TPI[p]));
-            const float h_r[2] = {hr.x, hr.y}, h_i[2] = {hi.x, hi.y};
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int i = base + 2 * p + e;
-                if (i < i1) {
-                    if (W.out_c64)
-                        reinterpret_cast<float2 *>(W.out)[i] = make_float2(h_r[e], h_i[e]);
-                    else
-                        reinterpret_cast<double2 *>(W.out)[i] =
-                            make_double2((double)h_r[e], (double)h_i[e]);
-                }
-            }
         }
     }
 };
@@ -415,11 +317,12 @@ __global__ void __launch_bounds__(256) k_sum(const PlanHdr *__restrict__ hp)
 
         const WaveDev &W = h.waves[cur.w];
         const unsigned char *buf = smem + (size_t)b * h.buf_bytes;
-        const SegPhase sp = seg_phase(W.tr, cur.s, W.dphi_phi, W.dphi_r);
+        PhaseSrc<typename V::Scalar> ps;
+        ps.init(W, cur.s);
         const int warp_first = (tid & ~31) * V::kSamples;
         for (int p0 = cur.i0; p0 < cur.i1; p0 += U) {
             if (p0 + warp_first >= cur.i1) continue;  // whole warp past the end: idle
-            V::run(W, buf, p0, cur.i1, sp);
+            V::run(W, buf, p0, cur.i1, ps);
         }
 
         int nw = cur.w, ni = cur.i1;
@@ -469,6 +372,66 @@ cudaError_t launch_phases(const TrajDev &tr, const int *seg_start, double t0, do
     return cudaGetLastError();
 }
 
+// Phase anchors of the mixed path, one thread per anchor: wave w, segment s and group q of the
+// anchor, then at the anchor sample a = kAnchorGroup * q (which may precede the segment's first
+// sample: the segment's cubic is used on both sides) the FP64 phases reduced modulo one turn and
+// the Taylor coefficients of each phase cubic in sample units,
+//   Phi(u + k du) - Phi(u) = k du Phi'(u) + (k du)^2 Phi''(u)/2 + (k du)^3 p3,  du = dt / h,
+// divided by 2 pi (turns).  The identity is exact for a cubic; only its FP32 evaluation over
+// k < kAnchorGroup samples in the summation kernel rounds.
+__global__ void __launch_bounds__(256) k_anchor(const PlanHdr *__restrict__ hp)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n_waves = hp->n_waves;
+    if (g >= hp->total_anchors) return;
+    const WaveDev *waves = hp->waves;
+    int lo = 0, hi = n_waves - 1;
+    while (lo < hi) {  // largest w with anchor_begin <= g
+        const int mid = (lo + hi + 1) >> 1;
+        if (waves[mid].anchor_begin <= g) lo = mid; else hi = mid - 1;
+    }
+    const WaveDev &W = waves[lo];
+    const int j = g - W.anchor_begin;
+    int s0 = 0, s1 = W.tr.S - 1;
+    while (s0 < s1) {  // largest s with anchor_off[s] <= j
+        const int mid = (s0 + s1 + 1) >> 1;
+        if (W.anchor_off[mid] <= j) s0 = mid; else s1 = mid - 1;
+    }
+    const int s = s0;
+    const int q = W.seg_start[s] / kAnchorGroup + (j - W.anchor_off[s]);
+    const SegPhase sp = seg_phase(W.tr, s, W.dphi_phi, W.dphi_r);
+    const double kInv2Pi = 0.15915494309189533577;
+    const double t = fma((double)q * kAnchorGroup, W.dt, W.t0);
+    const double u = (t - sp.tk) * sp.ih;
+    const double du = W.dt * sp.ih, du2 = du * du, du3 = du2 * du;
+    float f[2][4];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const double c0 = k ? sp.c0r : sp.c0phi;
+        const double *p = k ? sp.pr : sp.pphi;
+        const double ph = fma(fma(fma(p[2], u, p[1]), u, p[0]), u, c0);
+        const double d1 = fma(fma(3.0 * p[2], u, 2.0 * p[1]), u, p[0]) * du;
+        const double d2 = fma(3.0 * p[2], u, p[1]) * du2;
+        const double d3 = p[2] * du3;
+        const double x = ph * kInv2Pi;
+        f[k][0] = (float)(x - rint(x));
+        f[k][1] = (float)(d1 * kInv2Pi);
+        f[k][2] = (float)(d2 * kInv2Pi);
+        f[k][3] = (float)(d3 * kInv2Pi);
+    }
+    Anchor a;
+    a.phi = make_float4(f[0][0], f[0][1], f[0][2], f[0][3]);
+    a.r = make_float4(f[1][0], f[1][1], f[1][2], f[1][3]);
+    W.anchors[j] = a;
+}
+
+cudaError_t launch_anchor(const PlanHdr *hdr_dev, int total_anchors, cudaStream_t st)
+{
+    if (total_anchors <= 0) return cudaSuccess;
+    k_anchor<<<(total_anchors + 255) / 256, 256, 0, st>>>(hdr_dev);
+    return cudaGetLastError();
+}
+
 namespace {
 template <typename V>
 cudaError_t configure_one(int max_dyn)
@@ -491,10 +454,7 @@ cudaError_t launch_one(const PlanHdr *hdr, int grid, int threads, int smem, cuda
 }
 }  // namespace
 
-int sum_slot_bytes(int variant)
-{
-    return variant == kVariantFp64 ? 64 : (variant == kVariantPacked ? 64 : 32);
-}
+int sum_slot_bytes(int variant) { return variant == kVariantFp64 ? 64 : 32; }
 
 cudaError_t sum_configure()
 {
@@ -509,8 +469,6 @@ cudaError_t sum_configure()
     if ((e = configure_one<ScalarPass<float, 2>>(max_dyn)) != cudaSuccess) return e;
     if ((e = configure_one<ScalarPass<float, 4>>(max_dyn)) != cudaSuccess) return e;
     if ((e = configure_one<ScalarPass<float, 8>>(max_dyn)) != cudaSuccess) return e;
-    if ((e = configure_one<PackedPass<2>>(max_dyn)) != cudaSuccess) return e;
-    if ((e = configure_one<PackedPass<4>>(max_dyn)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -523,9 +481,6 @@ int sum_occupancy(int variant, int R, int threads, int smem)
         if (R == 2) return occupancy_one<ScalarPass<float, 2>>(threads, smem);
         if (R == 4) return occupancy_one<ScalarPass<float, 4>>(threads, smem);
         if (R == 8) return occupancy_one<ScalarPass<float, 8>>(threads, smem);
-    } else if (variant == kVariantPacked) {
-        if (R == 4) return occupancy_one<PackedPass<2>>(threads, smem);
-        if (R == 8) return occupancy_one<PackedPass<4>>(threads, smem);
     }
     return 0;
 }
@@ -541,9 +496,6 @@ cudaError_t launch_sum(const PlanHdr *hdr_dev, int grid, int threads, int R, int
         if (R == 2) return launch_one<ScalarPass<float, 2>>(hdr_dev, grid, threads, smem, st);
         if (R == 4) return launch_one<ScalarPass<float, 4>>(hdr_dev, grid, threads, smem, st);
         if (R == 8) return launch_one<ScalarPass<float, 8>>(hdr_dev, grid, threads, smem, st);
-    } else if (variant == kVariantPacked) {
-        if (R == 4) return launch_one<PackedPass<2>>(hdr_dev, grid, threads, smem, st);
-        if (R == 8) return launch_one<PackedPass<4>>(hdr_dev, grid, threads, smem, st);
     }
     return cudaErrorInvalidValue;
 }

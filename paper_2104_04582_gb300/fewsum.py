@@ -43,7 +43,7 @@ EXPORTED = [
     "few_traj_create", "few_traj_set_data", "few_traj_release", "few_traj_info", "few_waveform",
     "few_batch_plan", "few_batch_run", "few_batch_release", "few_sync_status", "few_set_tiles",
     "few_get_tiles", "few_plan_segments", "few_mode_slots", "few_ctx_set_timing",
-    "few_last_timing", "few_phase_samples", "few_waveform_noalloc", "few_set_packed",
+    "few_last_timing", "few_phase_samples", "few_waveform_noalloc",
     "few_mode_select", "few_direct_sum", "few_basis_create", "few_basis_release",
     "few_rb_amplitudes",
 ]
@@ -115,7 +115,6 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
             "few_sync_status": (ctypes.c_int, [_vp]),
             "few_set_tiles": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
             "few_get_tiles": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _ip]),
-            "few_set_packed": (ctypes.c_int, [_vp, ctypes.c_int]),
             "few_ctx_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
             "few_last_timing": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float)]),
             "few_phase_samples": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double,
@@ -273,10 +272,6 @@ def few_sync_status(ctx: int) -> int:
 def few_set_tiles(ctx: int, prec: int, samples_per_thread: int, threads_per_block: int) -> None:
     _check("few_set_tiles", load().few_set_tiles(ctx, int(prec), int(samples_per_thread),
                                                  int(threads_per_block)))
-
-
-def few_set_packed(ctx: int, enable: bool) -> None:
-    _check("few_set_packed", load().few_set_packed(ctx, 1 if enable else 0))
 
 
 def few_get_tiles(ctx: int, prec: int):

@@ -4,8 +4,7 @@ The summation kernel is tunable in three ways that change speed but never result
 is summed by one thread in a fixed order, so all choices are bit-identical):
 
 * samples per thread R (the segment tile: one pass covers threads x R consecutive samples),
-* threads per block (128 or 256),
-* the FMA instruction form of the mixed path (scalar FP32 or packed FP32x2).
+* threads per block (128 or 256).
 
 The mode tile is the per-segment harmonic slot table, staged whole in shared memory; its size is
 set by the mode set, and it decides occupancy together with R and the block size.
@@ -24,9 +23,8 @@ from typing import Dict, List, Optional, Sequence, Tuple
 from . import fewsum as F
 
 CANDIDATES = {
-    F.FEW_FP64: [(1, 256, False), (2, 256, False), (1, 128, False), (2, 128, False)],
-    F.FEW_MIXED: [(r, t, p) for p in (False, True) for r in (2, 4, 8) for t in (128, 256)
-                  if not (p and r == 2)],
+    F.FEW_FP64: [(1, 256), (2, 256), (1, 128), (2, 128)],
+    F.FEW_MIXED: [(r, t) for r in (2, 4, 8) for t in (128, 256)],
 }
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "fewsum_tiles.json")
@@ -54,19 +52,17 @@ def _save(path: str, data: Dict[str, dict]) -> None:
     os.replace(tmp, path)
 
 
-def install(ctx_handle: int, prec: int, choice: Tuple[int, int, bool]) -> None:
-    R, T, packed = choice
+def install(ctx_handle: int, prec: int, choice: Tuple[int, int]) -> None:
+    R, T = choice
     F.few_set_tiles(ctx_handle, prec, R, T)
-    if prec == F.FEW_MIXED:
-        F.few_set_packed(ctx_handle, packed)
 
 
 def tune(ctx_handle: int, run, prec: int, n_slots: int, n_samples: int, repeats: int = 3,
          cache_path: Optional[str] = DEFAULT_CACHE,
-         candidates: Optional[Sequence[Tuple[int, int, bool]]] = None) -> Tuple[Tuple[int, int, bool], Dict[str, float]]:
+         candidates: Optional[Sequence[Tuple[int, int]]] = None) -> Tuple[Tuple[int, int], Dict[str, float]]:
     """Time `run()` (which must queue one workload on the current stream) for every candidate.
 
-    Returns the best (R, threads, packed) and the per-candidate best time in ms; installs the
+    Returns the best (R, threads) and the per-candidate best time in ms; installs the
     winner in the context and stores it in the cache (unless cache_path is None).
     """
     import torch
@@ -88,7 +84,7 @@ def tune(ctx_handle: int, run, prec: int, n_slots: int, n_samples: int, repeats:
             b.record()
             b.synchronize()
             ms = min(ms, a.elapsed_time(b))
-        times[f"R={c[0]} T={c[1]} packed={int(c[2])}"] = ms
+        times[f"R={c[0]} T={c[1]}"] = ms
         if ms < best_ms:
             best, best_ms = c, ms
     if best is None:
@@ -96,18 +92,17 @@ def tune(ctx_handle: int, run, prec: int, n_slots: int, n_samples: int, repeats:
     install(ctx_handle, prec, best)
     if cache_path:
         data = _load(cache_path)
-        data[bucket(prec, n_slots, n_samples)] = {"R": best[0], "threads": best[1],
-                                                  "packed": bool(best[2]), "ms": best_ms}
+        data[bucket(prec, n_slots, n_samples)] = {"R": best[0], "threads": best[1], "ms": best_ms}
         _save(cache_path, data)
     return best, times
 
 
 def apply_cached(ctx_handle: int, prec: int, n_slots: int, n_samples: int,
-                 cache_path: str = DEFAULT_CACHE) -> Optional[Tuple[int, int, bool]]:
+                 cache_path: str = DEFAULT_CACHE) -> Optional[Tuple[int, int]]:
     """Install the cached choice for this bucket, if any; returns it."""
     e = _load(cache_path).get(bucket(prec, n_slots, n_samples))
     if not e:
         return None
-    choice = (int(e["R"]), int(e["threads"]), bool(e["packed"]))
+    choice = (int(e["R"]), int(e["threads"]))
     install(ctx_handle, prec, choice)
     return choice

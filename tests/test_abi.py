@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_strerror(lib):
-    assert F.few_abi_version() == 3
+    assert F.few_abi_version() == 4
     assert F.few_strerror(F.FEW_OK) == "FEW_OK"
     assert F.few_strerror(F.FEW_ERR_LIMIT) == "FEW_ERR_LIMIT"
     assert F.few_strerror(999) == "FEW_ERR_UNKNOWN"

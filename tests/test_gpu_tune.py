@@ -40,5 +40,4 @@ def test_tune_installs_and_caches_a_choice(gpu_ctx, tmp_path):
         assert gpu_ctx.get_tiles(F.FEW_MIXED) == (best[0], best[1])
     finally:
         gpu_ctx.set_tiles(F.FEW_MIXED, *saved)
-        F.few_set_packed(gpu_ctx.handle, False)
         tr.release()
