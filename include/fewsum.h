@@ -37,10 +37,9 @@
  *   the context's lock.
  * Layouts: complex outputs are interleaved (re, im) pairs, complex128 (2 x f64) or
  *   complex64 (2 x f32).  Per-knot mode arrays are row-major [K][N] (modes contiguous).
- * Limits: K >= 4 knots; 1 <= N modes; 2 <= l <= 32, 0 <= m <= l, |n| <= 1024, no duplicate
- *   (l,m,n); n_samples <= 2^31 - 1.  The per-segment harmonic table must fit in shared
- *   memory (see few_mode_slots): at most FEW_MAX_SLOTS_FP64 slots for FEW_FP64 and
- *   FEW_MAX_SLOTS_MIXED for FEW_MIXED; larger mode sets fail with FEW_ERR_LIMIT.
+ * Limits: 4 <= K <= FEW_MAX_KNOTS knots; 1 <= N modes; 2 <= l <= 32, 0 <= m <= l,
+ *   |n| <= 1024, no duplicate (l,m,n); n_samples <= 2^31 - 1.  The per-segment harmonic table
+ *   (see few_mode_slots) streams through shared memory in tiles, so its size is not limited.
  */
 #ifndef FEWSUM_H
 #define FEWSUM_H
@@ -53,8 +52,6 @@ extern "C" {
 #endif
 
 #define FEW_ABI_VERSION 4
-#define FEW_MAX_SLOTS_FP64 1776
-#define FEW_MAX_SLOTS_MIXED 3552
 
 typedef enum few_status {
     FEW_OK = 0,
@@ -334,12 +331,21 @@ few_status few_batch_release(few_ctx *ctx, few_batch *batch);
 few_status few_sync_status(few_ctx *ctx);
 
 /*
- * Tile configuration of the summation kernel for one precision: samples per thread (R) and
- * threads per block.  Supported: FEW_FP64: R in {1, 2}; FEW_MIXED: R in {2, 4, 8}; threads
- * in {128, 256}.  Affects speed only: every configuration gives bit-identical results.
+ * Tile configuration of the summation kernel for one precision:
+ *   samples_per_thread (R, the sample tile: a pass covers threads x R consecutive samples):
+ *     FEW_FP64: 1 or 2; FEW_MIXED: 2, 4 or 8;
+ *   threads_per_block: 128 or 256;
+ *   stage_slots (the mode tile: harmonic slots per shared-memory stage through which each
+ *     segment's table streams): a multiple of 16 in [16, 4096].
+ * Defaults: FEW_FP64 (1, 256, 256), FEW_MIXED (4, 256, 1024).  Three stages of stage_slots x 64
+ * bytes (FEW_FP64) or x 32 bytes (FEW_MIXED) must fit in one CTA's shared memory, else the
+ * waveform calls return FEW_ERR_LIMIT.  Affects speed only: every configuration gives
+ * bit-identical results.
  */
-few_status few_set_tiles(few_ctx *ctx, int prec, int samples_per_thread, int threads_per_block);
-few_status few_get_tiles(few_ctx *ctx, int prec, int *samples_per_thread, int *threads_per_block);
+few_status few_set_tiles(few_ctx *ctx, int prec, int samples_per_thread, int threads_per_block,
+                         int stage_slots);
+few_status few_get_tiles(few_ctx *ctx, int prec, int *samples_per_thread, int *threads_per_block,
+                         int *stage_slots);
 
 /*
  * Per-kernel device timing.  With timing enabled, the library records a CUDA event pair on the
@@ -368,9 +374,10 @@ few_status few_plan_segments(const double *t_knots, int K, double t0, double dt,
 
 /*
  * Harmonic slot plan of a mode list: the distinct signed (m, n) frequencies that the m >= 0
- * modes and their m < 0 partners (Eq. amp_symmetry) occupy, laid out as rows of constant m
- * (zero-filled between n = 0 and the row's extreme n).  Returns the slot count per segment and
- * the number of rows.  Validates the modes (FEW_ERR_MODES).
+ * modes and their m < 0 partners (Eq. amp_symmetry) occupy, laid out as rows of constant m,
+ * every m from the largest down to the most negative present, each row spanning its lowest to
+ * highest n (zero-filled in between; a row without modes has no slot).  Returns the slot count
+ * per segment and the number of rows.  Validates the modes (FEW_ERR_MODES).
  */
 few_status few_mode_slots(const int *l, const int *m, const int *n, int N, int *n_slots, int *n_rows);
 

@@ -106,6 +106,7 @@ struct few_ctx {
     PinnedPool pinned;
     int tile_R[2] = {1, 4};
     int tile_T[2] = {256, 256};
+    int tile_S[2] = {256, 1024};  // slots per ring stage (the mode tile)
     std::map<std::tuple<int, int, int, int>, int> occ_cache;
     bool timing = false;
     cudaEvent_t tev[8] = {};
@@ -176,8 +177,12 @@ few_status check_knots(const double *t, int K)
 }
 
 // Harmonic slot plan of a mode list (host planning of the fold and the Horner order).
+// Rows are the signed m from the largest down to m_last (-max m when any mode has m > 0, else
+// 0), every m in between included; row j holds the slots n = hi_j, hi_j - 1, ..., lo_j (the
+// extreme n of the signed modes with that m; zero-filled in between; an empty row has no slot
+// and keeps the previous row's lo).  rows[j] = (slots of row j, lo_{j-1} - lo_j).
 struct SlotPlan {
-    int n_slots = 0, n_rows_pos = 0, n_rows_neg = 0;
+    int n_slots = 0, m_last = 0, lo_last = 0;
     std::vector<int2> pair_lm;
     std::vector<int> mode_pair;
     std::vector<int> slot_ptr;
@@ -212,34 +217,38 @@ few_status plan_slots(const int *l, const int *m, const int *n, int N, SlotPlan 
             P.mode_pair[i] = it->second;
         }
     }
-    // per signed m: extreme positive n (np = max n + 1) and negative n (nn = max -n)
+    // n range of every signed m: the modes and, for m > 0, their (-m, -n) partners
     bool any_neg = false;
     for (int i = 0; i < N; ++i) any_neg |= (m[i] > 0);
-    const int mneg = any_neg ? mmax : 0;
-    std::vector<int> npos(2 * mmax + 1, 0), nneg(2 * mmax + 1, 0);
+    const int m_last = any_neg ? -mmax : 0;
+    const int n_rows = mmax - m_last + 1;
+    std::vector<int> lo(n_rows, kMaxAbsN + 1), hi(n_rows, -kMaxAbsN - 1);
     auto touch = [&](int ms, int ns) {
-        const int r = ms + mmax;
-        if (ns >= 0) npos[r] = std::max(npos[r], ns + 1);
-        else nneg[r] = std::max(nneg[r], -ns);
+        const int j = mmax - ms;
+        lo[j] = std::min(lo[j], ns);
+        hi[j] = std::max(hi[j], ns);
     };
     for (int i = 0; i < N; ++i) {
         touch(m[i], n[i]);
         if (m[i] > 0) touch(-m[i], -n[i]);
     }
-    // rows: m = mmax..0, then m = -mneg..-1; slot offsets in that order
+    // rows m = mmax..m_last, slots n = hi..lo in each
     std::map<std::pair<int, int>, int> slot_of;  // (signed m, n) -> slot
-    int slot = 0;
-    auto emit_row = [&](int ms) {
-        const int r = ms + mmax;
-        P.rows.push_back(make_int2(npos[r], nneg[r]));
-        for (int q = npos[r] - 1; q >= 0; --q) slot_of[std::make_pair(ms, q)] = slot++;
-        for (int q = nneg[r]; q >= 1; --q) slot_of[std::make_pair(ms, -q)] = slot++;
-    };
-    for (int ms = mmax; ms >= 0; --ms) emit_row(ms);
-    P.n_rows_pos = mmax + 1;
-    for (int ms = -mneg; ms <= -1; ++ms) emit_row(ms);
-    P.n_rows_neg = mneg;
+    int slot = 0, prev_lo = 0;
+    for (int j = 0; j < n_rows; ++j) {
+        const int ms = mmax - j;
+        int L = 0, cur_lo = prev_lo;
+        if (hi[j] >= lo[j]) {
+            L = hi[j] - lo[j] + 1;
+            cur_lo = lo[j];
+            for (int q = hi[j]; q >= lo[j]; --q) slot_of[std::make_pair(ms, q)] = slot++;
+        }
+        P.rows.push_back(make_int2(L, j == 0 ? 0 : prev_lo - cur_lo));
+        prev_lo = cur_lo;
+    }
     P.n_slots = slot;
+    P.m_last = m_last;
+    P.lo_last = prev_lo;
     // contributions CSR
     std::vector<std::vector<int>> lists(slot);
     for (int i = 0; i < N; ++i) {
@@ -318,7 +327,7 @@ struct PlanImage {
     bool fp64 = false;
     int variant = kVariantFp64;
     int grid = 0, threads = 0, R = 0, smem = 0, buf_bytes = 0, total_pairs = 0, total_fold = 0;
-    int total_anchors = 0;
+    int total_anchors = 0, stage_slots = 0, ring = 0;
 };
 
 int occupancy(few_ctx *c, int variant, int R, int T, int smem)
@@ -361,8 +370,6 @@ few_status validate_request(const few_request &r, bool need_device_out)
         const double last = std::fma((double)(r.n_samples - 1), r.dt, r.t0);
         if (r.t0 < tr->t_host[0] || last > tr->t_host[tr->K - 1]) return FEW_ERR_RANGE;
     }
-    const int lim = r.prec == FEW_FP64 ? kMaxSlotsFp64 : kMaxSlotsMixed;
-    if (tr->plan.n_slots > lim) return FEW_ERR_LIMIT;
     return FEW_OK;
 }
 
@@ -377,8 +384,10 @@ few_status build_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P)
     for (int q = 0; q < n; ++q) max_slots = std::max(max_slots, reqs[q].traj->plan.n_slots);
     P.variant = P.fp64 ? kVariantFp64 : kVariantScalar;
     const size_t slot_bytes = (size_t)sum_slot_bytes(P.variant);
-    P.buf_bytes = (int)align_up((size_t)max_slots * slot_bytes, 128);
-    P.smem = 2 * P.buf_bytes;
+    P.stage_slots = std::min(c->tile_S[pi], max_slots);  // no stage larger than any table
+    P.ring = kDefaultRing;
+    P.buf_bytes = (int)align_up((size_t)P.stage_slots * slot_bytes, 128);
+    P.smem = P.ring * P.buf_bytes;
     const int occ = occupancy(c, P.variant, P.R, P.threads, P.smem);
     if (occ <= 0) return FEW_ERR_LIMIT;
     P.grid = c->sm_count * occ;
@@ -509,6 +518,8 @@ void fill_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P, unsign
     hdr->total_anchors = P.total_anchors;
     hdr->grid_sum = P.grid;
     hdr->buf_bytes = P.buf_bytes;
+    hdr->stage_slots = P.stage_slots;
+    hdr->ring = P.ring;
     hdr->variant = P.variant;
     hdr->waves = reinterpret_cast<const WaveDev *>(blob_dev + P.off_waves);
     hdr->cta = reinterpret_cast<const CtaStart *>(blob_dev + P.off_cta);
@@ -699,8 +710,9 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
     D.S = tr->S;
     D.n_pairs = (int)P.pair_lm.size();
     D.n_slots = P.n_slots;
-    D.n_rows_pos = P.n_rows_pos;
-    D.n_rows_neg = P.n_rows_neg;
+    D.n_rows = (int)P.rows.size();
+    D.m_last = P.m_last;
+    D.lo_last = P.lo_last;
     D.t = reinterpret_cast<const double *>(d + o_t);
     D.h = reinterpret_cast<const double *>(d + o_h);
     D.inv_h = reinterpret_cast<const double *>(d + o_ih);
@@ -1287,7 +1299,7 @@ few_status few_last_timing(few_ctx *ctx, float *ms)
     return FEW_OK;
 }
 
-few_status few_set_tiles(few_ctx *ctx, int prec, int R, int threads)
+few_status few_set_tiles(few_ctx *ctx, int prec, int R, int threads, int stage_slots)
 {
     if (!ctx) return FEW_ERR_INVALID_ARG;
     if (threads != 128 && threads != 256) return FEW_ERR_INVALID_ARG;
@@ -1298,18 +1310,22 @@ few_status few_set_tiles(few_ctx *ctx, int prec, int R, int threads)
     } else {
         return FEW_ERR_INVALID_ARG;
     }
+    if (stage_slots < kMinStageSlots || stage_slots > kMaxStageSlots || stage_slots % 16)
+        return FEW_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     ctx->tile_R[prec] = R;
     ctx->tile_T[prec] = threads;
+    ctx->tile_S[prec] = stage_slots;
     return FEW_OK;
 }
 
-few_status few_get_tiles(few_ctx *ctx, int prec, int *R, int *threads)
+few_status few_get_tiles(few_ctx *ctx, int prec, int *R, int *threads, int *stage_slots)
 {
     if (!ctx || (prec != FEW_FP64 && prec != FEW_MIXED)) return FEW_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     if (R) *R = ctx->tile_R[prec];
     if (threads) *threads = ctx->tile_T[prec];
+    if (stage_slots) *stage_slots = ctx->tile_S[prec];
     return FEW_OK;
 }
 
@@ -1326,7 +1342,7 @@ few_status few_mode_slots(const int *l, const int *m, const int *n, int N, int *
     few_status st = plan_slots(l, m, n, N, P);
     if (st) return st;
     if (n_slots) *n_slots = P.n_slots;
-    if (n_rows) *n_rows = P.n_rows_pos + P.n_rows_neg;
+    if (n_rows) *n_rows = (int)P.rows.size();
     return FEW_OK;
 }
 
@@ -1347,6 +1363,8 @@ bool ctx_traj_view(few_ctx *ctx, const few_traj *tr, CtxTrajView *v)
     v->tile_R[1] = ctx->tile_R[1];
     v->tile_T[0] = ctx->tile_T[0];
     v->tile_T[1] = ctx->tile_T[1];
+    v->tile_S[0] = ctx->tile_S[0];
+    v->tile_S[1] = ctx->tile_S[1];
     v->has_data = tr->has_data;
     v->K = tr->K;
     v->n_slots = tr->plan.n_slots;

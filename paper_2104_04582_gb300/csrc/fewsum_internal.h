@@ -20,8 +20,12 @@ enum : unsigned {
 
 constexpr int kMaxL = 32;
 constexpr int kMaxAbsN = 1024;
-constexpr int kMaxSlotsFp64 = 1776;   // 2 buffers x slots x 64 B <= 227 KB
-constexpr int kMaxSlotsMixed = 3552;  // 2 buffers x slots x 32 B <= 227 KB
+// Summation kernel: up to kSumMaxThreads threads per CTA; the per-segment slot table streams
+// through a ring of shared-memory stages of stage_slots slots each.
+constexpr int kSumMaxThreads = 256;
+constexpr int kMaxRing = 4;
+constexpr int kDefaultRing = 3;
+constexpr int kMinStageSlots = 16, kMaxStageSlots = 4096;
 
 // Summation kernel variants (and the folded-coefficient layout each reads).
 enum : int {
@@ -37,6 +41,7 @@ constexpr int kAnchorGroup = 16;
 struct Anchor {
     float4 phi;  // (f0, d1, d2, d3): reduced phase (turns) and increment coefficients (turns / sample^k)
     float4 r;
+    float4 g;    // phase of the final factor z_phi^{m_last} z_r^{lo_last}, same form
 };
 constexpr int kFoldThreads = 128;
 constexpr int kYlmThreads = 16;  // few pairs per block: spreads the FP64 work over SMs
@@ -48,8 +53,8 @@ struct TrajDev {
     int K, N, J, S;        // knots, modes, splines (2 + 2N), segments (K - 1)
     int n_pairs;           // distinct (l, m) pairs
     int n_slots;           // harmonic slots per segment
-    int n_rows_pos;        // rows with m >= 0 (ordered m = M..0)
-    int n_rows_neg;        // rows with m < 0 (ordered m = -M'..-1)
+    int n_rows;            // rows of the slot table: signed m from max m down to m_last
+    int m_last, lo_last;   // signed m and lowest n of the last row
     const double *t;       // [K] knot times
     const double *inv_h;   // [S] 1/(t_{k+1}-t_k)
     const double *h;       // [S] t_{k+1}-t_k
@@ -64,7 +69,8 @@ struct TrajDev {
     const int *slot_ptr;   // [n_slots + 1] CSR into contrib
     const int2 *contrib;   // [n_contrib] (mode * 2 + kind, 2 * pair + kind); kind 0: A Y+,
                            //   1: conj(A) Y-
-    const int2 *rows;      // [n_rows_pos + n_rows_neg] (np, nn) slots per half row
+    const int2 *rows;      // [n_rows] (slots of the row, lowest n of the previous row minus
+                           //   this row's lowest n); a row's slots run from its highest n down
 };
 
 // One spline-build job: a trajectory and the knot data to fit.
@@ -113,7 +119,9 @@ struct PlanHdr {
     int total_fold_blocks;
     int grid_sum;
     int total_anchors;  // anchors over all waves (mixed plans; 0 for FP64 plans)
-    int buf_bytes;   // bytes of one shared-memory coefficient buffer (max slots x slot bytes)
+    int buf_bytes;   // bytes of one ring stage (stage_slots x slot bytes, rounded up)
+    int stage_slots; // slots per ring stage (the mode tile)
+    int ring;        // ring stages
     int variant;     // kVariant* of the summation kernel and the folded layout
     const WaveDev *waves;
     const CtaStart *cta;
@@ -204,7 +212,7 @@ few_status check_request(const few_request &r, bool need_device_out);
 struct CtxTrajView {
     int device, sm_count;
     unsigned *d_err;
-    int tile_R[2], tile_T[2];
+    int tile_R[2], tile_T[2], tile_S[2];
     bool has_data;
     int K, n_slots, n_pairs;
     const double *t_host;

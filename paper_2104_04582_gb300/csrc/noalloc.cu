@@ -98,8 +98,9 @@ extern "C" few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req,
     const int R = v.tile_R[pi], T = v.tile_T[pi];
     const int variant = fp64 ? kVariantFp64 : kVariantScalar;
     const size_t slot_bytes = (size_t)sum_slot_bytes(variant);
-    const int buf_bytes = (int)up((size_t)v.n_slots * slot_bytes, 128);
-    const int smem = 2 * buf_bytes;
+    const int stage_slots = v.tile_S[pi] < v.n_slots ? v.tile_S[pi] : v.n_slots;
+    const int buf_bytes = (int)up((size_t)stage_slots * slot_bytes, 128);
+    const int smem = kDefaultRing * buf_bytes;
     const int occ = sum_occupancy(variant, R, T, smem);
     if (occ <= 0) return FEW_ERR_LIMIT;
     const int grid = v.sm_count * occ;
@@ -187,6 +188,8 @@ extern "C" few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req,
     hdr->total_anchors = n_anchors;
     hdr->grid_sum = grid;
     hdr->buf_bytes = buf_bytes;
+    hdr->stage_slots = stage_slots;
+    hdr->ring = kDefaultRing;
     hdr->variant = variant;
     hdr->waves = reinterpret_cast<const WaveDev *>(base + off_waves);
     hdr->cta = reinterpret_cast<const CtaStart *>(base + off_cta);

@@ -6,33 +6,39 @@
 // where K_{m,n} are the per-segment complex cubics produced by k_fold (amplitude splines with
 // the spin-weighted harmonics, the m < 0 partners of Eq. amp_symmetry and the prefactor folded
 // in).  Since e^{-i Phi_mn} = z_phi^m z_r^n exactly, the whole sum is a bivariate Laurent
-// polynomial in (z_phi, z_r) and is evaluated by Horner's rule: along each row of constant m,
-// over n >= 0 in z_r and over n < 0 in conj(z_r); then over the rows, m >= 0 in z_phi and
-// m < 0 in conj(z_phi).  Per (slot, sample) that is one complex cubic (6 FMA) and one complex
+// polynomial in (z_phi, z_r) and is evaluated by Horner's rule.  The slot table is laid out in
+// rows of constant signed m, from the largest m down to m_last; row j holds n = hi_j .. lo_j.
+// One Horner chain in z_r per row gives A_j = sum_n K_{m_j,n} z_r^{n - lo_j}; the rows are
+// combined by Horner's rule in z_phi in a frame shifted by each row's lowest n,
+//     T_j = T_{j-1} z_phi z_r^{lo_{j-1} - lo_j} + A_j,     h = T_last z_phi^{m_last} z_r^{lo_last},
+// so a row with no gap to its neighbour's lowest n costs one complex multiply and no power is
+// formed per row.  Per (slot, sample) that is one complex cubic (6 FMA) and one complex
 // multiply-add (4 FMA) -- no transcendental per mode.
 //
 // Phases: FEW_FP64 evaluates the phase splines (in rad) in FP64 for every sample and reduces
-// each phase modulo one turn, x - rint(x), in FP64; the reduced phases give z_phi and z_r
-// (sincospi).  FEW_MIXED reads the phases from anchors written by k_anchor: at every
-// kAnchorGroup-th sample the FP64 splines are evaluated and reduced modulo one turn, and the
-// phase cubic's exact Taylor coefficients about that sample (in turns per sample^k) are stored;
-// the kernel adds the in-group increment r (d1 + r (d2 + r d3)), r < kAnchorGroup (at most a
-// few tenths of a turn), in FP32.  So every large phase value and every reduction is FP64,
-// and the mixed kernel itself issues no FP64 instruction per sample (FP64 issue is scarce on
-// this chip).  The integer combination m Phi_phi + n Phi_r is then carried exactly by the
-// unit-modulus powers, so (m Phi_phi + n Phi_r) mod 2 pi never has to be formed explicitly.
-// FEW_FP64 does everything else in FP64; FEW_MIXED evaluates amplitudes, exponential powers
-// and the accumulation in FP32.
+// each phase modulo one turn, x - rint(x), in FP64; the reduced phases give z_phi, z_r and the
+// final factor (sincospi).  FEW_MIXED reads the phases from anchors written by k_anchor: at
+// every kAnchorGroup-th sample the FP64 splines are evaluated and reduced modulo one turn (and
+// the final factor's phase m_last Phi_phi + lo_last Phi_r formed from the reduced phases and
+// reduced again, all in FP64), and each phase cubic's exact Taylor coefficients about that
+// sample (in turns per sample^k) are stored; the kernel adds the in-group increment
+// r (d1 + r (d2 + r d3)), r < kAnchorGroup, in FP32.  So every large phase value and every
+// reduction is FP64, and the mixed kernel issues no FP64 instruction per sample (FP64 issue is
+// scarce on this chip).  FEW_FP64 does everything else in FP64; FEW_MIXED evaluates amplitudes,
+// exponential powers and the accumulation in FP32.
 //
 // Work decomposition: a persistent grid; each CTA owns an equal-cost, contiguous slice of the
-// concatenated (waveform, sample) space (cost = samples x slots), walks it segment by segment,
-// and stages each segment's folded coefficient table into shared memory with TMA bulk copies
-// (cp.async.bulk + mbarrier transaction counts), double-buffered so the next segment's table
-// arrives while the current one is in use.  Within a segment a pass covers threads x R
-// consecutive samples, R per thread, each thread holding its samples' Horner state in
-// registers and reusing every coefficient it reads from shared memory R times.  Every sample
-// is summed by one thread in a fixed slot order, so results do not depend on the grid, the
-// tile shape or on which other waveforms share the launch.
+// concatenated (waveform, sample) space (cost = samples x slots) and walks it segment by
+// segment in passes of threads x R consecutive samples, R per thread, each thread holding its
+// samples' Horner state in registers.  The segment's folded coefficient table is streamed into
+// shared memory once per pass, in tiles of stage_slots slots (the mode tile), through a ring of
+// `ring` stages: the last warp to release a stage issues the TMA bulk copies (cp.async.bulk with
+// mbarrier transaction counts) of the tile `ring` positions ahead into it, so no warp ever waits
+// for a stage to empty, a table of any size passes through a fixed amount of shared memory, and
+// every coefficient read from it is reused R times.  Every wait is bounded: it gives up after
+// 2 s, latches FEW_ERR_TIMEOUT and the CTA winds down (letting its copies in flight land).  Every sample is summed by one thread
+// in a fixed slot order, so results do not depend on the grid, the tile shape or on which other
+// waveforms share the launch.
 #include "fewsum_internal.h"
 #include "phase_eval.cuh"
 #include "async.cuh"
@@ -41,7 +47,7 @@ namespace fewsum {
 
 namespace {
 
-constexpr int kSlotUnroll = 2;  // slots per iteration of the Horner chain loop
+constexpr int kSlotUnroll = 8;  // slots per iteration of the Horner chain loop
 constexpr int kBulkChunk = 32768;
 
 struct Piece {
@@ -99,18 +105,22 @@ template <> struct Cf<double> {
     }
 };
 
-// Per-sample local coordinate u and the powers' bases (cos, sin of 2 pi f) of one segment.
+// Per-sample local coordinate u, the powers' bases (cos, sin of 2 pi f) of one segment, and the
+// final factor z_phi^{m_last} z_r^{lo_last} = e^{-2 pi i g}.
 template <typename T> struct PhaseSrc;
 
 // FP64: both phase splines evaluated and reduced for every sample.
 template <> struct PhaseSrc<double> {
     SegPhase sp;
     double t0, dt;
+    int m_last, lo_last;
     __device__ __forceinline__ void init(const WaveDev &W, int s)
     {
         sp = seg_phase(W.tr, s, W.dphi_phi, W.dphi_r);
         t0 = W.t0;
         dt = W.dt;
+        m_last = W.tr.m_last;
+        lo_last = W.tr.lo_last;
     }
     __device__ __forceinline__ void at(int i, double &u, double &cphi, double &sphi, double &cr,
                                        double &sr) const
@@ -119,6 +129,14 @@ template <> struct PhaseSrc<double> {
         sample_phase(sp, t0, dt, i, fphi, fr, u);
         sincospi(2.0 * fphi, &sphi, &cphi);
         sincospi(2.0 * fr, &sr, &cr);
+    }
+    // cos and sin of 2 pi g, g = m_last f_phi + lo_last f_r reduced modulo one turn
+    __device__ __forceinline__ void last(int i, double &cg, double &sg) const
+    {
+        double fphi, fr, u;
+        sample_phase(sp, t0, dt, i, fphi, fr, u);
+        const double g = fma((double)m_last, fphi, (double)lo_last * fr);
+        sincospi(2.0 * (g - rint(g)), &sg, &cg);
     }
 };
 
@@ -138,17 +156,25 @@ template <> struct PhaseSrc<float> {
         u0 = (float)((fma((double)i0, W.dt, W.t0) - W.tr.t[s]) * ih);
         du = (float)(W.dt * ih);
     }
+    __device__ __forceinline__ static float phase(const float4 a, float x)
+    {
+        return fmaf(fmaf(fmaf(a.w, x, a.z), x, a.y), x, a.x);
+    }
     __device__ __forceinline__ void at(int i, float &u, float &cphi, float &sphi, float &cr,
                                        float &sr) const
     {
-        const float4 *a = reinterpret_cast<const float4 *>(anc + aidx + i / kAnchorGroup);
-        const float4 ap = __ldg(a), ar = __ldg(a + 1);
+        const Anchor *a = anc + aidx + i / kAnchorGroup;
+        const float4 ap = __ldg(&a->phi), ar = __ldg(&a->r);
         const float x = (float)(i % kAnchorGroup);
-        const float fphi = fmaf(fmaf(fmaf(ap.w, x, ap.z), x, ap.y), x, ap.x);
-        const float fr = fmaf(fmaf(fmaf(ar.w, x, ar.z), x, ar.y), x, ar.x);
-        sincospif(2.0f * fphi, &sphi, &cphi);
-        sincospif(2.0f * fr, &sr, &cr);
+        sincospif(2.0f * phase(ap, x), &sphi, &cphi);
+        sincospif(2.0f * phase(ar, x), &sr, &cr);
         u = fmaf((float)(i - i0), du, u0);
+    }
+    __device__ __forceinline__ void last(int i, float &cg, float &sg) const
+    {
+        const Anchor *a = anc + aidx + i / kAnchorGroup;
+        const float4 ag = __ldg(&a->g);
+        sincospif(2.0f * phase(ag, (float)(i % kAnchorGroup)), &sg, &cg);
     }
 };
 
@@ -174,20 +200,101 @@ __device__ __forceinline__ void horner_chain(const T *__restrict__ cf, int n, co
     }
 }
 
-// One pass of the scalar path: R consecutive samples per thread, one value per register.
-template <typename T, int R>
-struct ScalarPass {
-    using Scalar = T;
-    static constexpr int kSamples = R;
-    static constexpr int kSlotBytes = 8 * (int)sizeof(T);
+// Shared-memory ring of the coefficient tiles.  A stage is refilled by the last consumer warp
+// to release it (a per-stage arrival counter), so no thread ever waits for a stage to empty.
+struct Ring {
+    unsigned char *buf;   // ring x stage_bytes
+    uint64_t *full;       // [ring] transaction barrier of the tile in the stage
+    int *count;           // [ring] warps done with the stage's current tile
+    int *issued;          // [ring] CTA stage index last copied into the stage (-1: none)
+    volatile int *abort;
+    int ring, stage_slots, stage_bytes, n_warps;
+};
 
-    __device__ __forceinline__ static void run(const WaveDev &W, const unsigned char *buf, int p0,
-                                               int i1, const PhaseSrc<T> &ps)
-    {
-        const T *__restrict__ cf = reinterpret_cast<const T *>(buf);
-        const int tid = threadIdx.x;
-        const int base = p0 + tid * R;
-        T u[R], zr[R], zi[R], fr[R], fi[R];
+// Position in the CTA's sequence of tiles: piece (wave, segment, samples), pass, tile.
+struct Walk {
+    int w, i;          // wave and first sample of the current piece
+    int s, i1;         // its segment and end
+    int n_tiles, n_pass, pass, tile;
+    bool valid;
+};
+
+__device__ __forceinline__ void walk_piece(Walk &a, const PlanHdr &h, const CtaStart &end, int U,
+                                           int stage_slots)
+{
+    a.valid = normalize(h, a.w, a.i, end);
+    if (!a.valid) return;
+    const Piece pc = piece_at(h, a.w, a.i, end);
+    a.s = pc.s;
+    a.i1 = pc.i1;
+    a.n_tiles = (h.waves[pc.w].tr.n_slots + stage_slots - 1) / stage_slots;
+    a.n_pass = (pc.i1 - pc.i0 + U - 1) / U;
+    a.pass = 0;
+    a.tile = 0;
+}
+
+__device__ __forceinline__ void walk_next(Walk &a, const PlanHdr &h, const CtaStart &end, int U,
+                                          int stage_slots)
+{
+    if (!a.valid) return;
+    if (++a.tile < a.n_tiles) return;
+    a.tile = 0;
+    if (++a.pass < a.n_pass) return;
+    a.i = a.i1;
+    walk_piece(a, h, end, U, stage_slots);
+}
+
+// Copy the tile at `a` into stage b (one thread): its slots of the segment's folded table.
+template <typename T>
+__device__ void issue_tile(const PlanHdr &h, const Walk &a, int b, int k, const Ring &rg)
+{
+    constexpr int kSlotBytes = 8 * (int)sizeof(T);
+    const WaveDev &W = h.waves[a.w];
+    const int n_slots = W.tr.n_slots;
+    const int first = a.tile * rg.stage_slots;
+    const uint32_t bytes = (uint32_t)(min(rg.stage_slots, n_slots - first) * kSlotBytes);
+    const unsigned char *src = reinterpret_cast<const unsigned char *>(W.fcoef) +
+                               ((size_t)a.s * n_slots + first) * kSlotBytes;
+    unsigned char *dst = rg.buf + (size_t)b * rg.stage_bytes;
+    rg.issued[b] = k;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&rg.full[b], bytes);
+    for (uint32_t off = 0; off < bytes; off += kBulkChunk)
+        bulk_g2s(dst + off, src + off, min((uint32_t)kBulkChunk, bytes - off), &rg.full[b]);
+}
+
+// A warp is done with stage b (CTA stage index k): the last warp to say so refills the stage
+// with tile k + ring (the walk `ahead` points there), if the CTA has one.
+template <typename T>
+__device__ __forceinline__ void release_stage(const PlanHdr &h, const Walk &ahead, int b, int k,
+                                              const Ring &rg)
+{
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        __threadfence_block();  // this warp's reads of the stage come before the refill
+        if (atomicAdd(&rg.count[b], 1) == rg.n_warps - 1) {
+            __threadfence_block();
+            rg.count[b] = 0;
+            if (ahead.valid) issue_tile<T>(h, ahead, b, k + rg.ring, rg);
+        }
+    }
+}
+
+// One pass of the consumer warps: samples p0 + tid * R + r of piece [.., i1), every tile of
+// the segment's table in turn (CTA stage indices k0, k0 + 1, ...).  Warps with no sample in the
+// pass still take part in the tile hand-over.  False if a wait gave up.
+template <typename T, int R>
+__device__ bool consume_pass(const PlanHdr &h, const WaveDev &W, const PhaseSrc<T> &ps, int p0,
+                             int i1, bool active, const Ring &rg, int k0, int n_tiles, Walk &ahead,
+                             const CtaStart &end, int U)
+{
+    const int tid = threadIdx.x;
+    const int base = p0 + tid * R;
+    T u[R], zr[R], zi[R], fr[R], fi[R], tr_[R], ti_[R], ar[R], ai[R];
+    const int2 *__restrict__ rows = W.tr.rows;
+    const int n_rows = W.tr.n_rows, n_slots = W.tr.n_slots;
+    int row = 0, row_left = 0;
+    if (active) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int i = min(base + r, i1 - 1);
@@ -197,150 +304,177 @@ struct ScalarPass {
             fi[r] = -sp_;
             zr[r] = cr;   // z_r = e^{-i 2 pi f_r}
             zi[r] = -sr;
+            tr_[r] = ti_[r] = ar[r] = ai[r] = (T)0;
         }
-        T tpr[R], tpi[R], tnr[R], tni[R], nzi[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            tpr[r] = tpi[r] = tnr[r] = tni[r] = (T)0;
-            nzi[r] = -zi[r];
-        }
-        const int2 *__restrict__ rows = W.tr.rows;
-        const int nrp = W.tr.n_rows_pos, nrows = nrp + W.tr.n_rows_neg;
-        int slot = 0;
-        for (int row = 0; row < nrows; ++row) {
-            const int2 rw = __ldg(rows + row);
-            T ar[R], ai[R], br[R], bi[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) ar[r] = ai[r] = br[r] = bi[r] = (T)0;
-            horner_chain<T, R>(cf + 8 * slot, rw.x, u, zr, zi, ar, ai);
-            slot += rw.x;
-            horner_chain<T, R>(cf + 8 * slot, rw.y, u, zr, nzi, br, bi);
-            slot += rw.y;
-            const bool pos = row < nrp;
+        row_left = __ldg(rows).x;
+    }
+    // close every finished row: T <- T z_phi z_r^{shift} + A, then start the next row
+    auto close_rows = [&]() {
+        while (row < n_rows && row_left == 0) {
+            const int shift = __ldg(rows + row).y;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                // row value: a + conj(z_r) * b
-                const T vr = fma(br[r], zr[r], fma(bi[r], zi[r], ar[r]));
-                const T vi = fma(bi[r], zr[r], fma(br[r], nzi[r], ai[r]));
-                // T+ <- T+ z_phi + v  (m >= 0 rows),  T- <- T- conj(z_phi) + v  (m < 0 rows)
-                if (pos) {
-                    const T nr = fma(tpr[r], fr[r], fma(tpi[r], -fi[r], vr));
-                    const T ni = fma(tpr[r], fi[r], fma(tpi[r], fr[r], vi));
-                    tpr[r] = nr;
-                    tpi[r] = ni;
-                } else {
-                    const T nr = fma(tnr[r], fr[r], fma(tni[r], fi[r], vr));
-                    const T ni = fma(tni[r], fr[r], fma(tnr[r], -fi[r], vi));
-                    tnr[r] = nr;
-                    tni[r] = ni;
+                const T nr = fma(tr_[r], fr[r], -ti_[r] * fi[r]);
+                const T ni = fma(tr_[r], fi[r], ti_[r] * fr[r]);
+                tr_[r] = nr;
+                ti_[r] = ni;
+            }
+            for (int d = 0; d < (shift < 0 ? -shift : shift); ++d) {
+                const T s = shift < 0 ? (T)-1 : (T)1;  // z_r or conj(z_r)
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const T nr = fma(tr_[r], zr[r], -ti_[r] * (s * zi[r]));
+                    const T ni = fma(tr_[r], s * zi[r], ti_[r] * zr[r]);
+                    tr_[r] = nr;
+                    ti_[r] = ni;
                 }
             }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                tr_[r] += ar[r];
+                ti_[r] += ai[r];
+                ar[r] = ai[r] = (T)0;
+            }
+            if (++row < n_rows) row_left = __ldg(rows + row).x;
         }
+    };
+    if (active) close_rows();  // leading empty rows (none in a well-formed plan)
+    for (int t = 0; t < n_tiles; ++t) {
+        const int k = k0 + t;
+        const int b = k % rg.ring;
+        if (*rg.abort) return false;
+        if (!mbar_wait_bounded(&rg.full[b], (uint32_t)(k / rg.ring) & 1u)) {
+            *rg.abort = 1;
+            return false;
+        }
+        if (active) {
+            const T *__restrict__ cf = reinterpret_cast<const T *>(rg.buf + (size_t)b * rg.stage_bytes);
+            const int a = t * rg.stage_slots;
+            const int e = min(a + rg.stage_slots, n_slots);
+            int slot = a;
+            while (slot < e) {
+                const int n = min(row_left, e - slot);
+                if (n <= 0) break;  // slots beyond the last row: an inconsistent plan, never hang
+                horner_chain<T, R>(cf + 8 * (slot - a), n, u, zr, zi, ar, ai);
+                slot += n;
+                row_left -= n;
+                if (row_left == 0) close_rows();
+            }
+        }
+        release_stage<T>(h, ahead, b, k, rg);
+        walk_next(ahead, h, end, U, rg.stage_slots);
+    }
+    if (active) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int i = base + r;
             if (i >= i1) break;
-            // h = T+ + conj(z_phi) T-
-            const T hr = fma(tnr[r], fr[r], fma(tni[r], fi[r], tpr[r]));
-            const T hi = fma(tni[r], fr[r], fma(tnr[r], -fi[r], tpi[r]));
+            // h = T z_phi^{m_last} z_r^{lo_last}
+            T cg, sg;
+            ps.last(i, cg, sg);
+            const T hr = fma(tr_[r], cg, ti_[r] * sg);   // (tr + i ti)(cg - i sg)
+            const T hi = fma(ti_[r], cg, -tr_[r] * sg);
             if (W.out_c64)
                 reinterpret_cast<float2 *>(W.out)[i] = make_float2((float)hr, (float)hi);
             else
                 reinterpret_cast<double2 *>(W.out)[i] = make_double2((double)hr, (double)hi);
         }
     }
+    return true;
+}
+
+
+// R samples per thread; T the arithmetic type (float: FEW_MIXED, double: FEW_FP64).
+template <typename T, int R>
+struct ScalarPass {
+    using Scalar = T;
+    static constexpr int kSamples = R;
 };
 
 }  // namespace
 
+// blockDim.x consumer threads (all of them compute; the refills are issued by whichever warp
+// releases a stage last).
 template <typename V>
-__global__ void __launch_bounds__(256) k_sum(const PlanHdr *__restrict__ hp)
+__global__ void __launch_bounds__(kSumMaxThreads, 2) k_sum(const PlanHdr *__restrict__ hp)
 {
+    using T = typename V::Scalar;
+    constexpr int R = V::kSamples;
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ int s_abort;
+    __shared__ __align__(8) uint64_t s_full[kMaxRing];
+    __shared__ int s_count[kMaxRing], s_issued[kMaxRing];
+    __shared__ int s_abort, s_exit;
     const PlanHdr h = *hp;
     const int tid = threadIdx.x;
-    const int U = blockDim.x * V::kSamples;
+    const int U = blockDim.x * R;
     const CtaStart beg = h.cta[blockIdx.x];
     const CtaStart end = h.cta[blockIdx.x + 1];
-    int w = beg.wave, i = beg.sample;
-    if (!normalize(h, w, i, end)) return;  // uniform across the CTA
-
+    {
+        int w = beg.wave, i = beg.sample;
+        if (!normalize(h, w, i, end)) return;  // uniform across the CTA: no work
+    }
+    Ring rg;
+    rg.buf = smem;
+    rg.full = s_full;
+    rg.count = s_count;
+    rg.issued = s_issued;
+    rg.abort = &s_abort;
+    rg.ring = h.ring;
+    rg.stage_slots = h.stage_slots;
+    rg.stage_bytes = h.buf_bytes;
+    rg.n_warps = blockDim.x / 32;
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int b = 0; b < rg.ring; ++b) {
+            mbar_init(&rg.full[b], 1);
+            s_count[b] = 0;
+            s_issued[b] = -1;
+        }
         fence_mbar_init();
         s_abort = 0;
+        s_exit = 0;
     }
     __syncthreads();
 
-    // Producer state (thread 0): the last issued piece.
-    Piece cur = piece_at(h, w, i, end);
-    int prod_w = cur.w, prod_i1 = cur.i1;
-    bool prod_more = true;
-    auto issue = [&](const Piece &p, int b) {
-        const WaveDev &P = h.waves[p.w];
-        const uint32_t bytes = (uint32_t)P.tr.n_slots * (uint32_t)V::kSlotBytes;
-        const unsigned char *src =
-            reinterpret_cast<const unsigned char *>(P.fcoef) + (size_t)p.s * bytes;
-        unsigned char *dst = smem + (size_t)b * h.buf_bytes;
-        mbar_arrive_expect_tx(&bar[b], bytes);
-        for (uint32_t off = 0; off < bytes; off += kBulkChunk) {
-            const uint32_t n = min((uint32_t)kBulkChunk, bytes - off);
-            bulk_g2s(dst + off, src + off, n, &bar[b]);
-        }
-    };
-    auto issue_next = [&](int b) {
-        int nw = prod_w, ni = prod_i1;
-        if (prod_more && normalize(h, nw, ni, end)) {
-            const Piece p = piece_at(h, nw, ni, end);
-            issue(p, b);
-            prod_w = p.w;
-            prod_i1 = p.i1;
-        } else {
-            prod_more = false;
-        }
-    };
-    if (tid == 0) {
-        fence_proxy_async_smem();
-        issue(cur, 0);
-        issue_next(1);
+    // `ahead` walks `ring` tiles in front of this warp's position; thread 0 fills the ring first
+    Walk ahead;
+    ahead.w = beg.wave;
+    ahead.i = beg.sample;
+    walk_piece(ahead, h, end, U, rg.stage_slots);
+    for (int k = 0; k < rg.ring; ++k) {
+        if (tid == 0 && ahead.valid) issue_tile<T>(h, ahead, k, k, rg);
+        walk_next(ahead, h, end, U, rg.stage_slots);
     }
 
     int k = 0;
-    for (;; ++k) {
-        const int b = k & 1;
-        if (!mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1))) s_abort = 1;
-        __syncthreads();
-        if (s_abort) break;
-
-        const WaveDev &W = h.waves[cur.w];
-        const unsigned char *buf = smem + (size_t)b * h.buf_bytes;
-        PhaseSrc<typename V::Scalar> ps;
-        ps.init(W, cur.s);
-        const int warp_first = (tid & ~31) * V::kSamples;
-        for (int p0 = cur.i0; p0 < cur.i1; p0 += U) {
-            if (p0 + warp_first >= cur.i1) continue;  // whole warp past the end: idle
-            V::run(W, buf, p0, cur.i1, ps);
+    const int warp_first = (tid & ~31) * R;
+    int w = beg.wave, i = beg.sample;
+    bool ok = true;
+    while (ok && normalize(h, w, i, end)) {
+        const Piece pc = piece_at(h, w, i, end);
+        const WaveDev &W = h.waves[pc.w];
+        PhaseSrc<T> ps;
+        ps.init(W, pc.s);
+        const int n_tiles = (W.tr.n_slots + rg.stage_slots - 1) / rg.stage_slots;
+        for (int p0 = pc.i0; p0 < pc.i1 && ok; p0 += U) {
+            const bool active = p0 + warp_first < pc.i1;  // else the whole warp is past the end
+            ok = consume_pass<T, R>(h, W, ps, p0, pc.i1, active, rg, k, n_tiles, ahead, end, U);
+            k += n_tiles;
         }
-
-        int nw = cur.w, ni = cur.i1;
-        if (!normalize(h, nw, ni, end)) break;
-        cur = piece_at(h, nw, ni, end);
-        __syncthreads();  // every thread is done with buffer b before it is refilled
-        if (tid == 0) {
-            fence_proxy_async_smem();
-            issue_next(b);
-        }
+        w = pc.w;
+        i = pc.i1;
     }
-
-    if (s_abort && tid == 0) {
-        atomicOr(h.err, ERRBIT_TIMEOUT);
-        // Give the copies still in flight (the one that expired, and the next piece's if it
-        // was issued) a second bounded wait before the CTA exits and its shared memory goes.
-        mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1));
-        if (prod_more) mbar_wait_bounded(&bar[(k + 1) & 1], (uint32_t)(((k + 1) >> 1) & 1));
+    if ((tid & 31) == 0) {
+        if (!ok) atomicOr(h.err, ERRBIT_TIMEOUT);
+        __threadfence_block();
+        // the last warp out lets every copy still in flight land before the CTA's shared
+        // memory goes away (immediate when everything issued was consumed)
+        if (atomicAdd(&s_exit, 1) == rg.n_warps - 1) {
+            __threadfence_block();
+            for (int b = 0; b < rg.ring; ++b) {
+                const int kk = s_issued[b];
+                if (kk >= 0) mbar_wait_bounded(&rg.full[b], (uint32_t)(kk / rg.ring) & 1u);
+            }
+        }
     }
 }
 
@@ -378,7 +512,9 @@ cudaError_t launch_phases(const TrajDev &tr, const int *seg_start, double t0, do
 // the Taylor coefficients of each phase cubic in sample units,
 //   Phi(u + k du) - Phi(u) = k du Phi'(u) + (k du)^2 Phi''(u)/2 + (k du)^3 p3,  du = dt / h,
 // divided by 2 pi (turns).  The identity is exact for a cubic; only its FP32 evaluation over
-// k < kAnchorGroup samples in the summation kernel rounds.
+// k < kAnchorGroup samples in the summation kernel rounds.  The third stream is the phase of
+// the final factor, g = m_last f_phi + lo_last f_r (an integer combination of the reduced
+// phases, so equal to m_last Phi_phi + lo_last Phi_r modulo one turn), reduced again.
 __global__ void __launch_bounds__(256) k_anchor(const PlanHdr *__restrict__ hp)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -404,24 +540,27 @@ __global__ void __launch_bounds__(256) k_anchor(const PlanHdr *__restrict__ hp)
     const double t = fma((double)q * kAnchorGroup, W.dt, W.t0);
     const double u = (t - sp.tk) * sp.ih;
     const double du = W.dt * sp.ih, du2 = du * du, du3 = du2 * du;
-    float f[2][4];
+    double f[2][4];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const double c0 = k ? sp.c0r : sp.c0phi;
         const double *p = k ? sp.pr : sp.pphi;
         const double ph = fma(fma(fma(p[2], u, p[1]), u, p[0]), u, c0);
-        const double d1 = fma(fma(3.0 * p[2], u, 2.0 * p[1]), u, p[0]) * du;
-        const double d2 = fma(3.0 * p[2], u, p[1]) * du2;
-        const double d3 = p[2] * du3;
         const double x = ph * kInv2Pi;
-        f[k][0] = (float)(x - rint(x));
-        f[k][1] = (float)(d1 * kInv2Pi);
-        f[k][2] = (float)(d2 * kInv2Pi);
-        f[k][3] = (float)(d3 * kInv2Pi);
+        f[k][0] = x - rint(x);
+        f[k][1] = fma(fma(3.0 * p[2], u, 2.0 * p[1]), u, p[0]) * du * kInv2Pi;
+        f[k][2] = fma(3.0 * p[2], u, p[1]) * du2 * kInv2Pi;
+        f[k][3] = p[2] * du3 * kInv2Pi;
     }
+    const double ml = (double)W.tr.m_last, ll = (double)W.tr.lo_last;
+    double fg[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) fg[c] = fma(ml, f[0][c], ll * f[1][c]);
+    fg[0] -= rint(fg[0]);
     Anchor a;
-    a.phi = make_float4(f[0][0], f[0][1], f[0][2], f[0][3]);
-    a.r = make_float4(f[1][0], f[1][1], f[1][2], f[1][3]);
+    a.phi = make_float4((float)f[0][0], (float)f[0][1], (float)f[0][2], (float)f[0][3]);
+    a.r = make_float4((float)f[1][0], (float)f[1][1], (float)f[1][2], (float)f[1][3]);
+    a.g = make_float4((float)fg[0], (float)fg[1], (float)fg[2], (float)fg[3]);
     W.anchors[j] = a;
 }
 

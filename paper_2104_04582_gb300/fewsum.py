@@ -113,8 +113,9 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
             "few_batch_run": (ctypes.c_int, [_vp, _vp, _vp]),
             "few_batch_release": (ctypes.c_int, [_vp, _vp]),
             "few_sync_status": (ctypes.c_int, [_vp]),
-            "few_set_tiles": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
-            "few_get_tiles": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _ip]),
+            "few_set_tiles": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int]),
+            "few_get_tiles": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _ip, _ip]),
             "few_ctx_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
             "few_last_timing": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float)]),
             "few_phase_samples": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double,
@@ -269,15 +270,17 @@ def few_sync_status(ctx: int) -> int:
     return int(load().few_sync_status(ctx))
 
 
-def few_set_tiles(ctx: int, prec: int, samples_per_thread: int, threads_per_block: int) -> None:
+def few_set_tiles(ctx: int, prec: int, samples_per_thread: int, threads_per_block: int,
+                  stage_slots: int) -> None:
     _check("few_set_tiles", load().few_set_tiles(ctx, int(prec), int(samples_per_thread),
-                                                 int(threads_per_block)))
+                                                 int(threads_per_block), int(stage_slots)))
 
 
 def few_get_tiles(ctx: int, prec: int):
-    r, t = ctypes.c_int(), ctypes.c_int()
-    _check("few_get_tiles", load().few_get_tiles(ctx, int(prec), ctypes.byref(r), ctypes.byref(t)))
-    return r.value, t.value
+    r, t, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check("few_get_tiles", load().few_get_tiles(ctx, int(prec), ctypes.byref(r), ctypes.byref(t),
+                                                 ctypes.byref(s)))
+    return r.value, t.value, s.value
 
 
 def few_ctx_set_timing(ctx: int, enable: bool) -> None:

@@ -45,10 +45,15 @@ class Context:
     def sync_status(self) -> int:
         return F.few_sync_status(self.handle)
 
-    def set_tiles(self, prec: int, samples_per_thread: int, threads: int) -> None:
-        F.few_set_tiles(self.handle, prec, samples_per_thread, threads)
+    def set_tiles(self, prec: int, samples_per_thread: int, threads: int,
+                  stage_slots: Optional[int] = None) -> None:
+        """Tile shape of one precision; stage_slots (the mode tile) keeps its value if None."""
+        if stage_slots is None:
+            stage_slots = F.few_get_tiles(self.handle, prec)[2]
+        F.few_set_tiles(self.handle, prec, samples_per_thread, threads, stage_slots)
 
     def get_tiles(self, prec: int):
+        """(samples per thread, threads per block, slots per stage) of one precision."""
         return F.few_get_tiles(self.handle, prec)
 
     def memory(self):

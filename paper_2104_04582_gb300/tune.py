@@ -4,14 +4,15 @@ The summation kernel is tunable in three ways that change speed but never result
 is summed by one thread in a fixed order, so all choices are bit-identical):
 
 * samples per thread R (the segment tile: one pass covers threads x R consecutive samples),
-* threads per block (128 or 256).
-
-The mode tile is the per-segment harmonic slot table, staged whole in shared memory; its size is
-set by the mode set, and it decides occupancy together with R and the block size.
+* threads per block (128 or 256),
+* slots per shared-memory stage (the mode tile: each segment's harmonic slot table streams
+  through a ring of stages of this many slots, so it also sets the shared memory per CTA).
 
 `tune()` times every candidate on a representative workload with CUDA events (several runs,
 best of), picks the fastest, installs it in the context, and records it in a JSON cache keyed by
-(precision, slot-count bucket, samples bucket); `apply_cached()` installs a cached choice.
+(precision, slot-count bucket, samples bucket); `apply_cached()` installs a cached choice and
+`ensure()` does either, so that a caller (the batched path, the serving engine, the benchmark)
+runs every workload with a tuned tile.
 """
 from __future__ import annotations
 
@@ -23,8 +24,8 @@ from typing import Dict, List, Optional, Sequence, Tuple
 from . import fewsum as F
 
 CANDIDATES = {
-    F.FEW_FP64: [(1, 256), (2, 256), (1, 128), (2, 128)],
-    F.FEW_MIXED: [(r, t) for r in (2, 4, 8) for t in (128, 256)],
+    F.FEW_FP64: [(r, t, s) for r in (1, 2) for t in (128, 256) for s in (128, 256, 512)],
+    F.FEW_MIXED: [(r, t, s) for r in (2, 4, 8) for t in (128, 256) for s in (256, 512, 1024)],
 }
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "fewsum_tiles.json")
@@ -52,17 +53,17 @@ def _save(path: str, data: Dict[str, dict]) -> None:
     os.replace(tmp, path)
 
 
-def install(ctx_handle: int, prec: int, choice: Tuple[int, int]) -> None:
-    R, T = choice
-    F.few_set_tiles(ctx_handle, prec, R, T)
+def install(ctx_handle: int, prec: int, choice: Tuple[int, int, int]) -> None:
+    R, T, S = choice
+    F.few_set_tiles(ctx_handle, prec, R, T, S)
 
 
 def tune(ctx_handle: int, run, prec: int, n_slots: int, n_samples: int, repeats: int = 3,
          cache_path: Optional[str] = DEFAULT_CACHE,
-         candidates: Optional[Sequence[Tuple[int, int]]] = None) -> Tuple[Tuple[int, int], Dict[str, float]]:
+         candidates: Optional[Sequence[Tuple[int, int, int]]] = None) -> Tuple[Tuple[int, int, int], Dict[str, float]]:
     """Time `run()` (which must queue one workload on the current stream) for every candidate.
 
-    Returns the best (R, threads) and the per-candidate best time in ms; installs the
+    Returns the best (R, threads, stage_slots) and the per-candidate best time in ms; installs the
     winner in the context and stores it in the cache (unless cache_path is None).
     """
     import torch
@@ -84,7 +85,7 @@ def tune(ctx_handle: int, run, prec: int, n_slots: int, n_samples: int, repeats:
             b.record()
             b.synchronize()
             ms = min(ms, a.elapsed_time(b))
-        times[f"R={c[0]} T={c[1]}"] = ms
+        times[f"R={c[0]} T={c[1]} S={c[2]}"] = ms
         if ms < best_ms:
             best, best_ms = c, ms
     if best is None:
@@ -92,17 +93,33 @@ def tune(ctx_handle: int, run, prec: int, n_slots: int, n_samples: int, repeats:
     install(ctx_handle, prec, best)
     if cache_path:
         data = _load(cache_path)
-        data[bucket(prec, n_slots, n_samples)] = {"R": best[0], "threads": best[1], "ms": best_ms}
+        data[bucket(prec, n_slots, n_samples)] = {"R": best[0], "threads": best[1],
+                                                  "stage_slots": best[2], "ms": best_ms}
         _save(cache_path, data)
     return best, times
 
 
 def apply_cached(ctx_handle: int, prec: int, n_slots: int, n_samples: int,
-                 cache_path: str = DEFAULT_CACHE) -> Optional[Tuple[int, int]]:
+                 cache_path: str = DEFAULT_CACHE) -> Optional[Tuple[int, int, int]]:
     """Install the cached choice for this bucket, if any; returns it."""
     e = _load(cache_path).get(bucket(prec, n_slots, n_samples))
     if not e:
         return None
-    choice = (int(e["R"]), int(e["threads"]))
+    if "stage_slots" not in e:
+        return None
+    choice = (int(e["R"]), int(e["threads"]), int(e["stage_slots"]))
     install(ctx_handle, prec, choice)
     return choice
+
+
+def ensure(ctx_handle: int, run, prec: int, n_slots: int, n_samples: int,
+           cache_path: Optional[str] = DEFAULT_CACHE, repeats: int = 2) -> Tuple[Tuple[int, int, int], bool]:
+    """Install the cached tile for this workload bucket, tuning with `run` on a miss.
+
+    Returns (choice, tuned_now)."""
+    if cache_path:
+        c = apply_cached(ctx_handle, prec, n_slots, n_samples, cache_path)
+        if c is not None:
+            return c, False
+    best, _ = tune(ctx_handle, run, prec, n_slots, n_samples, repeats=repeats, cache_path=cache_path)
+    return best, True

@@ -52,11 +52,13 @@ def test_mode_slots_full_grid(lib):
 
 
 def test_mode_slots_partner_rows_and_zero_fill(lib):
-    # (2,2,3): row m=2 has n = 0..3 (4 slots, zero-filled), partner row m=-2 has n = -1..-3;
-    # rows m = 1, 0 exist (empty) for the Horner step in z_phi; row m = -1 is empty.
-    assert F.few_mode_slots([(2, 2, 3)]) == (4 + 3, 5)
-    # m = 0 only: no partner rows
-    assert F.few_mode_slots([(2, 0, 1), (3, 0, -2)]) == (2 + 2, 1)
+    # (2,2,3): row m=2 holds n = 3 only, its partner row m=-2 holds n = -3; rows m = 1, 0, -1
+    # exist (empty) for the Horner step in z_phi
+    assert F.few_mode_slots([(2, 2, 3)]) == (1 + 1, 5)
+    # m = 0 only: no partner rows; one row spanning n = -2..1 (zero-filled at n = -1, 0)
+    assert F.few_mode_slots([(2, 0, 1), (3, 0, -2)]) == (4, 1)
+    # rows span each one's own n range: m=1 holds n = 5..7 (3 slots), m=-1 holds n = -7..-5
+    assert F.few_mode_slots([(2, 1, 5), (3, 1, 7)]) == (3 + 0 + 3, 3)
 
 
 @pytest.mark.parametrize("modes", [

@@ -132,6 +132,43 @@ def test_mode_sets(gpu_ctx, name):
     assert oracle.mismatch(gm, o) <= MIXED_MISMATCH
 
 
+@pytest.mark.parametrize("lmax,nmax", [(6, 80), (12, 80)])
+def test_wide_mode_tables(gpu_ctx, lmax, nmax):
+    """|n| up to 80: slot tables of 13 x 161 = 2093 and 25 x 161 = 4025 slots per segment, more
+    than one shared-memory stage holds, streamed tile by tile (Sec. 3.C quotes 1e2-1e4 modes)."""
+    modes = W.mode_grid(lmax, nmax)
+    slots, rows = F.few_mode_slots(modes)
+    assert slots == (2 * lmax + 1) * (2 * nmax + 1)
+    # slow decay in l and n (sigma_l = 8, sigma_n = 60) so every slot carries weight
+    w = W.make_inputs(2.0e5, 9, 2.0e5 / 1500, modes, 77 + lmax, 8.0, 60.0, n_samples=1500)
+    o = _oracle(w)
+    g = _gpu(gpu_ctx, w, F.FEW_FP64)
+    assert rel_l2(g, o) <= FP64_REL_L2, rel_l2(g, o)
+    assert max_phase_err(g, o) <= FP64_PHASE
+    gm = _gpu(gpu_ctx, w, F.FEW_MIXED)
+    assert oracle.mismatch(gm, o) <= MIXED_MISMATCH
+
+
+def test_ragged_rows_with_shifts(gpu_ctx):
+    """Rows whose lowest n differ (shifts between rows in both directions) and gaps in m."""
+    modes = np.asarray([(2, 2, 5), (2, 2, 9), (3, 2, -4), (4, 1, 12), (4, 1, 13), (5, 5, -7),
+                        (5, 0, -2), (6, 0, 3), (7, 3, 0), (9, 9, 1)], dtype=np.int32)
+    w = W.tiny_inputs(5, K=8, n_samples=2500, modes=modes)
+    o = _oracle(w)
+    for S in (16, 512):
+        saved = {p: gpu_ctx.get_tiles(p) for p in (F.FEW_FP64, F.FEW_MIXED)}
+        try:
+            for p, (R, T, _) in saved.items():
+                gpu_ctx.set_tiles(p, R, T, S)
+            g = _gpu(gpu_ctx, w, F.FEW_FP64)
+            assert rel_l2(g, o) <= FP64_REL_L2, (S, rel_l2(g, o))
+            gm = _gpu(gpu_ctx, w, F.FEW_MIXED)
+            assert oracle.mismatch(gm, o) <= MIXED_MISMATCH
+        finally:
+            for p, tile in saved.items():
+                gpu_ctx.set_tiles(p, *tile)
+
+
 def test_offset_start_and_last_knot(gpu_ctx):
     """Samples from the middle of the trajectory up to exactly its last knot."""
     w = W.config1()
@@ -194,23 +231,26 @@ def test_pinned_host_output_matches_device_path(gpu_ctx):
 
 
 def test_tiles_are_bit_identical(gpu_ctx):
-    """Every tile shape gives the same bits: each sample is summed by one thread in a fixed
-    order, and the mixed path's phase anchors sit at fixed sample indices."""
-    w = W.config1()
+    """Every tile shape -- samples per thread, threads, slots per ring stage (including stages
+    smaller than a row, so that rows straddle stages) -- gives the same bits: each sample is
+    summed by one thread in a fixed order, and the mixed path's phase anchors sit at fixed
+    sample indices."""
+    w = W.config1()  # 9 rows of 11 slots
     ref = {}
     saved = {p: gpu_ctx.get_tiles(p) for p in (F.FEW_FP64, F.FEW_MIXED)}
     try:
         for prec, Rs in ((F.FEW_FP64, (1, 2)), (F.FEW_MIXED, (2, 4, 8))):
             for R in Rs:
                 for T in (128, 256):
-                    gpu_ctx.set_tiles(prec, R, T)
-                    g = _gpu(gpu_ctx, w, prec)
-                    if prec not in ref:
-                        ref[prec] = g
-                    np.testing.assert_array_equal(g, ref[prec])
+                    for S in (16, 48, 512):
+                        gpu_ctx.set_tiles(prec, R, T, S)
+                        g = _gpu(gpu_ctx, w, prec)
+                        if prec not in ref:
+                            ref[prec] = g
+                        np.testing.assert_array_equal(g, ref[prec], err_msg=f"{prec} {R} {T} {S}")
     finally:
-        for p, (R, T) in saved.items():
-            gpu_ctx.set_tiles(p, R, T)
+        for p, tile in saved.items():
+            gpu_ctx.set_tiles(p, *tile)
 
 
 def test_errors_and_noop(gpu_ctx):

@@ -28,16 +28,18 @@ def test_tune_installs_and_caches_a_choice(gpu_ctx, tmp_path):
         best, times = tune.tune(gpu_ctx.handle, run, F.FEW_MIXED, slots, w.n_samples, repeats=2,
                                 cache_path=cache)
         assert len(times) == len(tune.CANDIDATES[F.FEW_MIXED])
-        assert gpu_ctx.get_tiles(F.FEW_MIXED) == (best[0], best[1])
+        assert gpu_ctx.get_tiles(F.FEW_MIXED) == tuple(best)
         data = json.load(open(cache))
         key = tune.bucket(F.FEW_MIXED, slots, w.n_samples)
-        assert data[key]["R"] == best[0] and data[key]["threads"] == best[1]
+        assert (data[key]["R"], data[key]["threads"], data[key]["stage_slots"]) == tuple(best)
         run()
         torch.cuda.synchronize()
         np.testing.assert_array_equal(to_host(out), ref)
-        gpu_ctx.set_tiles(F.FEW_MIXED, 2, 128)
+        gpu_ctx.set_tiles(F.FEW_MIXED, 2, 128, 16)
         assert tune.apply_cached(gpu_ctx.handle, F.FEW_MIXED, slots, w.n_samples, cache) == best
-        assert gpu_ctx.get_tiles(F.FEW_MIXED) == (best[0], best[1])
+        assert gpu_ctx.get_tiles(F.FEW_MIXED) == tuple(best)
+        gpu_ctx.set_tiles(F.FEW_MIXED, 2, 128, 16)
+        assert tune.ensure(gpu_ctx.handle, run, F.FEW_MIXED, slots, w.n_samples, cache) == (best, False)
     finally:
         gpu_ctx.set_tiles(F.FEW_MIXED, *saved)
         tr.release()
