@@ -201,7 +201,7 @@ few_status few_waveform(few_ctx *ctx, const few_request *req, void *stream);
  *   caller's, as for few_waveform.
  * Limits: the request's scratch must fit in FEW_NOALLOC_SCRATCH_BYTES and K <= 4096; otherwise
  *   it returns FEW_ERR_LIMIT without queuing work.  The scratch is about 64 x slots x (K - 1)
- *   bytes for FEW_FP64; for FEW_MIXED 32 x slots x (K - 1) bytes plus 2 bytes per output sample
+ *   bytes for FEW_FP64; for FEW_MIXED 32 x slots x (K - 1) bytes plus 3 bytes per output sample
  *   (the phase anchors), plus a few KB.  The one-year 3843-mode waveform (K = 100,
  *   3,155,760 samples) fits in both precisions; the four-year one at dt = 2 s does not.
  * The first call made on a device looks up the array's device address (once per device);
@@ -329,6 +329,15 @@ few_status few_batch_release(few_ctx *ctx, few_batch *batch);
  * bounded wait), or FEW_ERR_CUDA if the device reported an error.  FEW_OK otherwise.
  */
 few_status few_sync_status(few_ctx *ctx);
+
+/*
+ * Self-test of the device error latch (the paper has no counterpart; it exists so that the
+ * timeout path can be exercised without a fault): queues on `stream` one kernel whose single
+ * bounded wait is on a barrier that nothing arrives on and no copy targets.  The wait gives up
+ * after limit_us microseconds (1 <= limit_us <= 2,000,000) and latches FEW_ERR_TIMEOUT, which
+ * the next few_sync_status returns (and clears).  Errors: FEW_ERR_INVALID_ARG, FEW_ERR_CUDA.
+ */
+few_status few_selftest_wait_expiry(few_ctx *ctx, unsigned limit_us, void *stream);
 
 /*
  * Tile configuration of the summation kernel for one precision:

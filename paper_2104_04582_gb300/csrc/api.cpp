@@ -1275,6 +1275,16 @@ few_status few_sync_status(few_ctx *ctx)
     return FEW_OK;
 }
 
+few_status few_selftest_wait_expiry(few_ctx *ctx, unsigned limit_us, void *stream)
+{
+    if (!ctx || limit_us < 1 || limit_us > 2000000u) return FEW_ERR_INVALID_ARG;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    DeviceScope dev_scope(ctx->device);
+    if (!dev_scope.ok) return FEW_ERR_CUDA;
+    FEW_CUDA_TRY(launch_wait_selftest(ctx->d_err, limit_us, static_cast<cudaStream_t>(stream)));
+    return FEW_OK;
+}
+
 few_status few_ctx_set_timing(few_ctx *ctx, int enable)
 {
     if (!ctx) return FEW_ERR_INVALID_ARG;

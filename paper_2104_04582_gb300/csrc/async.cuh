@@ -89,16 +89,21 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Wait for phase `parity` of `bar`, giving up after kWaitLimitNs or kWaitMaxIters polls.
-__device__ inline bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+// Wait for phase `parity` of `bar`, giving up after limit_ns or kWaitMaxIters polls.
+__device__ inline bool mbar_wait_limit(uint64_t *bar, uint32_t parity, unsigned long long limit_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (int it = 0; it < kWaitMaxIters; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > kWaitLimitNs) break;
+        if (global_ns() - t0 > limit_ns) break;
     }
     return false;
+}
+
+__device__ inline bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    return mbar_wait_limit(bar, parity, kWaitLimitNs);
 }
 
 }  // namespace fewsum

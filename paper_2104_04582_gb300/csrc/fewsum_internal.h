@@ -142,6 +142,7 @@ inline int anchors_in_segment(int s_begin, int s_end)
 {
     return s_end > s_begin ? (s_end - 1) / kAnchorGroup - s_begin / kAnchorGroup + 1 : 0;
 }
+cudaError_t launch_wait_selftest(unsigned *err, unsigned limit_us, cudaStream_t st);
 cudaError_t launch_sum(const PlanHdr *hdr_dev, int grid, int threads, int samples_per_thread,
                        int smem_bytes, int variant, cudaStream_t st);
 // Bytes of one folded slot in the layout a variant reads.

@@ -45,7 +45,7 @@ EXPORTED = [
     "few_get_tiles", "few_plan_segments", "few_mode_slots", "few_ctx_set_timing",
     "few_last_timing", "few_phase_samples", "few_waveform_noalloc",
     "few_mode_select", "few_direct_sum", "few_basis_create", "few_basis_release",
-    "few_rb_amplitudes",
+    "few_rb_amplitudes", "few_selftest_wait_expiry",
 ]
 
 
@@ -117,6 +117,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
                                              ctypes.c_int]),
             "few_get_tiles": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _ip, _ip]),
             "few_ctx_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+            "few_selftest_wait_expiry": (ctypes.c_int, [_vp, ctypes.c_uint, _vp]),
             "few_last_timing": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float)]),
             "few_phase_samples": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double,
                                                  ctypes.c_int64, ctypes.c_double, ctypes.c_double,
@@ -268,6 +269,10 @@ def few_batch_release(ctx: int, batch: int) -> None:
 def few_sync_status(ctx: int) -> int:
     """Returns the latched status code (does not raise)."""
     return int(load().few_sync_status(ctx))
+
+
+def few_selftest_wait_expiry(ctx: int, limit_us: int, stream: int = 0) -> None:
+    _check("few_selftest_wait_expiry", load().few_selftest_wait_expiry(ctx, int(limit_us), stream))
 
 
 def few_set_tiles(ctx: int, prec: int, samples_per_thread: int, threads_per_block: int,

@@ -85,16 +85,42 @@ def test_year_mixed_windows_and_full_series(gpu_ctx, year):
     assert oracle.mismatch(gm, g64) <= MIXED_MISMATCH
 
 
-def test_four_year_mixed_window(gpu_ctx):
+def _mismatch_on_device(a, b) -> float:
+    """1 - overlap (unit noise, no maximisation) of two device series, in FP64 on the GPU."""
+    import torch
+    a = a.to(torch.complex128)
+    b = b.to(torch.complex128)
+    ab = torch.sum(torch.conj(a) * b).real
+    aa = torch.sum(torch.abs(a) ** 2)
+    bb = torch.sum(torch.abs(b) ** 2)
+    return float(1.0 - ab / torch.sqrt(aa * bb))
+
+
+def test_four_year_mixed_window_and_full_series(gpu_ctx):
+    """The stress workload (4 yr at dt = 2 s, 63,115,200 samples, K = 300, 3843 modes): the mixed
+    path against the oracle on a 1e5-sample window at the end and on the first 2000 samples, and
+    by mismatch over the full series against the FP64 GPU path (itself checked against the
+    oracle on the same windows)."""
+    import torch
     w = W.config5()
-    g = _gpu(gpu_ctx, w, F.FEW_MIXED)
-    assert g.shape[0] == 63115200
+    tr = RT.from_inputs(gpu_ctx, w)
+    gm = RT.waveform_inputs(gpu_ctx, tr, w, F.FEW_MIXED)
+    g64 = RT.waveform_inputs(gpu_ctx, tr, w, F.FEW_FP64)
+    torch.cuda.synchronize()
+    assert gpu_ctx.sync_status() == F.FEW_OK
+    assert gm.shape[0] == 63115200
+    mm_full = _mismatch_on_device(gm, g64)
+    assert mm_full <= MIXED_MISMATCH, mm_full
     n = 100000
     i0 = w.n_samples - n
     o = _oracle(w, i0, n)
-    assert oracle.mismatch(g[i0:], o) <= MIXED_MISMATCH
+    assert oracle.mismatch(to_host(gm[i0:]), o) <= MIXED_MISMATCH
+    assert rel_l2(to_host(g64[i0:]), o) <= FP64_REL_L2
     o2 = _oracle(w, 0, 2000)
-    assert oracle.mismatch(g[:2000], o2) <= MIXED_MISMATCH
+    assert oracle.mismatch(to_host(gm[:2000]), o2) <= MIXED_MISMATCH
+    assert rel_l2(to_host(g64[:2000]), o2) <= FP64_REL_L2
+    del gm, g64
+    tr.release()
 
 
 TINY = [(1, 6, 1), (2, 7, 7), (3, 5, 255), (4, 9, 256), (5, 4, 257), (6, 12, 1023),

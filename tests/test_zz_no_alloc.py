@@ -45,6 +45,48 @@ def _both(ctx, tr, w, prec):
     return to_host(ref), to_host(got)
 
 
+def _allocation_state(ctx):
+    """(bytes the library context holds, free device bytes) -- both must stay put."""
+    import torch
+    in_use, _ = ctx.memory()
+    return in_use, torch.cuda.mem_get_info()[0]
+
+
+def test_noalloc_allocates_nothing(gpu_ctx):
+    import torch
+    w = W.config1()
+    tr = RT.from_inputs(gpu_ctx, w)
+    out = RT.alloc_out(w.n_samples, True)
+    req = RT.request(tr, out, w.n_samples, w.t0, w.dt, w.theta, w.phi, F.FEW_MIXED, w.scale)
+    F.few_waveform_noalloc(gpu_ctx.handle, req, RT.current_stream())  # first call: set-up
+    torch.cuda.synchronize()
+    before = _allocation_state(gpu_ctx)
+    for _ in range(3):
+        F.few_waveform_noalloc(gpu_ctx.handle, req, RT.current_stream())
+    torch.cuda.synchronize()
+    assert _allocation_state(gpu_ctx) == before
+    assert gpu_ctx.sync_status() == F.FEW_OK
+    tr.release()
+
+
+def test_noalloc_detector_frame(gpu_ctx):
+    """Detector-frame (Sec. 2.A) requests take the same path and agree with few_waveform."""
+    import torch
+    w = W.config1()
+    tr = RT.from_inputs(gpu_ctx, w)
+    outs = []
+    for fn in (F.few_waveform, F.few_waveform_noalloc):
+        out = RT.alloc_out(w.n_samples, False)
+        req = RT.request(tr, out, w.n_samples, w.t0, w.dt, 1.1, 0.4, F.FEW_FP64, w.scale,
+                         frame=F.FEW_FRAME_SSB, theta_K=0.3, phi_K=2.0)
+        fn(gpu_ctx.handle, req, RT.current_stream())
+        outs.append(out)
+    torch.cuda.synchronize()
+    assert gpu_ctx.sync_status() == F.FEW_OK
+    assert rel_l2(to_host(outs[1]), to_host(outs[0])) <= FP64_REL_L2
+    tr.release()
+
+
 def test_noalloc_matches_waveform_on_two_calls_in_a_row(gpu_ctx):
     # call 1: the one-year 3843-mode workload in FP64 (fills most of the fixed array)
     w1 = W.config2()
@@ -65,6 +107,7 @@ def test_noalloc_matches_waveform_on_two_calls_in_a_row(gpu_ctx):
 
 def test_noalloc_refuses_requests_beyond_its_array(gpu_ctx):
     # the four-year workload needs ~24.5 MB of folded FP64 coefficients: more than the array
+    # (and, mixed, ~190 MB of phase anchors)
     w = W.config5()
     tr = RT.from_inputs(gpu_ctx, w)
     out = RT.alloc_out(1000, False)
