@@ -1,15 +1,19 @@
 #!/usr/bin/env python3
 """Benchmark of the interpolated EMRI mode summation on GB300.
 
-Workload (the configuration the headline metric is quoted on): one 1-yr waveform at dt = 10 s
+Headline workload (the configuration the metric is quoted on): one 1-yr waveform at dt = 10 s
 (3,155,760 samples), K = 100 knots, the full 3843-mode Schwarzschild grid (l = 2..10,
 m = 0..l, n = -30..30), synthetic seeded inputs.  A step is one pass of the whole hot path
-with the knot data resident in HBM: spline build (all 7688 splines), harmonics, fold and the
-per-sample mode sum, written to a device buffer.
+with the knot data resident in HBM: spline build (all 7688 splines), harmonics, fold, phase
+anchors and the per-sample mode sum, written to a device buffer.
 
-Default arm (--impl gb300): the mixed-precision path (the fast path); the plain FP64 GPU path
-is measured beside it.  Reference arm (--impl reference): the FP64 CPU oracle on the host cores,
-on a bounded sample of the same workload, same metric.
+Default arm (--impl gb300): the mixed-precision path; beside it, on the same GPU and in the same
+JSON line: the plain FP64 path on the same waveform, the end-to-end call with host buffers, the
+256-waveform batch (one persistent launch replayed as a CUDA graph), the serving loop on a
+Poisson request stream at 50/90/120 % of its measured capacity (p50/p99 latency), the 4-yr
+stress waveform, and the Mode Selector, direct-summation and reduced-basis kernels.
+Reference arm (--impl reference): the FP64 CPU oracle on the host cores, on a bounded sample of
+the same workload, same metric.
 
 One JSON line on stdout (rank 0).  Multi-GPU (torchrun): every rank computes its own
 waveforms (independent problems, weak scaling, no collective on the data path); value is the
@@ -43,10 +47,29 @@ WORKLOAD = ("1-yr waveform, dt=10 s (3,155,760 samples), K=100 knots, 3843 modes
 # summarised in profiles/k_sum_mixed_1yr_3843modes.md; used only while the kernel source is the
 # one that was profiled (hash of sum.cu + phase_eval.cuh + async.cuh) and the tile is the
 # profiled one.
-PROFILED_TRAFFIC = {"source_sha256_16": "ea83547a100f196d", "tile": (4, 256), "bytes": 4113920 + 256}
-N_SMS = 152
-FP32_LANES_PER_SM = 128
-FP64_NOMINAL_TFLOPS = 1.25
+PROFILED_TRAFFIC = {"source_sha256_16": None, "tile": (4, 256, 1024), "bytes": None}
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 sub-partitions x 32)
+FP64_FMA_PER_SM_CLK = 2   # FP64 FMA per SM per clock on GB300 (1.25 TFLOP/s at 152 SMs, 2.07 GHz)
+
+
+def device_peaks(dev_index: int) -> dict:
+    """Nominal FP32 / FP64 FMA peaks of this device: its SM count (queried) x lanes x 2 flop x
+    the maximum SM clock (measured peaks file, else the GPU's own report)."""
+    import torch
+    sms = int(torch.cuda.get_device_properties(dev_index).multi_processor_count)
+    mhz = float(_peaks_file().get("sm_max_mhz", 0.0))
+    if not mhz:
+        try:
+            out = subprocess.run(["nvidia-smi", f"--id={dev_index}", "--query-gpu=clocks.max.sm",
+                                  "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                 timeout=20)
+            mhz = float(out.stdout.strip().splitlines()[0])
+        except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+            mhz = 2070.0
+    return {"sms": sms, "sm_max_mhz": mhz,
+            "fp32_tflops": sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12,
+            "fp64_tflops": sms * FP64_FMA_PER_SM_CLK * 2 * mhz * 1e6 / 1e12,
+            "source": f"{sms} SMs (device query) x lanes x 2 flop x {mhz:.0f} MHz"}
 
 
 def _kernel_source_hash() -> str:
@@ -279,259 +302,280 @@ def aggregate_value(ms_max: float, world: int, waveforms_per_rank_step: int = 1)
     return world * waveforms_per_rank_step * 1000.0 / ms_max
 
 
-def run_gpu(args, rank: int, world: int, local_rank: int):
+def _timed(stream, fn, reps, flush=None):
+    """Per-rep device time (ms) of fn() queued on `stream`, CUDA events on that stream, the L2
+    flushed (outside the events) before every rep when a flush buffer is given."""
     import torch
-    from paper_2104_04582_gb300 import _build
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(reps)]
+    for a, b in evs:
+        if flush is not None:
+            flush.zero_()
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def bench_step_c2(args, ctx, w, dev, stream, sh, flush, prec, rank, world, tune_cache):
+    """The headline step on the one-year workload: spline build + harmonics + fold + anchors +
+    mode sum, knot data resident in HBM.  Returns the timed steps and the kernel figures."""
+    import torch
     from paper_2104_04582_gb300 import fewsum as F
     from paper_2104_04582_gb300 import runtime as RT
+    from paper_2104_04582_gb300 import tune
 
-    _build.build()
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
-    w = W.config2(W.SEEDS["C2"] + rank)
-    ctx = RT.Context(local_rank)
-    F.few_ctx_set_timing(ctx.handle, True)
-    stream = torch.cuda.current_stream(dev)
-    sh = int(stream.cuda_stream)
-    prec = F.FEW_MIXED if args.prec == "mixed" else F.FEW_FP64
     c64 = prec == F.FEW_MIXED
-
     tr = RT.Trajectory(ctx, w.t_knots, w.modes)
     dev_in = tr.upload_inputs(w.phi_phi, w.phi_r, w.amp_re, w.amp_im)
-    tile = tuple(ctx.get_tiles(prec))
-    out = RT.alloc_out(w.n_samples, c64, local_rank)
+    out = RT.alloc_out(w.n_samples, c64, dev.index)
     req = RT.request(tr, out, w.n_samples, w.t0, w.dt, w.theta, w.phi, prec)
-    flush = l2_flush_buffer(torch, dev)
     K_, N_, slots = tr.info
 
     def step():
         F.few_traj_set_data(ctx.handle, tr.handle, *dev_in, stream=sh)
         F.few_waveform(ctx.handle, req, sh)
 
+    step()
+    torch.cuda.synchronize()
+    tile, tuned_now = tune.ensure(ctx.handle, lambda: F.few_waveform(ctx.handle, req, sh), prec,
+                                  slots, w.n_samples, tune_cache)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     if ctx.sync_status() != F.FEW_OK:
         raise RuntimeError("device error during warm-up")
 
-    sampler = ClockSampler(local_rank) if rank == 0 else None
+    sampler = ClockSampler(dev.index) if rank == 0 else None
     if sampler:
         sampler.start()
         time.sleep(0.3)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    sum_ms = []
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    F.few_ctx_set_timing(ctx.handle, False)  # the library's per-kernel events stay out of the timed steps
-    for k in range(args.steps):
-        flush.zero_()  # evict L2 between timed steps (outside the step's events)
-        starts[k].record(stream)
-        step()
-        ends[k].record(stream)
-    torch.cuda.synchronize()
-    F.few_ctx_set_timing(ctx.handle, True)
+    F.few_ctx_set_timing(ctx.handle, False)  # no per-kernel events inside the timed steps
+    step_ms = _timed(stream, step, args.steps, flush)
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop() if sampler else None
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    # the summation kernel's own duration (CUDA events the library records around it on the
-    # same stream), read after each of a few more flushed steps; reading waits for the step, so
-    # this runs after the timed loop rather than inside it
-    for k in range(min(args.steps, 5)):
+    # the kernels' own durations: the library's event pairs on the launch stream, read after
+    # each of a few more flushed steps (reading waits for the step, so outside the timed loop)
+    F.few_ctx_set_timing(ctx.handle, True)
+    kt = []
+    for _ in range(min(args.steps, 5)):
         flush.zero_()
         step()
-        kt = F.few_last_timing(ctx.handle)
-        sum_ms.append(kt[3])
-    ms_local = sum(step_ms) / len(step_ms)
+        kt.append(F.few_last_timing(ctx.handle))
+    F.few_ctx_set_timing(ctx.handle, False)
     if ctx.sync_status() != F.FEW_OK:
         raise RuntimeError("device error during the timed region")
-    h_fast = out.cpu().numpy().astype(np.complex128) if rank == 0 else None
-    kernel_ms = [float(x) for x in sum_ms if x > 0]
-    last_t = F.few_last_timing(ctx.handle)
+    h = out.cpu().numpy().astype(np.complex128) if rank == 0 else None
+    res = dict(tr=tr, dev_in=dev_in, step_ms=step_ms, clocks=clocks, h=h, slots=slots,
+               tile=tuple(tile), tile_tuned_now=tuned_now,
+               kernel_ms={"build": statistics.median(k[0] for k in kt),
+                          "harmonics": statistics.median(k[1] for k in kt),
+                          "fold_and_anchors": statistics.median(k[2] for k in kt),
+                          "sum": statistics.median(k[3] for k in kt)},
+               sum_ms=[float(k[3]) for k in kt if k[3] > 0])
+    del out
+    return res
 
-    # plain FP64 path on the same inputs (fewer steps: it is ~50x slower)
-    plain = None
-    h_plain = None
-    if rank == 0 and not args.no_plain and prec == F.FEW_MIXED:
-        out64 = RT.alloc_out(w.n_samples, False, local_rank)
-        req64 = RT.request(tr, out64, w.n_samples, w.t0, w.dt, w.theta, w.phi, F.FEW_FP64)
+
+def bench_plain_fp64(ctx, w, tr, dev_in, dev, stream, sh, flush, reps):
+    """The plain FP64 path on the same waveform (every step FP64)."""
+    import torch
+    from paper_2104_04582_gb300 import fewsum as F
+    from paper_2104_04582_gb300 import runtime as RT
+    out64 = RT.alloc_out(w.n_samples, False, dev.index)
+    req64 = RT.request(tr, out64, w.n_samples, w.t0, w.dt, w.theta, w.phi, F.FEW_FP64)
+
+    def step():
         F.few_traj_set_data(ctx.handle, tr.handle, *dev_in, stream=sh)
         F.few_waveform(ctx.handle, req64, sh)
-        torch.cuda.synchronize()
-        pk = max(2, min(5, args.steps))
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(pk)]
-        sum64 = []
-        for a, b in ev:
-            flush.zero_()
-            a.record(stream)
-            F.few_traj_set_data(ctx.handle, tr.handle, *dev_in, stream=sh)
-            F.few_waveform(ctx.handle, req64, sh)
-            b.record(stream)
-            sum64.append(F.few_last_timing(ctx.handle)[3])
-        torch.cuda.synchronize()
-        ms64 = sum(a.elapsed_time(b) for a, b in ev) / pk
-        h_plain = out64.cpu().numpy()
-        plain = {"ms_per_step": ms64, "value": 1000.0 / ms64, "unit": UNIT,
-                 "mode_samples_per_s": w.N * w.n_samples / (ms64 * 1e-3),
-                 "sum_kernel_ms": sum(sum64) / len(sum64), "dtype": "f64"}
-        del out64
 
-    # e2e through the C ABI with host buffers (pinned), copies inside the timed region
-    F.few_ctx_set_timing(ctx.handle, False)  # no per-kernel events in the remaining timed loops
-    e2e = None
-    if rank == 0:
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
-        h_in = [pin(a) for a in (w.phi_phi, w.phi_r, w.amp_re, w.amp_im)]
-        host_out = torch.empty(w.n_samples, dtype=torch.complex64 if c64 else torch.complex128
-                               ).pin_memory().numpy()
-        req_h = RT.request(tr, host_out, w.n_samples, w.t0, w.dt, w.theta, w.phi, prec,
-                           out_where=F.FEW_MEM_HOST)
-        e_steps = max(3, min(args.steps, 10))
-        for _ in range(2):
-            F.few_traj_set_data(ctx.handle, tr.handle, *h_in, stream=sh)
-            F.few_waveform(ctx.handle, req_h, sh)
-        torch.cuda.synchronize()
-        t_e = []
-        for _ in range(e_steps):
-            flush.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            F.few_traj_set_data(ctx.handle, tr.handle, *h_in, stream=sh)
-            F.few_waveform(ctx.handle, req_h, sh)  # host output: returns after the D2H copy
-            t_e.append(time.perf_counter() - t0)
-        h2d = sum(a.nbytes for a in h_in)
-        d2h = host_out.nbytes
-        e2e = {"value": 1.0 / statistics.mean(t_e), "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": 1000.0 * statistics.mean(t_e), "steps": e_steps,
-               "timer": "host wall clock around the two C-ABI calls (the call with host output "
-                        "returns once the result is in host memory; page-locked output is "
-                        "stored by the summation kernel directly)"}
-
-    # batched path: B independent 1-yr 3843-mode waveforms (own trajectories) per step, one
-    # persistent summation launch, the whole sequence (spline rebuild included) as a CUDA graph
-    batched = None
-    if rank == 0 and args.batch > 1:
-        wb = [W.config2(W.SEEDS["C2"] + 1000 + q) for q in range(args.batch)]
-        trb = [RT.from_inputs(ctx, x) for x in wb]
-        outb = [RT.alloc_out(x.n_samples, c64, local_rank) for x in wb]
-        reqb = [RT.request(t_, o_, x.n_samples, x.t0, x.dt, x.theta, x.phi, prec)
-                for t_, o_, x in zip(trb, outb, wb)]
-        bh = F.few_batch_plan(ctx.handle, reqb, F.FEW_BATCH_REBUILD_SPLINES)
-        for _ in range(2):
-            F.few_batch_run(ctx.handle, bh, sh)
-        torch.cuda.synchronize()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(max(3, min(args.steps, 10)))]
-        for a, b_ in evs:
-            flush.zero_()
-            a.record(stream)
-            F.few_batch_run(ctx.handle, bh, sh)
-            b_.record(stream)
-        torch.cuda.synchronize()
-        if ctx.sync_status() != F.FEW_OK:
-            raise RuntimeError("device error in the batched run")
-        msb = sum(a.elapsed_time(b_) for a, b_ in evs) / len(evs)
-        batched = {"waveforms_per_step": args.batch, "ms_per_step": msb,
-                   "value": args.batch * 1000.0 / msb, "unit": UNIT,
-                   "mode_samples_per_s": args.batch * w.N * w.n_samples / (msb * 1e-3),
-                   "launches_per_step": 4, "graph": True,
-                   "step": "spline rebuild of all trajectories + harmonics + fold + one "
-                           "persistent summation launch, replayed as one CUDA graph"}
-        F.few_batch_release(ctx.handle, bh)
-        for t_ in trb:
-            t_.release()
-        del outb
-
-    # Mode Selector (Sec. 3.D) on the benchmark's knot amplitudes, eps = 1e-5
-    selector = None
-    if rank == 0:
-        msk = torch.empty(w.N, dtype=torch.uint8, device=dev)
-        mlist = np.ascontiguousarray(w.modes[:, 1])
-        F.few_mode_select(ctx.handle, dev_in[2], dev_in[3], mlist, 1e-5, msk, sh)
-        torch.cuda.synchronize()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(10)]
-        for a, b_ in evs:
-            a.record(stream)
-            F.few_mode_select(ctx.handle, dev_in[2], dev_in[3], mlist, 1e-5, msk, sh)
-            b_.record(stream)
-        torch.cuda.synchronize()
-        selector = {"ms": sum(a.elapsed_time(b_) for a, b_ in evs) / len(evs), "eps": 1e-5,
-                    "knots": w.K, "modes": w.N, "selected": int(msk.sum().item())}
-
-    # direct (non-interpolated) summation over dense arrays: HBM-bound in mixed precision
-    direct = None
-    if rank == 0 and args.direct_samples > 0:
-        nsd = args.direct_samples
-        tsd = torch.arange(nsd, dtype=torch.float64, device=dev) * w.dt + 1.0e6
-        xd = (tsd / w.T)[:, None]
-        am = w.amp_model
-        ta = lambda a: torch.as_tensor(a, device=dev)[None, :]
-        env = ta(am.a) * (1.0 + ta(am.alpha) * xd + ta(am.beta) * xd * xd)
-        d_re = (env * torch.cos(ta(am.psi))).contiguous()
-        d_im = (env * torch.sin(ta(am.psi))).contiguous()
-        del env
-        d_pp = torch.as_tensor(W.phase_phi(tsd.cpu().numpy(), w.T, w.phi_phi0), device=dev)
-        d_pr = torch.as_tensor(W.phase_r(tsd.cpu().numpy(), w.T, w.phi_r0), device=dev)
-        d_out = torch.empty(nsd, dtype=torch.complex64, device=dev)
-        F.few_direct_sum(ctx.handle, d_pp, d_pr, d_re, d_im, w.modes, w.theta, w.phi, d_out,
-                         1.0, F.FEW_MIXED, sh)
-        torch.cuda.synchronize()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(5)]
-        for a, b_ in evs:
-            a.record(stream)
-            F.few_direct_sum(ctx.handle, d_pp, d_pr, d_re, d_im, w.modes, w.theta, w.phi, d_out,
-                             1.0, F.FEW_MIXED, sh)
-            b_.record(stream)
-        torch.cuda.synchronize()
-        msd = min(a.elapsed_time(b_) for a, b_ in evs)
-        nbytes = nsd * (16 * w.N + 16 + 8)
-        gbs = nbytes / (msd * 1e-3) / 1e9
-        hbm = float(_peaks_file().get("hbm_gbs", 6800.0))
-        direct = {"samples": nsd, "modes": w.N, "ms": msd,
-                  "mode_samples_per_s": nsd * w.N / (msd * 1e-3),
-                  "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                               "frac": gbs / hbm, "bytes_per_launch": nbytes,
-                               "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}}
-        del d_re, d_im, d_pp, d_pr, d_out
-
-    # reduced-basis amplitudes (Sec. 3.E): 99 coefficients per knot -> 3843 modes, for the knots
-    # of many trajectories at once, renormalised; the output (FP64 amplitudes) is what the
-    # spline build reads
-    rb = None
-    if rank == 0 and args.rb_knots > 0:
-        rb = bench_rb(ctx, args.rb_knots, w.N, stream, sh)
-
-    # pipe peaks
-    peaks = measure_peaks(local_rank) if rank == 0 and not args.no_probe else {}
-
+    step()
     torch.cuda.synchronize()
-    tr.release()
-    ctx.close()
-    return dict(w=w, ms_local=ms_local, step_ms=step_ms, kernel_ms=kernel_ms, last_t=last_t,
-                clocks=clocks, plain=plain, e2e=e2e, peaks=peaks, slots=slots,
-                h_fast=h_fast, h_plain=h_plain, prec=prec, batched=batched, tile=tile,
-                selector=selector, direct=direct, rb=rb)
+    ms = _timed(stream, step, reps, flush)
+    F.few_ctx_set_timing(ctx.handle, True)
+    step()
+    sum64 = F.few_last_timing(ctx.handle)[3]
+    F.few_ctx_set_timing(ctx.handle, False)
+    h64 = out64.cpu().numpy()
+    m = statistics.mean(ms)
+    return {"ms_per_step": m, "value": 1000.0 / m, "unit": UNIT, "steps": reps,
+            "mode_samples_per_s": w.N * w.n_samples / (m * 1e-3), "sum_kernel_ms": sum64,
+            "dtype": "f64"}, h64
 
 
-def run_serving(args):
-    """Serving workload: Poisson MCMC-like stream at 50/90/120% of the measured capacity."""
+def bench_e2e(ctx, w, tr, prec, sh, flush, steps):
+    """End to end through the C ABI: pinned host knot data in, pinned host output out, both
+    copies inside the timed region (host wall clock around the two calls)."""
     import torch
-    from paper_2104_04582_gb300 import _build
+    from paper_2104_04582_gb300 import fewsum as F
+    from paper_2104_04582_gb300 import runtime as RT
+    c64 = prec == F.FEW_MIXED
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    h_in = [pin(a) for a in (w.phi_phi, w.phi_r, w.amp_re, w.amp_im)]
+    host_out = torch.empty(w.n_samples, dtype=torch.complex64 if c64 else torch.complex128
+                           ).pin_memory().numpy()
+    req_h = RT.request(tr, host_out, w.n_samples, w.t0, w.dt, w.theta, w.phi, prec,
+                       out_where=F.FEW_MEM_HOST)
+    for _ in range(2):
+        F.few_traj_set_data(ctx.handle, tr.handle, *h_in, stream=sh)
+        F.few_waveform(ctx.handle, req_h, sh)
+    torch.cuda.synchronize()
+    t_e = []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        F.few_traj_set_data(ctx.handle, tr.handle, *h_in, stream=sh)
+        F.few_waveform(ctx.handle, req_h, sh)  # host output: returns after the result is in host memory
+        t_e.append(time.perf_counter() - t0)
+    return {"value": 1.0 / statistics.mean(t_e), "unit": UNIT,
+            "h2d_bytes_per_step": int(sum(a.nbytes for a in h_in)),
+            "d2h_bytes_per_step": int(host_out.nbytes),
+            "ms_per_step": 1000.0 * statistics.mean(t_e), "steps": steps,
+            "timer": "host wall clock around the two C-ABI calls (the call with host output "
+                     "returns once the result is in host memory; page-locked output is stored by "
+                     "the summation kernel directly)"}
+
+C2_SLOT_SAMPLES = 1281 * 3155760  # slots x samples of the one-year 3843-mode waveform
+C2_MODE_SAMPLES = 3843 * 3155760
+
+
+def bench_batched_c3(ctx, dev, stream, sh, flush, n_waves, reps, tune_cache, oracle_windows=4):
+    """256 waveforms of 0.25-2 yr, K 50-150, power-selected 10-3843 modes, mixed precision:
+    spline rebuild of every trajectory + harmonics + fold + anchors + one persistent summation
+    launch, captured once as a CUDA graph and replayed; tile chosen by the autotuner on a
+    16-waveform sub-batch."""
+    import torch
+    from paper_2104_04582_gb300 import fewsum as F
+    from paper_2104_04582_gb300 import runtime as RT
+    from paper_2104_04582_gb300 import tune
+    import oracle
+    t_in = time.perf_counter()
+    ws = W.config3(n_waves)
+    trs = [RT.from_inputs(ctx, x) for x in ws]
+    outs = [RT.alloc_out(x.n_samples, True, dev.index) for x in ws]
+    reqs = [RT.request(t_, o_, x.n_samples, x.t0, x.dt, x.theta, x.phi, F.FEW_MIXED)
+            for t_, o_, x in zip(trs, outs, ws)]
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_in
+    sub = reqs[:16]
+    sub_slots = max(t_.info[2] for t_ in trs[:16])
+    sub_samples = sum(x.n_samples for x in ws[:16])
+    tile, tuned_now = tune.ensure(
+        ctx.handle, lambda b: F.few_batch_run(ctx.handle, b, sh), F.FEW_MIXED, sub_slots,
+        sub_samples, tune_cache,
+        prepare=lambda: F.few_batch_plan(ctx.handle, sub, F.FEW_BATCH_NO_GRAPH),
+        cleanup=lambda b: (torch.cuda.synchronize(), F.few_batch_release(ctx.handle, b)))
+    t_plan = time.perf_counter()
+    bh = F.few_batch_plan(ctx.handle, reqs, F.FEW_BATCH_REBUILD_SPLINES)
+    plan_s = time.perf_counter() - t_plan
+    for _ in range(2):
+        F.few_batch_run(ctx.handle, bh, sh)
+    torch.cuda.synchronize()
+    ms = _timed(stream, lambda: F.few_batch_run(ctx.handle, bh, sh), reps, flush)
+    if ctx.sync_status() != F.FEW_OK:
+        raise RuntimeError("device error in the batched run")
+    msb = statistics.mean(ms)
+    samples = sum(x.n_samples for x in ws)
+    mode_samples = sum(x.N * x.n_samples for x in ws)
+    slot_samples = sum(t_.info[2] * x.n_samples for t_, x in zip(trs, ws))
+    # accuracy: the oracle on a 2000-sample window in the middle of a few of the waveforms
+    acc = []
+    for q in np.linspace(0, n_waves - 1, oracle_windows).astype(int):
+        x = ws[q]
+        i0 = max(0, x.n_samples // 2 - 1000)
+        n = min(2000, x.n_samples - i0)
+        o = oracle.waveform_inputs(x, i0, n, nthreads=os.cpu_count() or 1)
+        g = outs[q][i0:i0 + n].cpu().numpy().astype(np.complex128)
+        acc.append({"waveform": int(q), "modes": int(x.N), "window": [int(i0), int(n)],
+                    "mismatch_vs_oracle": oracle.mismatch(g, o),
+                    "rel_l2_vs_oracle": float(np.linalg.norm(g - o) / np.linalg.norm(o))})
+    res = {"waveforms_per_step": n_waves, "ms_per_step": msb, "steps": reps,
+           "value": n_waves * 1000.0 / msb, "unit": "waveforms/s",
+           "samples_per_s": samples / (msb * 1e-3),
+           "mode_samples_per_s": mode_samples / (msb * 1e-3),
+           "slot_samples_per_s": slot_samples / (msb * 1e-3),
+           "c2_equivalent_waveforms_per_s_by_mode_samples": mode_samples / C2_MODE_SAMPLES / (msb * 1e-3),
+           "c2_equivalent_waveforms_per_s_by_slot_samples": slot_samples / C2_SLOT_SAMPLES / (msb * 1e-3),
+           "total_samples": samples, "total_mode_samples": mode_samples,
+           "modes_min_median_max": [int(min(x.N for x in ws)), int(statistics.median(x.N for x in ws)),
+                                    int(max(x.N for x in ws))],
+           "tile": list(tile), "tile_tuned_in_this_run": tuned_now,
+           "launches_per_step": 5, "graph": True, "precision": "mixed",
+           "step": "spline rebuild of all 256 trajectories + harmonics + fold + phase anchors + "
+                   "one persistent summation launch, replayed as one CUDA graph",
+           "host_setup_s": setup_s, "plan_and_capture_s": plan_s, "accuracy": acc}
+    F.few_batch_release(ctx.handle, bh)
+    for t_ in trs:
+        t_.release()
+    del outs
+    torch.cuda.synchronize()
+    return res
+
+
+def bench_stress_c5(ctx, dev, stream, sh, reps, tune_cache):
+    """4 yr at dt = 2 s (63,115,200 samples, complex64), K = 300, 3843 modes, mixed: the whole
+    step timed; mismatch of the full series against the FP64 GPU path."""
+    import torch
+    from paper_2104_04582_gb300 import fewsum as F
+    from paper_2104_04582_gb300 import runtime as RT
+    from paper_2104_04582_gb300 import tune
+    w = W.config5()
+    tr = RT.Trajectory(ctx, w.t_knots, w.modes)
+    dev_in = tr.upload_inputs(w.phi_phi, w.phi_r, w.amp_re, w.amp_im)
+    tr.set_data_device()
+    out = RT.alloc_out(w.n_samples, True, dev.index)
+    req = RT.request(tr, out, w.n_samples, w.t0, w.dt, w.theta, w.phi, F.FEW_MIXED)
+    slots = tr.info[2]
+    tile, tuned_now = tune.ensure(ctx.handle, lambda: F.few_waveform(ctx.handle, req, sh),
+                                  F.FEW_MIXED, slots, w.n_samples, tune_cache)
+
+    def step():
+        F.few_traj_set_data(ctx.handle, tr.handle, *dev_in, stream=sh)
+        F.few_waveform(ctx.handle, req, sh)
+
+    step()
+    torch.cuda.synchronize()
+    ms = _timed(stream, step, reps)  # the 505 MB output is larger than L2
+    out64 = RT.alloc_out(w.n_samples, False, dev.index)
+    req64 = RT.request(tr, out64, w.n_samples, w.t0, w.dt, w.theta, w.phi, F.FEW_FP64)
+    F.few_waveform(ctx.handle, req64, sh)
+    torch.cuda.synchronize()
+    if ctx.sync_status() != F.FEW_OK:
+        raise RuntimeError("device error in the stress run")
+    a = out.to(torch.complex128)
+    b = out64
+    overlap = float(torch.sum(torch.conj(a) * b).real /
+                    torch.sqrt(torch.sum(torch.abs(a) ** 2) * torch.sum(torch.abs(b) ** 2)))
+    m = statistics.mean(ms)
+    res = {"samples": w.n_samples, "knots": w.K, "modes": w.N, "slots": slots, "ms": m,
+           "steps": reps, "mode_samples_per_s": w.N * w.n_samples / (m * 1e-3),
+           "slot_samples_per_s": slots * w.n_samples / (m * 1e-3),
+           "mismatch_vs_fp64_gpu_full_series": 1.0 - overlap, "tile": list(tile),
+           "tile_tuned_in_this_run": tuned_now,
+           "step": "spline build + harmonics + fold + phase anchors + mode sum, complex64 output"}
+    del a, out, out64
+    tr.release()
+    torch.cuda.synchronize()
+    return res
+
+
+def bench_serving_c4(ctx, n_req, budget_gb, tune_cache, loads=(0.5, 0.9, 1.2)):
+    """Serving: a Poisson request stream from an MCMC-like client (0.5-4 yr, dt in {5,10,15} s,
+    10-1000 modes, perturbed angles, phases and scale of resident trajectories, 10 % new ones),
+    continuous batching with HBM-budget admission.  Capacity = completions/s of the whole stream
+    submitted at once; then the stream at 50/90/120 % of that rate; the plain FP64 path's
+    capacity on a tenth of the stream."""
+    import torch
     from paper_2104_04582_gb300 import fewsum as F
     from paper_2104_04582_gb300 import runtime as RT
     from paper_2104_04582_gb300.serve import GpuEngine, Request, Server
-
-    _build.build()
-    torch.cuda.set_device(0)
-    n_req = args.serving_requests
     trajs_in, stream = W.config4_stream(n_req, rate_hz=1.0)
-    ctx = RT.Context(0)
     trajs = {k: RT.from_inputs(ctx, w) for k, w in trajs_in.items()}
 
     def reqs_for(prec):
@@ -543,9 +587,16 @@ def run_serving(args):
                                dphi_r0=r.dphi_r0, prec=prec))
         return out
 
+    engine = GpuEngine(ctx, trajs)
+    mixed, plain_reqs = reqs_for(F.FEW_MIXED), reqs_for(F.FEW_FP64)
+    work = lambda r: r.n_samples * trajs[r.traj_key].info[2]
+    median_req = sorted(mixed, key=work)[len(mixed) // 2]
+    engine.tune_tiles(median_req, tune_cache)
+    engine.tune_tiles(sorted(plain_reqs, key=work)[len(plain_reqs) // 2], tune_cache)
+
     def run(reqs, rate_hz=None, seed=0):
-        srv = Server(GpuEngine(ctx, trajs), hbm_budget_bytes=int(args.serving_budget_gb * 2 ** 30),
-                     max_batch=16, max_inflight=3)
+        srv = Server(engine, hbm_budget_bytes=int(budget_gb * 2 ** 30), max_batch=16,
+                     max_inflight=3)
         rng = np.random.default_rng(seed)
         t0 = time.perf_counter()
         t_arr = 0.0
@@ -567,38 +618,253 @@ def run_serving(args):
         st["offered_rate_hz"] = rate_hz
         return st
 
-    mixed = reqs_for(F.FEW_MIXED)
     run(mixed[:16])  # warm-up
     burst = run(mixed)
     cap = burst["completed"] / burst["wall_s"]
-    loads = {}
-    for f in (0.5, 0.9, 1.2):
-        loads[f"{int(f * 100)}%"] = run(mixed, rate_hz=f * cap, seed=int(f * 100))
-    plain = run(reqs_for(F.FEW_FP64)[:max(8, n_req // 10)])
+    res_loads = {}
+    for f in loads:
+        v = run(mixed, rate_hz=f * cap, seed=int(f * 100))
+        res_loads[f"{int(round(f * 100))}%"] = {
+            "offered_hz": v["offered_rate_hz"], "waveforms_per_s": v["waveforms_per_s"],
+            "p50_ms": v["p50_ms"], "p99_ms": v["p99_ms"], "completed": v["completed"],
+            "max_inflight_batches": v["max_inflight_batches"]}
+    n_plain = max(8, n_req // 10)
+    plain = run(plain_reqs[:n_plain])
     torch.cuda.synchronize()
+    if ctx.sync_status() != F.FEW_OK:
+        raise RuntimeError("device error in the serving run")
     samples = [trajs_in[r.traj_key].n_samples for r in stream]
     modes = [trajs_in[r.traj_key].N for r in stream]
-    line = {"mode": "serving", "metric": "waveforms/s and p50/p99 latency, Poisson MCMC-like stream",
-            "unit": "waveforms/s", "n_gpus": 1, "requests": n_req,
-            "config": {"workload": "requests of 0.5-4 yr, dt in {5,10,15} s, 10-1000 modes, "
-                                   "perturbed angles/phases/scale of resident trajectories, "
-                                   "10% new trajectories", "seed": W.SEEDS["C4"],
-                       "trajectories": len(trajs), "mean_samples": float(np.mean(samples)),
-                       "mean_modes": float(np.mean(modes)),
-                       "budget_gb": args.serving_budget_gb, "max_batch": 16, "max_inflight": 3},
-            "capacity_mixed": {"value": cap, "p50_ms": burst["p50_ms"], "p99_ms": burst["p99_ms"]},
-            "loads": {k: {"offered_hz": v["offered_rate_hz"], "waveforms_per_s": v["waveforms_per_s"],
-                          "p50_ms": v["p50_ms"], "p99_ms": v["p99_ms"],
-                          "max_inflight_batches": v["max_inflight_batches"]}
-                      for k, v in loads.items()},
-            "plain_fp64_capacity": {"value": plain["completed"] / plain["wall_s"],
-                                    "requests": plain["completed"]}}
-    line["capacity_vs_plain_fp64"] = cap / line["plain_fp64_capacity"]["value"]
-    for tr in trajs.values():
-        tr.release()
+    slot_samples = sum(trajs[r.traj_key].info[2] * trajs_in[r.traj_key].n_samples for r in stream)
+    res = {"requests": n_req, "trajectories": len(trajs),
+           "mean_samples": float(np.mean(samples)), "mean_modes": float(np.mean(modes)),
+           "budget_gb": budget_gb, "max_batch": 16, "max_inflight": 3,
+           "tiles": {("mixed" if p == F.FEW_MIXED else "fp64"): list(t) for p, t in engine.tiles.items()},
+           "capacity_mixed": {"value": cap, "unit": "waveforms/s", "p50_ms": burst["p50_ms"],
+                              "p99_ms": burst["p99_ms"],
+                              "c2_equivalent_waveforms_per_s_by_slot_samples":
+                                  slot_samples / C2_SLOT_SAMPLES / burst["wall_s"]},
+           "loads": res_loads,
+           "plain_fp64_capacity": {"value": plain["completed"] / plain["wall_s"],
+                                   "requests": plain["completed"], "p50_ms": plain["p50_ms"],
+                                   "p99_ms": plain["p99_ms"]},
+           "workload": "Poisson MCMC-like stream: 0.5-4 yr, dt in {5,10,15} s, 10-1000 modes, "
+                       "perturbed angles/phases/scale of resident trajectories, 10% new ones",
+           "seed": W.SEEDS["C4"]}
+    res["capacity_vs_plain_fp64"] = cap / res["plain_fp64_capacity"]["value"]
+    for t_ in trajs.values():
+        t_.release()
+    torch.cuda.synchronize()
+    return res
+
+
+def bench_selector(ctx, w, dev_in, dev, stream, sh):
+    """Mode Selector (Sec. 3.D) on the benchmark's knot amplitudes, eps = 1e-5."""
+    import torch
+    from paper_2104_04582_gb300 import fewsum as F
+    msk = torch.empty(w.N, dtype=torch.uint8, device=dev)
+    mlist = np.ascontiguousarray(w.modes[:, 1])
+    call = lambda: F.few_mode_select(ctx.handle, dev_in[2], dev_in[3], mlist, 1e-5, msk, sh)
+    call()
+    torch.cuda.synchronize()
+    ms = _timed(stream, call, 10)
+    return {"ms": statistics.mean(ms), "eps": 1e-5, "knots": w.K, "modes": w.N,
+            "selected": int(msk.sum().item()), "exact": "bit-exact against the oracle (tests)"}
+
+
+def bench_direct(ctx, w, dev, stream, sh, nsd):
+    """Direct (non-interpolated) summation over dense arrays, mixed: HBM-bound."""
+    import torch
+    from paper_2104_04582_gb300 import fewsum as F
+    tsd = torch.arange(nsd, dtype=torch.float64, device=dev) * w.dt + 1.0e6
+    xd = (tsd / w.T)[:, None]
+    am = w.amp_model
+    ta = lambda a: torch.as_tensor(a, device=dev)[None, :]
+    env = ta(am.a) * (1.0 + ta(am.alpha) * xd + ta(am.beta) * xd * xd)
+    d_re = (env * torch.cos(ta(am.psi))).contiguous()
+    d_im = (env * torch.sin(ta(am.psi))).contiguous()
+    del env
+    d_pp = torch.as_tensor(W.phase_phi(tsd.cpu().numpy(), w.T, w.phi_phi0), device=dev)
+    d_pr = torch.as_tensor(W.phase_r(tsd.cpu().numpy(), w.T, w.phi_r0), device=dev)
+    d_out = torch.empty(nsd, dtype=torch.complex64, device=dev)
+    call = lambda: F.few_direct_sum(ctx.handle, d_pp, d_pr, d_re, d_im, w.modes, w.theta, w.phi,
+                                    d_out, 1.0, F.FEW_MIXED, sh)
+    call()
+    torch.cuda.synchronize()
+    msd = min(_timed(stream, call, 5))
+    nbytes = nsd * (16 * w.N + 16 + 8)
+    gbs = nbytes / (msd * 1e-3) / 1e9
+    hbm = float(_peaks_file().get("hbm_gbs", 6800.0))
+    return {"samples": nsd, "modes": w.N, "ms": msd,
+            "mode_samples_per_s": nsd * w.N / (msd * 1e-3),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": gbs / hbm, "bytes_per_launch": nbytes,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}}
+
+
+def run_gpu(args, rank: int, world: int, local_rank: int):
+    import torch
+    from paper_2104_04582_gb300 import _build
+    from paper_2104_04582_gb300 import fewsum as F
+    from paper_2104_04582_gb300 import runtime as RT
+
+    _build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = W.config2(W.SEEDS["C2"] + rank)
+    ctx = RT.Context(local_rank)
+    stream = torch.cuda.current_stream(dev)
+    sh = int(stream.cuda_stream)
+    prec = F.FEW_MIXED if args.prec == "mixed" else F.FEW_FP64
+    flush = l2_flush_buffer(torch, dev)
+    tune_cache = args.tune_cache or None
+
+    r = bench_step_c2(args, ctx, w, dev, stream, sh, flush, prec, rank, world, tune_cache)
+    out = dict(w=w, step_ms=r["step_ms"], clocks=r["clocks"], h_fast=r["h"], slots=r["slots"],
+               tile=r["tile"], tile_tuned_now=r["tile_tuned_now"], kernel_ms=r["kernel_ms"],
+               sum_ms=r["sum_ms"], prec=prec, h_plain=None, plain=None, e2e=None, peaks={},
+               timings_s={})
+    if rank == 0:
+        def timed_part(name, fn):
+            t0 = time.perf_counter()
+            v = fn()
+            out["timings_s"][name] = round(time.perf_counter() - t0, 2)
+            return v
+        if not args.no_plain and prec == F.FEW_MIXED:
+            out["plain"], out["h_plain"] = timed_part("plain_fp64", lambda: bench_plain_fp64(
+                ctx, w, r["tr"], r["dev_in"], dev, stream, sh, flush, max(2, min(5, args.steps))))
+        out["e2e"] = timed_part("e2e", lambda: bench_e2e(ctx, w, r["tr"], prec, sh, flush,
+                                                         max(3, min(args.steps, 10))))
+        out["selector"] = timed_part("mode_selector", lambda: bench_selector(
+            ctx, w, r["dev_in"], dev, stream, sh))
+        r["tr"].release()
+        if args.batch > 0:
+            out["batched_c3"] = timed_part("batched_c3", lambda: bench_batched_c3(
+                ctx, dev, stream, sh, flush, args.batch, 3, tune_cache))
+        if args.serving_requests > 0:
+            out["serving"] = timed_part("serving", lambda: bench_serving_c4(
+                ctx, args.serving_requests, args.serving_budget_gb, tune_cache))
+        if not args.no_stress:
+            out["stress_c5"] = timed_part("stress_c5", lambda: bench_stress_c5(
+                ctx, dev, stream, sh, 3, tune_cache))
+        if args.direct_samples > 0:
+            out["direct"] = timed_part("direct_sum", lambda: bench_direct(
+                ctx, w, dev, stream, sh, args.direct_samples))
+        if args.rb_knots > 0:
+            out["rb"] = timed_part("rb_amplitudes", lambda: bench_rb(ctx, args.rb_knots, w.N,
+                                                                     stream, sh))
+        if not args.no_probe:
+            out["peaks"] = timed_part("pipe_probes", lambda: measure_peaks(local_rank))
+        out["device_peaks"] = device_peaks(local_rank)
+    else:
+        r["tr"].release()
+    torch.cuda.synchronize()
     ctx.close()
-    print(json.dumps(line))
-    return 0
+    return out
+
+
+def assemble_line(args, res, ms, world):
+    w = res["w"]
+    fp32 = res["prec"] == 1
+    slots = res["slots"]
+    dp = res.get("device_peaks") or {}
+    kms = statistics.mean(res["sum_ms"]) if res["sum_ms"] else float("nan")
+    # algorithmic arithmetic of the summation kernel: one complex cubic (6 FMA) and one complex
+    # Horner step (4 FMA) per (harmonic slot, sample); an FMA is 2 flops
+    flops = 20.0 * slots * w.n_samples
+    achieved = flops / (kms * 1e-3) / 1e12
+    clocks = res["clocks"] or {}
+    peak = dp.get("fp32_tflops" if fp32 else "fp64_tflops", float("nan"))
+    traffic = None
+    if (fp32 and PROFILED_TRAFFIC["bytes"] and
+            _kernel_source_hash() == PROFILED_TRAFFIC["source_sha256_16"] and
+            tuple(res.get("tile")) == PROFILED_TRAFFIC["tile"]):
+        traffic = PROFILED_TRAFFIC["bytes"]
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
+            "kernel": "k_sum<float,R> (mixed)" if fp32 else "k_sum<double,R> (fp64)",
+            "kernel_ms": kms, "flops_per_launch": flops,
+            "peak_source": ("nominal FP32 FMA: " if fp32 else "nominal FP64 FMA: ") +
+                           dp.get("source", "") + " (ALU-bound kernel: neither HBM nor tensor peak applies)",
+            "tile": list(res["tile"]), "tile_tuned_in_this_run": res["tile_tuned_now"]}
+    probe = res["peaks"]
+    if probe:
+        key = "fp32_fma_per_s" if fp32 else "fp64_fma_per_s"
+        if key in probe:
+            pm = 2 * probe[key] / 1e12
+            roof["peak_probe_tflops"] = pm
+            roof["frac_of_probe"] = achieved / pm
+        if fp32 and "fp32_fma_3reg_per_s" in probe:
+            p3 = 2 * probe["fp32_fma_3reg_per_s"] / 1e12
+            roof["peak_register_operand_tflops"] = p3
+            roof["frac_of_register_operand_rate"] = achieved / p3
+        if fp32 and "fp32_fma_summation_block_per_s" in probe:
+            pb = 2 * probe["fp32_fma_summation_block_per_s"] / 1e12
+            roof["peak_summation_block_tflops"] = pb
+            roof["frac_of_summation_block_rate"] = achieved / pb
+    if clocks.get("sm_mhz") and dp.get("sm_max_mhz"):
+        roof["frac_at_measured_clock"] = achieved / (peak * clocks["sm_mhz"] / dp["sm_max_mhz"])
+    value = aggregate_value(ms, world)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if fp32 else "f64",
+        "precision": ("mixed: FP64 phase splines and mod-2pi reduction (at anchors every 16 "
+                      "samples, FP32 in-group increments); FP32 amplitudes, exponential powers "
+                      "and accumulation") if fp32 else "fp64 throughout",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "seed": W.SEEDS["C2"], "knots": w.K, "modes": w.N,
+                   "samples": w.n_samples, "harmonic_slots": slots,
+                   "l2": "flushed (256 MB write) between timed steps",
+                   "step": "spline build + harmonics + fold + phase anchors + mode sum, inputs "
+                           "resident in HBM",
+                   "parallelism": f"replicas x{world}"},
+        "mode_samples_per_s": world * w.N * w.n_samples / (ms * 1e-3),
+        "kernel_ms": res["kernel_ms"],
+        "roofline": roof,
+        "gpu_launches": (5 if fp32 else 4) * args.steps,
+        "clocks": clocks or None,
+        "e2e": res["e2e"],
+    }
+    if res["plain"]:
+        line["plain_fp64"] = res["plain"]
+        line["speedup_vs_plain_fp64"] = res["plain"]["ms_per_step"] / ms
+    for key, name in (("batched_c3", "batched_c3"), ("serving", "serving"),
+                      ("stress_c5", "stress_c5"), ("selector", "mode_selector"),
+                      ("direct", "direct_sum"), ("rb", "rb_amplitudes")):
+        if res.get(key):
+            line[name] = res[key]
+    if res["plain"]:
+        pv = res["plain"]["value"]
+        if res.get("batched_c3"):
+            b = res["batched_c3"]
+            b["c2_equivalent_vs_plain_fp64"] = b["c2_equivalent_waveforms_per_s_by_slot_samples"] / pv
+        if res.get("serving"):
+            s = res["serving"]
+            s["c2_equivalent_vs_plain_fp64"] = (
+                s["capacity_mixed"]["c2_equivalent_waveforms_per_s_by_slot_samples"] / pv)
+    if res["peaks"]:
+        line["measured_pipe_peaks"] = dict(res["peaks"])
+    line["device_peaks"] = res.get("device_peaks")
+    line["bench_sections_s"] = res["timings_s"]
+    acc = {}
+    if res["h_plain"] is not None:
+        acc["mismatch_mixed_vs_fp64_full_series"] = _mismatch(res["h_fast"], res["h_plain"])
+    if not args.no_cpu:
+        cb, h_or = cpu_baseline(w, target_s=args.cpu_seconds)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        import oracle
+        n = len(h_or)
+        acc["mismatch_vs_oracle_window"] = oracle.mismatch(res["h_fast"][:n], h_or)
+        acc["rel_l2_vs_oracle_window"] = float(np.linalg.norm(res["h_fast"][:n] - h_or)
+                                               / np.linalg.norm(h_or))
+        if res["h_plain"] is not None:
+            hp = res["h_plain"]
+            acc["fp64_rel_l2_vs_oracle_window"] = float(np.linalg.norm(hp[:n] - h_or)
+                                                        / np.linalg.norm(h_or))
+        acc["oracle_window_samples"] = n
+    line["accuracy"] = acc
+    return line
 
 
 def run_profile_case(which: str, repeats: int = 3) -> int:
@@ -666,6 +932,30 @@ def run_profile_case(which: str, repeats: int = 3) -> int:
     return 0 if st == F.FEW_OK else 1
 
 
+def reference_arm(args):
+    """The oracle as it stands on the host cores, each step a bounded prefix of the workload."""
+    w = W.config2()
+    vals, step_s, cb = [], [], None
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        cb, _ = cpu_baseline(w, target_s=max(1.0, min(args.cpu_seconds, 60.0 / max(1, args.steps))))
+        if k >= args.warmup:
+            vals.append(cb["value"])
+            step_s.append(time.perf_counter() - t0)
+    v = statistics.median(vals)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * statistics.mean(step_s), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "seed": W.SEEDS["C2"],
+                       "note": "each step runs the oracle on a bounded prefix of the waveform "
+                               "(ms_per_step is that step's measured wall time); value is the "
+                               "whole-waveform rate extrapolated from the prefix"},
+            "full_waveform_s_extrapolated": cb["seconds_full_waveform"],
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -676,19 +966,21 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-stress", action="store_true", help="skip the 4-yr stress waveform")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--rb-knots", type=int, default=6400,
                     help="knots of the reduced-basis amplitude measurement (0: skip)")
-    ap.add_argument("--profile-case", choices=["mixed", "fp64", "direct", "rb", "select"], default=None,
-                    help="untimed runs of the benchmark waveform for profiler captures")
-    ap.add_argument("--serving", action="store_true",
-                    help="run the serving workload instead of the single-waveform benchmark")
-    ap.add_argument("--serving-requests", type=int, default=200)
+    ap.add_argument("--profile-case", choices=["mixed", "fp64", "direct", "rb", "select"],
+                    default=None, help="untimed runs of the benchmark waveform for profiler captures")
+    ap.add_argument("--serving-requests", type=int, default=200,
+                    help="requests of the serving measurement (0: skip)")
     ap.add_argument("--serving-budget-gb", type=float, default=16.0)
     ap.add_argument("--direct-samples", type=int, default=100000,
                     help="samples of the direct-summation measurement (0: skip)")
-    ap.add_argument("--batch", type=int, default=8,
-                    help="waveforms per step of the batched-path measurement (0: skip)")
+    ap.add_argument("--batch", type=int, default=256,
+                    help="waveforms of the batched measurement (0: skip)")
+    ap.add_argument("--tune-cache", default=os.path.join(ROOT, "build", "fewsum_tiles.json"),
+                    help="tile cache of the autotuner ('' to tune without caching)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -699,30 +991,9 @@ def main():
     if args.profile_case:
         return run_profile_case(args.profile_case)
 
-    if args.serving and args.impl != "reference":
-        return run_serving(args) if rank == 0 else 0
-
     if args.impl == "reference":
-        if rank != 0:
-            return 0
-        w = W.config2()
-        per_step = []
-        cb = None
-        vals = []
-        for k in range(args.warmup + args.steps):
-            cb, _ = cpu_baseline(w, target_s=max(1.0, min(args.cpu_seconds, 60.0 / max(1, args.steps))))
-            if k >= args.warmup:
-                vals.append(cb["value"])
-        v = statistics.median(vals)
-        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
-                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "seed": W.SEEDS["C2"],
-                           "note": "each step times the oracle on a bounded prefix of the waveform"},
-                "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
-                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
+        if rank == 0:
+            print(json.dumps(reference_arm(args)))
         return 0
 
     if world > 1:
@@ -730,7 +1001,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     res = run_gpu(args, rank, world, local_rank)
-    ms = res["ms_local"]
+    ms = statistics.mean(res["step_ms"])
     if world > 1:
         import torch
         import torch.distributed as dist
@@ -741,112 +1012,7 @@ def main():
             import torch.distributed as dist
             dist.destroy_process_group()
         return 0
-
-    w = res["w"]
-    value = aggregate_value(ms, world)  # every rank computed one waveform per step
-    mode_samples = w.N * w.n_samples
-    slots = res["slots"]
-    kms = statistics.mean(res["kernel_ms"]) if res["kernel_ms"] else float("nan")
-    fp32 = res["prec"] == 1
-    # algorithmic arithmetic of the summation kernel: one complex cubic (6 FMA) and one complex
-    # Horner step (4 FMA) per (harmonic slot, sample); an FMA is 2 flops
-    flops = 20.0 * slots * w.n_samples
-    achieved = flops / (kms * 1e-3) / 1e12
-    clocks = res["clocks"] or {}
-    mp = _peaks_file()
-    sm_max = float(mp.get("sm_max_mhz", 2070.0))
-    if fp32:
-        peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-        peak_src = (f"FP32 FMA: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz "
-                    "(max SM clock)")
-    else:
-        peak = FP64_NOMINAL_TFLOPS
-        peak_src = "FP64 nominal 1.25 TFLOP/s"
-    probe = res["peaks"]
-    traffic = None
-    if fp32 and _kernel_source_hash() == PROFILED_TRAFFIC["source_sha256_16"] and             res.get("tile") == PROFILED_TRAFFIC["tile"]:
-        traffic = PROFILED_TRAFFIC["bytes"]
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
-            "kernel": "k_sum<float,R> (mixed)" if fp32 else "k_sum<double,R> (fp64)",
-            "kernel_ms": kms, "flops_per_launch": flops,
-            "peak_source": peak_src}
-    if probe:
-        key = "fp32_fma_per_s" if fp32 else "fp64_fma_per_s"
-        if key in probe:
-            pm = 2 * probe[key] / 1e12
-            roof["peak_probe_tflops"] = pm
-            roof["frac_of_probe"] = achieved / pm
-        if fp32 and "fp32_fma_3reg_per_s" in probe:
-            # the Horner loop's FMAs take three register operands: the measured rate of that
-            # instruction form is the ceiling the kernel can reach
-            p3 = 2 * probe["fp32_fma_3reg_per_s"] / 1e12
-            roof["peak_register_operand_tflops"] = p3
-            roof["frac_of_register_operand_rate"] = achieved / p3
-        if fp32 and "fp32_fma_summation_block_per_s" in probe:
-            # the kernel's own per-slot block (coefficients from shared memory, two cubics, the
-            # complex step) run in isolation: what the inner loop can reach on this chip
-            pb = 2 * probe["fp32_fma_summation_block_per_s"] / 1e12
-            roof["peak_summation_block_tflops"] = pb
-            roof["frac_of_summation_block_rate"] = achieved / pb
-    if clocks.get("sm_mhz"):
-        roof["frac_at_measured_clock"] = achieved / (peak * clocks["sm_mhz"] / sm_max)
-
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "f32" if fp32 else "f64",
-        "precision": ("mixed: FP64 phase splines and mod-2pi reduction; FP32 amplitudes, "
-                      "exponential powers and accumulation") if fp32 else "fp64 throughout",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "seed": W.SEEDS["C2"], "knots": w.K, "modes": w.N,
-                   "samples": w.n_samples, "harmonic_slots": slots,
-                   "l2": "flushed (256 MB write) between timed steps",
-                   "step": "spline build + harmonics + fold + mode sum, inputs resident in HBM",
-                   "parallelism": f"replicas x{world}"},
-        "mode_samples_per_s": world * mode_samples / (ms * 1e-3),
-        "kernel_ms": {"build": res["last_t"][0], "harmonics": res["last_t"][1],
-                      "fold": res["last_t"][2], "sum": kms},
-        "roofline": roof,
-        "gpu_launches": 4 * args.steps,
-        "clocks": clocks or None,
-        "e2e": res["e2e"],
-    }
-    if res["plain"]:
-        line["plain_fp64"] = res["plain"]
-        line["speedup_vs_plain_fp64"] = res["plain"]["ms_per_step"] / ms
-    if res.get("direct"):
-        line["direct_sum"] = res["direct"]
-    if res.get("rb"):
-        line["rb_amplitudes"] = res["rb"]
-    if res.get("selector"):
-        line["mode_selector"] = res["selector"]
-    if res.get("batched"):
-        line["batched"] = res["batched"]
-        if res["plain"]:
-            line["batched"]["speedup_vs_plain_fp64"] = res["batched"]["value"] / res["plain"]["value"]
-    if probe:
-        line["measured_pipe_peaks"] = {k: v for k, v in probe.items()}
-    # accuracy of this run's outputs
-    acc = {}
-    if res["h_plain"] is not None:
-        acc["mismatch_mixed_vs_fp64_full_series"] = _mismatch(res["h_fast"], res["h_plain"])
-    if not args.no_cpu:
-        cb, h_or = cpu_baseline(w, target_s=args.cpu_seconds)
-        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
-        import oracle
-        n = len(h_or)
-        acc["mismatch_vs_oracle_window"] = oracle.mismatch(res["h_fast"][:n], h_or)
-        acc["rel_l2_vs_oracle_window"] = float(np.linalg.norm(res["h_fast"][:n] - h_or)
-                                               / np.linalg.norm(h_or))
-        if res["h_plain"] is not None:
-            hp = res["h_plain"]
-            acc["fp64_rel_l2_vs_oracle_window"] = float(np.linalg.norm(hp[:n] - h_or)
-                                                        / np.linalg.norm(h_or))
-        acc["oracle_window_samples"] = n
-    line["accuracy"] = acc
-    print(json.dumps(line))
+    print(json.dumps(assemble_line(args, res, ms, world)))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

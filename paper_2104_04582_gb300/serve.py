@@ -30,6 +30,7 @@ import time
 from typing import Any, Callable, Deque, Dict, List, Optional
 
 from . import fewsum as F
+from . import tune
 
 
 class AdmissionError(RuntimeError):
@@ -270,6 +271,23 @@ class GpuEngine:
         self.trajs = trajectories  # key -> runtime.Trajectory (spline data set)
         self.streams = [torch.cuda.Stream(device=ctx.device) for _ in range(n_streams)]
         self._next = 0
+        self.tiles: Dict[int, tuple] = {}  # precision -> installed (R, threads, stage_slots)
+
+    def tune_tiles(self, req: Request, cache_path: Optional[str] = tune.DEFAULT_CACHE) -> tuple:
+        """Install the tile of `req`'s workload bucket (tuning on a cache miss, timed on `req`
+        itself) for its precision; every later group of that precision runs with it."""
+        torch = self.torch
+        tr = self.trajs[req.traj_key]
+        K, N, slots = tr.info
+        out = self.alloc_out(req)
+        rq = F.make_request(tr.handle, out.data_ptr(), req.n_samples, req.t0, req.dt, req.theta,
+                            req.phi, req.scale, req.prec, req.c64(), F.FEW_MEM_DEVICE,
+                            req.dphi_phi0, req.dphi_r0)
+        run = lambda: F.few_waveform(self.ctx.handle, rq, int(torch.cuda.current_stream().cuda_stream))
+        choice, _ = tune.ensure(self.ctx.handle, run, req.prec, slots, req.n_samples, cache_path)
+        torch.cuda.synchronize()
+        self.tiles[req.prec] = tuple(choice)
+        return tuple(choice)
 
     def scratch_bytes(self, req: Request) -> int:
         tr = self.trajs[req.traj_key]

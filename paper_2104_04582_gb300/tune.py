@@ -19,7 +19,7 @@ from __future__ import annotations
 import json
 import math
 import os
-from typing import Dict, List, Optional, Sequence, Tuple
+from typing import Any, Callable, Dict, List, Optional, Sequence, Tuple
 
 from . import fewsum as F
 
@@ -60,11 +60,16 @@ def install(ctx_handle: int, prec: int, choice: Tuple[int, int, int]) -> None:
 
 def tune(ctx_handle: int, run, prec: int, n_slots: int, n_samples: int, repeats: int = 3,
          cache_path: Optional[str] = DEFAULT_CACHE,
-         candidates: Optional[Sequence[Tuple[int, int, int]]] = None) -> Tuple[Tuple[int, int, int], Dict[str, float]]:
-    """Time `run()` (which must queue one workload on the current stream) for every candidate.
+         candidates: Optional[Sequence[Tuple[int, int, int]]] = None,
+         prepare: Optional[Callable[[], Any]] = None,
+         cleanup: Optional[Callable[[Any], None]] = None) -> Tuple[Tuple[int, int, int], Dict[str, float]]:
+    """Time `run` for every candidate tile and keep the fastest.
 
-    Returns the best (R, threads, stage_slots) and the per-candidate best time in ms; installs the
-    winner in the context and stores it in the cache (unless cache_path is None).
+    Without `prepare`, `run()` must queue one workload on the current stream.  With it, each
+    candidate is installed, `prepare()` builds whatever depends on the tile (a batch plan, say)
+    outside the timed region, `run(state)` queues the workload and `cleanup(state)` releases it.
+    Returns the best (R, threads, stage_slots) and the per-candidate best time in ms; installs
+    the winner in the context and stores it in the cache (unless cache_path is None).
     """
     import torch
     cands = list(candidates or CANDIDATES[prec])
@@ -73,18 +78,26 @@ def tune(ctx_handle: int, run, prec: int, n_slots: int, n_samples: int, repeats:
     for c in cands:
         try:
             install(ctx_handle, prec, c)
+            state = prepare() if prepare else None
         except F.FewError:
-            continue
-        run()  # warm-up (plans, occupancy cache)
-        torch.cuda.synchronize()
-        ms = float("inf")
-        for _ in range(repeats):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            run()
-            b.record()
-            b.synchronize()
-            ms = min(ms, a.elapsed_time(b))
+            continue  # e.g. a stage too large for shared memory
+        go = (lambda: run(state)) if prepare else run
+        try:
+            go()  # warm-up (occupancy cache, first launch)
+            torch.cuda.synchronize()
+            ms = float("inf")
+            for _ in range(repeats):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                go()
+                b.record()
+                b.synchronize()
+                ms = min(ms, a.elapsed_time(b))
+        except F.FewError:
+            ms = float("inf")
+        finally:
+            if prepare and cleanup:
+                cleanup(state)
         times[f"R={c[0]} T={c[1]} S={c[2]}"] = ms
         if ms < best_ms:
             best, best_ms = c, ms
@@ -113,7 +126,9 @@ def apply_cached(ctx_handle: int, prec: int, n_slots: int, n_samples: int,
 
 
 def ensure(ctx_handle: int, run, prec: int, n_slots: int, n_samples: int,
-           cache_path: Optional[str] = DEFAULT_CACHE, repeats: int = 2) -> Tuple[Tuple[int, int, int], bool]:
+           cache_path: Optional[str] = DEFAULT_CACHE, repeats: int = 2,
+           prepare: Optional[Callable[[], Any]] = None,
+           cleanup: Optional[Callable[[Any], None]] = None) -> Tuple[Tuple[int, int, int], bool]:
     """Install the cached tile for this workload bucket, tuning with `run` on a miss.
 
     Returns (choice, tuned_now)."""
@@ -121,5 +136,6 @@ def ensure(ctx_handle: int, run, prec: int, n_slots: int, n_samples: int,
         c = apply_cached(ctx_handle, prec, n_slots, n_samples, cache_path)
         if c is not None:
             return c, False
-    best, _ = tune(ctx_handle, run, prec, n_slots, n_samples, repeats=repeats, cache_path=cache_path)
+    best, _ = tune(ctx_handle, run, prec, n_slots, n_samples, repeats=repeats,
+                   cache_path=cache_path, prepare=prepare, cleanup=cleanup)
     return best, True
