@@ -23,7 +23,8 @@ PROBE_LIB = os.path.join(LIBDIR, "libfewprobe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
           f"-I{os.path.join(ROOT, 'include')}", f"-I{CSRC}"]
-SOURCES = ["api.cpp", "spline.cu", "fold.cu", "sum.cu", "noalloc.cu", "select.cu", "direct.cu", "rb.cu"]
+SOURCES = ["api.cpp", "spline.cu", "fold.cu", "sum.cu", "anchor.cu", "selftest.cu", "noalloc.cu",
+           "select.cu", "direct.cu", "rb.cu"]
 HEADERS = ["fewsum_internal.h", "phase_eval.cuh", "harmonics.cuh", "convert.cuh", "async.cuh"]
 
 

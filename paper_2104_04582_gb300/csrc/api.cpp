@@ -308,9 +308,9 @@ struct few_batch {
     void *blob_dev = nullptr;
     void *scratch_dev = nullptr;
     void *jobs_dev = nullptr;
-    int n_jobs = 0, build_blocks = 0, max_knots = 0;
+    int n_jobs = 0, build_blocks = 0, build_coef_blocks = 0, max_knots = 0;
     int grid = 0, threads = 0, R = 0, smem = 0, total_pairs = 0, total_fold = 0;
-    int total_anchors = 0;
+    int total_anchor_segs = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -327,7 +327,7 @@ struct PlanImage {
     bool fp64 = false;
     int variant = kVariantFp64;
     int grid = 0, threads = 0, R = 0, smem = 0, buf_bytes = 0, total_pairs = 0, total_fold = 0;
-    int total_anchors = 0, stage_slots = 0, ring = 0;
+    int total_anchor_segs = 0, stage_slots = 0, ring = 0;
 };
 
 int occupancy(few_ctx *c, int variant, int R, int T, int smem)
@@ -446,7 +446,7 @@ void fill_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P, unsign
     int *seg = reinterpret_cast<int *>(P.blob.data() + P.off_seg);
     int *anc = reinterpret_cast<int *>(P.blob.data() + P.off_anc);
     size_t seg_pos = 0;
-    int pair_begin = 0, fold_begin = 0, anchor_begin = 0;
+    int pair_begin = 0, fold_begin = 0, anchor_seg_begin = 0;
     std::vector<long double> cum(n + 1, 0.0L);
     for (int q = 0; q < n; ++q) {
         const few_request &r = reqs[q];
@@ -481,8 +481,8 @@ void fill_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P, unsign
             anc[seg_pos + tr->K - 1] = a;
             W.anchors = reinterpret_cast<Anchor *>(scratch_dev + P.anchor_off[q]);
             W.anchor_off = reinterpret_cast<const int *>(blob_dev + P.off_anc) + seg_pos;
-            W.anchor_begin = anchor_begin;
-            anchor_begin += a;
+            W.anchor_seg_begin = anchor_seg_begin;
+            anchor_seg_begin += tr->S;
         }
         seg_pos += tr->K;
         W.pair_begin = pair_begin;
@@ -495,7 +495,7 @@ void fill_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P, unsign
     }
     P.total_pairs = pair_begin;
     P.total_fold = fold_begin;
-    P.total_anchors = anchor_begin;
+    P.total_anchor_segs = anchor_seg_begin;
     // equal-cost CTA slices of the concatenated (wave, sample) space
     const long double total = cum[n];
     int q = 0;
@@ -515,7 +515,7 @@ void fill_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P, unsign
     hdr->n_waves = n;
     hdr->total_pairs = P.total_pairs;
     hdr->total_fold_blocks = P.total_fold;
-    hdr->total_anchors = P.total_anchors;
+    hdr->total_anchor_segs = P.total_anchor_segs;
     hdr->grid_sum = P.grid;
     hdr->buf_bytes = P.buf_bytes;
     hdr->stage_slots = P.stage_slots;
@@ -527,7 +527,7 @@ void fill_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P, unsign
 }
 
 few_status launch_kernels(few_ctx *c, const PlanHdr *hdr_dev, int total_pairs, int total_fold,
-                          int total_anchors, int grid, int threads, int R, int smem, int variant,
+                          int total_anchor_segs, int grid, int threads, int R, int smem, int variant,
                           cudaStream_t st)
 {
     tmark(c, 1, false, st);
@@ -535,7 +535,7 @@ few_status launch_kernels(few_ctx *c, const PlanHdr *hdr_dev, int total_pairs, i
     tmark(c, 1, true, st);
     tmark(c, 2, false, st);
     FEW_CUDA_TRY(launch_fold(hdr_dev, total_fold, variant == kVariantFp64, st));
-    FEW_CUDA_TRY(launch_anchor(hdr_dev, total_anchors, st));
+    FEW_CUDA_TRY(launch_anchor(hdr_dev, total_anchor_segs, st));
     tmark(c, 2, true, st);
     tmark(c, 3, false, st);
     FEW_CUDA_TRY(launch_sum(hdr_dev, grid, threads, R, smem, variant, st));
@@ -681,6 +681,7 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
                  o_ih = take(sizeof(double) * K), o_w = take(sizeof(double) * K),
                  o_ip = take(sizeof(double) * K), o_v = take(sizeof(double) * K),
                  o_coef = take(sizeof(double) * 4 * (size_t)tr->S * tr->J),
+                 o_slopes = take(sizeof(double) * (size_t)K * tr->J),
                  o_pair = take(sizeof(int2) * P.pair_lm.size()), o_mp = take(sizeof(int) * N),
                  o_sp = take(sizeof(int) * P.slot_ptr.size()),
                  o_ct = take(sizeof(int2) * std::max<size_t>(1, P.contrib.size())),
@@ -720,6 +721,7 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
     D.fac_ip = reinterpret_cast<const double *>(d + o_ip);
     D.fac_v = reinterpret_cast<const double *>(d + o_v);
     D.coef = reinterpret_cast<double *>(d + o_coef);
+    D.slopes = reinterpret_cast<double *>(d + o_slopes);
     D.pair_lm = reinterpret_cast<const int2 *>(d + o_pair);
     D.mode_pair = reinterpret_cast<const int *>(d + o_mp);
     D.slot_ptr = reinterpret_cast<const int *>(d + o_sp);
@@ -794,11 +796,13 @@ few_status few_traj_set_data(few_ctx *ctx, few_traj *tr, const double *phi_phi, 
         job.amp_im = amp_im;
     }
     job.block_begin = 0;
+    job.coef_block_begin = 0;
     few_status s = upload(ctx, tr->job_dev, &job, sizeof(job), st);
     const int blocks = (tr->J + kBuildSplines - 1) / kBuildSplines;
     if (!s) {
         tmark(ctx, 0, false, st);
-        if (launch_build(tr->job_dev, 1, blocks, tr->K, ctx->d_err, st) != cudaSuccess) {
+        if (launch_build(tr->job_dev, 1, blocks, coef_blocks(tr->S, tr->J), tr->K, ctx->d_err,
+                         st) != cudaSuccess) {
             (void)cudaGetLastError();
             s = FEW_ERR_CUDA;
         }
@@ -888,7 +892,7 @@ few_status few_waveform(few_ctx *ctx, const few_request *req, void *stream)
     st = upload(ctx, blob, P.blob.data(), P.blob.size(), s);
     if (!st)
         st = launch_kernels(ctx, static_cast<const PlanHdr *>(blob), P.total_pairs, P.total_fold,
-                            P.total_anchors, P.grid, P.threads, P.R, P.smem, P.variant, s);
+                            P.total_anchor_segs, P.grid, P.threads, P.R, P.smem, P.variant, s);
     if (!st && dout) {
         cudaError_t e = cudaMemcpyAsync(req->out, dout, out_bytes, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) {
@@ -1161,7 +1165,7 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
     if (flags & FEW_BATCH_REBUILD_SPLINES) {
         std::vector<BuildJob> jobs;
         std::set<const few_traj *> seen;
-        int blocks = 0;
+        int blocks = 0, cblocks = 0;
         for (int q = 0; q < n; ++q) {
             const few_traj *tr = reqs[q].traj;
             if (!seen.insert(tr).second) continue;
@@ -1173,6 +1177,8 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
             j.amp_im = tr->src_im;
             j.block_begin = blocks;
             blocks += (tr->J + kBuildSplines - 1) / kBuildSplines;
+            j.coef_block_begin = cblocks;
+            cblocks += coef_blocks(tr->S, tr->J);
             b->max_knots = std::max(b->max_knots, tr->K);
             jobs.push_back(j);
         }
@@ -1181,6 +1187,7 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
             return fail(st);
         b->n_jobs = (int)jobs.size();
         b->build_blocks = blocks;
+        b->build_coef_blocks = cblocks;
     }
     b->grid = P.grid;
     b->threads = P.threads;
@@ -1188,7 +1195,7 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
     b->smem = P.smem;
     b->total_pairs = P.total_pairs;
     b->total_fold = P.total_fold;
-    b->total_anchors = P.total_anchors;
+    b->total_anchor_segs = P.total_anchor_segs;
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(FEW_ERR_CUDA);
     if (!(flags & FEW_BATCH_NO_GRAPH)) {
         cudaStream_t cap = nullptr;
@@ -1198,10 +1205,10 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
             const PlanHdr *hd = static_cast<const PlanHdr *>(b->blob_dev);
             if (b->n_jobs)
                 launch_build(static_cast<const BuildJob *>(b->jobs_dev), b->n_jobs, b->build_blocks,
-                             b->max_knots, ctx->d_err, cap);
+                             b->build_coef_blocks, b->max_knots, ctx->d_err, cap);
             launch_ylm(hd, b->total_pairs, b->fp64, cap);
             launch_fold(hd, b->total_fold, b->fp64, cap);
-            launch_anchor(hd, b->total_anchors, cap);
+            launch_anchor(hd, b->total_anchor_segs, cap);
             launch_sum(hd, b->grid, b->threads, b->R, b->smem, b->variant, cap);
             e = cudaStreamEndCapture(cap, &b->graph);
         }
@@ -1229,10 +1236,11 @@ few_status few_batch_run(few_ctx *ctx, few_batch *b, void *stream)
     if (b->n_jobs) {
         tmark(ctx, 0, false, s);
         FEW_CUDA_TRY(launch_build(static_cast<const BuildJob *>(b->jobs_dev), b->n_jobs,
-                                  b->build_blocks, b->max_knots, ctx->d_err, s));
+                                  b->build_blocks, b->build_coef_blocks, b->max_knots, ctx->d_err,
+                                  s));
         tmark(ctx, 0, true, s);
     }
-    return launch_kernels(ctx, hd, b->total_pairs, b->total_fold, b->total_anchors, b->grid,
+    return launch_kernels(ctx, hd, b->total_pairs, b->total_fold, b->total_anchor_segs, b->grid,
                           b->threads, b->R, b->smem, b->variant, s);
 }
 

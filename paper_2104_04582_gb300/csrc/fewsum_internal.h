@@ -38,6 +38,7 @@ enum : int {
 // with the exact Taylor coefficients of the phase cubic about that sample in sample units; the
 // summation kernel adds the increment to the following samples of the group in FP32.
 constexpr int kAnchorGroup = 16;
+constexpr int kAnchorThreads = 128, kAnchorBlocksPerSeg = 4;  // anchor kernel grid per segment
 struct Anchor {
     float4 phi;  // (f0, d1, d2, d3): reduced phase (turns) and increment coefficients (turns / sample^k)
     float4 r;
@@ -47,6 +48,7 @@ constexpr int kFoldThreads = 128;
 constexpr int kYlmThreads = 16;  // few pairs per block: spreads the FP64 work over SMs
 constexpr int kBuildThreads = 64;
 constexpr int kBuildSplines = kBuildThreads / 2;  // two threads (top and bottom sweep) per spline
+constexpr int kCoefThreads = 256;  // (segment, spline) pairs per coefficient block
 
 // Trajectory-resident data (one per few_traj).
 struct TrajDev {
@@ -61,6 +63,7 @@ struct TrajDev {
     const double *fac_w;   // [K] top-down multipliers w_k (rows 2..m) of the shared twisted factorization
     const double *fac_ip;  // [K] inverse pivots: top rows < m, bottom rows > m, twist pivot at m
     const double *fac_v;  // [K] bottom-up multipliers v_k (rows m..K-3)
+    double *slopes;        // [K][J] knot slopes of every spline (spline build scratch)
     double *coef;          // [S][J][4] spline coefficients in u = (t - t_k)/h_k;
                            //   columns 0,1 = Phi_phi, Phi_r (rad),
                            //   column 2+2i / 3+2i = Re / Im A_i
@@ -80,8 +83,8 @@ struct BuildJob {
     const double *phi_r;    // [K] rad
     const double *amp_re;   // [K][N]
     const double *amp_im;   // [K][N]
-    int block_begin;        // first block of this job in the flattened grid
-    int pad;
+    int block_begin;        // first block of this job in the flattened slope-sweep grid
+    int coef_block_begin;   // first block of this job in the flattened coefficient grid
 };
 
 // One waveform of a plan (a request).
@@ -96,7 +99,7 @@ struct WaveDev {
     void *fcoef;          // [S][n_slots][8] folded coefficients (float or double)
     Anchor *anchors;      // mixed plans: [n_anchors] phase anchors (segment by segment)
     const int *anchor_off;  // mixed plans: [K] first anchor of each segment, then the total
-    int anchor_begin;     // first global anchor index of this wave (anchor kernel)
+    int anchor_seg_begin; // first global segment index of this wave (anchor kernel grid)
     double2 *ylm;         // [n_pairs][2]: Y+ = -2Y_{l,m}, Y- = (-1)^l -2Y_{l,-m} (0 if m = 0)
     const int *seg_start; // [K] sample range of each segment
     int pair_begin;       // first global pair index of this wave (ylm kernel)
@@ -118,7 +121,7 @@ struct PlanHdr {
     int total_pairs;
     int total_fold_blocks;
     int grid_sum;
-    int total_anchors;  // anchors over all waves (mixed plans; 0 for FP64 plans)
+    int total_anchor_segs;  // segments over all waves of a mixed plan (0 for FP64 plans)
     int buf_bytes;   // bytes of one ring stage (stage_slots x slot bytes, rounded up)
     int stage_slots; // slots per ring stage (the mode tile)
     int ring;        // ring stages
@@ -131,11 +134,12 @@ struct PlanHdr {
 // Kernel launchers (defined in the .cu files; every launcher returns the launch error).
 cudaError_t launch_factor(const double *t, int K, double *h, double *inv_h, double *fac_w,
                           double *fac_ip, double *fac_v, cudaStream_t st);
-cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks, int max_knots,
-                         unsigned *err, cudaStream_t st);
+cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks,
+                         int total_coef_blocks, int max_knots, unsigned *err, cudaStream_t st);
+inline int coef_blocks(int S, int J) { return (int)(((long long)S * J + kCoefThreads - 1) / kCoefThreads); }
 cudaError_t launch_ylm(const PlanHdr *hdr_dev, int total_pairs, bool fp64, cudaStream_t st);
 cudaError_t launch_fold(const PlanHdr *hdr_dev, int total_fold_blocks, bool fp64, cudaStream_t st);
-cudaError_t launch_anchor(const PlanHdr *hdr_dev, int total_anchors, cudaStream_t st);
+cudaError_t launch_anchor(const PlanHdr *hdr_dev, int total_anchor_segs, cudaStream_t st);
 // Anchors of one segment's samples [s_begin, s_end): groups floor(s_begin / G) ..
 // floor((s_end - 1) / G); none for an empty segment.
 inline int anchors_in_segment(int s_begin, int s_end)

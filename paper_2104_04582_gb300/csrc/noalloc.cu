@@ -172,7 +172,7 @@ extern "C" few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req,
     if (!fp64) {
         W->anchors = reinterpret_cast<Anchor *>(d_anc);
         W->anchor_off = reinterpret_cast<const int *>(base + off_anc);
-        W->anchor_begin = 0;
+        W->anchor_seg_begin = 0;
     }
 
     // equal slices of the samples (one waveform: equal cost per sample)
@@ -185,7 +185,7 @@ extern "C" few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req,
     hdr->n_waves = 1;
     hdr->total_pairs = v.n_pairs;
     hdr->total_fold_blocks = S * W->fold_blocks_per_seg;
-    hdr->total_anchors = n_anchors;
+    hdr->total_anchor_segs = fp64 ? 0 : S;
     hdr->grid_sum = grid;
     hdr->buf_bytes = buf_bytes;
     hdr->stage_slots = stage_slots;
@@ -206,7 +206,7 @@ extern "C" few_status few_waveform_noalloc(few_ctx *ctx, const few_request *req,
     const PlanHdr *hd = reinterpret_cast<const PlanHdr *>(base);
     if (launch_ylm(hd, v.n_pairs, fp64, s) != cudaSuccess ||
         launch_fold(hd, hdr->total_fold_blocks, fp64, s) != cudaSuccess ||
-        launch_anchor(hd, n_anchors, s) != cudaSuccess ||
+        launch_anchor(hd, fp64 ? 0 : S, s) != cudaSuccess ||
         launch_sum(hd, grid, T, R, smem, variant, s) != cudaSuccess) {
         (void)cudaGetLastError();
         return FEW_ERR_CUDA;

@@ -16,12 +16,13 @@
 // (R_0, R_L the end rows' right-hand sides), interior rows as above.  Its matrix depends only on
 // the knots, so it is factorised once per trajectory (k_factor) in twisted form: top-down
 // elimination of rows 1..m and bottom-up elimination of rows K-2..m, m = (K-1)/2, both stable
-// by diagonal dominance.  Every spline reuses that factorisation with two threads: the top one
-// sweeps rows 1..m, the bottom one rows K-2..m, they combine at row m
+// by diagonal dominance.  Every spline reuses that factorisation with two threads (k_build): the
+// top one sweeps rows 1..m, the bottom one rows K-2..m, they combine at row m
 //     s_m = (y_m + z_m - rhs_m) / (p_m + q_m - d_m),
-// and substitute away from m in opposite directions, each writing the segments on its side;
-// s_0 and s_{K-1} follow from the end rows.  Coefficients are stored in the normalised local
-// variable u = (t - t_k)/h_k in [0, 1]:
+// and substitute away from m in opposite directions, each writing the slopes on its side;
+// s_0 and s_{K-1} follow from the end rows.  The sweeps are serial chains of FP64 operations,
+// so they carry nothing else; a second kernel (k_coef), one thread per (segment, spline), then
+// forms the coefficients in the normalised local variable u = (t - t_k)/h_k in [0, 1]:
 //     p(u) = y_k + h_k s_k u + (3 D - h_k (2 s_k + s_{k+1})) u^2 + (h_k (s_k + s_{k+1}) - 2 D) u^3,
 // D = y_{k+1} - y_k.  The two phase arrays are fitted in radians as given (their reduction
 // modulo 2 pi happens per segment and per sample in the summation kernel).
@@ -95,7 +96,9 @@ __device__ __forceinline__ unsigned nonfinite_bit(double x)
 // bottom sweep of the same column, in one instruction stream (direction and coefficients are
 // per-lane data), so the pair meets at row m without divergence and exchanges its reduced
 // right-hand side with one shuffle.  The knot-only arrays are staged in shared memory and the
-// column values are fetched kChunk rows ahead into registers, so kChunk loads are in flight.
+// column values (and, in the substitution, the parked values) are fetched kChunk rows ahead
+// into registers, so kChunk loads are in flight: the grid has only a few warps per SM, so
+// memory latency is hidden by depth, not by occupancy.
 constexpr int kChunk = 8;
 
 __global__ void __launch_bounds__(kBuildThreads)
@@ -130,7 +133,7 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
     const int j = (b - jb.block_begin) * kBuildSplines + (threadIdx.x >> 5) * 16 + (lane & 15);
     const bool live = j < J;
     const int jj = live ? j : 0;  // a column past J computes on column 0 and stores nothing
-    double *__restrict__ coef = tr.coef;
+    double *__restrict__ slopes = tr.slopes;
     unsigned bad = 0u;  // bit 31: some column value was not finite
     const int m = (K - 1) / 2;
     const int dir = top ? 1 : -1, k0 = top ? 1 : K - 2;
@@ -171,26 +174,26 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
             }
             if (k == m) rm = r;
             acc = r - (i == 0 ? 0.0 : (top ? fw[k] : fv[k])) * acc;
-            if (k != m && live) coef[((size_t)k * J + j) * 4 + 1] = acc;  // parked for the substitution
+            if (k != m && live) slopes[(size_t)k * J + j] = acc;  // parked for the substitution
             yb = yc;
             yc = ya[q];
         }
     }
-    // row m: both threads hold rhs_m and their own reduced value; yb = y_m for both
+    // row m: both threads hold rhs_m and their own reduced value
     const double other = __shfl_xor_sync(0xffffffffu, acc, 16);
     double s_prev = (acc + other - rm) * fip[m];
-    double y_prev = yb;
+    if (top && live) slopes[(size_t)m * J + j] = s_prev;
 
-    // substitution away from m: rows m - 1, ..., 0 (top) or m + 1, ..., K - 1 (bottom)
+    // substitution away from m: rows m - 1, ..., 0 (top) or m + 1, ..., K - 1 (bottom); each
+    // slope replaces the value parked in its place
     const int ds = -dir;
     for (int i0 = 0; i0 < steps_max; i0 += kChunk) {
-        double pv[kChunk], yv[kChunk];
+        double pv[kChunk];
 #pragma unroll
         for (int q = 0; q < kChunk; ++q) {
             const int i = i0 + q, k = m + ds * (1 + i);
             const bool act = i < steps;
-            pv[q] = (act && k >= 1 && k <= K - 2) ? coef[((size_t)k * J + jj) * 4 + 1] : 0.0;
-            yv[q] = act ? load_y(jb, jj, k) : 0.0;
+            pv[q] = (act && k >= 1 && k <= K - 2) ? slopes[(size_t)k * J + jj] : 0.0;
         }
 #pragma unroll
         for (int q = 0; q < kChunk; ++q) {
@@ -206,26 +209,44 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
                 par = pv[q]; c = top ? h[k - 1] : h[k]; ipv = fip[k];
             }
             const double s = (par - c * s_prev) * ipv;
-            const int seg = top ? k : k - 1;  // the segment between rows k and k - ds
-            const double yl = top ? yv[q] : y_prev, yr = top ? y_prev : yv[q];
-            const double sl = top ? s : s_prev, sr = top ? s_prev : s;
-            // power basis in u = (t - t_seg) / h: y_l, h s_l, 3 D - 2 h s_l - h s_r, h s_l + h s_r - 2 D
-            const double D = yr - yl, hk = h[seg];
-            const double a = hk * sl, b = hk * sr;
-            if (live) {
-                double2 *cc = reinterpret_cast<double2 *>(coef + ((size_t)seg * J + j) * 4);
-                cc[0] = make_double2(yl, a);
-                cc[1] = make_double2(fma(-2.0, a, fma(3.0, D, -b)), fma(-2.0, D, a + b));
-            }
+            if (live) slopes[(size_t)k * J + j] = s;
             s_prev = s;
-            y_prev = yv[q];
         }
     }
     if ((bad & 0x80000000u) && live) atomicOr(err, ERRBIT_NONFINITE);
 }
 
-cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks, int max_knots,
-                         unsigned *err, cudaStream_t st)
+// Cubic coefficients of every (segment, spline) once the knot slopes are known, one thread each
+// (consecutive threads: consecutive splines of one segment, so the 32-byte rows are written
+// contiguously): in the local variable u = (t - t_k)/h_k,
+//     p(u) = y_k + h s_k u + (3 D - 2 h s_k - h s_{k+1}) u^2 + (h s_k + h s_{k+1} - 2 D) u^3,
+// D = y_{k+1} - y_k, h = h_k.
+__global__ void __launch_bounds__(kCoefThreads)
+k_coef(const BuildJob *__restrict__ jobs, int n_jobs)
+{
+    int lo = 0, hi = n_jobs - 1;
+    const int b = blockIdx.x;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].coef_block_begin <= b) lo = mid; else hi = mid - 1;
+    }
+    const BuildJob &jb = jobs[lo];
+    const TrajDev &tr = jb.tr;
+    const int J = tr.J;
+    const long long g = (long long)(b - jb.coef_block_begin) * kCoefThreads + threadIdx.x;
+    if (g >= (long long)tr.S * J) return;
+    const int seg = (int)(g / J), j = (int)(g - (long long)seg * J);
+    const double yl = load_y(jb, j, seg), yr = load_y(jb, j, seg + 1);
+    const double sl = tr.slopes[(size_t)seg * J + j], sr = tr.slopes[(size_t)(seg + 1) * J + j];
+    const double hk = tr.h[seg];
+    const double D = yr - yl, a = hk * sl, c = hk * sr;
+    double2 *cc = reinterpret_cast<double2 *>(tr.coef + ((size_t)seg * J + j) * 4);
+    cc[0] = make_double2(yl, a);
+    cc[1] = make_double2(fma(-2.0, a, fma(3.0, D, -c)), fma(-2.0, D, a + c));
+}
+
+cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks,
+                         int total_coef_blocks, int max_knots, unsigned *err, cudaStream_t st)
 {
     const int smem_bytes = 6 * max_knots * (int)sizeof(double);
     if (smem_bytes > 48 * 1024) {
@@ -235,6 +256,9 @@ cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks,
     }
     if (total_blocks <= 0) return cudaSuccess;
     k_build<<<total_blocks, kBuildThreads, smem_bytes, st>>>(jobs_dev, n_jobs, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_coef<<<total_coef_blocks, kCoefThreads, 0, st>>>(jobs_dev, n_jobs);
     return cudaGetLastError();
 }
 

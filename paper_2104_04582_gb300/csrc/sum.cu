@@ -506,90 +506,6 @@ cudaError_t launch_phases(const TrajDev &tr, const int *seg_start, double t0, do
     return cudaGetLastError();
 }
 
-// Phase anchors of the mixed path, one thread per anchor: wave w, segment s and group q of the
-// anchor, then at the anchor sample a = kAnchorGroup * q (which may precede the segment's first
-// sample: the segment's cubic is used on both sides) the FP64 phases reduced modulo one turn and
-// the Taylor coefficients of each phase cubic in sample units,
-//   Phi(u + k du) - Phi(u) = k du Phi'(u) + (k du)^2 Phi''(u)/2 + (k du)^3 p3,  du = dt / h,
-// divided by 2 pi (turns).  The identity is exact for a cubic; only its FP32 evaluation over
-// k < kAnchorGroup samples in the summation kernel rounds.  The third stream is the phase of
-// the final factor, g = m_last f_phi + lo_last f_r (an integer combination of the reduced
-// phases, so equal to m_last Phi_phi + lo_last Phi_r modulo one turn), reduced again.
-__global__ void __launch_bounds__(256) k_anchor(const PlanHdr *__restrict__ hp)
-{
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n_waves = hp->n_waves;
-    if (g >= hp->total_anchors) return;
-    const WaveDev *waves = hp->waves;
-    int lo = 0, hi = n_waves - 1;
-    while (lo < hi) {  // largest w with anchor_begin <= g
-        const int mid = (lo + hi + 1) >> 1;
-        if (waves[mid].anchor_begin <= g) lo = mid; else hi = mid - 1;
-    }
-    const WaveDev &W = waves[lo];
-    const int j = g - W.anchor_begin;
-    int s0 = 0, s1 = W.tr.S - 1;
-    while (s0 < s1) {  // largest s with anchor_off[s] <= j
-        const int mid = (s0 + s1 + 1) >> 1;
-        if (W.anchor_off[mid] <= j) s0 = mid; else s1 = mid - 1;
-    }
-    const int s = s0;
-    const int q = W.seg_start[s] / kAnchorGroup + (j - W.anchor_off[s]);
-    const SegPhase sp = seg_phase(W.tr, s, W.dphi_phi, W.dphi_r);
-    const double kInv2Pi = 0.15915494309189533577;
-    const double t = fma((double)q * kAnchorGroup, W.dt, W.t0);
-    const double u = (t - sp.tk) * sp.ih;
-    const double du = W.dt * sp.ih, du2 = du * du, du3 = du2 * du;
-    double f[2][4];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const double c0 = k ? sp.c0r : sp.c0phi;
-        const double *p = k ? sp.pr : sp.pphi;
-        const double ph = fma(fma(fma(p[2], u, p[1]), u, p[0]), u, c0);
-        const double x = ph * kInv2Pi;
-        f[k][0] = x - rint(x);
-        f[k][1] = fma(fma(3.0 * p[2], u, 2.0 * p[1]), u, p[0]) * du * kInv2Pi;
-        f[k][2] = fma(3.0 * p[2], u, p[1]) * du2 * kInv2Pi;
-        f[k][3] = p[2] * du3 * kInv2Pi;
-    }
-    const double ml = (double)W.tr.m_last, ll = (double)W.tr.lo_last;
-    double fg[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) fg[c] = fma(ml, f[0][c], ll * f[1][c]);
-    fg[0] -= rint(fg[0]);
-    Anchor a;
-    a.phi = make_float4((float)f[0][0], (float)f[0][1], (float)f[0][2], (float)f[0][3]);
-    a.r = make_float4((float)f[1][0], (float)f[1][1], (float)f[1][2], (float)f[1][3]);
-    a.g = make_float4((float)fg[0], (float)fg[1], (float)fg[2], (float)fg[3]);
-    W.anchors[j] = a;
-}
-
-cudaError_t launch_anchor(const PlanHdr *hdr_dev, int total_anchors, cudaStream_t st)
-{
-    if (total_anchors <= 0) return cudaSuccess;
-    k_anchor<<<(total_anchors + 255) / 256, 256, 0, st>>>(hdr_dev);
-    return cudaGetLastError();
-}
-
-// Self-test of the bounded waits and the error latch: one thread waits on an mbarrier that
-// nothing arrives on and no copy targets, gives up after limit_ns, and latches the timeout bit
-// exactly as the summation and reduced-basis kernels do when a wait expires.
-__global__ void k_wait_selftest(unsigned *err, unsigned long long limit_ns)
-{
-    __shared__ __align__(8) uint64_t bar;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        fence_mbar_init();
-        if (!mbar_wait_limit(&bar, 0u, limit_ns)) atomicOr(err, ERRBIT_TIMEOUT);
-    }
-}
-
-cudaError_t launch_wait_selftest(unsigned *err, unsigned limit_us, cudaStream_t st)
-{
-    k_wait_selftest<<<1, 32, 0, st>>>(err, 1000ull * limit_us);
-    return cudaGetLastError();
-}
-
 namespace {
 template <typename V>
 cudaError_t configure_one(int max_dyn)
