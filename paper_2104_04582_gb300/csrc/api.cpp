@@ -308,7 +308,7 @@ struct few_batch {
     void *blob_dev = nullptr;
     void *scratch_dev = nullptr;
     void *jobs_dev = nullptr;
-    int n_jobs = 0, build_blocks = 0, build_coef_blocks = 0, max_knots = 0;
+    int n_jobs = 0, build_blocks = 0, max_knots = 0;
     int grid = 0, threads = 0, R = 0, smem = 0, total_pairs = 0, total_fold = 0;
     int total_anchor_segs = 0;
     cudaGraph_t graph = nullptr;
@@ -680,6 +680,7 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
     const size_t o_t = take(sizeof(double) * K), o_h = take(sizeof(double) * K),
                  o_ih = take(sizeof(double) * K), o_w = take(sizeof(double) * K),
                  o_ip = take(sizeof(double) * K), o_v = take(sizeof(double) * K),
+                 o_x = take(sizeof(double) * K), o_parts = take(sizeof(int) * (kBuildParts + 2)),
                  o_coef = take(sizeof(double) * 4 * (size_t)tr->S * tr->J),
                  o_slopes = take(sizeof(double) * (size_t)K * tr->J),
                  o_pair = take(sizeof(int2) * P.pair_lm.size()), o_mp = take(sizeof(int) * N),
@@ -720,6 +721,8 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
     D.fac_w = reinterpret_cast<const double *>(d + o_w);
     D.fac_ip = reinterpret_cast<const double *>(d + o_ip);
     D.fac_v = reinterpret_cast<const double *>(d + o_v);
+    D.fac_x = reinterpret_cast<const double *>(d + o_x);
+    D.parts = reinterpret_cast<const int *>(d + o_parts);
     D.coef = reinterpret_cast<double *>(d + o_coef);
     D.slopes = reinterpret_cast<double *>(d + o_slopes);
     D.pair_lm = reinterpret_cast<const int2 *>(d + o_pair);
@@ -735,7 +738,8 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
     cudaError_t e = cudaSuccess;
     if (!us) e = launch_factor(D.t, K, const_cast<double *>(D.h), const_cast<double *>(D.inv_h),
                                const_cast<double *>(D.fac_w), const_cast<double *>(D.fac_ip),
-                               const_cast<double *>(D.fac_v), s);
+                               const_cast<double *>(D.fac_v), const_cast<double *>(D.fac_x),
+                               const_cast<int *>(D.parts), s);
     cudaError_t e2 = cudaStreamSynchronize(s);
     if (us || e != cudaSuccess || e2 != cudaSuccess) {
         (void)cudaGetLastError();
@@ -796,13 +800,11 @@ few_status few_traj_set_data(few_ctx *ctx, few_traj *tr, const double *phi_phi, 
         job.amp_im = amp_im;
     }
     job.block_begin = 0;
-    job.coef_block_begin = 0;
     few_status s = upload(ctx, tr->job_dev, &job, sizeof(job), st);
     const int blocks = (tr->J + kBuildSplines - 1) / kBuildSplines;
     if (!s) {
         tmark(ctx, 0, false, st);
-        if (launch_build(tr->job_dev, 1, blocks, coef_blocks(tr->S, tr->J), tr->K, ctx->d_err,
-                         st) != cudaSuccess) {
+        if (launch_build(tr->job_dev, 1, blocks, tr->K, ctx->d_err, st) != cudaSuccess) {
             (void)cudaGetLastError();
             s = FEW_ERR_CUDA;
         }
@@ -1165,7 +1167,7 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
     if (flags & FEW_BATCH_REBUILD_SPLINES) {
         std::vector<BuildJob> jobs;
         std::set<const few_traj *> seen;
-        int blocks = 0, cblocks = 0;
+        int blocks = 0;
         for (int q = 0; q < n; ++q) {
             const few_traj *tr = reqs[q].traj;
             if (!seen.insert(tr).second) continue;
@@ -1177,8 +1179,6 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
             j.amp_im = tr->src_im;
             j.block_begin = blocks;
             blocks += (tr->J + kBuildSplines - 1) / kBuildSplines;
-            j.coef_block_begin = cblocks;
-            cblocks += coef_blocks(tr->S, tr->J);
             b->max_knots = std::max(b->max_knots, tr->K);
             jobs.push_back(j);
         }
@@ -1187,7 +1187,6 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
             return fail(st);
         b->n_jobs = (int)jobs.size();
         b->build_blocks = blocks;
-        b->build_coef_blocks = cblocks;
     }
     b->grid = P.grid;
     b->threads = P.threads;
@@ -1205,7 +1204,7 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
             const PlanHdr *hd = static_cast<const PlanHdr *>(b->blob_dev);
             if (b->n_jobs)
                 launch_build(static_cast<const BuildJob *>(b->jobs_dev), b->n_jobs, b->build_blocks,
-                             b->build_coef_blocks, b->max_knots, ctx->d_err, cap);
+                             b->max_knots, ctx->d_err, cap);
             launch_ylm(hd, b->total_pairs, b->fp64, cap);
             launch_fold(hd, b->total_fold, b->fp64, cap);
             launch_anchor(hd, b->total_anchor_segs, cap);
@@ -1236,8 +1235,7 @@ few_status few_batch_run(few_ctx *ctx, few_batch *b, void *stream)
     if (b->n_jobs) {
         tmark(ctx, 0, false, s);
         FEW_CUDA_TRY(launch_build(static_cast<const BuildJob *>(b->jobs_dev), b->n_jobs,
-                                  b->build_blocks, b->build_coef_blocks, b->max_knots, ctx->d_err,
-                                  s));
+                                  b->build_blocks, b->max_knots, ctx->d_err, s));
         tmark(ctx, 0, true, s);
     }
     return launch_kernels(ctx, hd, b->total_pairs, b->total_fold, b->total_anchor_segs, b->grid,

@@ -47,8 +47,8 @@ struct Anchor {
 constexpr int kFoldThreads = 128;
 constexpr int kYlmThreads = 16;  // few pairs per block: spreads the FP64 work over SMs
 constexpr int kBuildThreads = 64;
-constexpr int kBuildSplines = kBuildThreads / 2;  // two threads (top and bottom sweep) per spline
-constexpr int kCoefThreads = 256;  // (segment, spline) pairs per coefficient block
+constexpr int kBuildParts = 8;  // blocks of a spline's partitioned solve = lanes per spline
+constexpr int kBuildSplines = kBuildThreads / kBuildParts;
 
 // Trajectory-resident data (one per few_traj).
 struct TrajDev {
@@ -60,10 +60,12 @@ struct TrajDev {
     const double *t;       // [K] knot times
     const double *inv_h;   // [S] 1/(t_{k+1}-t_k)
     const double *h;       // [S] t_{k+1}-t_k
-    const double *fac_w;   // [K] top-down multipliers w_k (rows 2..m) of the shared twisted factorization
-    const double *fac_ip;  // [K] inverse pivots: top rows < m, bottom rows > m, twist pivot at m
-    const double *fac_v;  // [K] bottom-up multipliers v_k (rows m..K-3)
-    double *slopes;        // [K][J] knot slopes of every spline (spline build scratch)
+    const double *fac_w;   // [K] block Thomas multipliers of the partitioned factorisation
+    const double *fac_ip;  // [K] inverse pivots (block rows; separator system at separator rows)
+    const double *fac_v;   // [K] block responses v to the left separator (separator multipliers)
+    const double *fac_x;   // [K] block responses w to the right separator (separator couplings)
+    const int *parts;      // [kBuildParts + 2]: block count P, block starts, then K - 1
+    double *slopes;        // [K][J] spline build scratch (parked elimination values)
     double *coef;          // [S][J][4] spline coefficients in u = (t - t_k)/h_k;
                            //   columns 0,1 = Phi_phi, Phi_r (rad),
                            //   column 2+2i / 3+2i = Re / Im A_i
@@ -83,8 +85,8 @@ struct BuildJob {
     const double *phi_r;    // [K] rad
     const double *amp_re;   // [K][N]
     const double *amp_im;   // [K][N]
-    int block_begin;        // first block of this job in the flattened slope-sweep grid
-    int coef_block_begin;   // first block of this job in the flattened coefficient grid
+    int block_begin;        // first block of this job in the flattened build grid
+    int pad;
 };
 
 // One waveform of a plan (a request).
@@ -133,10 +135,9 @@ struct PlanHdr {
 
 // Kernel launchers (defined in the .cu files; every launcher returns the launch error).
 cudaError_t launch_factor(const double *t, int K, double *h, double *inv_h, double *fac_w,
-                          double *fac_ip, double *fac_v, cudaStream_t st);
+                          double *fac_ip, double *fac_v, double *fac_x, int *parts, cudaStream_t st);
 cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks,
-                         int total_coef_blocks, int max_knots, unsigned *err, cudaStream_t st);
-inline int coef_blocks(int S, int J) { return (int)(((long long)S * J + kCoefThreads - 1) / kCoefThreads); }
+                         int max_knots, unsigned *err, cudaStream_t st);
 cudaError_t launch_ylm(const PlanHdr *hdr_dev, int total_pairs, bool fp64, cudaStream_t st);
 cudaError_t launch_fold(const PlanHdr *hdr_dev, int total_fold_blocks, bool fp64, cudaStream_t st);
 cudaError_t launch_anchor(const PlanHdr *hdr_dev, int total_anchor_segs, cudaStream_t st);

@@ -14,15 +14,13 @@
 //     row 1:    (h_0 + h_1) s_1 + h_0 s_2 = r_1 - R_0,
 //     row K-2:  h_{K-2} s_{K-3} + (h_{K-3} + h_{K-2}) s_{K-2} = r_{K-2} - R_L,
 // (R_0, R_L the end rows' right-hand sides), interior rows as above.  Its matrix depends only on
-// the knots, so it is factorised once per trajectory (k_factor) in twisted form: top-down
-// elimination of rows 1..m and bottom-up elimination of rows K-2..m, m = (K-1)/2, both stable
-// by diagonal dominance.  Every spline reuses that factorisation with two threads (k_build): the
-// top one sweeps rows 1..m, the bottom one rows K-2..m, they combine at row m
-//     s_m = (y_m + z_m - rhs_m) / (p_m + q_m - d_m),
-// and substitute away from m in opposite directions, each writing the slopes on its side;
-// s_0 and s_{K-1} follow from the end rows.  The sweeps are serial chains of FP64 operations,
-// so they carry nothing else; a second kernel (k_coef), one thread per (segment, spline), then
-// forms the coefficients in the normalised local variable u = (t - t_k)/h_k in [0, 1]:
+// the knots, so it is factorised once per trajectory (k_factor), partitioned into up to
+// kBuildParts blocks separated by single rows; every spline then reuses the factors with
+// kBuildParts lanes (k_build): each lane solves one block, the lanes combine through the small
+// separator system, s_0 and s_{K-1} follow from the end rows, and each lane forms the cubic
+// coefficients of the segments next to its rows.  A spline's solve is thus several short
+// chains of FP64 operations in parallel instead of one long one (FP64 latency is long on this
+// chip).  Coefficients are stored in the normalised local variable u = (t - t_k)/h_k in [0, 1]:
 //     p(u) = y_k + h_k s_k u + (3 D - h_k (2 s_k + s_{k+1})) u^2 + (h_k (s_k + s_{k+1}) - 2 D) u^3,
 // D = y_{k+1} - y_k.  The two phase arrays are fitted in radians as given (their reduction
 // modulo 2 pi happens per segment and per sample in the summation kernel).
@@ -30,48 +28,96 @@
 
 namespace fewsum {
 
-// Shared twisted factorisation of the reduced not-a-knot matrix of one knot grid (single
-// thread; O(K)).  fac_w[k] = w_k (top rows 2..m), fac_v[k] = v_k (bottom rows m..K-3),
-// fac_ip[k] = 1/p_k (k < m), 1/q_k (k > m), 1/(p_m + q_m - d_m) (k = m).
+// Partitioned factorisation of the reduced not-a-knot matrix of one knot grid (single thread;
+// O(K)), rows k = 1..K-2 with diagonal dg(k), lower coefficient lo(k) = h_k (k >= 2) and upper
+// up(k) = h_{k-1} (k <= K-3).  The rows are split into P blocks separated by single rows (the
+// separators): block b spans rows start_b .. start_b + size_b - 1, separator b + 1 is the row
+// after it.  With x_sigma the separators' unknowns, block b's rows solve
+//     A_b x_b = f_b - lo(first) x_{sigma_b} e_first - up(last) x_{sigma_{b+1}} e_last,
+// i.e. x_b = y_b - x_{sigma_b} v_b - x_{sigma_{b+1}} w_b with y_b = A_b^-1 f_b and the spline-
+// independent responses v_b = A_b^-1 lo(first) e_first, w_b = A_b^-1 up(last) e_last; the
+// separator rows then form a tridiagonal system in the x_sigma alone,
+//     (dg - lo w_{b-1}[last] - up v_b[first]) x_sigma - lo v_{b-1}[last] x_{sigma_{b-1}}
+//         - up w_b[first] x_{sigma_{b+1}} = f_sigma - lo y_{b-1}[last] - up y_b[first].
+// Stored per row: fac_w = block Thomas multiplier, fac_ip = inverse pivot, fac_v = v, fac_x = w
+// on block rows; on a separator row: fac_v = its Thomas multiplier, fac_ip = inverse pivot,
+// fac_x = the coupling to the next separator.  parts[0] = P, parts[1 + b] = start_b,
+// parts[1 + P] = K - 1.  Every block matrix and the separator system are strictly diagonally
+// dominant, so no pivoting is needed.
 __global__ void k_factor(const double *__restrict__ t, int K, double *h, double *inv_h,
-                         double *fac_w, double *fac_ip, double *fac_v)
+                         double *fac_w, double *fac_ip, double *fac_v, double *fac_x, int *parts)
 {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    const int S = K - 1, m = (K - 1) / 2;
+    const int S = K - 1, n = K - 2;
     for (int k = 0; k < S; ++k) {
         h[k] = t[k + 1] - t[k];
         inv_h[k] = 1.0 / h[k];
     }
-    for (int k = 0; k < K; ++k) fac_w[k] = fac_ip[k] = fac_v[k] = 0.0;
-    // reduced rows 1..K-2: lo_k = h_k (k >= 2), up_k = h_{k-1} (k <= K-3), diagonal dg(k)
+    for (int k = 0; k < K; ++k) fac_w[k] = fac_ip[k] = fac_v[k] = fac_x[k] = 0.0;
     auto dg = [&](int k) {
         if (k == 1) return h[0] + h[1];
         if (k == K - 2) return h[K - 3] + h[K - 2];
         return 2.0 * (h[k - 1] + h[k]);
     };
-    double p = dg(1);
-    fac_ip[1] = 1.0 / p;
-    for (int k = 2; k <= m; ++k) {
-        const double w = h[k] / p;
-        p = dg(k) - w * h[k - 2];
-        fac_w[k] = w;
-        fac_ip[k] = 1.0 / p;
+    auto lo = [&](int k) { return k >= 2 ? h[k] : 0.0; };
+    auto up = [&](int k) { return k <= K - 3 ? h[k - 1] : 0.0; };
+    int P = (n + 1) / 2;
+    if (P > kBuildParts) P = kBuildParts;
+    if (P < 1) P = 1;
+    const int nb = n - (P - 1), base = nb / P, extra = nb % P;
+    int start[kBuildParts + 1];
+    int k = 1;
+    for (int b = 0; b < P; ++b) {
+        start[b] = k;
+        k += base + (b < extra ? 1 : 0) + 1;  // block rows, then its right separator
     }
-    double q = dg(K - 2);
-    if (K - 2 > m) fac_ip[K - 2] = 1.0 / q;
-    for (int k = K - 3; k >= m; --k) {
-        const double v = h[k - 1] / q;
-        q = dg(k) - v * h[k + 1];
-        fac_v[k] = v;
-        if (k > m) fac_ip[k] = 1.0 / q;
+    start[P] = K - 1;
+    parts[0] = P;
+    for (int b = 0; b <= P; ++b) parts[1 + b] = start[b];
+    for (int b = 0; b < P; ++b) {
+        const int a = start[b], e = (b + 1 < P ? start[b + 1] - 1 : K - 1) - 1;
+        double p = dg(a);
+        fac_ip[a] = 1.0 / p;
+        for (int r = a + 1; r <= e; ++r) {
+            const double m = lo(r) / p;
+            p = dg(r) - m * up(r - 1);
+            fac_w[r] = m;
+            fac_ip[r] = 1.0 / p;
+        }
+        if (b > 0) {  // v_b = A_b^-1 lo(a) e_first
+            fac_v[a] = lo(a);
+            for (int r = a + 1; r <= e; ++r) fac_v[r] = -fac_w[r] * fac_v[r - 1];
+            fac_v[e] *= fac_ip[e];
+            for (int r = e - 1; r >= a; --r) fac_v[r] = (fac_v[r] - up(r) * fac_v[r + 1]) * fac_ip[r];
+        }
+        if (b + 1 < P) {  // w_b = A_b^-1 up(e) e_last
+            fac_x[e] = up(e) * fac_ip[e];
+            for (int r = e - 1; r >= a; --r) fac_x[r] = -up(r) * fac_x[r + 1] * fac_ip[r];
+        }
     }
-    fac_ip[m] = 1.0 / (p + q - dg(m));
+    double piv = 0.0, cup_prev = 0.0;
+    for (int i = 1; i < P; ++i) {
+        const int sg = start[i] - 1, L = sg - 1, F = sg + 1;
+        const double D = dg(sg) - lo(sg) * fac_x[L] - up(sg) * fac_v[F];
+        const double clo = -lo(sg) * fac_v[L], cup = -up(sg) * fac_x[F];
+        double mu = 0.0;
+        if (i == 1) {
+            piv = D;
+        } else {
+            mu = clo / piv;
+            piv = D - mu * cup_prev;
+        }
+        fac_v[sg] = mu;
+        fac_ip[sg] = 1.0 / piv;
+        fac_x[sg] = cup;
+        cup_prev = cup;
+    }
 }
 
 cudaError_t launch_factor(const double *t, int K, double *h, double *inv_h, double *fac_w,
-                          double *fac_ip, double *fac_v, cudaStream_t st)
+                          double *fac_ip, double *fac_v, double *fac_x, int *parts, cudaStream_t st)
 {
-    k_factor<<<1, 32, 0, st>>>(t, K, h, inv_h, fac_w, fac_ip, fac_v);
+    k_factor<<<1, 32, 0, st>>>(t, K, h, inv_h, fac_w, fac_ip, fac_v, fac_x, parts);
     return cudaGetLastError();
 }
 
@@ -92,32 +138,32 @@ __device__ __forceinline__ unsigned nonfinite_bit(double x)
     return ((unsigned)__double2hiint(x) & 0x7ff00000u) + 0x00100000u;
 }
 
-// Two threads per spline column: lane l (< 16) of a warp runs the top sweep and lane l + 16 the
-// bottom sweep of the same column, in one instruction stream (direction and coefficients are
-// per-lane data), so the pair meets at row m without divergence and exchanges its reduced
-// right-hand side with one shuffle.  The knot-only arrays are staged in shared memory and the
-// column values (and, in the substitution, the parked values) are fetched kChunk rows ahead
-// into registers, so kChunk loads are in flight: the grid has only a few warps per SM, so
-// memory latency is hidden by depth, not by occupancy.
+// kBuildParts lanes per spline column (a spline's lanes are consecutive in a warp): lane b
+// solves block b of the partitioned system (forward and back substitution with the shared
+// factors, its values parked in the slope array), the lanes exchange their blocks' end values by
+// shuffles, every lane solves the small separator system, and lane b corrects its rows,
+// x = y - x_left v - x_right w, and writes the coefficients of the segments beside them.  The
+// knot-only arrays are staged in shared memory; column values are fetched kChunk rows ahead.
 constexpr int kChunk = 8;
 
 __global__ void __launch_bounds__(kBuildThreads)
 k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
 {
-    extern __shared__ double sk[];  // [6][K]: h, ra, rb, top multipliers, inverse pivots, bottom multipliers
-    // job of this block: largest q with jobs[q].block_begin <= blockIdx.x
+    extern __shared__ double sk[];  // [7][K]: h, ra, rb, multipliers, inverse pivots, v, w
+    __shared__ int s_parts[kBuildParts + 2];
     int lo = 0, hi = n_jobs - 1;
-    const int b = blockIdx.x;
-    while (lo < hi) {
+    const int blk = blockIdx.x;
+    while (lo < hi) {  // job of this block: largest q with jobs[q].block_begin <= blk
         int mid = (lo + hi + 1) >> 1;
-        if (jobs[mid].block_begin <= b) lo = mid; else hi = mid - 1;
+        if (jobs[mid].block_begin <= blk) lo = mid; else hi = mid - 1;
     }
     const BuildJob &jb = jobs[lo];
     const TrajDev &tr = jb.tr;
     const int K = tr.K, J = tr.J;
     // ra_k = 3 h_k / h_{k-1}, rb_k = 3 h_{k-1} / h_k: the interior right-hand side
     // 3 (h_k d_{k-1} + h_{k-1} d_k) becomes ra_k (y_k - y_{k-1}) + rb_k (y_{k+1} - y_k)
-    double *h = sk, *ra = sk + K, *rb = sk + 2 * K, *fw = sk + 3 * K, *fip = sk + 4 * K, *fv = sk + 5 * K;
+    double *h = sk, *ra = sk + K, *rb = sk + 2 * K, *fw = sk + 3 * K, *fip = sk + 4 * K,
+           *fv = sk + 5 * K, *fx = sk + 6 * K;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         h[k] = k < K - 1 ? tr.h[k] : 0.0;
         const bool in = k >= 1 && k <= K - 2;
@@ -126,129 +172,169 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
         fw[k] = tr.fac_w[k];
         fip[k] = tr.fac_ip[k];
         fv[k] = tr.fac_v[k];
+        fx[k] = tr.fac_x[k];
     }
+    if (threadIdx.x < kBuildParts + 2) s_parts[threadIdx.x] = tr.parts[threadIdx.x];
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const bool top = lane < 16;
-    const int j = (b - jb.block_begin) * kBuildSplines + (threadIdx.x >> 5) * 16 + (lane & 15);
+    const int P = s_parts[0];
+    const int b = threadIdx.x & (kBuildParts - 1);
+    const int j = (blk - jb.block_begin) * kBuildSplines + (threadIdx.x / kBuildParts);
     const bool live = j < J;
     const int jj = live ? j : 0;  // a column past J computes on column 0 and stores nothing
+    const bool mine = b < P;      // this lane has a block
     double *__restrict__ slopes = tr.slopes;
     unsigned bad = 0u;  // bit 31: some column value was not finite
-    const int m = (K - 1) / 2;
-    const int dir = top ? 1 : -1, k0 = top ? 1 : K - 2;
-    const int steps = top ? m : K - 1 - m, steps_max = K - 1 - m;
+    const int a = mine ? s_parts[1 + b] : 1;
+    const int e = mine ? (b + 1 < P ? s_parts[2 + b] - 2 : K - 2) : 0;
+    const int steps = e - a + 1;  // <= 0 for a lane without a block
 
-    // elimination: acc = rhs_k - mult_k acc along rows k0, k0 + dir, ..., m; the window holds
-    // y_{k - dir} (yb) and y_k (yc)
-    double yb = load_y(jb, jj, k0 - dir), yc = load_y(jb, jj, k0);
-    bad |= nonfinite_bit(yb) | nonfinite_bit(yc);
-    double acc = 0.0, rend = 0.0, rm = 0.0;
-    for (int i0 = 0; i0 < steps_max; i0 += kChunk) {
-        double ya[kChunk];  // y_{k + dir} for the chunk's rows
+    // end-row right-hand sides: R_0 at row 1 (block 0), R_L at row K-2 (last block)
+    auto r0 = [&](double y0, double y1, double y2) {
+        const double dl = (y1 - y0) / h[0], dr = (y2 - y1) / h[1];
+        return ((2.0 * h[1] + 3.0 * h[0]) * h[1] * dl + h[0] * h[0] * dr) / (h[0] + h[1]);
+    };
+    auto rl = [&](double ya, double yb, double yc) {
+        const double av = h[K - 2], c = h[K - 3];
+        const double dl = (yb - ya) / c, dr = (yc - yb) / av;
+        return (av * av * dl + (2.0 * c + 3.0 * av) * c * dr) / (c + av);
+    };
+
+    // forward substitution over the block: fp_k = f_k - m_k fp_{k-1}, parked in place
+    double yb = 0.0, yc = 0.0, ylm2 = 0.0, fp = 0.0, rend0 = 0.0, rendl = 0.0;
+    if (mine) {
+        yb = load_y(jb, jj, a - 1);
+        yc = load_y(jb, jj, a);
+        bad |= nonfinite_bit(yb) | nonfinite_bit(yc);
+        if (b > 0) ylm2 = load_y(jb, jj, a - 2);  // for the left separator's row
+    }
+    const double y_sep_l = yb, y_first_col = yc;  // y_{a-1}, y_a
+    for (int i0 = 0; i0 < steps; i0 += kChunk) {
+        double ya[kChunk];  // y_{k + 1} for the chunk's rows
 #pragma unroll
         for (int q = 0; q < kChunk; ++q)
-            ya[q] = (i0 + q < steps) ? load_y(jb, jj, k0 + dir * (i0 + q + 1)) : 0.0;
+            ya[q] = (i0 + q < steps) ? load_y(jb, jj, a + i0 + q + 1) : 0.0;
 #pragma unroll
         for (int q = 0; q < kChunk; ++q) {
             const int i = i0 + q;
             if (i >= steps) break;
-            const int k = k0 + dir * i;
+            const int k = a + i;
             bad |= nonfinite_bit(ya[q]);
-            const double ylo = top ? yb : ya[q], yhi = top ? ya[q] : yb;  // y_{k-1}, y_{k+1}
-            const double el = yc - ylo, er = yhi - yc;
-            double r = fma(ra[k], el, rb[k] * er);
-            if (k == 1 || k == K - 2) {
-                const double dl = el / h[k - 1], dr = er / h[k];
-                if (k == 1) {
-                    const double R0 = ((2.0 * h[1] + 3.0 * h[0]) * h[1] * dl + h[0] * h[0] * dr) / (h[0] + h[1]);
-                    r -= R0;
-                    if (top) rend = R0;
-                }
-                if (k == K - 2) {
-                    const double a = h[K - 2], c = h[K - 3];
-                    const double RL = (a * a * dl + (2.0 * c + 3.0 * a) * c * dr) / (c + a);
-                    r -= RL;
-                    if (!top) rend = RL;
-                }
+            // differences first: the phase arrays are large (1e5 rad) with small steps, and
+            // y_k - y_{k-1} is exact where an expanded form would cancel
+            double r = fma(ra[k], yc - yb, rb[k] * (ya[q] - yc));
+            if (k == 1) {
+                const double R0 = r0(yb, yc, ya[q]);
+                r -= R0;
+                rend0 = R0;
             }
-            if (k == m) rm = r;
-            acc = r - (i == 0 ? 0.0 : (top ? fw[k] : fv[k])) * acc;
-            if (k != m && live) slopes[(size_t)k * J + j] = acc;  // parked for the substitution
+            if (k == K - 2) {
+                const double RL = rl(yb, yc, ya[q]);
+                r -= RL;
+                rendl = RL;
+            }
+            fp = i == 0 ? r : fma(-fw[k], fp, r);
+            if (live) slopes[(size_t)k * J + j] = fp;
             yb = yc;
             yc = ya[q];
         }
     }
-    // row m: both threads hold rhs_m and their own reduced value
-    const double other = __shfl_xor_sync(0xffffffffu, acc, 16);
-    double s_prev = (acc + other - rm) * fip[m];
-    if (top && live) slopes[(size_t)m * J + j] = s_prev;
-
-    // substitution away from m: rows m - 1, ..., 0 (top) or m + 1, ..., K - 1 (bottom); each
-    // slope replaces the value parked in its place
-    const int ds = -dir;
-    for (int i0 = 0; i0 < steps_max; i0 += kChunk) {
+    // back substitution: y_k = (fp_k - up_k y_{k+1}) / p_k, parked in place
+    double y_next = fp * fip[e > 0 ? e : 0];
+    const double y_last = y_next;
+    if (mine && live) slopes[(size_t)e * J + j] = y_next;
+    for (int i0 = 1; i0 < steps; i0 += kChunk) {
         double pv[kChunk];
 #pragma unroll
+        for (int q = 0; q < kChunk; ++q)
+            pv[q] = (i0 + q < steps) ? slopes[(size_t)(e - i0 - q) * J + jj] : 0.0;
+#pragma unroll
         for (int q = 0; q < kChunk; ++q) {
-            const int i = i0 + q, k = m + ds * (1 + i);
-            const bool act = i < steps;
-            pv[q] = (act && k >= 1 && k <= K - 2) ? slopes[(size_t)k * J + jj] : 0.0;
+            if (i0 + q >= steps) break;
+            const int k = e - i0 - q;
+            y_next = (pv[q] - h[k - 1] * y_next) * fip[k];
+            if (live) slopes[(size_t)k * J + j] = y_next;
+        }
+    }
+    const double y_first = steps > 1 ? y_next : y_last;
+
+    // separator system: lane b (>= 1) forms the right-hand side of its left separator
+    const double y_last_left = __shfl_up_sync(0xffffffffu, y_last, 1, kBuildParts);
+    double g = 0.0;
+    if (mine && b > 0) {
+        const int sg = a - 1;
+        const double fs = fma(ra[sg], y_sep_l - ylm2, rb[sg] * (y_first_col - y_sep_l));
+        g = fs - h[sg] * y_last_left - h[sg - 1] * y_first;
+        bad |= nonfinite_bit(ylm2);
+    }
+    double X[kBuildParts + 1];
+#pragma unroll
+    for (int i = 0; i <= kBuildParts; ++i) X[i] = 0.0;
+    double gp[kBuildParts];
+#pragma unroll
+    for (int i = 1; i < kBuildParts; ++i) {
+        const double gi = __shfl_sync(0xffffffffu, g, i, kBuildParts);
+        gp[i] = 0.0;
+        if (i < P) gp[i] = i == 1 ? gi : fma(-fv[s_parts[1 + i] - 1], gp[i - 1], gi);
+    }
+#pragma unroll
+    for (int i = kBuildParts - 1; i >= 1; --i)
+        if (i < P) X[i] = (gp[i] - fx[s_parts[1 + i] - 1] * X[i + 1]) * fip[s_parts[1 + i] - 1];
+    double xl = 0.0, xr = 0.0;
+#pragma unroll
+    for (int i = 1; i < kBuildParts; ++i) {
+        if (i == b) xl = X[i];
+        if (i == b + 1) xr = X[i];
+    }
+
+    // correction, x_k = y_k - x_left v_k - x_right w_k, and the cubic coefficients of segments
+    // a - 1 .. e (block 0: from segment 0; the last block: to segment K-2), in the local variable
+    // u = (t - t_k)/h_k: p(u) = y_k + h s_k u + (3 D - 2 h s_k - h s_{k+1}) u^2
+    // + (h s_k + h s_{k+1} - 2 D) u^3, D = y_{k+1} - y_k, h = h_k
+    double *__restrict__ coef = tr.coef;
+    auto put = [&](int seg, double yl, double yr, double sl, double sr) {
+        const double D = yr - yl, hk = h[seg], av = hk * sl, c = hk * sr;
+        double2 *cc = reinterpret_cast<double2 *>(coef + ((size_t)seg * J + j) * 4);
+        cc[0] = make_double2(yl, av);
+        cc[1] = make_double2(fma(-2.0, av, fma(3.0, D, -c)), fma(-2.0, D, av + c));
+    };
+    // the slope and value left of the block: row a - 1 (the left separator, or row 0)
+    double s_prev = b == 0 ? 0.0 : xl, y_prev = y_sep_l;
+    for (int i0 = 0; i0 < steps; i0 += kChunk) {
+        double pv[kChunk], yv[kChunk];
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+            const bool act = i0 + q < steps;
+            pv[q] = act ? slopes[(size_t)(a + i0 + q) * J + jj] : 0.0;
+            yv[q] = act ? load_y(jb, jj, a + i0 + q) : 0.0;
         }
 #pragma unroll
         for (int q = 0; q < kChunk; ++q) {
             const int i = i0 + q;
             if (i >= steps) break;
-            const int k = m + ds * (1 + i);
-            double par, c, ipv;
-            if (k == 0) {  // end row 0: h_1 s_0 + (h_0 + h_1) s_1 = R_0
-                par = rend; c = h[0] + h[1]; ipv = 1.0 / h[1];
-            } else if (k == K - 1) {  // end row K-1: (h_{K-2} + h_{K-3}) s_{K-2} + h_{K-3} s_{K-1} = R_L
-                par = rend; c = h[K - 2] + h[K - 3]; ipv = 1.0 / h[K - 3];
-            } else {  // s_k = (y_k - up_k s_{k+1}) / p_k  or  (z_k - lo_k s_{k-1}) / q_k
-                par = pv[q]; c = top ? h[k - 1] : h[k]; ipv = fip[k];
-            }
-            const double s = (par - c * s_prev) * ipv;
-            if (live) slopes[(size_t)k * J + j] = s;
-            s_prev = s;
+            const int k = a + i;
+            const double x = fma(-xr, fx[k], fma(-xl, fv[k], pv[q]));
+            if (i == 0 && b == 0)  // end row 0: h_1 s_0 + (h_0 + h_1) s_1 = R_0
+                s_prev = (rend0 - (h[0] + h[1]) * x) / h[1];
+            if (live) put(k - 1, y_prev, yv[q], s_prev, x);
+            s_prev = x;
+            y_prev = yv[q];
+        }
+    }
+    if (mine && live) {
+        if (b + 1 < P) {  // segment e between row e and the right separator
+            put(e, y_prev, load_y(jb, jj, e + 1), s_prev, xr);
+        } else {  // end row K-1: (h_{K-2} + h_{K-3}) s_{K-2} + h_{K-3} s_{K-1} = R_L
+            const double s_last = (rendl - (h[K - 2] + h[K - 3]) * s_prev) / h[K - 3];
+            put(K - 2, y_prev, load_y(jb, jj, K - 1), s_prev, s_last);
         }
     }
     if ((bad & 0x80000000u) && live) atomicOr(err, ERRBIT_NONFINITE);
 }
 
-// Cubic coefficients of every (segment, spline) once the knot slopes are known, one thread each
-// (consecutive threads: consecutive splines of one segment, so the 32-byte rows are written
-// contiguously): in the local variable u = (t - t_k)/h_k,
-//     p(u) = y_k + h s_k u + (3 D - 2 h s_k - h s_{k+1}) u^2 + (h s_k + h s_{k+1} - 2 D) u^3,
-// D = y_{k+1} - y_k, h = h_k.
-__global__ void __launch_bounds__(kCoefThreads)
-k_coef(const BuildJob *__restrict__ jobs, int n_jobs)
+cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks, int max_knots,
+                         unsigned *err, cudaStream_t st)
 {
-    int lo = 0, hi = n_jobs - 1;
-    const int b = blockIdx.x;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (jobs[mid].coef_block_begin <= b) lo = mid; else hi = mid - 1;
-    }
-    const BuildJob &jb = jobs[lo];
-    const TrajDev &tr = jb.tr;
-    const int J = tr.J;
-    const long long g = (long long)(b - jb.coef_block_begin) * kCoefThreads + threadIdx.x;
-    if (g >= (long long)tr.S * J) return;
-    const int seg = (int)(g / J), j = (int)(g - (long long)seg * J);
-    const double yl = load_y(jb, j, seg), yr = load_y(jb, j, seg + 1);
-    const double sl = tr.slopes[(size_t)seg * J + j], sr = tr.slopes[(size_t)(seg + 1) * J + j];
-    const double hk = tr.h[seg];
-    const double D = yr - yl, a = hk * sl, c = hk * sr;
-    double2 *cc = reinterpret_cast<double2 *>(tr.coef + ((size_t)seg * J + j) * 4);
-    cc[0] = make_double2(yl, a);
-    cc[1] = make_double2(fma(-2.0, a, fma(3.0, D, -c)), fma(-2.0, D, a + c));
-}
-
-cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks,
-                         int total_coef_blocks, int max_knots, unsigned *err, cudaStream_t st)
-{
-    const int smem_bytes = 6 * max_knots * (int)sizeof(double);
+    const int smem_bytes = 7 * max_knots * (int)sizeof(double);
     if (smem_bytes > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              smem_bytes);
@@ -256,9 +342,6 @@ cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks,
     }
     if (total_blocks <= 0) return cudaSuccess;
     k_build<<<total_blocks, kBuildThreads, smem_bytes, st>>>(jobs_dev, n_jobs, err);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_coef<<<total_coef_blocks, kCoefThreads, 0, st>>>(jobs_dev, n_jobs);
     return cudaGetLastError();
 }
 
