@@ -66,7 +66,8 @@ struct TrajDev {
     const double *fac_x;   // [K] block responses w to the right separator (separator couplings)
     const int *parts;      // [kBuildParts + 2]: block count P, block starts, then K - 1
     double *slopes;        // [K][J] spline build scratch (parked elimination values)
-    double *coef;          // [S][J][4] spline coefficients in u = (t - t_k)/h_k;
+    double *coef;          // [S][J][4] Hermite data of every segment: (y_k, y_{k+1}, s_k,
+                           //   s_{k+1}), values and knot slopes (see hermite_to_power);
                            //   columns 0,1 = Phi_phi, Phi_r (rad),
                            //   column 2+2i / 3+2i = Re / Im A_i
     const int2 *pair_lm;   // [n_pairs] (l, m)
@@ -77,6 +78,19 @@ struct TrajDev {
     const int2 *rows;      // [n_rows] (slots of the row, lowest n of the previous row minus
                            //   this row's lowest n); a row's slots run from its highest n down
 };
+
+// Power coefficients of a segment's cubic in the local variable u = (t - t_k)/h_k, u in [0, 1],
+// from its Hermite data (values y0 = y_k, y1 = y_{k+1}, slopes s0, s1, width h = h_k):
+//     p(u) = y0 + a u + (3 D - 2 a - b) u^2 + (a + b - 2 D) u^3,  a = h s0, b = h s1, D = y1 - y0.
+template <typename T>
+__host__ __device__ __forceinline__ void hermite_to_power(T y0, T y1, T s0, T s1, T h, T (&c)[4])
+{
+    const T D = y1 - y0, a = h * s0, b = h * s1;
+    c[0] = y0;
+    c[1] = a;
+    c[2] = fma((T)-2, a, fma((T)3, D, -b));
+    c[3] = fma((T)-2, D, a + b);
+}
 
 // One spline-build job: a trajectory and the knot data to fit.
 struct BuildJob {

@@ -139,7 +139,9 @@ template <> struct Slot8<float> {
     }
 };
 
-// One thread per (wave, segment, slot): K_slot = scale * sum of its contributions.
+// One thread per (wave, segment, slot): K_slot = scale * sum of its contributions, summed on the
+// splines' Hermite data (values and slopes at the segment's two knots) and turned into power
+// coefficients in u once.
 // T is the arithmetic and storage type of the folded coefficients (double for FEW_FP64,
 // float for FEW_MIXED, whose amplitudes are FP32 by design).
 template <typename T>
@@ -176,14 +178,19 @@ __global__ void __launch_bounds__(kFoldThreads) k_fold(const PlanHdr *__restrict
             im[q] += ar[q] * yi + ai[q] * yr;
         }
     }
-    const T sc = cvt(W.scale, T());
+    // the folded values are Hermite data (the fold is linear in them): power coefficients in u
+    // once per (segment, slot)
+    const T hk = cvt(tr.h[s], T()), sc = cvt(W.scale, T());
+    T pre[4], pim[4];
+    hermite_to_power(re[0], re[1], re[2], re[3], hk, pre);
+    hermite_to_power(im[0], im[1], im[2], im[3], hk, pim);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        re[q] *= sc;
-        im[q] *= sc;
+        pre[q] *= sc;
+        pim[q] *= sc;
     }
     T *dst = reinterpret_cast<T *>(W.fcoef) + ((size_t)s * tr.n_slots + slot) * 8;
-    Slot8<T>::store(dst, re, im);
+    Slot8<T>::store(dst, pre, pim);
 }
 
 cudaError_t launch_fold(const PlanHdr *hdr_dev, int total_fold_blocks, bool fp64, cudaStream_t st)

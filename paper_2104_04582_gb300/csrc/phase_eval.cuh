@@ -36,11 +36,15 @@ __device__ __forceinline__ SegPhase seg_phase(const TrajDev &tr, int s, double d
                                               double dphi_r)
 {
     const double *pc = tr.coef + (size_t)s * tr.J * 4;
+    const double hk = tr.h[s];
+    double cphi[4], cr[4];
+    hermite_to_power(pc[0], pc[1], pc[2], pc[3], hk, cphi);
+    hermite_to_power(pc[4], pc[5], pc[6], pc[7], hk, cr);
     SegPhase sp;
-    sp.c0phi = reduce_2pi(pc[0]) + reduce_2pi(dphi_phi);
-    sp.c0r = reduce_2pi(pc[4]) + reduce_2pi(dphi_r);
-    sp.pphi[0] = pc[1]; sp.pphi[1] = pc[2]; sp.pphi[2] = pc[3];
-    sp.pr[0] = pc[5]; sp.pr[1] = pc[6]; sp.pr[2] = pc[7];
+    sp.c0phi = reduce_2pi(cphi[0]) + reduce_2pi(dphi_phi);
+    sp.c0r = reduce_2pi(cr[0]) + reduce_2pi(dphi_r);
+    sp.pphi[0] = cphi[1]; sp.pphi[1] = cphi[2]; sp.pphi[2] = cphi[3];
+    sp.pr[0] = cr[1]; sp.pr[1] = cr[2]; sp.pr[2] = cr[3];
     sp.tk = tr.t[s];
     sp.ih = tr.inv_h[s];
     return sp;

@@ -17,13 +17,13 @@
 // the knots, so it is factorised once per trajectory (k_factor), partitioned into up to
 // kBuildParts blocks separated by single rows; every spline then reuses the factors with
 // kBuildParts lanes (k_build): each lane solves one block, the lanes combine through the small
-// separator system, s_0 and s_{K-1} follow from the end rows, and each lane forms the cubic
-// coefficients of the segments next to its rows.  A spline's solve is thus several short
-// chains of FP64 operations in parallel instead of one long one (FP64 latency is long on this
-// chip).  Coefficients are stored in the normalised local variable u = (t - t_k)/h_k in [0, 1]:
-//     p(u) = y_k + h_k s_k u + (3 D - h_k (2 s_k + s_{k+1})) u^2 + (h_k (s_k + s_{k+1}) - 2 D) u^3,
-// D = y_{k+1} - y_k.  The two phase arrays are fitted in radians as given (their reduction
-// modulo 2 pi happens per segment and per sample in the summation kernel).
+// separator system, s_0 and s_{K-1} follow from the end rows, and each lane stores the Hermite
+// data (y_k, y_{k+1}, s_k, s_{k+1}) of the segments next to its rows.  A spline's solve is thus
+// several short chains of FP64 operations in parallel instead of one long one (FP64 latency is
+// long on this chip), and the build issues only the solve's FP64 operations (the cubic's power
+// coefficients, hermite_to_power, are formed by the consumers: in FP32 by the mixed fold).  The
+// two phase arrays are fitted in radians as given (their reduction modulo 2 pi happens per
+// segment and per sample in the summation kernel).
 #include "fewsum_internal.h"
 
 namespace fewsum {
@@ -142,7 +142,7 @@ __device__ __forceinline__ unsigned nonfinite_bit(double x)
 // solves block b of the partitioned system (forward and back substitution with the shared
 // factors, its values parked in the slope array), the lanes exchange their blocks' end values by
 // shuffles, every lane solves the small separator system, and lane b corrects its rows,
-// x = y - x_left v - x_right w, and writes the coefficients of the segments beside them.  The
+// x = y - x_left v - x_right w, and writes the Hermite data of the segments beside them.  The
 // knot-only arrays are staged in shared memory; column values are fetched kChunk rows ahead.
 constexpr int kChunk = 8;
 
@@ -208,6 +208,7 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
         if (b > 0) ylm2 = load_y(jb, jj, a - 2);  // for the left separator's row
     }
     const double y_sep_l = yb, y_first_col = yc;  // y_{a-1}, y_a
+    double dprev = yc - yb;
     for (int i0 = 0; i0 < steps; i0 += kChunk) {
         double ya[kChunk];  // y_{k + 1} for the chunk's rows
 #pragma unroll
@@ -220,8 +221,11 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
             const int k = a + i;
             bad |= nonfinite_bit(ya[q]);
             // differences first: the phase arrays are large (1e5 rad) with small steps, and
-            // y_k - y_{k-1} is exact where an expanded form would cancel
-            double r = fma(ra[k], yc - yb, rb[k] * (ya[q] - yc));
+            // y_k - y_{k-1} is exact where an expanded form would cancel; each difference is
+            // formed once (row k's right difference is row k + 1's left one)
+            const double dr = ya[q] - yc;
+            double r = fma(ra[k], dprev, rb[k] * dr);
+            dprev = dr;
             if (k == 1) {
                 const double R0 = r0(yb, yc, ya[q]);
                 r -= R0;
@@ -266,6 +270,7 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
         g = fs - h[sg] * y_last_left - h[sg - 1] * y_first;
         bad |= nonfinite_bit(ylm2);
     }
+    // lane 0 of the spline solves it (FP64 issue is the scarce resource) and broadcasts
     double X[kBuildParts + 1];
 #pragma unroll
     for (int i = 0; i <= kBuildParts; ++i) X[i] = 0.0;
@@ -274,28 +279,27 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
     for (int i = 1; i < kBuildParts; ++i) {
         const double gi = __shfl_sync(0xffffffffu, g, i, kBuildParts);
         gp[i] = 0.0;
-        if (i < P) gp[i] = i == 1 ? gi : fma(-fv[s_parts[1 + i] - 1], gp[i - 1], gi);
+        if (b == 0 && i < P) gp[i] = i == 1 ? gi : fma(-fv[s_parts[1 + i] - 1], gp[i - 1], gi);
     }
 #pragma unroll
     for (int i = kBuildParts - 1; i >= 1; --i)
-        if (i < P) X[i] = (gp[i] - fx[s_parts[1 + i] - 1] * X[i + 1]) * fip[s_parts[1 + i] - 1];
+        if (b == 0 && i < P) X[i] = (gp[i] - fx[s_parts[1 + i] - 1] * X[i + 1]) * fip[s_parts[1 + i] - 1];
     double xl = 0.0, xr = 0.0;
 #pragma unroll
     for (int i = 1; i < kBuildParts; ++i) {
-        if (i == b) xl = X[i];
-        if (i == b + 1) xr = X[i];
+        const double xi = __shfl_sync(0xffffffffu, X[i], 0, kBuildParts);
+        if (i == b) xl = xi;
+        if (i == b + 1) xr = xi;
     }
 
-    // correction, x_k = y_k - x_left v_k - x_right w_k, and the cubic coefficients of segments
-    // a - 1 .. e (block 0: from segment 0; the last block: to segment K-2), in the local variable
-    // u = (t - t_k)/h_k: p(u) = y_k + h s_k u + (3 D - 2 h s_k - h s_{k+1}) u^2
-    // + (h s_k + h s_{k+1} - 2 D) u^3, D = y_{k+1} - y_k, h = h_k
+    // correction, x_k = y_k - x_left v_k - x_right w_k, and the Hermite data (y_k, y_{k+1},
+    // s_k, s_{k+1}) of segments a - 1 .. e (block 0: from segment 0; the last block: to segment
+    // K-2); the consumers form the cubic's power coefficients (hermite_to_power)
     double *__restrict__ coef = tr.coef;
     auto put = [&](int seg, double yl, double yr, double sl, double sr) {
-        const double D = yr - yl, hk = h[seg], av = hk * sl, c = hk * sr;
         double2 *cc = reinterpret_cast<double2 *>(coef + ((size_t)seg * J + j) * 4);
-        cc[0] = make_double2(yl, av);
-        cc[1] = make_double2(fma(-2.0, av, fma(3.0, D, -c)), fma(-2.0, D, av + c));
+        cc[0] = make_double2(yl, yr);
+        cc[1] = make_double2(sl, sr);
     };
     // the slope and value left of the block: row a - 1 (the left separator, or row 0)
     double s_prev = b == 0 ? 0.0 : xl, y_prev = y_sep_l;
