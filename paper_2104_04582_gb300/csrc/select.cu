@@ -15,11 +15,10 @@
 // consecutive slots each in registers.  Bitonic sort of (power, index) pairs: the exchanges at
 // distances 1 and 2 stay inside a thread, distances 4..64 are warp shuffles (a warp holds 128
 // consecutive slots), and only distances >= 128 pass through shared memory.  The sorted powers
-// then go to shared memory and one thread runs the sequential sum.  The powers are non-negative
-// and sorted in descending order, so once an addition leaves the running sum unchanged every
-// later one does too (rounding is monotone): the chain stops there and the sums that follow all
-// equal the total.  The first rank whose sum reaches the target is found by all threads with an
-// atomic minimum, and the kept modes are marked with plain byte stores of 1 into a mask zeroed
+// then go to shared memory.  The cumulative sums are exact integer prefix sums inside each binade
+// of the running sum (see the comment at the scan), so the whole block computes them in a few
+// rounds of a block-wide scan instead of one thread running N dependent FP64 additions.  The first
+// rank whose sum reaches the target is found by all threads with an atomic minimum, and the kept modes are marked with plain byte stores of 1 into a mask zeroed
 // beforehand (every writer stores the same value, so the union needs no atomics).
 #include "fewsum_internal.h"
 
@@ -28,7 +27,7 @@ namespace fewsum {
 constexpr int kSelectMaxThreads = 1024;
 constexpr int kSelectPerThread = 4;  // consecutive sort slots per thread
 constexpr int kSelectWarpSlots = 32 * kSelectPerThread;
-constexpr int kChainChunk = 8;  // powers loaded ahead of the sequential sum's additions
+constexpr int kSelectMaxRounds = 64;  // scan rounds before the sequential chain takes over
 
 // Non-negative doubles order exactly like their IEEE bit patterns read as unsigned integers, so
 // the sort compares 64-bit integer keys (descending power = ascending inverted bits), with the
@@ -77,9 +76,11 @@ k_mode_select(const double *__restrict__ amp_re, const double *__restrict__ amp_
     extern __shared__ __align__(16) unsigned long long sel_key[];  // [P] keys, then [P] indices
     int *sel_ix = reinterpret_cast<int *>(sel_key + P);
     __shared__ double s_total;
-    __shared__ int s_conv;
-    __shared__ int s_cut;
+    __shared__ unsigned long long s_cbits;  // bits of the running sum where a round starts
+    __shared__ unsigned long long s_wsum[kSelectMaxThreads / 32];
+    __shared__ int s_a, s_exit, s_fallback, s_cut;
     const int k = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, wid = tid >> 5;
     const int p0 = kSelectPerThread * tid;  // first slot of this thread
 
     unsigned long long key[kSelectPerThread];
@@ -151,52 +152,141 @@ k_mode_select(const double *__restrict__ amp_re, const double *__restrict__ amp_
 
     // sorted powers to shared memory (slot j = rank j; padding holds +0)
     double *s_pw = reinterpret_cast<double *>(sel_key);
+    double *s_cs = s_pw;  // c_j overwrites p_j: a round writes only ranks below where the next starts
     __syncthreads();  // the last shared-memory exchange stage may still be read
 #pragma unroll
     for (int r = 0; r < kSelectPerThread; ++r) s_pw[p0 + r] = key_power(key[r]);
     __syncthreads();
 
-    // the sequential cumulative sum, c_j = fl(c_{j-1} + p_j), in place: s_pw[j] <- c_j for
-    // j < s_conv; every c_j with j >= s_conv equals the total
+    // the cumulative sums c_j = fl(c_{j-1} + p_j), c_{-1} = 0, into s_cs[j] for every j < N.
+    // While c stays in one binade [2^E, 2^(E+1)) (ulp U = 2^(E-52), E >= -1022), c/U is an
+    // integer below 2^53 and fl(c + p) adds to it the integer nearest p/U (p <= c, so p/U < 2^53
+    // and is read off p's bits); those additions are prefix sums, computed block-wide at once.
+    // A step whose integer sum reaches 2^53 (the sum leaves the binade) or whose p/U lies exactly
+    // halfway between integers (a tie, resolved by the parity of the sum) is taken by the FP64
+    // adder itself, and the block starts again from there: a few rounds (binade changes are at
+    // most log2 N + 1 apart) give the same bits as the left-to-right chain.
+    const unsigned long long kTop = 1ull << 53;
+    unsigned long long pm[kSelectPerThread];
+    int pe[kSelectPerThread];
+    double pv[kSelectPerThread];
+    unsigned bad = 0u;
+#pragma unroll
+    for (int r = 0; r < kSelectPerThread; ++r) {
+        pv[r] = key_power(key[r]);
+        const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(pv[r]));
+        const int ef = (int)((bits >> 52) & 0x7ffu);
+        pm[r] = (bits & (kTop / 2 - 1)) | (ef ? kTop / 2 : 0ull);
+        pe[r] = ef ? ef - 1023 : -1022;
+        if (p0 + r < N && ef == 0x7ff) bad = 1u;  // inf or nan: the chain below handles them
+    }
     if (tid == 0) {
-        double c = 0.0;
-        int conv = N;
-        double v[kChainChunk], nv[kChainChunk];
-#pragma unroll
-        for (int q = 0; q < kChainChunk; ++q) v[q] = s_pw[q];
-        for (int j0 = 0; j0 < N; j0 += kChainChunk) {
-            // next chunk's loads ahead of this chunk's additions (P is a multiple of the chunk)
-            const int jn = j0 + kChainChunk < P ? j0 + kChainChunk : j0;
-#pragma unroll
-            for (int q = 0; q < kChainChunk; ++q) nv[q] = s_pw[jn + q];
-            const double c_start = c;
-#pragma unroll
-            for (int q = 0; q < kChainChunk; ++q) {
-                c = __dadd_rn(c, v[q]);
-                s_pw[j0 + q] = c;
-            }
-            // c never decreases: unchanged across the chunk means no addition changed it, so
-            // neither does any later (smaller) power
-            if (c == c_start) {
-                conv = j0;
-                break;
-            }
-#pragma unroll
-            for (int q = 0; q < kChainChunk; ++q) v[q] = nv[q];
-        }
-        s_conv = conv;
-        s_total = c;
+        s_cbits = static_cast<unsigned long long>(__double_as_longlong(s_pw[0]));
+        s_cs[0] = s_pw[0];
+        s_a = 1;
+        s_fallback = 0;
     }
     __syncthreads();
+    if (bad) s_fallback = 1;
+    for (int round = 0;; ++round) {
+        __syncthreads();
+        const int a = s_a;
+        if (a >= N || s_fallback) break;
+        if (round >= kSelectMaxRounds) {  // many ties: finish with the sequential chain
+            if (tid == 0) s_fallback = 1;
+            continue;
+        }
+        const unsigned long long cb = s_cbits;
+        const int cef = (int)((cb >> 52) & 0x7ffu);
+        const int E = cef ? cef - 1023 : -1022;
+        const unsigned long long Mc = (cb & (kTop / 2 - 1)) | (cef ? kTop / 2 : 0ull);
+        unsigned long long q[kSelectPerThread], run = 0ull;
+        bool tie[kSelectPerThread];
+#pragma unroll
+        for (int r = 0; r < kSelectPerThread; ++r) {
+            const int j = p0 + r;
+            q[r] = 0ull;
+            tie[r] = false;
+            if (j >= a && j < N) {
+                const int d = E - pe[r];  // >= 0: p_j <= c
+                if (d == 0) {
+                    q[r] = pm[r];
+                } else if (d < 64) {
+                    const unsigned long long rem = pm[r] & ((1ull << d) - 1ull), half = 1ull << (d - 1);
+                    q[r] = (pm[r] >> d) + (rem > half ? 1ull : 0ull);
+                    tie[r] = rem == half;
+                }  // d >= 64: p/U < 1/2, nothing added
+            }
+            run += q[r];
+        }
+        // block-wide exclusive prefix of the threads' sums
+        unsigned long long incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) s_wsum[wid] = incl;
+        if (tid == 0) s_exit = 0x7fffffff;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned long long v = lane < nt / 32 ? s_wsum[lane] : 0ull, w = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long u = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += u;
+            }
+            if (lane < nt / 32) s_wsum[lane] = w - v;  // exclusive over warps
+        }
+        __syncthreads();
+        unsigned long long M[kSelectPerThread];
+        unsigned long long m = Mc + s_wsum[wid] + (incl - run);
+#pragma unroll
+        for (int r = 0; r < kSelectPerThread; ++r) {
+            m += q[r];
+            M[r] = m;
+            const int j = p0 + r;
+            if (j >= a && j < N && (m >= kTop || tie[r])) atomicMin(&s_exit, j);
+        }
+        __syncthreads();
+        const int jx = s_exit;
+        // c_j = M_j U for the steps inside the binade: exponent field E + 1022 plus M's bits
+        const unsigned long long ebase = static_cast<unsigned long long>(E + 1022) << 52;
+#pragma unroll
+        for (int r = 0; r < kSelectPerThread; ++r) {
+            const int j = p0 + r;
+            if (j >= a && j < N && j < jx) s_cs[j] = __longlong_as_double((long long)(ebase + M[r]));
+            if (j == jx) {  // the FP64 adder takes the step that leaves the binade or ties
+                const double cprev = j == a ? __longlong_as_double((long long)cb)
+                                            : __longlong_as_double((long long)(ebase + M[r] - q[r]));
+                const double cnew = __dadd_rn(cprev, pv[r]);
+                s_cs[j] = cnew;
+                s_cbits = static_cast<unsigned long long>(__double_as_longlong(cnew));
+                s_a = j + 1;
+            }
+        }
+        if (jx == 0x7fffffff && tid == 0) s_a = N;
+    }
+    __syncthreads();
+    // the sequential chain from where the rounds stopped (non-finite powers, many ties)
+    if (s_fallback && tid == 0) {
+        int j = s_a;
+        double c = s_cs[j - 1];
+        for (; j < N; ++j) {
+            c = __dadd_rn(c, s_pw[j]);
+            s_cs[j] = c;
+        }
+    }
+    if (tid == 0) s_total = s_cs[N - 1];
+    __syncthreads();
     const double total = s_total;
-    const int conv = s_conv;
     if (!(total > 0.0)) return;  // uniform: nothing kept at a knot without power
     const double target = (1.0 - eps) * total;
 #pragma unroll
     for (int r = 0; r < kSelectPerThread; ++r) {
         const int j = p0 + r;
         if (j >= N) break;
-        const double cj = j < conv ? s_pw[j] : total;
+        const double cj = s_cs[j];
         if (cj >= target) {
             atomicMin(&s_cut, j);
             break;

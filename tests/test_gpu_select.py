@@ -103,3 +103,44 @@ def test_mode_select_decades_exact(gpu_ctx):
         g = _gpu_select(gpu_ctx, re, im, modes, eps)
         o = oracle.mode_select(re, im, modes, eps)
         np.testing.assert_array_equal(g, o, err_msg=f"eps={eps}")
+
+
+def _tie_knots(N, rng):
+    # Powers a^2 + b^2 in units of 2^-54 beside a leading power 1: 2 (exactly half an ulp of the
+    # running sum 1, a rounding tie decided by the parity of the sum), 5 (above half), 1 (below
+    # half) and 8 (a whole ulp).  Every power and every product is exact, so the masks depend only
+    # on how each addition rounds.
+    ab = np.array([[1, 1], [1, 2], [0, 1], [2, 2]])
+    pick = rng.integers(0, 4, (3, N))
+    re, im = ab[pick, 0] * 2.0 ** -27, ab[pick, 1] * 2.0 ** -27
+    re[:, 0], im[:, 0] = 1.0, 0.0
+    return re, im
+
+
+@pytest.mark.parametrize("N", [40, 300, 3843])
+def test_mode_select_rounding_ties_exact(gpu_ctx, N):
+    # few ties (N = 40) stay inside the block-wide scan; hundreds of ties also run the sequential
+    # chain that finishes the sums after the scan's round limit
+    rng = np.random.default_rng(4000 + N)
+    re, im = _tie_knots(N, rng)
+    modes = np.stack([np.full(N, 2), np.zeros(N, int), np.zeros(N, int)], axis=1)
+    for eps in (1e-16, 1e-17, 0.0):
+        g = _gpu_select(gpu_ctx, re, im, modes, eps)
+        o = oracle.mode_select(re, im, modes, eps)
+        np.testing.assert_array_equal(g, o, err_msg=f"N={N} eps={eps}")
+
+
+def test_mode_select_subnormal_and_infinite_powers(gpu_ctx):
+    # subnormal powers (sums of multiples of 2^-1074, then crossing into the normal range), and a
+    # knot with an infinite power, which the cut reaches at its first rank
+    N = 1500
+    rng = np.random.default_rng(4100)
+    modes = np.stack([np.full(N, 2), rng.integers(0, 3, N), np.zeros(N, int)], axis=1)
+    re = 10.0 ** rng.uniform(-162, -154, (4, N))
+    im = 10.0 ** rng.uniform(-163, -160, (4, N))
+    re[1, :3] = [1e-150, 3e-151, 2e-152]
+    re[3, 17] = 1e200
+    for eps in (1e-3, 1e-12, 0.0):
+        g = _gpu_select(gpu_ctx, re, im, modes, eps)
+        o = oracle.mode_select(re, im, modes, eps)
+        np.testing.assert_array_equal(g, o, err_msg=f"eps={eps}")
