@@ -678,7 +678,9 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
         return o;
     };
     const size_t o_t = take(sizeof(double) * K), o_h = take(sizeof(double) * K),
-                 o_ih = take(sizeof(double) * K), o_w = take(sizeof(double) * K),
+                 o_ih = take(sizeof(double) * K), o_ra = take(sizeof(double) * K),
+                 o_rb = take(sizeof(double) * K), o_lo = take(sizeof(double) * K),
+                 o_up = take(sizeof(double) * K),
                  o_ip = take(sizeof(double) * K), o_v = take(sizeof(double) * K),
                  o_x = take(sizeof(double) * K), o_parts = take(sizeof(int) * (kBuildParts + 2)),
                  o_coef = take(sizeof(double) * 4 * (size_t)tr->S * tr->J),
@@ -718,7 +720,10 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
     D.t = reinterpret_cast<const double *>(d + o_t);
     D.h = reinterpret_cast<const double *>(d + o_h);
     D.inv_h = reinterpret_cast<const double *>(d + o_ih);
-    D.fac_w = reinterpret_cast<const double *>(d + o_w);
+    D.fac_ra = reinterpret_cast<const double *>(d + o_ra);
+    D.fac_rb = reinterpret_cast<const double *>(d + o_rb);
+    D.fac_lo = reinterpret_cast<const double *>(d + o_lo);
+    D.fac_up = reinterpret_cast<const double *>(d + o_up);
     D.fac_ip = reinterpret_cast<const double *>(d + o_ip);
     D.fac_v = reinterpret_cast<const double *>(d + o_v);
     D.fac_x = reinterpret_cast<const double *>(d + o_x);
@@ -736,10 +741,20 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
     few_status us = upload(ctx, d, img.data(), o_h, s);  // knot times
     if (!us) us = upload(ctx, d + o_pair, img2.data(), off - o_pair, s);
     cudaError_t e = cudaSuccess;
-    if (!us) e = launch_factor(D.t, K, const_cast<double *>(D.h), const_cast<double *>(D.inv_h),
-                               const_cast<double *>(D.fac_w), const_cast<double *>(D.fac_ip),
-                               const_cast<double *>(D.fac_v), const_cast<double *>(D.fac_x),
-                               const_cast<int *>(D.parts), s);
+    if (!us) {
+        FactorArrays fa;
+        fa.h = reinterpret_cast<double *>(d + o_h);
+        fa.inv_h = reinterpret_cast<double *>(d + o_ih);
+        fa.ra = reinterpret_cast<double *>(d + o_ra);
+        fa.rb = reinterpret_cast<double *>(d + o_rb);
+        fa.lo = reinterpret_cast<double *>(d + o_lo);
+        fa.up = reinterpret_cast<double *>(d + o_up);
+        fa.ip = reinterpret_cast<double *>(d + o_ip);
+        fa.v = reinterpret_cast<double *>(d + o_v);
+        fa.x = reinterpret_cast<double *>(d + o_x);
+        fa.parts = reinterpret_cast<int *>(d + o_parts);
+        e = launch_factor(D.t, K, fa, s);
+    }
     cudaError_t e2 = cudaStreamSynchronize(s);
     if (us || e != cudaSuccess || e2 != cudaSuccess) {
         (void)cudaGetLastError();

@@ -60,7 +60,13 @@ struct TrajDev {
     const double *t;       // [K] knot times
     const double *inv_h;   // [S] 1/(t_{k+1}-t_k)
     const double *h;       // [S] t_{k+1}-t_k
-    const double *fac_w;   // [K] block Thomas multipliers of the partitioned factorisation
+    // the partitioned factorisation of the reduced not-a-knot system (k_factor); p_k = pivot
+    const double *fac_ra;  // [K] right-hand side f_k = ra_k (y_k - y_{k-1}) + rb_k (y_{k+1} - y_k):
+    const double *fac_rb;  //   block rows scaled by 1/p_k, separator rows plain; rows 0 and K-1
+                           //   hold the end slopes' coefficients (see k_factor)
+    const double *fac_lo;  // [K] block rows: sub-diagonal / p_k (0 on a block's first row);
+                           //   rows 0 and K-1: the end slopes' coupling to s_1 / s_{K-2}
+    const double *fac_up;  // [K] block rows: super-diagonal / p_k
     const double *fac_ip;  // [K] inverse pivots (block rows; separator system at separator rows)
     const double *fac_v;   // [K] block responses v to the left separator (separator multipliers)
     const double *fac_x;   // [K] block responses w to the right separator (separator couplings)
@@ -148,8 +154,12 @@ struct PlanHdr {
 };
 
 // Kernel launchers (defined in the .cu files; every launcher returns the launch error).
-cudaError_t launch_factor(const double *t, int K, double *h, double *inv_h, double *fac_w,
-                          double *fac_ip, double *fac_v, double *fac_x, int *parts, cudaStream_t st);
+// Output arrays of k_factor (the trajectory's TrajDev fields of the same names).
+struct FactorArrays {
+    double *h, *inv_h, *ra, *rb, *lo, *up, *ip, *v, *x;
+    int *parts;
+};
+cudaError_t launch_factor(const double *t, int K, const FactorArrays &f, cudaStream_t st);
 cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks,
                          int max_knots, unsigned *err, cudaStream_t st);
 cudaError_t launch_ylm(const PlanHdr *hdr_dev, int total_pairs, bool fp64, cudaStream_t st);

@@ -29,38 +29,61 @@
 namespace fewsum {
 
 // Partitioned factorisation of the reduced not-a-knot matrix of one knot grid (single thread;
-// O(K)), rows k = 1..K-2 with diagonal dg(k), lower coefficient lo(k) = h_k (k >= 2) and upper
-// up(k) = h_{k-1} (k <= K-3).  The rows are split into P blocks separated by single rows (the
+// O(K)), rows k = 1..K-2 with diagonal dg(k), lower coefficient sub(k) = h_k (k >= 2) and upper
+// sup(k) = h_{k-1} (k <= K-3).  The rows are split into P blocks separated by single rows (the
 // separators): block b spans rows start_b .. start_b + size_b - 1, separator b + 1 is the row
 // after it.  With x_sigma the separators' unknowns, block b's rows solve
-//     A_b x_b = f_b - lo(first) x_{sigma_b} e_first - up(last) x_{sigma_{b+1}} e_last,
+//     A_b x_b = f_b - sub(first) x_{sigma_b} e_first - sup(last) x_{sigma_{b+1}} e_last,
 // i.e. x_b = y_b - x_{sigma_b} v_b - x_{sigma_{b+1}} w_b with y_b = A_b^-1 f_b and the spline-
-// independent responses v_b = A_b^-1 lo(first) e_first, w_b = A_b^-1 up(last) e_last; the
+// independent responses v_b = A_b^-1 sub(first) e_first, w_b = A_b^-1 sup(last) e_last; the
 // separator rows then form a tridiagonal system in the x_sigma alone,
-//     (dg - lo w_{b-1}[last] - up v_b[first]) x_sigma - lo v_{b-1}[last] x_{sigma_{b-1}}
-//         - up w_b[first] x_{sigma_{b+1}} = f_sigma - lo y_{b-1}[last] - up y_b[first].
-// Stored per row: fac_w = block Thomas multiplier, fac_ip = inverse pivot, fac_v = v, fac_x = w
-// on block rows; on a separator row: fac_v = its Thomas multiplier, fac_ip = inverse pivot,
-// fac_x = the coupling to the next separator.  parts[0] = P, parts[1 + b] = start_b,
-// parts[1 + P] = K - 1.  Every block matrix and the separator system are strictly diagonally
-// dominant, so no pivoting is needed.
-__global__ void k_factor(const double *__restrict__ t, int K, double *h, double *inv_h,
-                         double *fac_w, double *fac_ip, double *fac_v, double *fac_x, int *parts)
+//     (dg - sub w_{b-1}[last] - sup v_b[first]) x_sigma - sub v_{b-1}[last] x_{sigma_{b-1}}
+//         - sup w_b[first] x_{sigma_{b+1}} = f_sigma - sub y_{b-1}[last] - sup y_b[first].
+// Within a block, Thomas elimination with every row divided by its pivot p_k gives
+//     g_k = (ra_k D_{k-1} + rb_k D_k)/p_k - (sub(k)/p_k) g_{k-1},   y_k = g_k - (sup(k)/p_k) y_{k+1}
+// (D_k = y_{k+1} - y_k), one operation fewer per row than the unscaled form.  Stored per row:
+// ra, rb (divided by p_k on block rows), lo = sub/p_k (0 on a block's first row), up = sup/p_k,
+// ip = 1/p_k, v, x = w on block rows; on a separator row: ra, rb plain, v = its multiplier in the
+// separator elimination, ip = inverse pivot, x = the coupling to the next separator.
+// parts[0] = P, parts[1 + b] = start_b, parts[1 + P] = K - 1.  Every block matrix and the
+// separator system are strictly diagonally dominant, so no pivoting is needed.
+//
+// The end rows: in differences the interior right-hand side is 3 (h_k/h_{k-1}) D_{k-1} +
+// 3 (h_{k-1}/h_k) D_k, and R_0 = (2 h_1 + 3 h_0) h_1 D_0/(h_0 (h_0 + h_1)) + h_0^2 D_1/(h_1 (h_0 +
+// h_1)), so row 1's r_1 - R_0 has the coefficients h_1^2/(h_0 (h_0 + h_1)) and h_0 (2 h_0 +
+// 3 h_1)/(h_1 (h_0 + h_1)); mirrored (hc = h_{K-3}, hd = h_{K-2}) row K-2's r_{K-2} - R_L has
+// hd (3 hc + 2 hd)/(hc (hc + hd)) and hc^2/(hd (hc + hd)).  Rows 0 and K-1 hold the end slopes
+//     s_0 = ra_0 D_0 + rb_0 D_1 - lo_0 s_1,   s_{K-1} = ra_{K-1} D_{K-3} + rb_{K-1} D_{K-2} -
+//     lo_{K-1} s_{K-2}
+// (the end rows divided by h_1 and hc).  K >= 4, so rows 1 and K-2 are distinct, and neither is
+// a separator.
+__global__ void k_factor(const double *__restrict__ t, int K, FactorArrays f)
 {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double *h = f.h, *ip = f.ip, *fl = f.lo, *fu = f.up, *fv = f.v, *fx = f.x, *ra = f.ra,
+           *rb = f.rb;
     const int S = K - 1, n = K - 2;
     for (int k = 0; k < S; ++k) {
         h[k] = t[k + 1] - t[k];
-        inv_h[k] = 1.0 / h[k];
+        f.inv_h[k] = 1.0 / h[k];
     }
-    for (int k = 0; k < K; ++k) fac_w[k] = fac_ip[k] = fac_v[k] = fac_x[k] = 0.0;
+    for (int k = 0; k < K; ++k) ip[k] = fl[k] = fu[k] = fv[k] = fx[k] = ra[k] = rb[k] = 0.0;
     auto dg = [&](int k) {
         if (k == 1) return h[0] + h[1];
         if (k == K - 2) return h[K - 3] + h[K - 2];
         return 2.0 * (h[k - 1] + h[k]);
     };
-    auto lo = [&](int k) { return k >= 2 ? h[k] : 0.0; };
-    auto up = [&](int k) { return k <= K - 3 ? h[k - 1] : 0.0; };
+    auto sub = [&](int k) { return k >= 2 ? h[k] : 0.0; };
+    auto sup = [&](int k) { return k <= K - 3 ? h[k - 1] : 0.0; };
+    for (int k = 2; k <= K - 3; ++k) {
+        ra[k] = 3.0 * h[k] * f.inv_h[k - 1];
+        rb[k] = 3.0 * h[k - 1] * f.inv_h[k];
+    }
+    const double h0 = h[0], h1 = h[1], hc = h[K - 3], hd = h[K - 2];
+    ra[1] = h1 * h1 / (h0 * (h0 + h1));
+    rb[1] = h0 * (2.0 * h0 + 3.0 * h1) / (h1 * (h0 + h1));
+    ra[K - 2] = hd * (3.0 * hc + 2.0 * hd) / (hc * (hc + hd));
+    rb[K - 2] = hc * hc / (hd * (hc + hd));
     int P = (n + 1) / 2;
     if (P > kBuildParts) P = kBuildParts;
     if (P < 1) P = 1;
@@ -72,34 +95,40 @@ __global__ void k_factor(const double *__restrict__ t, int K, double *h, double 
         k += base + (b < extra ? 1 : 0) + 1;  // block rows, then its right separator
     }
     start[P] = K - 1;
-    parts[0] = P;
-    for (int b = 0; b <= P; ++b) parts[1 + b] = start[b];
+    f.parts[0] = P;
+    for (int b = 0; b <= P; ++b) f.parts[1 + b] = start[b];
     for (int b = 0; b < P; ++b) {
         const int a = start[b], e = (b + 1 < P ? start[b + 1] - 1 : K - 1) - 1;
         double p = dg(a);
-        fac_ip[a] = 1.0 / p;
-        for (int r = a + 1; r <= e; ++r) {
-            const double m = lo(r) / p;
-            p = dg(r) - m * up(r - 1);
-            fac_w[r] = m;
-            fac_ip[r] = 1.0 / p;
+        ip[a] = 1.0 / p;
+        for (int r = a + 1; r <= e; ++r) {  // fl holds the Thomas multipliers for now
+            const double m = sub(r) / p;
+            p = dg(r) - m * sup(r - 1);
+            fl[r] = m;
+            ip[r] = 1.0 / p;
         }
-        if (b > 0) {  // v_b = A_b^-1 lo(a) e_first
-            fac_v[a] = lo(a);
-            for (int r = a + 1; r <= e; ++r) fac_v[r] = -fac_w[r] * fac_v[r - 1];
-            fac_v[e] *= fac_ip[e];
-            for (int r = e - 1; r >= a; --r) fac_v[r] = (fac_v[r] - up(r) * fac_v[r + 1]) * fac_ip[r];
+        if (b > 0) {  // v_b = A_b^-1 sub(a) e_first
+            fv[a] = sub(a);
+            for (int r = a + 1; r <= e; ++r) fv[r] = -fl[r] * fv[r - 1];
+            fv[e] *= ip[e];
+            for (int r = e - 1; r >= a; --r) fv[r] = (fv[r] - sup(r) * fv[r + 1]) * ip[r];
         }
-        if (b + 1 < P) {  // w_b = A_b^-1 up(e) e_last
-            fac_x[e] = up(e) * fac_ip[e];
-            for (int r = e - 1; r >= a; --r) fac_x[r] = -up(r) * fac_x[r + 1] * fac_ip[r];
+        if (b + 1 < P) {  // w_b = A_b^-1 sup(e) e_last
+            fx[e] = sup(e) * ip[e];
+            for (int r = e - 1; r >= a; --r) fx[r] = -sup(r) * fx[r + 1] * ip[r];
+        }
+        for (int r = a; r <= e; ++r) {  // the pivot-scaled rows
+            fl[r] = r > a ? sub(r) * ip[r] : 0.0;
+            fu[r] = sup(r) * ip[r];
+            ra[r] *= ip[r];
+            rb[r] *= ip[r];
         }
     }
     double piv = 0.0, cup_prev = 0.0;
     for (int i = 1; i < P; ++i) {
         const int sg = start[i] - 1, L = sg - 1, F = sg + 1;
-        const double D = dg(sg) - lo(sg) * fac_x[L] - up(sg) * fac_v[F];
-        const double clo = -lo(sg) * fac_v[L], cup = -up(sg) * fac_x[F];
+        const double D = dg(sg) - sub(sg) * fx[L] - sup(sg) * fv[F];
+        const double clo = -sub(sg) * fv[L], cup = -sup(sg) * fx[F];
         double mu = 0.0;
         if (i == 1) {
             piv = D;
@@ -107,17 +136,22 @@ __global__ void k_factor(const double *__restrict__ t, int K, double *h, double 
             mu = clo / piv;
             piv = D - mu * cup_prev;
         }
-        fac_v[sg] = mu;
-        fac_ip[sg] = 1.0 / piv;
-        fac_x[sg] = cup;
+        fv[sg] = mu;
+        ip[sg] = 1.0 / piv;
+        fx[sg] = cup;
         cup_prev = cup;
     }
+    ra[0] = (2.0 * h1 + 3.0 * h0) / (h0 * (h0 + h1));
+    rb[0] = h0 * h0 / (h1 * h1 * (h0 + h1));
+    fl[0] = (h0 + h1) / h1;
+    ra[K - 1] = hd * hd / (hc * hc * (hc + hd));
+    rb[K - 1] = (2.0 * hc + 3.0 * hd) / (hd * (hc + hd));
+    fl[K - 1] = (hc + hd) / hc;
 }
 
-cudaError_t launch_factor(const double *t, int K, double *h, double *inv_h, double *fac_w,
-                          double *fac_ip, double *fac_v, double *fac_x, int *parts, cudaStream_t st)
+cudaError_t launch_factor(const double *t, int K, const FactorArrays &f, cudaStream_t st)
 {
-    k_factor<<<1, 32, 0, st>>>(t, K, h, inv_h, fac_w, fac_ip, fac_v, fac_x, parts);
+    k_factor<<<1, 32, 0, st>>>(t, K, f);
     return cudaGetLastError();
 }
 
@@ -139,17 +173,18 @@ __device__ __forceinline__ unsigned nonfinite_bit(double x)
 }
 
 // kBuildParts lanes per spline column (a spline's lanes are consecutive in a warp): lane b
-// solves block b of the partitioned system (forward and back substitution with the shared
-// factors, its values parked in the slope array), the lanes exchange their blocks' end values by
-// shuffles, every lane solves the small separator system, and lane b corrects its rows,
+// solves block b of the partitioned system (the pivot-scaled forward and back substitution with
+// the shared factors, its values parked in the slope array), the lanes exchange their blocks' end
+// values by shuffles, lane 0 solves the small separator system, and lane b corrects its rows,
 // x = y - x_left v - x_right w, and writes the Hermite data of the segments beside them.  The
 // knot-only arrays are staged in shared memory; column values are fetched kChunk rows ahead.
 constexpr int kChunk = 8;
+constexpr int kBuildStaged = 6;  // knot arrays in shared memory: ra, rb, lo, up, v, w
 
 __global__ void __launch_bounds__(kBuildThreads)
 k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
 {
-    extern __shared__ double sk[];  // [7][K]: h, ra, rb, multipliers, inverse pivots, v, w
+    extern __shared__ double sk[];  // [kBuildStaged][K]
     __shared__ int s_parts[kBuildParts + 2];
     int lo = 0, hi = n_jobs - 1;
     const int blk = blockIdx.x;
@@ -160,17 +195,13 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
     const BuildJob &jb = jobs[lo];
     const TrajDev &tr = jb.tr;
     const int K = tr.K, J = tr.J;
-    // ra_k = 3 h_k / h_{k-1}, rb_k = 3 h_{k-1} / h_k: the interior right-hand side
-    // 3 (h_k d_{k-1} + h_{k-1} d_k) becomes ra_k (y_k - y_{k-1}) + rb_k (y_{k+1} - y_k)
-    double *h = sk, *ra = sk + K, *rb = sk + 2 * K, *fw = sk + 3 * K, *fip = sk + 4 * K,
-           *fv = sk + 5 * K, *fx = sk + 6 * K;
+    double *ra = sk, *rb = sk + K, *fl = sk + 2 * K, *fu = sk + 3 * K, *fv = sk + 4 * K,
+           *fx = sk + 5 * K;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        h[k] = k < K - 1 ? tr.h[k] : 0.0;
-        const bool in = k >= 1 && k <= K - 2;
-        ra[k] = in ? 3.0 * tr.h[k] * tr.inv_h[k - 1] : 0.0;
-        rb[k] = in ? 3.0 * tr.h[k - 1] * tr.inv_h[k] : 0.0;
-        fw[k] = tr.fac_w[k];
-        fip[k] = tr.fac_ip[k];
+        ra[k] = tr.fac_ra[k];
+        rb[k] = tr.fac_rb[k];
+        fl[k] = tr.fac_lo[k];
+        fu[k] = tr.fac_up[k];
         fv[k] = tr.fac_v[k];
         fx[k] = tr.fac_x[k];
     }
@@ -187,20 +218,13 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
     const int a = mine ? s_parts[1 + b] : 1;
     const int e = mine ? (b + 1 < P ? s_parts[2 + b] - 2 : K - 2) : 0;
     const int steps = e - a + 1;  // <= 0 for a lane without a block
+    // the left separator's inverse pivot, for lane 0's separator solve
+    const bool sep = mine && b > 0;  // this lane's block has a left separator, row a - 1
+    const double ip_sep = sep ? tr.fac_ip[a - 1] : 0.0;  // its separator-system data
+    const double h_sep = sep ? tr.h[a - 1] : 0.0, h_sep1 = sep ? tr.h[a - 2] : 0.0;
 
-    // end-row right-hand sides: R_0 at row 1 (block 0), R_L at row K-2 (last block)
-    auto r0 = [&](double y0, double y1, double y2) {
-        const double dl = (y1 - y0) / h[0], dr = (y2 - y1) / h[1];
-        return ((2.0 * h[1] + 3.0 * h[0]) * h[1] * dl + h[0] * h[0] * dr) / (h[0] + h[1]);
-    };
-    auto rl = [&](double ya, double yb, double yc) {
-        const double av = h[K - 2], c = h[K - 3];
-        const double dl = (yb - ya) / c, dr = (yc - yb) / av;
-        return (av * av * dl + (2.0 * c + 3.0 * av) * c * dr) / (c + av);
-    };
-
-    // forward substitution over the block: fp_k = f_k - m_k fp_{k-1}, parked in place
-    double yb = 0.0, yc = 0.0, ylm2 = 0.0, fp = 0.0, rend0 = 0.0, rendl = 0.0;
+    // forward substitution over the block, g_k = ra_k D_{k-1} + rb_k D_k - lo_k g_{k-1}, parked
+    double yb = 0.0, yc = 0.0, ylm2 = 0.0;
     if (mine) {
         yb = load_y(jb, jj, a - 1);
         yc = load_y(jb, jj, a);
@@ -208,7 +232,11 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
         if (b > 0) ylm2 = load_y(jb, jj, a - 2);  // for the left separator's row
     }
     const double y_sep_l = yb, y_first_col = yc;  // y_{a-1}, y_a
-    double dprev = yc - yb;
+    // differences first: the phase arrays are large (1e5 rad) with small steps, and
+    // y_{k+1} - y_k is exact where an expanded form would cancel; each difference is formed once
+    // (row k's right difference is row k + 1's left one)
+    const double d_left = yc - yb;  // D_{a-1}
+    double dprev = d_left, dprev2 = 0.0, d_first = 0.0, g = 0.0;
     for (int i0 = 0; i0 < steps; i0 += kChunk) {
         double ya[kChunk];  // y_{k + 1} for the chunk's rows
 #pragma unroll
@@ -220,32 +248,19 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
             if (i >= steps) break;
             const int k = a + i;
             bad |= nonfinite_bit(ya[q]);
-            // differences first: the phase arrays are large (1e5 rad) with small steps, and
-            // y_k - y_{k-1} is exact where an expanded form would cancel; each difference is
-            // formed once (row k's right difference is row k + 1's left one)
             const double dr = ya[q] - yc;
-            double r = fma(ra[k], dprev, rb[k] * dr);
+            const double r = fma(ra[k], dprev, rb[k] * dr);
+            g = i == 0 ? r : fma(-fl[k], g, r);
+            if (i == 0) d_first = dr;
+            if (live) slopes[(size_t)k * J + j] = g;
+            dprev2 = dprev;
             dprev = dr;
-            if (k == 1) {
-                const double R0 = r0(yb, yc, ya[q]);
-                r -= R0;
-                rend0 = R0;
-            }
-            if (k == K - 2) {
-                const double RL = rl(yb, yc, ya[q]);
-                r -= RL;
-                rendl = RL;
-            }
-            fp = i == 0 ? r : fma(-fw[k], fp, r);
-            if (live) slopes[(size_t)k * J + j] = fp;
-            yb = yc;
             yc = ya[q];
         }
     }
-    // back substitution: y_k = (fp_k - up_k y_{k+1}) / p_k, parked in place
-    double y_next = fp * fip[e > 0 ? e : 0];
+    // back substitution, y_k = g_k - up_k y_{k+1} (y_e = g_e is parked already)
+    double y_next = g;
     const double y_last = y_next;
-    if (mine && live) slopes[(size_t)e * J + j] = y_next;
     for (int i0 = 1; i0 < steps; i0 += kChunk) {
         double pv[kChunk];
 #pragma unroll
@@ -255,35 +270,36 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
         for (int q = 0; q < kChunk; ++q) {
             if (i0 + q >= steps) break;
             const int k = e - i0 - q;
-            y_next = (pv[q] - h[k - 1] * y_next) * fip[k];
+            y_next = fma(-fu[k], y_next, pv[q]);
             if (live) slopes[(size_t)k * J + j] = y_next;
         }
     }
-    const double y_first = steps > 1 ? y_next : y_last;
+    const double y_first = y_next;  // y_a (y_e when the block has one row)
 
-    // separator system: lane b (>= 1) forms the right-hand side of its left separator
+    // separator system: lane b (>= 1) forms the right-hand side of its left separator row
     const double y_last_left = __shfl_up_sync(0xffffffffu, y_last, 1, kBuildParts);
-    double g = 0.0;
+    double gs = 0.0;
     if (mine && b > 0) {
         const int sg = a - 1;
         const double fs = fma(ra[sg], y_sep_l - ylm2, rb[sg] * (y_first_col - y_sep_l));
-        g = fs - h[sg] * y_last_left - h[sg - 1] * y_first;
+        gs = fs - h_sep * y_last_left - h_sep1 * y_first;
         bad |= nonfinite_bit(ylm2);
     }
     // lane 0 of the spline solves it (FP64 issue is the scarce resource) and broadcasts
     double X[kBuildParts + 1];
 #pragma unroll
     for (int i = 0; i <= kBuildParts; ++i) X[i] = 0.0;
-    double gp[kBuildParts];
+    double gp[kBuildParts], ipv[kBuildParts];
 #pragma unroll
     for (int i = 1; i < kBuildParts; ++i) {
-        const double gi = __shfl_sync(0xffffffffu, g, i, kBuildParts);
+        const double gi = __shfl_sync(0xffffffffu, gs, i, kBuildParts);
+        ipv[i] = __shfl_sync(0xffffffffu, ip_sep, i, kBuildParts);
         gp[i] = 0.0;
         if (b == 0 && i < P) gp[i] = i == 1 ? gi : fma(-fv[s_parts[1 + i] - 1], gp[i - 1], gi);
     }
 #pragma unroll
     for (int i = kBuildParts - 1; i >= 1; --i)
-        if (b == 0 && i < P) X[i] = (gp[i] - fx[s_parts[1 + i] - 1] * X[i + 1]) * fip[s_parts[1 + i] - 1];
+        if (b == 0 && i < P) X[i] = (gp[i] - fx[s_parts[1 + i] - 1] * X[i + 1]) * ipv[i];
     double xl = 0.0, xr = 0.0;
 #pragma unroll
     for (int i = 1; i < kBuildParts; ++i) {
@@ -302,7 +318,7 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
         cc[1] = make_double2(sl, sr);
     };
     // the slope and value left of the block: row a - 1 (the left separator, or row 0)
-    double s_prev = b == 0 ? 0.0 : xl, y_prev = y_sep_l;
+    double s_prev = xl, y_prev = y_sep_l;
     for (int i0 = 0; i0 < steps; i0 += kChunk) {
         double pv[kChunk], yv[kChunk];
 #pragma unroll
@@ -317,8 +333,8 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
             if (i >= steps) break;
             const int k = a + i;
             const double x = fma(-xr, fx[k], fma(-xl, fv[k], pv[q]));
-            if (i == 0 && b == 0)  // end row 0: h_1 s_0 + (h_0 + h_1) s_1 = R_0
-                s_prev = (rend0 - (h[0] + h[1]) * x) / h[1];
+            if (i == 0 && b == 0)  // s_0 = ra_0 D_0 + rb_0 D_1 - lo_0 s_1
+                s_prev = fma(ra[0], d_left, fma(rb[0], d_first, -fl[0] * x));
             if (live) put(k - 1, y_prev, yv[q], s_prev, x);
             s_prev = x;
             y_prev = yv[q];
@@ -327,8 +343,8 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
     if (mine && live) {
         if (b + 1 < P) {  // segment e between row e and the right separator
             put(e, y_prev, load_y(jb, jj, e + 1), s_prev, xr);
-        } else {  // end row K-1: (h_{K-2} + h_{K-3}) s_{K-2} + h_{K-3} s_{K-1} = R_L
-            const double s_last = (rendl - (h[K - 2] + h[K - 3]) * s_prev) / h[K - 3];
+        } else {  // s_{K-1} = ra_{K-1} D_{K-3} + rb_{K-1} D_{K-2} - lo_{K-1} s_{K-2}
+            const double s_last = fma(ra[K - 1], dprev2, fma(rb[K - 1], dprev, -fl[K - 1] * s_prev));
             put(K - 2, y_prev, load_y(jb, jj, K - 1), s_prev, s_last);
         }
     }
@@ -338,7 +354,7 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
 cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks, int max_knots,
                          unsigned *err, cudaStream_t st)
 {
-    const int smem_bytes = 7 * max_knots * (int)sizeof(double);
+    const int smem_bytes = kBuildStaged * max_knots * (int)sizeof(double);
     if (smem_bytes > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              smem_bytes);
