@@ -682,7 +682,9 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
                  o_rb = take(sizeof(double) * K), o_lo = take(sizeof(double) * K),
                  o_up = take(sizeof(double) * K),
                  o_ip = take(sizeof(double) * K), o_v = take(sizeof(double) * K),
-                 o_x = take(sizeof(double) * K), o_parts = take(sizeof(int) * (kBuildParts + 2)),
+                 o_x = take(sizeof(double) * K),
+                 o_sinv = take(sizeof(double) * (kBuildParts - 1) * (kBuildParts - 1)),
+                 o_parts = take(sizeof(int) * (kBuildParts + 2)),
                  o_coef = take(sizeof(double) * 4 * (size_t)tr->S * tr->J),
                  o_slopes = take(sizeof(double) * (size_t)K * tr->J),
                  o_pair = take(sizeof(int2) * P.pair_lm.size()), o_mp = take(sizeof(int) * N),
@@ -727,6 +729,7 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
     D.fac_ip = reinterpret_cast<const double *>(d + o_ip);
     D.fac_v = reinterpret_cast<const double *>(d + o_v);
     D.fac_x = reinterpret_cast<const double *>(d + o_x);
+    D.fac_sinv = reinterpret_cast<const double *>(d + o_sinv);
     D.parts = reinterpret_cast<const int *>(d + o_parts);
     D.coef = reinterpret_cast<double *>(d + o_coef);
     D.slopes = reinterpret_cast<double *>(d + o_slopes);
@@ -752,6 +755,7 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
         fa.ip = reinterpret_cast<double *>(d + o_ip);
         fa.v = reinterpret_cast<double *>(d + o_v);
         fa.x = reinterpret_cast<double *>(d + o_x);
+        fa.sinv = reinterpret_cast<double *>(d + o_sinv);
         fa.parts = reinterpret_cast<int *>(d + o_parts);
         e = launch_factor(D.t, K, fa, s);
     }

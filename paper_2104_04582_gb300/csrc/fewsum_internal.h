@@ -70,6 +70,7 @@ struct TrajDev {
     const double *fac_ip;  // [K] inverse pivots (block rows; separator system at separator rows)
     const double *fac_v;   // [K] block responses v to the left separator (separator multipliers)
     const double *fac_x;   // [K] block responses w to the right separator (separator couplings)
+    const double *fac_sinv;  // [(kBuildParts-1)^2] inverse of the separator system, row-major
     const int *parts;      // [kBuildParts + 2]: block count P, block starts, then K - 1
     double *slopes;        // [K][J] spline build scratch (parked elimination values)
     double *coef;          // [S][J][4] Hermite data of every segment: (y_k, y_{k+1}, s_k,
@@ -156,7 +157,7 @@ struct PlanHdr {
 // Kernel launchers (defined in the .cu files; every launcher returns the launch error).
 // Output arrays of k_factor (the trajectory's TrajDev fields of the same names).
 struct FactorArrays {
-    double *h, *inv_h, *ra, *rb, *lo, *up, *ip, *v, *x;
+    double *h, *inv_h, *ra, *rb, *lo, *up, *ip, *v, *x, *sinv;
     int *parts;
 };
 cudaError_t launch_factor(const double *t, int K, const FactorArrays &f, cudaStream_t st);

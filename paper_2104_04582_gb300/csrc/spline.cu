@@ -141,6 +141,22 @@ __global__ void k_factor(const double *__restrict__ t, int K, FactorArrays f)
         fx[sg] = cup;
         cup_prev = cup;
     }
+    // the separator system's inverse, column m from the unit right-hand side e_m (entries past
+    // P - 1 stay zero): every lane of a spline then forms its right separator's slope as one
+    // short dot product instead of a chain of 3 (P - 1) dependent operations
+    constexpr int NS = kBuildParts - 1;
+    for (int i = 0; i < NS * NS; ++i) f.sinv[i] = 0.0;
+    for (int m = 1; m < P; ++m) {
+        double gp[kBuildParts], X[kBuildParts + 1];
+        for (int i = 1; i < P; ++i) {
+            const double gi = i == m ? 1.0 : 0.0;
+            gp[i] = i == 1 ? gi : gi - fv[start[i] - 1] * gp[i - 1];
+        }
+        X[P] = 0.0;
+        for (int i = P - 1; i >= 1; --i)
+            X[i] = (gp[i] - fx[start[i] - 1] * X[i + 1]) * ip[start[i] - 1];
+        for (int i = 1; i < P; ++i) f.sinv[(i - 1) * NS + (m - 1)] = X[i];
+    }
     ra[0] = (2.0 * h1 + 3.0 * h0) / (h0 * (h0 + h1));
     rb[0] = h0 * h0 / (h1 * h1 * (h0 + h1));
     fl[0] = (h0 + h1) / h1;
@@ -174,17 +190,26 @@ __device__ __forceinline__ unsigned nonfinite_bit(double x)
 
 // kBuildParts lanes per spline column (a spline's lanes are consecutive in a warp): lane b
 // solves block b of the partitioned system (the pivot-scaled forward and back substitution with
-// the shared factors, its values parked in the slope array), the lanes exchange their blocks' end
-// values by shuffles, lane 0 solves the small separator system, and lane b corrects its rows,
-// x = y - x_left v - x_right w, and writes the Hermite data of the segments beside them.  The
-// knot-only arrays are staged in shared memory; column values are fetched kChunk rows ahead.
+// the shared factors, its values parked), the lanes exchange their blocks' end values by
+// shuffles, every lane forms its right separator's slope from the separator system's inverse,
+// and lane b corrects its rows, x = y - x_left v - x_right w.  The knot-only arrays are staged in
+// shared memory; column values are fetched kChunk rows ahead.
+//   kShared (K <= kBuildSharedKnots): values and slopes are parked in shared memory, [K][8
+//     splines], and the block writes the Hermite data of its 8 consecutive columns together at
+//     the end (a segment's 8 columns are 256 contiguous bytes).
+//   otherwise: values are parked in the trajectory's slope scratch [K][J], and each lane writes
+//     the Hermite data (y_k, y_{k+1}, s_k, s_{k+1}) of the segments beside its rows.
 constexpr int kChunk = 8;
 constexpr int kBuildStaged = 6;  // knot arrays in shared memory: ra, rb, lo, up, v, w
+constexpr int kBuildSharedKnots = 180;  // largest K parked in shared memory (< 32 KB per block)
+constexpr int kSepN = kBuildParts - 1;  // separators of a spline at most
 
+template <bool kShared>
 __global__ void __launch_bounds__(kBuildThreads)
 k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
 {
-    extern __shared__ double sk[];  // [kBuildStaged][K]
+    extern __shared__ double sk[];  // [kBuildStaged][K], then (kShared) values, slopes [K][8]
+    __shared__ double s_sinv[kSepN * kSepN];
     __shared__ int s_parts[kBuildParts + 2];
     int lo = 0, hi = n_jobs - 1;
     const int blk = blockIdx.x;
@@ -205,22 +230,29 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
         fv[k] = tr.fac_v[k];
         fx[k] = tr.fac_x[k];
     }
+    for (int i = threadIdx.x; i < kSepN * kSepN; i += blockDim.x) s_sinv[i] = tr.fac_sinv[i];
     if (threadIdx.x < kBuildParts + 2) s_parts[threadIdx.x] = tr.parts[threadIdx.x];
     __syncthreads();
     const int P = s_parts[0];
     const int b = threadIdx.x & (kBuildParts - 1);
-    const int j = (blk - jb.block_begin) * kBuildSplines + (threadIdx.x / kBuildParts);
+    const int sl = threadIdx.x / kBuildParts;  // column slot in this block
+    const int j0 = (blk - jb.block_begin) * kBuildSplines;
+    const int j = j0 + sl;
     const bool live = j < J;
     const int jj = live ? j : 0;  // a column past J computes on column 0 and stores nothing
     const bool mine = b < P;      // this lane has a block
-    double *__restrict__ slopes = tr.slopes;
+    double *yS = sk + kBuildStaged * K, *sS = yS + K * kBuildSplines;  // kShared only
+    // parked values of this column: row k at park[prow(k)]
+    double *park = kShared ? sS + sl : tr.slopes + jj;
+    auto prow = [&](int k) -> size_t {
+        return kShared ? (size_t)(k * kBuildSplines) : (size_t)k * J;
+    };
+    const bool pw = kShared || live;  // a column past J has no global row to park in
     unsigned bad = 0u;  // bit 31: some column value was not finite
     const int a = mine ? s_parts[1 + b] : 1;
     const int e = mine ? (b + 1 < P ? s_parts[2 + b] - 2 : K - 2) : 0;
     const int steps = e - a + 1;  // <= 0 for a lane without a block
-    // the left separator's inverse pivot, for lane 0's separator solve
     const bool sep = mine && b > 0;  // this lane's block has a left separator, row a - 1
-    const double ip_sep = sep ? tr.fac_ip[a - 1] : 0.0;  // its separator-system data
     const double h_sep = sep ? tr.h[a - 1] : 0.0, h_sep1 = sep ? tr.h[a - 2] : 0.0;
 
     // forward substitution over the block, g_k = ra_k D_{k-1} + rb_k D_k - lo_k g_{k-1}, parked
@@ -230,6 +262,10 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
         yc = load_y(jb, jj, a);
         bad |= nonfinite_bit(yb) | nonfinite_bit(yc);
         if (b > 0) ylm2 = load_y(jb, jj, a - 2);  // for the left separator's row
+        if (kShared) {
+            yS[(a - 1) * kBuildSplines + sl] = yb;
+            yS[a * kBuildSplines + sl] = yc;
+        }
     }
     const double y_sep_l = yb, y_first_col = yc;  // y_{a-1}, y_a
     // differences first: the phase arrays are large (1e5 rad) with small steps, and
@@ -252,7 +288,8 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
             const double r = fma(ra[k], dprev, rb[k] * dr);
             g = i == 0 ? r : fma(-fl[k], g, r);
             if (i == 0) d_first = dr;
-            if (live) slopes[(size_t)k * J + j] = g;
+            if (pw) park[prow(k)] = g;
+            if (kShared) yS[(k + 1) * kBuildSplines + sl] = ya[q];
             dprev2 = dprev;
             dprev = dr;
             yc = ya[q];
@@ -265,13 +302,13 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
         double pv[kChunk];
 #pragma unroll
         for (int q = 0; q < kChunk; ++q)
-            pv[q] = (i0 + q < steps) ? slopes[(size_t)(e - i0 - q) * J + jj] : 0.0;
+            pv[q] = (i0 + q < steps) ? park[prow(e - i0 - q)] : 0.0;
 #pragma unroll
         for (int q = 0; q < kChunk; ++q) {
             if (i0 + q >= steps) break;
             const int k = e - i0 - q;
             y_next = fma(-fu[k], y_next, pv[q]);
-            if (live) slopes[(size_t)k * J + j] = y_next;
+            if (pw) park[prow(k)] = y_next;
         }
     }
     const double y_first = y_next;  // y_a (y_e when the block has one row)
@@ -279,43 +316,32 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
     // separator system: lane b (>= 1) forms the right-hand side of its left separator row
     const double y_last_left = __shfl_up_sync(0xffffffffu, y_last, 1, kBuildParts);
     double gs = 0.0;
-    if (mine && b > 0) {
+    if (sep) {
         const int sg = a - 1;
         const double fs = fma(ra[sg], y_sep_l - ylm2, rb[sg] * (y_first_col - y_sep_l));
         gs = fs - h_sep * y_last_left - h_sep1 * y_first;
         bad |= nonfinite_bit(ylm2);
     }
-    // lane 0 of the spline solves it (FP64 issue is the scarce resource) and broadcasts
-    double X[kBuildParts + 1];
+    // lane b's right separator (number b + 1) from the inverse: X_{b+1} = sum_m Sinv[b][m-1] g_m
+    // (lanes without a separator hold g = 0, and Sinv is zero past P - 1)
+    const bool has_right = b + 1 < P;
+    const double *srow = s_sinv + (has_right ? b : 0) * kSepN;
+    double xr = 0.0;
 #pragma unroll
-    for (int i = 0; i <= kBuildParts; ++i) X[i] = 0.0;
-    double gp[kBuildParts], ipv[kBuildParts];
-#pragma unroll
-    for (int i = 1; i < kBuildParts; ++i) {
-        const double gi = __shfl_sync(0xffffffffu, gs, i, kBuildParts);
-        ipv[i] = __shfl_sync(0xffffffffu, ip_sep, i, kBuildParts);
-        gp[i] = 0.0;
-        if (b == 0 && i < P) gp[i] = i == 1 ? gi : fma(-fv[s_parts[1 + i] - 1], gp[i - 1], gi);
-    }
-#pragma unroll
-    for (int i = kBuildParts - 1; i >= 1; --i)
-        if (b == 0 && i < P) X[i] = (gp[i] - fx[s_parts[1 + i] - 1] * X[i + 1]) * ipv[i];
-    double xl = 0.0, xr = 0.0;
-#pragma unroll
-    for (int i = 1; i < kBuildParts; ++i) {
-        const double xi = __shfl_sync(0xffffffffu, X[i], 0, kBuildParts);
-        if (i == b) xl = xi;
-        if (i == b + 1) xr = xi;
-    }
+    for (int m = 1; m < kBuildParts; ++m)
+        xr = fma(srow[m - 1], __shfl_sync(0xffffffffu, gs, m, kBuildParts), xr);
+    if (!has_right) xr = 0.0;
+    const double xl_up = __shfl_up_sync(0xffffffffu, xr, 1, kBuildParts);
+    const double xl = b == 0 ? 0.0 : xl_up;
 
-    // correction, x_k = y_k - x_left v_k - x_right w_k, and the Hermite data (y_k, y_{k+1},
-    // s_k, s_{k+1}) of segments a - 1 .. e (block 0: from segment 0; the last block: to segment
-    // K-2); the consumers form the cubic's power coefficients (hermite_to_power)
+    // correction, x_k = y_k - x_left v_k - x_right w_k; the Hermite data (y_k, y_{k+1}, s_k,
+    // s_{k+1}) of every segment follow (the consumers form the power coefficients,
+    // hermite_to_power)
     double *__restrict__ coef = tr.coef;
-    auto put = [&](int seg, double yl, double yr, double sl, double sr) {
+    auto put = [&](int seg, double yl, double yr, double sl_, double sr) {
         double2 *cc = reinterpret_cast<double2 *>(coef + ((size_t)seg * J + j) * 4);
         cc[0] = make_double2(yl, yr);
-        cc[1] = make_double2(sl, sr);
+        cc[1] = make_double2(sl_, sr);
     };
     // the slope and value left of the block: row a - 1 (the left separator, or row 0)
     double s_prev = xl, y_prev = y_sep_l;
@@ -324,8 +350,8 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
 #pragma unroll
         for (int q = 0; q < kChunk; ++q) {
             const bool act = i0 + q < steps;
-            pv[q] = act ? slopes[(size_t)(a + i0 + q) * J + jj] : 0.0;
-            yv[q] = act ? load_y(jb, jj, a + i0 + q) : 0.0;
+            pv[q] = act ? park[prow(a + i0 + q)] : 0.0;
+            yv[q] = (act && !kShared) ? load_y(jb, jj, a + i0 + q) : 0.0;
         }
 #pragma unroll
         for (int q = 0; q < kChunk; ++q) {
@@ -333,19 +359,42 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
             if (i >= steps) break;
             const int k = a + i;
             const double x = fma(-xr, fx[k], fma(-xl, fv[k], pv[q]));
-            if (i == 0 && b == 0)  // s_0 = ra_0 D_0 + rb_0 D_1 - lo_0 s_1
+            if (i == 0 && b == 0) {  // s_0 = ra_0 D_0 + rb_0 D_1 - lo_0 s_1
                 s_prev = fma(ra[0], d_left, fma(rb[0], d_first, -fl[0] * x));
-            if (live) put(k - 1, y_prev, yv[q], s_prev, x);
+                if (kShared) park[0] = s_prev;
+            }
+            if (kShared) {
+                park[prow(k)] = x;
+            } else if (live) {
+                put(k - 1, y_prev, yv[q], s_prev, x);
+            }
             s_prev = x;
             y_prev = yv[q];
         }
     }
-    if (mine && live) {
-        if (b + 1 < P) {  // segment e between row e and the right separator
-            put(e, y_prev, load_y(jb, jj, e + 1), s_prev, xr);
-        } else {  // s_{K-1} = ra_{K-1} D_{K-3} + rb_{K-1} D_{K-2} - lo_{K-1} s_{K-2}
-            const double s_last = fma(ra[K - 1], dprev2, fma(rb[K - 1], dprev, -fl[K - 1] * s_prev));
-            put(K - 2, y_prev, load_y(jb, jj, K - 1), s_prev, s_last);
+    if (mine) {
+        // s_{K-1} = ra_{K-1} D_{K-3} + rb_{K-1} D_{K-2} - lo_{K-1} s_{K-2} (the last block)
+        const double s_last = fma(ra[K - 1], dprev2, fma(rb[K - 1], dprev, -fl[K - 1] * s_prev));
+        if (kShared) {
+            if (b > 0) park[prow(a - 1)] = xl;  // the left separator's slope
+            if (!has_right) park[prow(K - 1)] = s_last;
+        } else if (live) {
+            if (has_right) {  // segment e between row e and the right separator
+                put(e, y_prev, load_y(jb, jj, e + 1), s_prev, xr);
+            } else {
+                put(K - 2, y_prev, load_y(jb, jj, K - 1), s_prev, s_last);
+            }
+        }
+    }
+    if (kShared) {  // the block's 8 columns, segment by segment: 16-byte stores, 256 B per segment
+        __syncthreads();
+        constexpr int kPerSeg = 2 * kBuildSplines;
+        for (int idx = threadIdx.x; idx < (K - 1) * kPerSeg; idx += blockDim.x) {
+            const int seg = idx / kPerSeg, rr = idx - seg * kPerSeg, c = rr >> 1, half = rr & 1;
+            if (j0 + c >= J) continue;
+            const double *src = half ? sS : yS;
+            *reinterpret_cast<double2 *>(coef + ((size_t)seg * J + j0 + c) * 4 + 2 * half) =
+                make_double2(src[seg * kBuildSplines + c], src[(seg + 1) * kBuildSplines + c]);
         }
     }
     if ((bad & 0x80000000u) && live) atomicOr(err, ERRBIT_NONFINITE);
@@ -354,14 +403,17 @@ k_build(const BuildJob *__restrict__ jobs, int n_jobs, unsigned *err)
 cudaError_t launch_build(const BuildJob *jobs_dev, int n_jobs, int total_blocks, int max_knots,
                          unsigned *err, cudaStream_t st)
 {
-    const int smem_bytes = kBuildStaged * max_knots * (int)sizeof(double);
+    const bool shared = max_knots <= kBuildSharedKnots;
+    const int per_knot = kBuildStaged + (shared ? 2 * kBuildSplines : 0);
+    const int smem_bytes = per_knot * max_knots * (int)sizeof(double);
+    auto kern = shared ? k_build<true> : k_build<false>;
     if (smem_bytes > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              smem_bytes);
         if (e != cudaSuccess) return e;
     }
     if (total_blocks <= 0) return cudaSuccess;
-    k_build<<<total_blocks, kBuildThreads, smem_bytes, st>>>(jobs_dev, n_jobs, err);
+    kern<<<total_blocks, kBuildThreads, smem_bytes, st>>>(jobs_dev, n_jobs, err);
     return cudaGetLastError();
 }
 
