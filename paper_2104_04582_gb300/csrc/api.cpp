@@ -447,7 +447,6 @@ void fill_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P, unsign
     int *anc = reinterpret_cast<int *>(P.blob.data() + P.off_anc);
     size_t seg_pos = 0;
     int pair_begin = 0, fold_begin = 0, anchor_seg_begin = 0;
-    std::vector<long double> cum(n + 1, 0.0L);
     for (int q = 0; q < n; ++q) {
         const few_request &r = reqs[q];
         const few_traj *tr = r.traj;
@@ -490,15 +489,30 @@ void fill_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P, unsign
         W.fold_blocks_per_seg = (tr->plan.n_slots + kFoldThreads - 1) / kFoldThreads;
         W.fold_begin = fold_begin;
         fold_begin += tr->S * W.fold_blocks_per_seg;
-        // cost of a sample: one Horner step per slot plus the fixed per-sample phase work
-        cum[q + 1] = cum[q] + (long double)r.n_samples * (long double)(tr->plan.n_slots + 16);
     }
     P.total_pairs = pair_begin;
     P.total_fold = fold_begin;
     P.total_anchor_segs = anchor_seg_begin;
-    // equal-cost CTA slices of the concatenated (wave, sample) space
+    // CTA slices of the concatenated (wave, sample) space, cut at pass boundaries.  A pass is
+    // threads x R consecutive samples of one segment, and it costs a full pass (one Horner step
+    // per slot plus the fixed phase work, for every thread) even when its segment ends early; so
+    // every slice gets an equal share of the total pass cost, to within one pass, rather than an
+    // equal share of the samples (which left some slices several short passes more than others).
+    const long long pass = (long long)P.threads * P.R;
+    std::vector<long double> cost(n), cum(n + 1, 0.0L);
+    std::vector<long long> npass(n, 0);
+    auto seg_passes = [&](int q, int k) {
+        return (P.seg[q][k + 1] - P.seg[q][k] + pass - 1) / pass;
+    };
+    for (int q = 0; q < n; ++q) {
+        const few_traj *tr = reqs[q].traj;
+        for (int k = 0; k + 1 < tr->K; ++k) npass[q] += seg_passes(q, k);
+        cost[q] = (long double)(tr->plan.n_slots + 16);
+        cum[q + 1] = cum[q] + (long double)npass[q] * cost[q];
+    }
     const long double total = cum[n];
-    int q = 0;
+    int q = 0, sk = 0;
+    long long before = 0;  // passes of wave q before its segment sk
     cta[P.grid] = CtaStart{n, 0};
     for (int g = 0; g < P.grid; ++g) {
         if (total <= 0.0L) {
@@ -506,11 +520,21 @@ void fill_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P, unsign
             continue;
         }
         const long double x = total * g / P.grid;
-        while (q < n - 1 && cum[q + 1] <= x) ++q;
-        const long double per = (long double)(reqs[q].traj->plan.n_slots + 16);
-        long double si = std::ceil((x - cum[q]) / per);
-        int sample = (int)std::min<long double>(si, (long double)reqs[q].n_samples);
-        cta[g] = CtaStart{q, sample};
+        while (q < n - 1 && cum[q + 1] <= x) {
+            ++q;
+            sk = 0;
+            before = 0;
+        }
+        // first pass of wave q whose cost starts at or after x, then the segment holding it
+        long long k = (long long)std::ceil((x - cum[q]) / cost[q]);
+        k = std::max(0LL, std::min(k, npass[q]));
+        const int S = reqs[q].traj->K - 1;
+        while (sk < S && before + seg_passes(q, sk) <= k) {
+            before += seg_passes(q, sk);
+            ++sk;
+        }
+        const long long sample = sk < S ? P.seg[q][sk] + (k - before) * pass : reqs[q].n_samples;
+        cta[g] = CtaStart{q, (int)std::min<long long>(sample, reqs[q].n_samples)};
     }
     hdr->n_waves = n;
     hdr->total_pairs = P.total_pairs;
