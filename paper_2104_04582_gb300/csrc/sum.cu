@@ -27,8 +27,9 @@
 // scarce on this chip).  FEW_FP64 does everything else in FP64; FEW_MIXED evaluates amplitudes,
 // exponential powers and the accumulation in FP32.
 //
-// Work decomposition: a persistent grid; each CTA owns an equal-cost, contiguous slice of the
-// concatenated (waveform, sample) space (cost = samples x slots) and walks it segment by
+// Work decomposition: a persistent grid; each CTA owns a contiguous slice of the concatenated
+// (waveform, sample) space, cut at pass boundaries with equal pass cost per slice (a pass costs
+// threads x R samples x slots whether or not its segment ends first), and walks it segment by
 // segment in passes of threads x R consecutive samples, R per thread, each thread holding its
 // samples' Horner state in registers.  The segment's folded coefficient table is streamed into
 // shared memory once per pass, in tiles of stage_slots slots (the mode tile), through a ring of
