@@ -47,7 +47,7 @@ WORKLOAD = ("1-yr waveform, dt=10 s (3,155,760 samples), K=100 knots, 3843 modes
 # summarised in profiles/k_sum_mixed_1yr_3843modes.md; used only while the kernel source is the
 # one that was profiled (hash of sum.cu + phase_eval.cuh + async.cuh) and the tile is the
 # profiled one.
-PROFILED_TRAFFIC = {"source_sha256_16": "1fad30d5e67283ee", "tile": (4, 256, 1024), "bytes": 13583616 + 1536}
+PROFILED_TRAFFIC = {"source_sha256_16": "111157b0b1702c51", "tile": (4, 256, 1024), "bytes": 13573888 + 0}
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 sub-partitions x 32)
 FP64_FMA_PER_SM_CLK = 2   # FP64 FMA per SM per clock on GB300 (1.25 TFLOP/s at 152 SMs, 2.07 GHz)
 
