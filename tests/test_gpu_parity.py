@@ -236,6 +236,26 @@ def test_host_buffers_match_device_path(gpu_ctx):
     np.testing.assert_array_equal(host, g_dev)
 
 
+@pytest.mark.parametrize("pinned", [(1, 1, 1, 1), (0, 1, 1, 0), (1, 0, 0, 1)])
+def test_pinned_host_inputs_match_device_inputs(gpu_ctx, pinned):
+    """Knot arrays from page-locked and pageable host memory, in any mix, give the same spline
+    data as device-resident ones, so the same output bits."""
+    import torch
+    w = W.config1()
+    g_dev = _gpu(gpu_ctx, w, F.FEW_MIXED)
+    arrays = (w.phi_phi, w.phi_r, w.amp_re, w.amp_im)
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() if p
+            else np.ascontiguousarray(a) for a, p in zip(arrays, pinned)]
+    tr = RT.Trajectory(gpu_ctx, w.t_knots, w.modes)
+    tr.set_data_host(*host)
+    out = RT.waveform_inputs(gpu_ctx, tr, w, F.FEW_MIXED, None)
+    torch.cuda.synchronize()
+    assert gpu_ctx.sync_status() == F.FEW_OK
+    h = to_host(out)
+    tr.release()
+    np.testing.assert_array_equal(h, g_dev)
+
+
 def test_pinned_host_output_matches_device_path(gpu_ctx):
     """Page-locked host output is stored directly by the summation kernel: same bits as a
     device-resident output, in both precisions."""
