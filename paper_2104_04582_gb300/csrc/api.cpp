@@ -97,6 +97,8 @@ struct few_ctx {
     size_t in_use = 0;
     cudaMemPool_t pool = nullptr;
     cudaStream_t internal = nullptr;
+    cudaStream_t side = nullptr;  // the phase anchors, beside the harmonics and the fold
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     unsigned *d_err = nullptr;
     std::recursive_mutex mu;
     std::unordered_map<void *, size_t> sizes;
@@ -554,12 +556,21 @@ few_status launch_kernels(few_ctx *c, const PlanHdr *hdr_dev, int total_pairs, i
                           int total_anchor_segs, int grid, int threads, int R, int smem, int variant,
                           cudaStream_t st)
 {
+    // the phase anchors depend on the splines only: they run on the side stream beside the
+    // harmonics and the fold (FP64-pipe work next to latency-bound work), joined before the sum
+    const bool fork = total_anchor_segs > 0;
+    if (fork) {
+        FEW_CUDA_TRY(cudaEventRecord(c->fork_ev, st));
+        FEW_CUDA_TRY(cudaStreamWaitEvent(c->side, c->fork_ev, 0));
+        FEW_CUDA_TRY(launch_anchor(hdr_dev, total_anchor_segs, c->side));
+        FEW_CUDA_TRY(cudaEventRecord(c->join_ev, c->side));
+    }
     tmark(c, 1, false, st);
     FEW_CUDA_TRY(launch_ylm(hdr_dev, total_pairs, variant == kVariantFp64, st));
     tmark(c, 1, true, st);
     tmark(c, 2, false, st);
     FEW_CUDA_TRY(launch_fold(hdr_dev, total_fold, variant == kVariantFp64, st));
-    FEW_CUDA_TRY(launch_anchor(hdr_dev, total_anchor_segs, st));
+    if (fork) FEW_CUDA_TRY(cudaStreamWaitEvent(st, c->join_ev, 0));
     tmark(c, 2, true, st);
     tmark(c, 3, false, st);
     FEW_CUDA_TRY(launch_sum(hdr_dev, grid, threads, R, smem, variant, st));
@@ -604,6 +615,11 @@ few_status few_ctx_create(few_ctx **out, int device, size_t hbm_budget_bytes)
     auto fail = [&](few_status s) {
         if (c->d_err) cudaFree(c->d_err);
         if (c->internal) cudaStreamDestroy(c->internal);
+        if (c->side) cudaStreamDestroy(c->side);
+        if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+        if (c->join_ev) cudaEventDestroy(c->join_ev);
+        for (auto &e : c->tev)
+            if (e) cudaEventDestroy(e);
         if (c->pool) cudaMemPoolDestroy(c->pool);
         (void)cudaGetLastError();
         delete c;
@@ -620,7 +636,10 @@ few_status few_ctx_create(few_ctx **out, int device, size_t hbm_budget_bytes)
     if (cudaMemPoolCreate(&c->pool, &props) != cudaSuccess) return fail(FEW_ERR_CUDA);
     uint64_t thresh = UINT64_MAX;
     cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thresh);
-    if (cudaStreamCreateWithFlags(&c->internal, cudaStreamNonBlocking) != cudaSuccess)
+    if (cudaStreamCreateWithFlags(&c->internal, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess)
         return fail(FEW_ERR_CUDA);
     if (cudaMalloc(&c->d_err, sizeof(unsigned)) != cudaSuccess) return fail(FEW_ERR_NOMEM);
     if (cudaMemset(c->d_err, 0, sizeof(unsigned)) != cudaSuccess) return fail(FEW_ERR_CUDA);
@@ -654,6 +673,9 @@ few_status few_ctx_destroy(few_ctx *ctx)
         ctx->pinned.release();
         cudaFree(ctx->d_err);
         cudaStreamDestroy(ctx->internal);
+        cudaStreamDestroy(ctx->side);
+        cudaEventDestroy(ctx->fork_ev);
+        cudaEventDestroy(ctx->join_ev);
         cudaMemPoolDestroy(ctx->pool);
         (void)cudaGetLastError();
     }
@@ -1248,9 +1270,17 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
             if (b->n_jobs)
                 launch_build(static_cast<const BuildJob *>(b->jobs_dev), b->n_jobs, b->build_blocks,
                              b->max_knots, ctx->d_err, cap);
+            // the same fork and join as launch_kernels, recorded into the graph
+            const bool fork = b->total_anchor_segs > 0;
+            if (fork) {
+                cudaEventRecord(ctx->fork_ev, cap);
+                cudaStreamWaitEvent(ctx->side, ctx->fork_ev, 0);
+                launch_anchor(hd, b->total_anchor_segs, ctx->side);
+                cudaEventRecord(ctx->join_ev, ctx->side);
+            }
             launch_ylm(hd, b->total_pairs, b->fp64, cap);
             launch_fold(hd, b->total_fold, b->fp64, cap);
-            launch_anchor(hd, b->total_anchor_segs, cap);
+            if (fork) cudaStreamWaitEvent(cap, ctx->join_ev, 0);
             launch_sum(hd, b->grid, b->threads, b->R, b->smem, b->variant, cap);
             e = cudaStreamEndCapture(cap, &b->graph);
         }
