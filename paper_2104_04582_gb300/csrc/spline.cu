@@ -28,9 +28,11 @@
 
 namespace fewsum {
 
-// Partitioned factorisation of the reduced not-a-knot matrix of one knot grid (single thread;
-// O(K)), rows k = 1..K-2 with diagonal dg(k), lower coefficient sub(k) = h_k (k >= 2) and upper
-// sup(k) = h_{k-1} (k <= K-3).  The rows are split into P blocks separated by single rows (the
+constexpr int kFactorThreads = 32;  // one warp: per-knot loops strided, one thread per block
+
+// Partitioned factorisation of the reduced not-a-knot matrix of one knot grid (one warp; O(K)
+// work, each block's elimination on its own thread), rows k = 1..K-2 with diagonal dg(k), lower
+// coefficient sub(k) = h_k (k >= 2) and upper sup(k) = h_{k-1} (k <= K-3).  The rows are split into P blocks separated by single rows (the
 // separators): block b spans rows start_b .. start_b + size_b - 1, separator b + 1 is the row
 // after it.  With x_sigma the separators' unknowns, block b's rows solve
 //     A_b x_b = f_b - sub(first) x_{sigma_b} e_first - sup(last) x_{sigma_{b+1}} e_last,
@@ -57,17 +59,23 @@ namespace fewsum {
 //     lo_{K-1} s_{K-2}
 // (the end rows divided by h_1 and hc).  K >= 4, so rows 1 and K-2 are distinct, and neither is
 // a separator.
-__global__ void k_factor(const double *__restrict__ t, int K, FactorArrays f)
+__global__ void __launch_bounds__(kFactorThreads) k_factor(const double *__restrict__ t, int K,
+                                                             FactorArrays f)
 {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    if (blockIdx.x != 0) return;
+    const int tid = threadIdx.x, nt = blockDim.x;
     double *h = f.h, *ip = f.ip, *fl = f.lo, *fu = f.up, *fv = f.v, *fx = f.x, *ra = f.ra,
            *rb = f.rb;
     const int S = K - 1, n = K - 2;
-    for (int k = 0; k < S; ++k) {
+    // knot widths and cleared arrays (every thread a stride of k)
+    for (int k = tid; k < S; k += nt) {
         h[k] = t[k + 1] - t[k];
         f.inv_h[k] = 1.0 / h[k];
     }
-    for (int k = 0; k < K; ++k) ip[k] = fl[k] = fu[k] = fv[k] = fx[k] = ra[k] = rb[k] = 0.0;
+    for (int k = tid; k < K; k += nt) ip[k] = fl[k] = fu[k] = fv[k] = fx[k] = ra[k] = rb[k] = 0.0;
+    constexpr int NS = kBuildParts - 1;
+    for (int i = tid; i < NS * NS; i += nt) f.sinv[i] = 0.0;
+    __syncthreads();
     auto dg = [&](int k) {
         if (k == 1) return h[0] + h[1];
         if (k == K - 2) return h[K - 3] + h[K - 2];
@@ -75,15 +83,18 @@ __global__ void k_factor(const double *__restrict__ t, int K, FactorArrays f)
     };
     auto sub = [&](int k) { return k >= 2 ? h[k] : 0.0; };
     auto sup = [&](int k) { return k <= K - 3 ? h[k - 1] : 0.0; };
-    for (int k = 2; k <= K - 3; ++k) {
+    for (int k = 2 + tid; k <= K - 3; k += nt) {
         ra[k] = 3.0 * h[k] * f.inv_h[k - 1];
         rb[k] = 3.0 * h[k - 1] * f.inv_h[k];
     }
     const double h0 = h[0], h1 = h[1], hc = h[K - 3], hd = h[K - 2];
-    ra[1] = h1 * h1 / (h0 * (h0 + h1));
-    rb[1] = h0 * (2.0 * h0 + 3.0 * h1) / (h1 * (h0 + h1));
-    ra[K - 2] = hd * (3.0 * hc + 2.0 * hd) / (hc * (hc + hd));
-    rb[K - 2] = hc * hc / (hd * (hc + hd));
+    if (tid == 0) {
+        ra[1] = h1 * h1 / (h0 * (h0 + h1));
+        rb[1] = h0 * (2.0 * h0 + 3.0 * h1) / (h1 * (h0 + h1));
+        ra[K - 2] = hd * (3.0 * hc + 2.0 * hd) / (hc * (hc + hd));
+        rb[K - 2] = hc * hc / (hd * (hc + hd));
+    }
+    // the partition (every thread derives the same)
     int P = (n + 1) / 2;
     if (P > kBuildParts) P = kBuildParts;
     if (P < 1) P = 1;
@@ -95,9 +106,13 @@ __global__ void k_factor(const double *__restrict__ t, int K, FactorArrays f)
         k += base + (b < extra ? 1 : 0) + 1;  // block rows, then its right separator
     }
     start[P] = K - 1;
-    f.parts[0] = P;
-    for (int b = 0; b <= P; ++b) f.parts[1 + b] = start[b];
-    for (int b = 0; b < P; ++b) {
+    if (tid == 0) {
+        f.parts[0] = P;
+        for (int b = 0; b <= P; ++b) f.parts[1 + b] = start[b];
+    }
+    __syncthreads();
+    // each block's elimination, responses and scaled rows: independent, one thread per block
+    for (int b = tid; b < P; b += nt) {
         const int a = start[b], e = (b + 1 < P ? start[b + 1] - 1 : K - 1) - 1;
         double p = dg(a);
         ip[a] = 1.0 / p;
@@ -124,29 +139,39 @@ __global__ void k_factor(const double *__restrict__ t, int K, FactorArrays f)
             rb[r] *= ip[r];
         }
     }
-    double piv = 0.0, cup_prev = 0.0;
-    for (int i = 1; i < P; ++i) {
-        const int sg = start[i] - 1, L = sg - 1, F = sg + 1;
-        const double D = dg(sg) - sub(sg) * fx[L] - sup(sg) * fv[F];
-        const double clo = -sub(sg) * fv[L], cup = -sup(sg) * fx[F];
-        double mu = 0.0;
-        if (i == 1) {
-            piv = D;
-        } else {
-            mu = clo / piv;
-            piv = D - mu * cup_prev;
+    __syncthreads();
+    // the separator system's elimination (sequential, P - 1 <= 7 rows) and the end slopes
+    if (tid == 0) {
+        double piv = 0.0, cup_prev = 0.0;
+        for (int i = 1; i < P; ++i) {
+            const int sg = start[i] - 1, L = sg - 1, F = sg + 1;
+            const double D = dg(sg) - sub(sg) * fx[L] - sup(sg) * fv[F];
+            const double clo = -sub(sg) * fv[L], cup = -sup(sg) * fx[F];
+            double mu = 0.0;
+            if (i == 1) {
+                piv = D;
+            } else {
+                mu = clo / piv;
+                piv = D - mu * cup_prev;
+            }
+            fv[sg] = mu;
+            ip[sg] = 1.0 / piv;
+            fx[sg] = cup;
+            cup_prev = cup;
         }
-        fv[sg] = mu;
-        ip[sg] = 1.0 / piv;
-        fx[sg] = cup;
-        cup_prev = cup;
+        ra[0] = (2.0 * h1 + 3.0 * h0) / (h0 * (h0 + h1));
+        rb[0] = h0 * h0 / (h1 * h1 * (h0 + h1));
+        fl[0] = (h0 + h1) / h1;
+        ra[K - 1] = hd * hd / (hc * hc * (hc + hd));
+        rb[K - 1] = (2.0 * hc + 3.0 * hd) / (hd * (hc + hd));
+        fl[K - 1] = (hc + hd) / hc;
     }
-    // the separator system's inverse, column m from the unit right-hand side e_m (entries past
-    // P - 1 stay zero): every lane of a spline then forms its right separator's slope as one
-    // short dot product instead of a chain of 3 (P - 1) dependent operations
-    constexpr int NS = kBuildParts - 1;
-    for (int i = 0; i < NS * NS; ++i) f.sinv[i] = 0.0;
-    for (int m = 1; m < P; ++m) {
+    __syncthreads();
+    // the separator system's inverse, column m from the unit right-hand side e_m (one thread per
+    // column; entries past P - 1 stay zero): every lane of a spline then forms its right
+    // separator's slope as one short dot product instead of a chain of 3 (P - 1) dependent
+    // operations
+    for (int m = 1 + tid; m < P; m += nt) {
         double gp[kBuildParts], X[kBuildParts + 1];
         for (int i = 1; i < P; ++i) {
             const double gi = i == m ? 1.0 : 0.0;
@@ -157,17 +182,11 @@ __global__ void k_factor(const double *__restrict__ t, int K, FactorArrays f)
             X[i] = (gp[i] - fx[start[i] - 1] * X[i + 1]) * ip[start[i] - 1];
         for (int i = 1; i < P; ++i) f.sinv[(i - 1) * NS + (m - 1)] = X[i];
     }
-    ra[0] = (2.0 * h1 + 3.0 * h0) / (h0 * (h0 + h1));
-    rb[0] = h0 * h0 / (h1 * h1 * (h0 + h1));
-    fl[0] = (h0 + h1) / h1;
-    ra[K - 1] = hd * hd / (hc * hc * (hc + hd));
-    rb[K - 1] = (2.0 * hc + 3.0 * hd) / (hd * (hc + hd));
-    fl[K - 1] = (hc + hd) / hc;
 }
 
 cudaError_t launch_factor(const double *t, int K, const FactorArrays &f, cudaStream_t st)
 {
-    k_factor<<<1, 32, 0, st>>>(t, K, f);
+    k_factor<<<1, kFactorThreads, 0, st>>>(t, K, f);
     return cudaGetLastError();
 }
 
