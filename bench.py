@@ -568,33 +568,42 @@ def bench_stress_c5(ctx, dev, stream, sh, reps, tune_cache):
 def bench_serving_c4(ctx, n_req, budget_gb, tune_cache, loads=(0.5, 0.9, 1.2)):
     """Serving: a Poisson request stream from an MCMC-like client (0.5-4 yr, dt in {5,10,15} s,
     10-1000 modes, perturbed angles, phases and scale of resident trajectories, 10 % new ones),
-    continuous batching with HBM-budget admission.  Capacity = completions/s of the whole stream
-    submitted at once; then the stream at 50/90/120 % of that rate; the plain FP64 path's
-    capacity on a tenth of the stream."""
+    continuous batching with HBM-budget admission.  Every run starts with no trajectory on the
+    device: the first request of each trajectory brings its knot data, and the server creates
+    the trajectory and builds its splines on that request's path.  Capacity = completions/s of
+    the whole stream submitted at once; then the stream at 50/90/120 % of that rate; the plain
+    FP64 path's capacity on a tenth of the stream."""
+    import dataclasses
     import torch
     from paper_2104_04582_gb300 import fewsum as F
-    from paper_2104_04582_gb300 import runtime as RT
     from paper_2104_04582_gb300.serve import GpuEngine, Request, Server
     trajs_in, stream = W.config4_stream(n_req, rate_hz=1.0)
-    trajs = {k: RT.from_inputs(ctx, w) for k, w in trajs_in.items()}
+    slots_of = {k: F.few_mode_slots(w.modes)[0] for k, w in trajs_in.items()}
 
     def reqs_for(prec):
-        out = []
+        out, seen = [], set()
         for r in stream:
             w = trajs_in[r.traj_key]
+            first = r.traj_key not in seen
+            seen.add(r.traj_key)
             out.append(Request(traj_key=r.traj_key, n_samples=w.n_samples, dt=w.dt, t0=w.t0,
                                theta=r.theta, phi=r.phi, scale=r.scale, dphi_phi0=r.dphi_phi0,
-                               dphi_r0=r.dphi_r0, prec=prec))
+                               dphi_r0=r.dphi_r0, prec=prec, traj_inputs=w if first else None))
         return out
 
-    engine = GpuEngine(ctx, trajs)
     mixed, plain_reqs = reqs_for(F.FEW_MIXED), reqs_for(F.FEW_FP64)
-    work = lambda r: r.n_samples * trajs[r.traj_key].info[2]
-    median_req = sorted(mixed, key=work)[len(mixed) // 2]
-    engine.tune_tiles(median_req, tune_cache)
-    engine.tune_tiles(sorted(plain_reqs, key=work)[len(plain_reqs) // 2], tune_cache)
+    work = lambda r: r.n_samples * slots_of[r.traj_key]
+    tuner = GpuEngine(ctx)
+    tiles = {}
+    for reqs in (mixed, plain_reqs):
+        med = sorted(reqs, key=work)[len(reqs) // 2]
+        med = dataclasses.replace(med, traj_inputs=trajs_in[med.traj_key])
+        tiles[med.prec] = tuner.tune_tiles(med, tune_cache)
+    torch.cuda.synchronize()
+    tuner.close()
 
     def run(reqs, rate_hz=None, seed=0):
+        engine = GpuEngine(ctx)  # no trajectory resident: each is created by its first request
         srv = Server(engine, hbm_budget_bytes=int(budget_gb * 2 ** 30), max_batch=16,
                      max_inflight=3)
         rng = np.random.default_rng(seed)
@@ -614,6 +623,8 @@ def bench_serving_c4(ctx, n_req, budget_gb, tune_cache, loads=(0.5, 0.9, 1.2)):
         srv.close()
         for f in futs:
             f.result()
+        torch.cuda.synchronize()
+        engine.close()
         st["wall_s"] = wall
         st["offered_rate_hz"] = rate_hz
         return st
@@ -635,11 +646,13 @@ def bench_serving_c4(ctx, n_req, budget_gb, tune_cache, loads=(0.5, 0.9, 1.2)):
         raise RuntimeError("device error in the serving run")
     samples = [trajs_in[r.traj_key].n_samples for r in stream]
     modes = [trajs_in[r.traj_key].N for r in stream]
-    slot_samples = sum(trajs[r.traj_key].info[2] * trajs_in[r.traj_key].n_samples for r in stream)
-    res = {"requests": n_req, "trajectories": len(trajs),
+    slot_samples = sum(slots_of[r.traj_key] * trajs_in[r.traj_key].n_samples for r in stream)
+    res = {"requests": n_req, "trajectories": len(trajs_in),
+           "trajectory_creation": "on the request path: the first request of each trajectory "
+                                  "creates it and builds its splines from host knot data",
            "mean_samples": float(np.mean(samples)), "mean_modes": float(np.mean(modes)),
            "budget_gb": budget_gb, "max_batch": 16, "max_inflight": 3,
-           "tiles": {("mixed" if p == F.FEW_MIXED else "fp64"): list(t) for p, t in engine.tiles.items()},
+           "tiles": {("mixed" if p == F.FEW_MIXED else "fp64"): list(t) for p, t in tiles.items()},
            "capacity_mixed": {"value": cap, "unit": "waveforms/s", "p50_ms": burst["p50_ms"],
                               "p99_ms": burst["p99_ms"],
                               "c2_equivalent_waveforms_per_s_by_slot_samples":
@@ -649,12 +662,10 @@ def bench_serving_c4(ctx, n_req, budget_gb, tune_cache, loads=(0.5, 0.9, 1.2)):
                                    "requests": plain["completed"], "p50_ms": plain["p50_ms"],
                                    "p99_ms": plain["p99_ms"]},
            "workload": "Poisson MCMC-like stream: 0.5-4 yr, dt in {5,10,15} s, 10-1000 modes, "
-                       "perturbed angles/phases/scale of resident trajectories, 10% new ones",
+                       "perturbed angles/phases/scale of resident trajectories, 10% new ones "
+                       "(created on their first request's path)",
            "seed": W.SEEDS["C4"]}
     res["capacity_vs_plain_fp64"] = cap / res["plain_fp64_capacity"]["value"]
-    for t_ in trajs.values():
-        t_.release()
-    torch.cuda.synchronize()
     return res
 
 

@@ -3,7 +3,10 @@
 Requests arrive as an MCMC sampler emits them (different durations, cadences, mode counts,
 angles and phase offsets of resident trajectories).  The server
 
-* keeps trajectory splines resident on the device (registered once per trajectory key);
+* keeps trajectory splines resident on the device (registered once per trajectory key); a
+  request may bring the knot data of a trajectory the server does not hold yet, which is then
+  created and its splines built on that request's path (the paper's sampler proposes new
+  trajectories as well as new angles and phases of known ones);
 * admits queued requests in arrival order while their device memory (output + plan scratch)
   fits the HBM budget and a launch slot is free -- requests that arrive while others run are
   admitted as soon as slots and memory free up;
@@ -50,6 +53,9 @@ class Request:
     dphi_r0: float = 0.0
     prec: int = F.FEW_MIXED
     out_c64: Optional[bool] = None
+    # knot data (t_knots, modes, phi_phi, phi_r, amp_re, amp_im) of a trajectory the engine may
+    # not hold yet: created under traj_key before the first group that uses it runs
+    traj_inputs: Any = None
 
     def c64(self) -> bool:
         return self.prec == F.FEW_MIXED if self.out_c64 is None else bool(self.out_c64)
@@ -103,7 +109,11 @@ class Server:
     # ------------------------------------------------------------------ API
     def submit(self, req: Request) -> cf.Future:
         fut: cf.Future = cf.Future()
-        need = req.out_bytes() + self.engine.scratch_bytes(req)
+        try:
+            need = req.out_bytes() + self.engine.scratch_bytes(req)
+        except Exception as e:  # noqa: BLE001 -- e.g. an unknown trajectory without knot data
+            fut.set_exception(AdmissionError(f"request cannot be sized: {e}"))
+            return fut
         if need > self.budget:
             fut.set_exception(AdmissionError(f"request needs {need} bytes > budget {self.budget}"))
             return fut
@@ -264,20 +274,60 @@ class Server:
 class GpuEngine:
     """Executes request groups with libfewsum.so: one batched plan per group, worker streams."""
 
-    def __init__(self, ctx, trajectories: Dict[Any, Any], n_streams: int = 3):
+    def __init__(self, ctx, trajectories: Optional[Dict[Any, Any]] = None, n_streams: int = 3):
         import torch
         self.torch = torch
         self.ctx = ctx
-        self.trajs = trajectories  # key -> runtime.Trajectory (spline data set)
+        # key -> runtime.Trajectory (spline data set); the caller's stay the caller's
+        self.trajs: Dict[Any, Any] = dict(trajectories or {})
+        self._owned: List[Any] = []  # keys of trajectories this engine created
+        self._ready: Dict[Any, Any] = {}  # key -> event after its spline build
+        # knot data announced by submitted requests, until their trajectory exists (later
+        # requests of a new trajectory may be submitted before the first one runs)
+        self._announced: Dict[Any, Any] = {}
         self.streams = [torch.cuda.Stream(device=ctx.device) for _ in range(n_streams)]
         self._next = 0
         self.tiles: Dict[int, tuple] = {}  # precision -> installed (R, threads, stage_slots)
+
+    def _ensure_traj(self, req: Request, stream) -> Any:
+        """The request's trajectory, created from its knot data (splines built on `stream`)
+        if the engine does not hold it yet."""
+        tr = self.trajs.get(req.traj_key)
+        if tr is None:
+            w = req.traj_inputs if req.traj_inputs is not None else self._announced.get(req.traj_key)
+            if w is None:
+                raise KeyError(f"unknown trajectory {req.traj_key!r} and no knot data")
+            from . import runtime as RT
+            tr = RT.Trajectory(self.ctx, w.t_knots, w.modes)
+            try:
+                tr.set_data_host(w.phi_phi, w.phi_r, w.amp_re, w.amp_im,
+                                 stream=int(stream.cuda_stream))
+            except Exception:
+                tr.release()
+                raise
+            ev = self.torch.cuda.Event()
+            ev.record(stream)  # groups on other streams wait for the build
+            self.trajs[req.traj_key] = tr
+            self._ready[req.traj_key] = ev
+            self._owned.append(req.traj_key)
+            self._announced.pop(req.traj_key, None)
+        return tr
+
+    def close(self) -> None:
+        """Release the trajectories this engine created (their work must have completed)."""
+        for k in self._owned:
+            tr = self.trajs.pop(k, None)
+            self._ready.pop(k, None)
+            if tr is not None:
+                tr.release()
+        self._owned = []
 
     def tune_tiles(self, req: Request, cache_path: Optional[str] = tune.DEFAULT_CACHE) -> tuple:
         """Install the tile of `req`'s workload bucket (tuning on a cache miss, timed on `req`
         itself) for its precision; every later group of that precision runs with it."""
         torch = self.torch
-        tr = self.trajs[req.traj_key]
+        tr = self._ensure_traj(req, self.streams[0])
+        torch.cuda.synchronize()
         K, N, slots = tr.info
         out = self.alloc_out(req)
         rq = F.make_request(tr.handle, out.data_ptr(), req.n_samples, req.t0, req.dt, req.theta,
@@ -290,8 +340,18 @@ class GpuEngine:
         return tuple(choice)
 
     def scratch_bytes(self, req: Request) -> int:
-        tr = self.trajs[req.traj_key]
-        K, N, slots = tr.info
+        """Plan scratch of `req` (called by Server.submit for every request, which also lets
+        the engine note the knot data a request brings)."""
+        tr = self.trajs.get(req.traj_key)
+        if req.traj_inputs is not None and tr is None:
+            self._announced.setdefault(req.traj_key, req.traj_inputs)
+        if tr is not None:
+            K, N, slots = tr.info
+        else:  # not created yet: sized from its knot data
+            w = self._announced.get(req.traj_key)
+            if w is None:
+                raise KeyError(f"unknown trajectory {req.traj_key!r} and no knot data")
+            K, slots = len(w.t_knots), F.few_mode_slots(w.modes)[0]
         elem = 8 if req.prec == F.FEW_FP64 else 4
         return (K - 1) * slots * 8 * elem + 64 * 1024
 
@@ -306,6 +366,12 @@ class GpuEngine:
         torch = self.torch
         s = self.streams[self._next % len(self.streams)]
         self._next += 1
+        for r in reqs:
+            self._ensure_traj(r, s)
+        for k in {r.traj_key for r in reqs}:
+            ev = self._ready.get(k)
+            if ev is not None:
+                s.wait_event(ev)
         rq = [F.make_request(self.trajs[r.traj_key].handle, o.data_ptr(), r.n_samples, r.t0, r.dt,
                              r.theta, r.phi, r.scale, r.prec, r.c64(), F.FEW_MEM_DEVICE,
                              r.dphi_phi0, r.dphi_r0) for r, o in zip(reqs, outs)]

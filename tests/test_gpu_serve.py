@@ -66,3 +66,36 @@ def test_serving_results_same_alone_and_in_the_mix(gpu_ctx, budget_gb):
     srv.close()
     for tr in trajs.values():
         tr.release()
+
+
+def test_serving_creates_new_trajectories_on_first_use(gpu_ctx):
+    """An engine that starts empty: the first request of each trajectory brings its knot data,
+    the engine creates the trajectory and builds its splines on that request's path, later
+    requests reuse it; the results equal those on trajectories created beforehand."""
+    import torch
+    trajs_in, stream = W.config4_stream(20, rate_hz=400.0, seed=W.SEEDS["C4"] + 7, p_new=0.3)
+    reqs, seen = [], set()
+    for r in _requests(trajs_in, stream):
+        if r.traj_key not in seen:
+            r.traj_inputs = trajs_in[r.traj_key]
+            seen.add(r.traj_key)
+        reqs.append(r)
+    assert len(seen) >= 3
+    engine = GpuEngine(gpu_ctx)
+    srv = Server(engine, hbm_budget_bytes=8 * 2 ** 30, max_batch=4, max_inflight=2)
+    futs = [srv.submit(r) for r in reqs]
+    assert srv.drain(timeout=600)
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert sorted(engine.trajs) == sorted(seen)
+    ref = {k: RT.from_inputs(gpu_ctx, w) for k, w in trajs_in.items()}
+    for r, f in zip(reqs, futs):
+        alone = RT.waveform(gpu_ctx, ref[r.traj_key], r.n_samples, r.t0, r.dt, r.theta, r.phi,
+                            r.prec, scale=r.scale, dphi_phi0=r.dphi_phi0, dphi_r0=r.dphi_r0)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(to_host(alone), to_host(f.result()))
+    srv.close()
+    engine.close()
+    assert not engine.trajs
+    for tr in ref.values():
+        tr.release()

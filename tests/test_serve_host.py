@@ -138,3 +138,21 @@ def test_fault_injection_and_cancellation():
     st = srv.stats()
     assert st["failed"] == 3
     srv.close()
+
+
+def test_request_that_cannot_be_sized_is_refused_through_its_future():
+    """An engine that cannot size a request (an unknown trajectory without knot data) refuses
+    it through the future; the server keeps serving the others."""
+    class Picky(FakeEngine):
+        def scratch_bytes(self, req):
+            if req.traj_key == 2:
+                raise KeyError("unknown trajectory 2 and no knot data")
+            return 1000
+    eng = Picky()
+    srv = Server(eng, hbm_budget_bytes=10 ** 9, max_batch=4, max_inflight=2)
+    futs = [srv.submit(_req(k)) for k in range(5)]
+    assert srv.drain(timeout=20)
+    with pytest.raises(AdmissionError, match="cannot be sized"):
+        futs[2].result()
+    assert [futs[k].result()["value"][0] for k in (0, 1, 3, 4)] == [0, 1, 3, 4]
+    srv.close()
