@@ -1180,7 +1180,8 @@ few_status few_rb_amplitudes(few_ctx *ctx, const few_basis *b, const double *are
     cudaError_t e = launch_rb(are, aim, M, b->Nb, b->N, nu, fp64, b->bre, b->bim, b->gt64, b->gt32,
                               b->bexp, b->bpack, reinterpret_cast<double *>(p),
                               reinterpret_cast<int *>(p + sc_bytes), p + sc_bytes + ex_bytes, ore,
-                              oim, ctx->d_err, ctx->sm_count, s);
+                              oim, ctx->d_err, ctx->sm_count, s, ctx->side, ctx->fork_ev,
+                              ctx->join_ev);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         st = FEW_ERR_CUDA;

@@ -207,7 +207,8 @@ cudaError_t launch_rb(const double *are, const double *aim, int M, int Nb, int N
                       bool fp64, const double *bre, const double *bim, const double2 *gt64,
                       const float2 *gt32, const int *bexp, const unsigned char *bpack, double *scale,
                       int *aexp, unsigned char *apack, double *ore, double *oim, unsigned *err,
-                      int sm_count, cudaStream_t st);
+                      int sm_count, cudaStream_t st, cudaStream_t side, cudaEvent_t fork_ev,
+                      cudaEvent_t join_ev);
 // Maximum resident CTAs per SM of the summation kernel for a configuration (0 if invalid).
 int sum_occupancy(int variant, int samples_per_thread, int threads, int smem_bytes);
 // One-time kernel attribute setup (dynamic shared memory opt-in).

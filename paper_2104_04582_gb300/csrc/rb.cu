@@ -9,7 +9,7 @@
 //
 // FP64 path: a tiled complex GEMM on the FP64 pipe.
 // Mixed path: the complex product as one real GEMM on the tcgen05 tensor cores,
-//     [Re A_i, Im A_i] = sum_q a_q Bhat_q,(2i, 2i+1),  a = [Re(s alpha) | Im(s alpha)] (2 Nb),
+//     [Re A_i, Im A_i] = s sum_q a_q Bhat_q,(2i, 2i+1),  a = [Re alpha | Im alpha] (2 Nb),
 //     Bhat_q,2i = (Re B_qi | -Im B_qi),  Bhat_q,2i+1 = (Im B_qi | Re B_qi),
 // in fp16 with FP32 accumulation in tensor memory.  To keep near-FP32 accuracy every operand is
 // split into two fp16 parts x = hi + lo (11 significant bits each) and the three products of
@@ -17,7 +17,9 @@
 // 3 x 2 Nb sums them all.  fp16's narrow exponent range is handled by exact power-of-two
 // scaling: each knot's coefficient row and each mode's basis column are scaled so that their
 // largest magnitude lies in [2^14, 2^15) before the split, and the epilogue multiplies the
-// accumulator back by both inverse powers.  An entry far below its row or column maximum keeps
+// accumulator back by both inverse powers and by the knot's renormalisation s (so the scale's
+// kernels run beside the coefficient pack, on a second stream, and are joined before the
+// product).  An entry far below its row or column maximum keeps
 // an absolute error near 2^-24 of that maximum.
 //
 // The product is computed transposed, A^T = Bhat^T a^T: the MMA's M side (tensor-memory lanes)
@@ -356,17 +358,16 @@ __global__ void k_rb_norm(const double *__restrict__ q, const double *__restrict
 }
 
 // Coefficient operand (the MMA's B side), one warp per row: row k of tile k/256, column
-// c = g * 2Nb + q holds part
-// part_a(g) of 2^aexp[k] x_q, x_q = s_k alpha_k,q (real parts for q < Nb, imaginary parts after).
-// The row's x_q are formed once (one FP64 product each, converted on the integer pipe) in shared
+// c = g * 2Nb + q holds part part_a(g) of 2^aexp[k] x_q, x_q = alpha_k,q (real parts for q < Nb,
+// imaginary parts after; the renormalisation s_k is applied by the product's epilogue, so this
+// pack does not wait for it).  The row's x_q are converted once (on the integer pipe) into shared
 // memory, its largest magnitude sets aexp[k], then the lanes write its 16-byte chunks.  Rows past
 // M are zero.
 constexpr int kRbPackWarps = 8;
 
 __global__ void __launch_bounds__(kRbPackWarps * 32)
 k_rb_pack_a(const double *__restrict__ are, const double *__restrict__ aim, int M, int Nb, int n_kb,
-            int m_tiles, const double *__restrict__ scale, unsigned char *__restrict__ apack,
-            int *__restrict__ aexp)
+            int m_tiles, unsigned char *__restrict__ apack, int *__restrict__ aexp)
 {
     __shared__ float xs[kRbPackWarps][2 * FEW_MAX_BASIS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, Kr = 2 * Nb;
@@ -374,10 +375,9 @@ k_rb_pack_a(const double *__restrict__ are, const double *__restrict__ aim, int 
     const int rows = m_tiles * kRbTileN, chunks = n_kb * (kRbTileK / 8);
     for (int row = blockIdx.x * kRbPackWarps + w; row < rows; row += gridDim.x * kRbPackWarps) {
         const bool live = row < M;
-        const double s = (live && scale) ? scale[row] : 1.0;
         float mx = 0.0f;
         for (int q = lane; q < Kr; q += 32) {
-            x[q] = live ? f64_to_f32(s * (q < Nb ? are[(size_t)row * Nb + q] : aim[(size_t)row * Nb + q - Nb]))
+            x[q] = live ? f64_to_f32(q < Nb ? are[(size_t)row * Nb + q] : aim[(size_t)row * Nb + q - Nb])
                         : 0.0f;
             mx = fmaxf(mx, fabsf(x[q]));
         }
@@ -466,6 +466,7 @@ struct RbMmaArgs {
     const unsigned char *bpack;  // basis: [n_tiles][n_kb] blocks of kRbABytes (A operand)
     double *out_re, *out_im;     // [M][N]
     const int *aexp, *bexp;      // scaling exponents of the coefficient rows and basis columns
+    const double *scale;         // [M] renormalisation s_k, applied in the epilogue (or null)
     int M, N, n_kb, m_tiles, n_tiles;
     unsigned *err;
 };
@@ -589,7 +590,9 @@ __global__ void __launch_bounds__(kRbMmaThreads, 1) k_rb_mma(RbMmaArgs a)
                 uint32_t v[32];
                 tc_ld32(tmem + (uint32_t)(b * kRbTileN) + ((uint32_t)(32 * qd) << 16) + (uint32_t)(32 * c), v);
                 const int kc = k0 + 32 * c;
-                const float fa_lane = pow2f(-a.aexp[kc + lane]);  // knot kc + lane's row scaling
+                // knot kc + lane's row scaling (exact) times its renormalisation s_k
+                float fa_lane = pow2f(-a.aexp[kc + lane]);
+                if (a.scale && kc + lane < a.M) fa_lane *= (float)a.scale[kc + lane];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const float fa = __shfl_sync(0xffffffffu, fa_lane, j);
@@ -708,38 +711,48 @@ cudaError_t launch_rb(const double *are, const double *aim, int M, int Nb, int N
                       bool fp64, const double *bre, const double *bim, const double2 *gt64,
                       const float2 *gt32, const int *bexp, const unsigned char *bpack, double *scale,
                       int *aexp, unsigned char *apack, double *ore, double *oim, unsigned *err,
-                      int sm_count, cudaStream_t st)
+                      int sm_count, cudaStream_t st, cudaStream_t side, cudaEvent_t fork_ev,
+                      cudaEvent_t join_ev)
 {
     if (M == 0) return cudaSuccess;
     const RbLayout L = rb_layout(Nb, N, M);
     cudaError_t e;
     const double *sc = nullptr;
+    // mixed path: the scale is applied in the product's epilogue, so its kernels run on the side
+    // stream beside the coefficient pack and are joined before the product
+    const bool fork = nu && !fp64 && side;
+    cudaStream_t ss = fork ? side : st;
+    if (fork) {
+        if ((e = cudaEventRecord(fork_ev, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(side, fork_ev, 0)) != cudaSuccess) return e;
+    }
     if (nu && !fp64 && Nb <= kTMaxBasis) {
         const int smem = (kTRows * Nb + Nb * kTJ) * (int)sizeof(float2);
         e = cudaFuncSetAttribute(k_rb_scale_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        k_rb_scale_tile<<<(M + kTRows - 1) / kTRows, kTThreads, smem, st>>>(are, aim, M, Nb, gt32, nu,
+        k_rb_scale_tile<<<(M + kTRows - 1) / kTRows, kTThreads, smem, ss>>>(are, aim, M, Nb, gt32, nu,
                                                                              scale, err);
         sc = scale;
     } else if (nu) {
         double *q = scale + M;  // the caller's scratch holds scale [M] then q [M]
-        e = cudaMemsetAsync(q, 0, sizeof(double) * (size_t)M, st);
+        e = cudaMemsetAsync(q, 0, sizeof(double) * (size_t)M, ss);
         if (e != cudaSuccess) return e;
         const dim3 grid((Nb + kQJ - 1) / kQJ, (M + kQRows - 1) / kQRows);
         if (fp64) {
             e = cudaFuncSetAttribute(k_rb_quad<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      rb_quad_smem<double2>());
             if (e != cudaSuccess) return e;
-            k_rb_quad<double, double2><<<grid, kQThreads, rb_quad_smem<double2>(), st>>>(are, aim, M, Nb, gt64, q);
+            k_rb_quad<double, double2><<<grid, kQThreads, rb_quad_smem<double2>(), ss>>>(are, aim, M, Nb, gt64, q);
         } else {
             e = cudaFuncSetAttribute(k_rb_quad<float, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      rb_quad_smem<float2>());
             if (e != cudaSuccess) return e;
-            k_rb_quad<float, float2><<<grid, kQThreads, rb_quad_smem<float2>(), st>>>(are, aim, M, Nb, gt32, q);
+            k_rb_quad<float, float2><<<grid, kQThreads, rb_quad_smem<float2>(), ss>>>(are, aim, M, Nb, gt32, q);
         }
-        k_rb_norm<<<(M + 255) / 256, 256, 0, st>>>(q, nu, M, scale, err);
+        k_rb_norm<<<(M + 255) / 256, 256, 0, ss>>>(q, nu, M, scale, err);
         sc = scale;
     }
+    if (fork && (e = cudaEventRecord(join_ev, side)) != cudaSuccess) return e;
     if (fp64) {
         dim3 grid((N + kRb64Modes - 1) / kRb64Modes, (M + kRb64Rows - 1) / kRb64Rows);
         k_rb_fp64<<<grid, 256, 0, st>>>(are, aim, bre, bim, M, Nb, N, sc, ore, oim);
@@ -748,12 +761,13 @@ cudaError_t launch_rb(const double *are, const double *aim, int M, int Nb, int N
     const int rows = L.m_tiles * kRbTileN;
     const int pgrid = (rows + kRbPackWarps - 1) / kRbPackWarps;
     k_rb_pack_a<<<pgrid < sm_count * 8 ? pgrid : sm_count * 8, kRbPackWarps * 32, 0, st>>>(
-        are, aim, M, Nb, L.n_kb, L.m_tiles, sc, apack, aexp);
+        are, aim, M, Nb, L.n_kb, L.m_tiles, apack, aexp);
+    if (fork && (e = cudaStreamWaitEvent(st, join_ev, 0)) != cudaSuccess) return e;
     const int smem = kRbStages * (int)kRbStageBytes + 128;
     e = cudaFuncSetAttribute(k_rb_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int tiles = L.m_tiles * L.n_tiles;
-    RbMmaArgs args{apack, bpack, ore, oim, aexp, bexp, M, N, L.n_kb, L.m_tiles, L.n_tiles, err};
+    RbMmaArgs args{apack, bpack, ore, oim, aexp, bexp, sc, M, N, L.n_kb, L.m_tiles, L.n_tiles, err};
     k_rb_mma<<<tiles < sm_count ? tiles : sm_count, kRbMmaThreads, smem, st>>>(args);
     return cudaGetLastError();
 }
