@@ -138,6 +138,20 @@ def test_tiny_ragged(gpu_ctx, seed, K, ns):
     assert oracle.mismatch(gm, o) <= MIXED_MISMATCH
 
 
+@pytest.mark.parametrize("K", [180, 181, 4096])
+def test_knot_counts_up_to_the_maximum(gpu_ctx, K):
+    """Both forms of the spline build (values parked in shared memory up to K = 180, in the
+    global scratch above) and the largest trajectory FEW_MAX_KNOTS = 4096, with a few samples
+    per segment so that almost every pass is cut short by its segment's end."""
+    w = W.tiny_inputs(900 + K, K=K, n_samples=5 * K)
+    o = _oracle(w)
+    g = _gpu(gpu_ctx, w, F.FEW_FP64)
+    assert rel_l2(g, o) <= FP64_REL_L2, rel_l2(g, o)
+    assert max_phase_err(g, o) <= FP64_PHASE
+    gm = _gpu(gpu_ctx, w, F.FEW_MIXED)
+    assert oracle.mismatch(gm, o) <= MIXED_MISMATCH
+
+
 MODESETS = {
     "single_22": [(2, 2, 0)],
     "m0_only": [(2, 0, -3), (2, 0, 3), (3, 0, 0), (4, 0, 1)],
