@@ -560,16 +560,31 @@ few_status launch_kernels(few_ctx *c, const PlanHdr *hdr_dev, int total_pairs, i
     // harmonics and the fold (FP64-pipe work next to latency-bound work), joined before the sum
     const bool fork = total_anchor_segs > 0;
     if (fork) {
-        FEW_CUDA_TRY(cudaEventRecord(c->fork_ev, st));
-        FEW_CUDA_TRY(cudaStreamWaitEvent(c->side, c->fork_ev, 0));
-        FEW_CUDA_TRY(launch_anchor(hdr_dev, total_anchor_segs, c->side));
-        FEW_CUDA_TRY(cudaEventRecord(c->join_ev, c->side));
+        // any failure after this point still leaves the side stream's work ordered before what
+        // the caller queues next on `st` (the release of the call's scratch)
+        if (cudaEventRecord(c->fork_ev, st) != cudaSuccess ||
+            cudaStreamWaitEvent(c->side, c->fork_ev, 0) != cudaSuccess)
+            return FEW_ERR_CUDA;
+        const cudaError_t ea = launch_anchor(hdr_dev, total_anchor_segs, c->side);
+        if (cudaEventRecord(c->join_ev, c->side) != cudaSuccess) {
+            cudaStreamSynchronize(c->side);
+            return FEW_ERR_CUDA;
+        }
+        if (ea != cudaSuccess) {
+            cudaStreamWaitEvent(st, c->join_ev, 0);
+            return FEW_ERR_CUDA;
+        }
     }
+    auto joined = [&](cudaError_t e) {  // a failed launch: join the side stream, then report
+        if (e == cudaSuccess) return true;
+        if (fork) cudaStreamWaitEvent(st, c->join_ev, 0);
+        return false;
+    };
     tmark(c, 1, false, st);
-    FEW_CUDA_TRY(launch_ylm(hdr_dev, total_pairs, variant == kVariantFp64, st));
+    if (!joined(launch_ylm(hdr_dev, total_pairs, variant == kVariantFp64, st))) return FEW_ERR_CUDA;
     tmark(c, 1, true, st);
     tmark(c, 2, false, st);
-    FEW_CUDA_TRY(launch_fold(hdr_dev, total_fold, variant == kVariantFp64, st));
+    if (!joined(launch_fold(hdr_dev, total_fold, variant == kVariantFp64, st))) return FEW_ERR_CUDA;
     if (fork) FEW_CUDA_TRY(cudaStreamWaitEvent(st, c->join_ev, 0));
     tmark(c, 2, true, st);
     tmark(c, 3, false, st);

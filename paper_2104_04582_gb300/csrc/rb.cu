@@ -726,33 +726,39 @@ cudaError_t launch_rb(const double *are, const double *aim, int M, int Nb, int N
         if ((e = cudaEventRecord(fork_ev, st)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(side, fork_ev, 0)) != cudaSuccess) return e;
     }
+    // a failure after the fork waits for the side stream, so nothing of it outlives the call's
+    // scratch, which the caller releases on `st`
+    auto fail = [&](cudaError_t err) {
+        if (fork) cudaStreamSynchronize(side);
+        return err;
+    };
     if (nu && !fp64 && Nb <= kTMaxBasis) {
         const int smem = (kTRows * Nb + Nb * kTJ) * (int)sizeof(float2);
         e = cudaFuncSetAttribute(k_rb_scale_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) return fail(e);
         k_rb_scale_tile<<<(M + kTRows - 1) / kTRows, kTThreads, smem, ss>>>(are, aim, M, Nb, gt32, nu,
                                                                              scale, err);
         sc = scale;
     } else if (nu) {
         double *q = scale + M;  // the caller's scratch holds scale [M] then q [M]
         e = cudaMemsetAsync(q, 0, sizeof(double) * (size_t)M, ss);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) return fail(e);
         const dim3 grid((Nb + kQJ - 1) / kQJ, (M + kQRows - 1) / kQRows);
         if (fp64) {
             e = cudaFuncSetAttribute(k_rb_quad<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      rb_quad_smem<double2>());
-            if (e != cudaSuccess) return e;
+            if (e != cudaSuccess) return fail(e);
             k_rb_quad<double, double2><<<grid, kQThreads, rb_quad_smem<double2>(), ss>>>(are, aim, M, Nb, gt64, q);
         } else {
             e = cudaFuncSetAttribute(k_rb_quad<float, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      rb_quad_smem<float2>());
-            if (e != cudaSuccess) return e;
+            if (e != cudaSuccess) return fail(e);
             k_rb_quad<float, float2><<<grid, kQThreads, rb_quad_smem<float2>(), ss>>>(are, aim, M, Nb, gt32, q);
         }
         k_rb_norm<<<(M + 255) / 256, 256, 0, ss>>>(q, nu, M, scale, err);
         sc = scale;
     }
-    if (fork && (e = cudaEventRecord(join_ev, side)) != cudaSuccess) return e;
+    if (fork && (e = cudaEventRecord(join_ev, side)) != cudaSuccess) return fail(e);
     if (fp64) {
         dim3 grid((N + kRb64Modes - 1) / kRb64Modes, (M + kRb64Rows - 1) / kRb64Rows);
         k_rb_fp64<<<grid, 256, 0, st>>>(are, aim, bre, bim, M, Nb, N, sc, ore, oim);
@@ -762,7 +768,8 @@ cudaError_t launch_rb(const double *are, const double *aim, int M, int Nb, int N
     const int pgrid = (rows + kRbPackWarps - 1) / kRbPackWarps;
     k_rb_pack_a<<<pgrid < sm_count * 8 ? pgrid : sm_count * 8, kRbPackWarps * 32, 0, st>>>(
         are, aim, M, Nb, L.n_kb, L.m_tiles, apack, aexp);
-    if (fork && (e = cudaStreamWaitEvent(st, join_ev, 0)) != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    if (fork && (e = cudaStreamWaitEvent(st, join_ev, 0)) != cudaSuccess) return fail(e);
     const int smem = kRbStages * (int)kRbStageBytes + 128;
     e = cudaFuncSetAttribute(k_rb_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
