@@ -97,8 +97,14 @@ struct few_ctx {
     size_t in_use = 0;
     cudaMemPool_t pool = nullptr;
     cudaStream_t internal = nullptr;
-    cudaStream_t side = nullptr;  // the phase anchors, beside the harmonics and the fold
-    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    // second streams for work beside a call's main chain (the phase anchors beside the
+    // harmonics and the fold; the reduced-basis scale beside its pack), each with its fork and
+    // join events; taken in turn, so calls on different user streams seldom share one
+    struct SideLane {
+        cudaStream_t s = nullptr;
+        cudaEvent_t fork = nullptr, join = nullptr;
+    } lanes[4];
+    unsigned lane_next = 0;
     unsigned *d_err = nullptr;
     std::recursive_mutex mu;
     std::unordered_map<void *, size_t> sizes;
@@ -556,28 +562,29 @@ few_status launch_kernels(few_ctx *c, const PlanHdr *hdr_dev, int total_pairs, i
                           int total_anchor_segs, int grid, int threads, int R, int smem, int variant,
                           cudaStream_t st)
 {
-    // the phase anchors depend on the splines only: they run on the side stream beside the
+    // the phase anchors depend on the splines only: they run on a side lane beside the
     // harmonics and the fold (FP64-pipe work next to latency-bound work), joined before the sum
     const bool fork = total_anchor_segs > 0;
+    auto &L = c->lanes[c->lane_next++ % 4];
     if (fork) {
         // any failure after this point still leaves the side stream's work ordered before what
         // the caller queues next on `st` (the release of the call's scratch)
-        if (cudaEventRecord(c->fork_ev, st) != cudaSuccess ||
-            cudaStreamWaitEvent(c->side, c->fork_ev, 0) != cudaSuccess)
+        if (cudaEventRecord(L.fork, st) != cudaSuccess ||
+            cudaStreamWaitEvent(L.s, L.fork, 0) != cudaSuccess)
             return FEW_ERR_CUDA;
-        const cudaError_t ea = launch_anchor(hdr_dev, total_anchor_segs, c->side);
-        if (cudaEventRecord(c->join_ev, c->side) != cudaSuccess) {
-            cudaStreamSynchronize(c->side);
+        const cudaError_t ea = launch_anchor(hdr_dev, total_anchor_segs, L.s);
+        if (cudaEventRecord(L.join, L.s) != cudaSuccess) {
+            cudaStreamSynchronize(L.s);
             return FEW_ERR_CUDA;
         }
         if (ea != cudaSuccess) {
-            cudaStreamWaitEvent(st, c->join_ev, 0);
+            cudaStreamWaitEvent(st, L.join, 0);
             return FEW_ERR_CUDA;
         }
     }
     auto joined = [&](cudaError_t e) {  // a failed launch: join the side stream, then report
         if (e == cudaSuccess) return true;
-        if (fork) cudaStreamWaitEvent(st, c->join_ev, 0);
+        if (fork) cudaStreamWaitEvent(st, L.join, 0);
         return false;
     };
     tmark(c, 1, false, st);
@@ -585,7 +592,7 @@ few_status launch_kernels(few_ctx *c, const PlanHdr *hdr_dev, int total_pairs, i
     tmark(c, 1, true, st);
     tmark(c, 2, false, st);
     if (!joined(launch_fold(hdr_dev, total_fold, variant == kVariantFp64, st))) return FEW_ERR_CUDA;
-    if (fork) FEW_CUDA_TRY(cudaStreamWaitEvent(st, c->join_ev, 0));
+    if (fork) FEW_CUDA_TRY(cudaStreamWaitEvent(st, L.join, 0));
     tmark(c, 2, true, st);
     tmark(c, 3, false, st);
     FEW_CUDA_TRY(launch_sum(hdr_dev, grid, threads, R, smem, variant, st));
@@ -630,9 +637,11 @@ few_status few_ctx_create(few_ctx **out, int device, size_t hbm_budget_bytes)
     auto fail = [&](few_status s) {
         if (c->d_err) cudaFree(c->d_err);
         if (c->internal) cudaStreamDestroy(c->internal);
-        if (c->side) cudaStreamDestroy(c->side);
-        if (c->fork_ev) cudaEventDestroy(c->fork_ev);
-        if (c->join_ev) cudaEventDestroy(c->join_ev);
+        for (auto &l : c->lanes) {
+            if (l.s) cudaStreamDestroy(l.s);
+            if (l.fork) cudaEventDestroy(l.fork);
+            if (l.join) cudaEventDestroy(l.join);
+        }
         for (auto &e : c->tev)
             if (e) cudaEventDestroy(e);
         if (c->pool) cudaMemPoolDestroy(c->pool);
@@ -651,11 +660,13 @@ few_status few_ctx_create(few_ctx **out, int device, size_t hbm_budget_bytes)
     if (cudaMemPoolCreate(&c->pool, &props) != cudaSuccess) return fail(FEW_ERR_CUDA);
     uint64_t thresh = UINT64_MAX;
     cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thresh);
-    if (cudaStreamCreateWithFlags(&c->internal, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess)
+    if (cudaStreamCreateWithFlags(&c->internal, cudaStreamNonBlocking) != cudaSuccess)
         return fail(FEW_ERR_CUDA);
+    for (auto &l : c->lanes)
+        if (cudaStreamCreateWithFlags(&l.s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&l.fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&l.join, cudaEventDisableTiming) != cudaSuccess)
+            return fail(FEW_ERR_CUDA);
     if (cudaMalloc(&c->d_err, sizeof(unsigned)) != cudaSuccess) return fail(FEW_ERR_NOMEM);
     if (cudaMemset(c->d_err, 0, sizeof(unsigned)) != cudaSuccess) return fail(FEW_ERR_CUDA);
     if (sum_configure() != cudaSuccess) return fail(FEW_ERR_CUDA);
@@ -688,9 +699,11 @@ few_status few_ctx_destroy(few_ctx *ctx)
         ctx->pinned.release();
         cudaFree(ctx->d_err);
         cudaStreamDestroy(ctx->internal);
-        cudaStreamDestroy(ctx->side);
-        cudaEventDestroy(ctx->fork_ev);
-        cudaEventDestroy(ctx->join_ev);
+        for (auto &l : ctx->lanes) {
+            cudaStreamDestroy(l.s);
+            cudaEventDestroy(l.fork);
+            cudaEventDestroy(l.join);
+        }
         cudaMemPoolDestroy(ctx->pool);
         (void)cudaGetLastError();
     }
@@ -1192,11 +1205,11 @@ few_status few_rb_amplitudes(few_ctx *ctx, const few_basis *b, const double *are
     few_status st = dev_alloc(ctx, sc_bytes + ex_bytes + (fp64 ? 0 : L.apack_bytes), s, &d);
     if (st) return st;
     unsigned char *p = static_cast<unsigned char *>(d);
+    auto &lane = ctx->lanes[ctx->lane_next++ % 4];
     cudaError_t e = launch_rb(are, aim, M, b->Nb, b->N, nu, fp64, b->bre, b->bim, b->gt64, b->gt32,
                               b->bexp, b->bpack, reinterpret_cast<double *>(p),
                               reinterpret_cast<int *>(p + sc_bytes), p + sc_bytes + ex_bytes, ore,
-                              oim, ctx->d_err, ctx->sm_count, s, ctx->side, ctx->fork_ev,
-                              ctx->join_ev);
+                              oim, ctx->d_err, ctx->sm_count, s, lane.s, lane.fork, lane.join);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         st = FEW_ERR_CUDA;
@@ -1288,15 +1301,16 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
                              b->max_knots, ctx->d_err, cap);
             // the same fork and join as launch_kernels, recorded into the graph
             const bool fork = b->total_anchor_segs > 0;
+            auto &L = ctx->lanes[ctx->lane_next++ % 4];
             if (fork) {
-                cudaEventRecord(ctx->fork_ev, cap);
-                cudaStreamWaitEvent(ctx->side, ctx->fork_ev, 0);
-                launch_anchor(hd, b->total_anchor_segs, ctx->side);
-                cudaEventRecord(ctx->join_ev, ctx->side);
+                cudaEventRecord(L.fork, cap);
+                cudaStreamWaitEvent(L.s, L.fork, 0);
+                launch_anchor(hd, b->total_anchor_segs, L.s);
+                cudaEventRecord(L.join, L.s);
             }
             launch_ylm(hd, b->total_pairs, b->fp64, cap);
             launch_fold(hd, b->total_fold, b->fp64, cap);
-            if (fork) cudaStreamWaitEvent(cap, ctx->join_ev, 0);
+            if (fork) cudaStreamWaitEvent(cap, L.join, 0);
             launch_sum(hd, b->grid, b->threads, b->R, b->smem, b->variant, cap);
             e = cudaStreamEndCapture(cap, &b->graph);
         }
