@@ -19,6 +19,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "fewsum_internal.h"
 
@@ -122,6 +123,15 @@ struct few_ctx {
 };
 
 namespace {
+
+// A named NVTX range over an entry point's host work (inert unless a profiler is attached), so a
+// timeline shows which call queued which kernels.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 few_status dev_alloc(few_ctx *c, size_t bytes, cudaStream_t st, void **out)
 {
@@ -723,6 +733,7 @@ few_status few_ctx_memory(few_ctx *ctx, size_t *bytes_in_use, size_t *budget_byt
 few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int *l, const int *m,
                            const int *n, int N, few_traj **out)
 {
+    NvtxRange nvtx_range("few_traj_create");
     if (!ctx || !out) return FEW_ERR_INVALID_ARG;
     *out = nullptr;
     few_status st = check_knots(t_knots, K);
@@ -849,6 +860,7 @@ few_status few_traj_create(few_ctx *ctx, const double *t_knots, int K, const int
 few_status few_traj_set_data(few_ctx *ctx, few_traj *tr, const double *phi_phi, const double *phi_r,
                              const double *amp_re, const double *amp_im, few_mem where, void *stream)
 {
+    NvtxRange nvtx_range("few_traj_set_data");
     if (!ctx || !tr || tr->ctx != ctx) return FEW_ERR_INVALID_ARG;
     if (!phi_phi || !phi_r || !amp_re || !amp_im) return FEW_ERR_INVALID_ARG;
     if (where != FEW_MEM_HOST && where != FEW_MEM_DEVICE) return FEW_ERR_INVALID_ARG;
@@ -945,6 +957,7 @@ few_status few_traj_info(const few_traj *tr, int *K, int *N, int *n_slots)
 
 few_status few_waveform(few_ctx *ctx, const few_request *req, void *stream)
 {
+    NvtxRange nvtx_range("few_waveform");
     if (!ctx || !req) return FEW_ERR_INVALID_ARG;
     few_status st = validate_request(*req, false);
     if (st) return st;
@@ -1010,6 +1023,7 @@ few_status few_waveform(few_ctx *ctx, const few_request *req, void *stream)
 few_status few_phase_samples(few_ctx *ctx, const few_traj *tr, double t0, double dt, int64_t n,
                              double dphi_phi0, double dphi_r0, double *out_dev, void *stream)
 {
+    NvtxRange nvtx_range("few_phase_samples");
     if (!ctx || !tr || tr->ctx != ctx || !out_dev) return FEW_ERR_INVALID_ARG;
     if (!tr->has_data) return FEW_ERR_STATE;
     if (!is_fin(dphi_phi0) || !is_fin(dphi_r0)) return FEW_ERR_INVALID_ARG;
@@ -1040,6 +1054,7 @@ few_status few_phase_samples(few_ctx *ctx, const few_traj *tr, double t0, double
 few_status few_mode_select(few_ctx *ctx, const double *amp_re, const double *amp_im, int K, int N,
                            const int *m, double eps, unsigned char *mask, void *stream)
 {
+    NvtxRange nvtx_range("few_mode_select");
     if (!ctx || !amp_re || !amp_im || !m || !mask) return FEW_ERR_INVALID_ARG;
     if (K < 1 || N < 1 || !is_fin(eps) || eps < 0.0) return FEW_ERR_INVALID_ARG;
     if (N > mode_select_max_modes()) return FEW_ERR_LIMIT;
@@ -1064,6 +1079,7 @@ few_status few_direct_sum(few_ctx *ctx, const double *pphi, const double *pr, co
                           int N, double theta, double phi, double scale, int prec, void *out,
                           int out_c64, void *stream)
 {
+    NvtxRange nvtx_range("few_direct_sum");
     if (!ctx || !pphi || !pr || !are || !aim || !out) return FEW_ERR_INVALID_ARG;
     if (prec != FEW_FP64 && prec != FEW_MIXED) return FEW_ERR_INVALID_ARG;
     if (!is_fin(theta) || !is_fin(phi) || !is_fin(scale) || ns < 0) return FEW_ERR_INVALID_ARG;
@@ -1116,6 +1132,7 @@ struct few_basis {
 few_status few_basis_create(few_ctx *ctx, const double *b_re, const double *b_im, int Nb, int N,
                             few_mem where, void *stream, few_basis **out)
 {
+    NvtxRange nvtx_range("few_basis_create");
     if (!ctx || !b_re || !b_im || !out || Nb < 1 || N < 1) return FEW_ERR_INVALID_ARG;
     if (where != FEW_MEM_HOST && where != FEW_MEM_DEVICE) return FEW_ERR_INVALID_ARG;
     if (Nb > FEW_MAX_BASIS) return FEW_ERR_LIMIT;
@@ -1189,6 +1206,7 @@ few_status few_rb_amplitudes(few_ctx *ctx, const few_basis *b, const double *are
                              const double *aim, int M, const double *nu, int prec, double *ore,
                              double *oim, void *stream)
 {
+    NvtxRange nvtx_range("few_rb_amplitudes");
     if (!ctx || !b || b->ctx != ctx || M < 0) return FEW_ERR_INVALID_ARG;
     if (prec != FEW_FP64 && prec != FEW_MIXED) return FEW_ERR_INVALID_ARG;
     if (M == 0) return FEW_OK;
@@ -1220,6 +1238,7 @@ few_status few_rb_amplitudes(few_ctx *ctx, const few_basis *b, const double *are
 
 few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned flags, few_batch **out)
 {
+    NvtxRange nvtx_range("few_batch_plan");
     if (!ctx || !reqs || n < 1 || !out) return FEW_ERR_INVALID_ARG;
     *out = nullptr;
     for (int q = 0; q < n; ++q) {
@@ -1325,6 +1344,7 @@ few_status few_batch_plan(few_ctx *ctx, const few_request *reqs, int n, unsigned
 
 few_status few_batch_run(few_ctx *ctx, few_batch *b, void *stream)
 {
+    NvtxRange nvtx_range("few_batch_run");
     if (!ctx || !b || b->ctx != ctx) return FEW_ERR_INVALID_ARG;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     DeviceScope dev_scope(ctx->device);
