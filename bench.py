@@ -465,38 +465,91 @@ def bench_plain_fp64(ctx, w, tr, dev_in, dev, stream, sh, flush, reps):
             "dtype": "f64"}, h64
 
 
-def bench_e2e(ctx, w, tr, prec, sh, flush, steps):
+def bench_e2e(ctx, w, tr, prec, sh, flush, steps, in_flight=1):
     """End to end through the C ABI: pinned host knot data in, pinned host output out, both
-    copies inside the timed region (host wall clock around the two calls)."""
+    copies inside the timed region (host wall clock around the two calls).  With in_flight > 1,
+    as many host threads make the same calls at once, each with its own trajectory, host
+    buffers and stream (the library does not hold the context while a call waits for its
+    copies or its result); value = all their steps / wall time."""
+    import threading
     import torch
     from paper_2104_04582_gb300 import fewsum as F
     from paper_2104_04582_gb300 import runtime as RT
     c64 = prec == F.FEW_MIXED
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
-    h_in = [pin(a) for a in (w.phi_phi, w.phi_r, w.amp_re, w.amp_im)]
-    host_out = torch.empty(w.n_samples, dtype=torch.complex64 if c64 else torch.complex128
-                           ).pin_memory().numpy()
-    req_h = RT.request(tr, host_out, w.n_samples, w.t0, w.dt, w.theta, w.phi, prec,
-                       out_where=F.FEW_MEM_HOST)
+
+    def make(tr_):
+        h_in = [pin(a) for a in (w.phi_phi, w.phi_r, w.amp_re, w.amp_im)]
+        host_out = torch.empty(w.n_samples, dtype=torch.complex64 if c64 else torch.complex128
+                               ).pin_memory().numpy()
+        req = RT.request(tr_, host_out, w.n_samples, w.t0, w.dt, w.theta, w.phi, prec,
+                         out_where=F.FEW_MEM_HOST)
+        return tr_, h_in, host_out, req
+
+    def one(st, s_):
+        tr_, h_in, _, req = st
+        F.few_traj_set_data(ctx.handle, tr_.handle, *h_in, stream=s_)
+        F.few_waveform(ctx.handle, req, s_)  # host output: returns once the result is in host memory
+
+    main = make(tr)
     for _ in range(2):
-        F.few_traj_set_data(ctx.handle, tr.handle, *h_in, stream=sh)
-        F.few_waveform(ctx.handle, req_h, sh)
+        one(main, sh)
     torch.cuda.synchronize()
     t_e = []
     for _ in range(steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        F.few_traj_set_data(ctx.handle, tr.handle, *h_in, stream=sh)
-        F.few_waveform(ctx.handle, req_h, sh)  # host output: returns after the result is in host memory
+        one(main, sh)
         t_e.append(time.perf_counter() - t0)
-    return {"value": 1.0 / statistics.mean(t_e), "unit": UNIT,
-            "h2d_bytes_per_step": int(sum(a.nbytes for a in h_in)),
-            "d2h_bytes_per_step": int(host_out.nbytes),
-            "ms_per_step": 1000.0 * statistics.mean(t_e), "steps": steps,
-            "timer": "host wall clock around the two C-ABI calls (the call with host output "
-                     "returns once the result is in host memory; page-locked output is stored by "
-                     "the summation kernel directly)"}
+    res = {"value": 1.0 / statistics.mean(t_e), "unit": UNIT,
+           "h2d_bytes_per_step": int(sum(a.nbytes for a in main[1])),
+           "d2h_bytes_per_step": int(main[2].nbytes),
+           "ms_per_step": 1000.0 * statistics.mean(t_e), "steps": steps,
+           "timer": "host wall clock around the two C-ABI calls (the call with host output "
+                    "returns once the result is in host memory; page-locked output is stored by "
+                    "the summation kernel directly)"}
+    if in_flight > 1:
+        extra = [RT.Trajectory(ctx, w.t_knots, w.modes) for _ in range(in_flight - 1)]
+        sets = [main] + [make(t_) for t_ in extra]
+        streams = [torch.cuda.Stream() for _ in sets]
+        per = max(2, steps)
+        go = threading.Barrier(len(sets) + 1)
+        errs = []
+
+        def worker(st, strm):
+            try:
+                one(st, int(strm.cuda_stream))  # warm-up of this thread's set
+                go.wait()
+                for _ in range(per):
+                    one(st, int(strm.cuda_stream))
+            except Exception as e:  # noqa: BLE001 -- reported below
+                errs.append(e)
+                go.abort()
+        ths = [threading.Thread(target=worker, args=(st, strm)) for st, strm in zip(sets, streams)]
+        for th in ths:
+            th.start()
+        go.wait()
+        t0 = time.perf_counter()
+        for th in ths:
+            th.join()
+        wall = time.perf_counter() - t0
+        for t_ in extra:
+            t_.release()
+        if errs:
+            raise errs[0]
+        seq = dict(res)
+        res = {"value": per * len(sets) / wall, "unit": UNIT,
+               "h2d_bytes_per_step": seq["h2d_bytes_per_step"],
+               "d2h_bytes_per_step": seq["d2h_bytes_per_step"],
+               "ms_per_step": 1000.0 * wall / (per * len(sets)), "steps": per * len(sets),
+               "in_flight": len(sets),
+               "timer": "host wall clock from a barrier before the first step of %d host "
+                        "threads to the end of the last; each thread makes the two C-ABI calls "
+                        "per step with its own trajectory, pinned buffers and stream" % len(sets),
+               "sequential": {k: seq[k] for k in ("value", "ms_per_step", "steps", "timer")}}
+    return res
+
 
 C2_SLOT_SAMPLES = 1281 * 3155760  # slots x samples of the one-year 3843-mode waveform
 C2_MODE_SAMPLES = 3843 * 3155760
@@ -803,7 +856,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
             out["plain"], out["h_plain"] = timed_part("plain_fp64", lambda: bench_plain_fp64(
                 ctx, w, r["tr"], r["dev_in"], dev, stream, sh, flush, max(2, min(5, args.steps))))
         out["e2e"] = timed_part("e2e", lambda: bench_e2e(ctx, w, r["tr"], prec, sh, flush,
-                                                         max(3, min(args.steps, 10))))
+                                                         max(3, min(args.steps, 10)),
+                                                         args.in_flight))
         out["selector"] = timed_part("mode_selector", lambda: bench_selector(
             ctx, w, r["dev_in"], dev, stream, sh))
         r["tr"].release()

@@ -34,7 +34,9 @@
  *   documented otherwise.  Work on one handle from several streams must be ordered by the
  *   caller.
  * Threads: a context may be used from several host threads; every call on a context takes
- *   the context's lock.
+ *   the context's lock while it plans and queues work, and releases it before a wait for its
+ *   own host copies or host output (few_traj_set_data from host memory, few_waveform into host
+ *   memory), so calls from threads with their own handles and streams overlap.
  * Layouts: complex outputs are interleaved (re, im) pairs, complex128 (2 x f64) or
  *   complex64 (2 x f32).  Per-knot mode arrays are row-major [K][N] (modes contiguous).
  * Limits: 4 <= K <= FEW_MAX_KNOTS knots; 1 <= N modes; 2 <= l <= 32, 0 <= m <= l,

@@ -864,7 +864,7 @@ few_status few_traj_set_data(few_ctx *ctx, few_traj *tr, const double *phi_phi, 
     if (!ctx || !tr || tr->ctx != ctx) return FEW_ERR_INVALID_ARG;
     if (!phi_phi || !phi_r || !amp_re || !amp_im) return FEW_ERR_INVALID_ARG;
     if (where != FEW_MEM_HOST && where != FEW_MEM_DEVICE) return FEW_ERR_INVALID_ARG;
-    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    std::unique_lock<std::recursive_mutex> lk(ctx->mu);
     DeviceScope dev_scope(ctx->device);
     if (!dev_scope.ok) return FEW_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -916,6 +916,7 @@ few_status few_traj_set_data(few_ctx *ctx, few_traj *tr, const double *phi_phi, 
         tmark(ctx, 0, true, st);
     }
     if (copied) {
+        lk.unlock();  // the copies' completion concerns this call only
         if (cudaEventSynchronize(copied) != cudaSuccess && !s) {
             (void)cudaGetLastError();
             s = FEW_ERR_CUDA;
@@ -963,7 +964,7 @@ few_status few_waveform(few_ctx *ctx, const few_request *req, void *stream)
     if (st) return st;
     if (req->traj->ctx != ctx) return FEW_ERR_INVALID_ARG;
     if (req->n_samples == 0) return FEW_OK;
-    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    std::unique_lock<std::recursive_mutex> lk(ctx->mu);
     DeviceScope dev_scope(ctx->device);
     if (!dev_scope.ok) return FEW_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1012,6 +1013,9 @@ few_status few_waveform(few_ctx *ctx, const few_request *req, void *stream)
     dev_free(ctx, scratch, s);
     dev_free(ctx, blob, s);
     if (!st && req->out_where == FEW_MEM_HOST) {
+        // everything is queued: wait for the result without holding the context, so calls from
+        // other host threads (their own streams) overlap this one's transfer and compute
+        lk.unlock();
         if (cudaStreamSynchronize(s) != cudaSuccess) {
             (void)cudaGetLastError();
             st = FEW_ERR_CUDA;

@@ -460,3 +460,42 @@ def test_knot_count_limit(gpu_ctx):
     with pytest.raises(F.FewError) as e:
         F.few_traj_create(gpu_ctx.handle, t, np.array([[2, 2, 0]], dtype=np.int32))
     assert e.value.status == F.FEW_ERR_LIMIT
+
+
+def test_host_threads_in_flight(gpu_ctx):
+    """Host threads calling few_traj_set_data / few_waveform with host buffers at once, each with
+    its own trajectory, page-locked buffers and stream (the library releases the context while a
+    call waits): every result equals the same waveform computed alone."""
+    import threading
+    import torch
+    ws = [W.tiny_inputs(700 + k, K=12 + 5 * k, n_samples=20000 + 3001 * k) for k in range(3)]
+    ref = [_gpu(gpu_ctx, w, F.FEW_MIXED) for w in ws]
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    errs, results = [], [None] * len(ws)
+
+    def worker(k):
+        try:
+            w = ws[k]
+            tr = RT.Trajectory(gpu_ctx, w.t_knots, w.modes)
+            h_in = [pin(a) for a in (w.phi_phi, w.phi_r, w.amp_re, w.amp_im)]
+            out = torch.empty(w.n_samples, dtype=torch.complex64).pin_memory().numpy()
+            req = RT.request(tr, out, w.n_samples, w.t0, w.dt, w.theta, w.phi, F.FEW_MIXED,
+                             scale=w.scale, out_where=F.FEW_MEM_HOST)
+            s = torch.cuda.Stream()
+            for _ in range(5):
+                out[:] = 0
+                F.few_traj_set_data(gpu_ctx.handle, tr.handle, *h_in, stream=int(s.cuda_stream))
+                F.few_waveform(gpu_ctx.handle, req, int(s.cuda_stream))
+                results[k] = out.copy()
+                np.testing.assert_array_equal(results[k], ref[k])
+            tr.release()
+        except Exception as e:  # noqa: BLE001 -- re-raised below
+            errs.append(e)
+    ths = [threading.Thread(target=worker, args=(k,)) for k in range(len(ws))]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    if errs:
+        raise errs[0]
+    assert gpu_ctx.sync_status() == F.FEW_OK
