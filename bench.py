@@ -555,7 +555,8 @@ C2_SLOT_SAMPLES = 1281 * 3155760  # slots x samples of the one-year 3843-mode wa
 C2_MODE_SAMPLES = 3843 * 3155760
 
 
-def bench_batched_c3(ctx, dev, stream, sh, flush, n_waves, reps, tune_cache, oracle_windows=4):
+def bench_batched_c3(ctx, dev, stream, sh, flush, n_waves, reps, tune_cache, oracle_windows=4,
+                     in_flight=1):
     """256 waveforms of 0.25-2 yr, K 50-150, power-selected 10-3843 modes, mixed precision:
     spline rebuild of every trajectory + harmonics + fold + anchors + one persistent summation
     launch, captured once as a CUDA graph and replayed; tile chosen by the autotuner on a
@@ -591,6 +592,47 @@ def bench_batched_c3(ctx, dev, stream, sh, flush, n_waves, reps, tune_cache, ora
     if ctx.sync_status() != F.FEW_OK:
         raise RuntimeError("device error in the batched run")
     msb = statistics.mean(ms)
+    flight = None
+    if in_flight > 1:
+        # more batches in flight: each its own trajectories, outputs and graph, on its own stream
+        sets = [(bh, None, None)]
+        for _ in range(in_flight - 1):
+            trs2 = [RT.from_inputs(ctx, x) for x in ws]
+            outs2 = [RT.alloc_out(x.n_samples, True, dev.index) for x in ws]
+            reqs2 = [RT.request(t_, o_, x.n_samples, x.t0, x.dt, x.theta, x.phi, F.FEW_MIXED)
+                     for t_, o_, x in zip(trs2, outs2, ws)]
+            sets.append((F.few_batch_plan(ctx.handle, reqs2, F.FEW_BATCH_REBUILD_SPLINES), trs2,
+                         outs2))
+        streams = [torch.cuda.Stream(device=dev) for _ in sets]
+        for (b_, _, _), s_ in zip(sets, streams):
+            F.few_batch_run(ctx.handle, b_, int(s_.cuda_stream))
+        torch.cuda.synchronize()
+        cur = torch.cuda.current_stream()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(cur)
+        for s_ in streams:
+            s_.wait_event(a)
+        for _ in range(reps):
+            for (b_, _, _), s_ in zip(sets, streams):
+                F.few_batch_run(ctx.handle, b_, int(s_.cuda_stream))
+        for s_ in streams:
+            cur.wait_stream(s_)
+        e.record(cur)
+        torch.cuda.synchronize()
+        tot = a.elapsed_time(e)
+        if ctx.sync_status() != F.FEW_OK:
+            raise RuntimeError("device error in the batched run")
+        nb = reps * len(sets)
+        flight = {"batches_in_flight": len(sets), "batches": nb, "ms_per_batch": tot / nb,
+                  "value": n_waves * nb * 1000.0 / tot, "unit": "waveforms/s",
+                  "note": "each batch with its own 256 trajectories, outputs and graph, replayed "
+                          "on its own stream; CUDA events from before the first batch to after "
+                          "the last"}
+        for b_, trs2, outs2 in sets[1:]:
+            F.few_batch_release(ctx.handle, b_)
+            for t_ in trs2:
+                t_.release()
+            del outs2
     samples = sum(x.n_samples for x in ws)
     mode_samples = sum(x.N * x.n_samples for x in ws)
     slot_samples = sum(t_.info[2] * x.n_samples for t_, x in zip(trs, ws))
@@ -620,6 +662,11 @@ def bench_batched_c3(ctx, dev, stream, sh, flush, n_waves, reps, tune_cache, ora
            "step": "spline rebuild of all 256 trajectories + harmonics + fold + phase anchors + "
                    "one persistent summation launch, replayed as one CUDA graph",
            "host_setup_s": setup_s, "plan_and_capture_s": plan_s, "accuracy": acc}
+    if flight:
+        flight["slot_samples_per_s"] = slot_samples * flight["value"] / n_waves
+        flight["c2_equivalent_waveforms_per_s_by_slot_samples"] = \
+            slot_samples / C2_SLOT_SAMPLES * flight["value"] / n_waves
+        res["in_flight"] = flight
     F.few_batch_release(ctx.handle, bh)
     for t_ in trs:
         t_.release()
@@ -863,7 +910,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         r["tr"].release()
         if args.batch > 0:
             out["batched_c3"] = timed_part("batched_c3", lambda: bench_batched_c3(
-                ctx, dev, stream, sh, flush, args.batch, 3, tune_cache))
+                ctx, dev, stream, sh, flush, args.batch, 3, tune_cache,
+                in_flight=args.in_flight))
         if args.serving_requests > 0:
             out["serving"] = timed_part("serving", lambda: bench_serving_c4(
                 ctx, args.serving_requests, args.serving_budget_gb, tune_cache))
