@@ -152,6 +152,20 @@ def test_knot_counts_up_to_the_maximum(gpu_ctx, K):
     assert oracle.mismatch(gm, o) <= MIXED_MISMATCH
 
 
+@pytest.mark.parametrize("K,ns", [(600, 50), (4096, 300), (40, 3)])
+def test_segments_without_samples(gpu_ctx, K, ns):
+    """Knots closer together than the sampling step: most segments hold no sample at all (their
+    passes, anchors and folds must contribute nothing and write nothing)."""
+    w = W.tiny_inputs(1200 + K, K=K, n_samples=ns, T=2.0e5, dt=2.0e5 / ns)
+    seg = F.few_plan_segments(w.t_knots, w.t0, w.dt, w.n_samples)
+    assert np.sum(np.diff(seg) == 0) > 0
+    o = _oracle(w)
+    g = _gpu(gpu_ctx, w, F.FEW_FP64)
+    assert rel_l2(g, o) <= FP64_REL_L2, rel_l2(g, o)
+    gm = _gpu(gpu_ctx, w, F.FEW_MIXED)
+    assert oracle.mismatch(gm, o) <= MIXED_MISMATCH
+
+
 MODESETS = {
     "single_22": [(2, 2, 0)],
     "m0_only": [(2, 0, -3), (2, 0, 3), (3, 0, 0), (4, 0, 1)],
