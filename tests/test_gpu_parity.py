@@ -172,13 +172,18 @@ MODESETS = {
     "odd_l": [(3, 1, 2), (3, 3, -4), (5, 2, 7), (7, 7, -1)],
     "wide_n": [(2, 2, -30), (2, 2, 30), (2, 1, 17), (10, 10, -25)],
     "high_l": [(12, 5, 3), (20, 20, -2), (32, 0, 1), (32, 31, 0)],
+    # |n| at its limit: a row of 2049 slots streamed in many tiles, ~2000 powers of z_r in FP32
+    "extreme_n": [(2, 2, -1024), (2, 2, 1024), (3, 1, 500), (2, 0, -700)],
 }
 
 
 @pytest.mark.parametrize("name", sorted(MODESETS))
 def test_mode_sets(gpu_ctx, name):
     modes = np.asarray(MODESETS[name], dtype=np.int32)
-    w = W.tiny_inputs(42, K=10, n_samples=3000, modes=modes)
+    if name == "extreme_n":  # amplitudes that do not decay in n (FP32 range for the mixed path)
+        w = W.make_inputs(2.0e5, 10, 2.0e5 / 3000, modes, 42, 8.0, 1.0e4, n_samples=3000)
+    else:
+        w = W.tiny_inputs(42, K=10, n_samples=3000, modes=modes)
     o = _oracle(w)
     g = _gpu(gpu_ctx, w, F.FEW_FP64)
     assert rel_l2(g, o) <= FP64_REL_L2, rel_l2(g, o)
