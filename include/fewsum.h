@@ -309,7 +309,7 @@ few_status few_rb_amplitudes(few_ctx *ctx, const few_basis *basis, const double 
 /*
  * Plan a batch of requests (all with the same `prec`; any mix of trajectories, durations,
  * cadences and mode counts) executed as one persistent summation launch whose CTAs take
- * equal-cost slices of the concatenated (waveform, sample) work.  The plan holds its own
+ * slices of the concatenated (waveform, sample) work of equal pass cost.  The plan holds its own
  * scratch; the kernels are captured once into a CUDA graph (unless FEW_BATCH_NO_GRAPH), and
  * each few_batch_run replays it.  Every request must use out_where == FEW_MEM_DEVICE.  The
  * trajectories and output buffers must stay valid while the batch exists.  Blocking (uploads

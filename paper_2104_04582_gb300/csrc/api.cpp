@@ -1,7 +1,7 @@
 // api.cpp -- host side of libfewsum.so: the C ABI declared in include/fewsum.h.
 //
 // Responsibilities: input validation, the planning step (mode -> harmonic slot layout,
-// segment sample ranges, equal-cost CTA slices), device memory from a context-owned
+// segment sample ranges, CTA slices of equal pass cost), device memory from a context-owned
 // stream-ordered pool with an HBM budget, plan uploads through pinned staging buffers, kernel
 // launches, CUDA-graph capture of batches, and the device error latch.  No arithmetic of the
 // waveform itself happens here; every numerical step runs in the kernels.
