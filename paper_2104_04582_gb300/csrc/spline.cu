@@ -218,7 +218,7 @@ __device__ __forceinline__ unsigned nonfinite_bit(double x)
 //     the end (a segment's 8 columns are 256 contiguous bytes).
 //   otherwise: values are parked in the trajectory's slope scratch [K][J], and each lane writes
 //     the Hermite data (y_k, y_{k+1}, s_k, s_{k+1}) of the segments beside its rows.
-constexpr int kChunk = 8;
+constexpr int kChunk = 16;  // rows of column values fetched at once per lane (loads in flight)
 constexpr int kBuildStaged = 6;  // knot arrays in shared memory: ra, rb, lo, up, v, w
 constexpr int kBuildSharedKnots = 180;  // largest K parked in shared memory (< 32 KB per block)
 constexpr int kSepN = kBuildParts - 1;  // separators of a spline at most
