@@ -12,13 +12,15 @@
 // to the last of them.  Any other summation order can round differently and move the cut.
 //
 // One CTA per knot, P = max(128, next power of two >= N) sort slots, P/4 threads holding four
-// consecutive slots each in registers.  Bitonic sort of (power, index) pairs: the exchanges at
-// distances 1 and 2 stay inside a thread, distances 4..64 are warp shuffles (a warp holds 128
-// consecutive slots), and only distances >= 128 pass through shared memory.  The sorted powers
-// then go to shared memory.  The cumulative sums are exact integer prefix sums inside each binade
-// of the running sum (see the comment at the scan), so the whole block computes them in a few
-// rounds of a block-wide scan instead of one thread running N dependent FP64 additions.  The first
-// rank whose sum reaches the target is found by all threads with an atomic minimum, and the kept modes are marked with plain byte stores of 1 into a mask zeroed
+// consecutive slots each in registers.  Each warp sorts its 128 slots of (power, index) pairs by
+// a bitonic network (exchanges at distances 1 and 2 inside a thread, 4..64 by warp shuffles),
+// then the sorted runs are merged pairwise in shared memory by merge path (a binary search per
+// thread for where its four outputs split between the two runs), log2(P / 128) levels.  The
+// sorted powers then go to shared memory.  The cumulative sums are exact integer prefix sums
+// inside each binade of the running sum (see the comment at the scan), so the whole block
+// computes them in a few rounds of a block-wide scan instead of one thread running N dependent
+// FP64 additions.  The first rank whose sum reaches the target is found by all threads with an
+// atomic minimum, and the kept modes are marked with plain byte stores of 1 into a mask zeroed
 // beforehand (every writer stores the same value, so the union needs no atomics).
 #include "fewsum_internal.h"
 
@@ -101,37 +103,15 @@ k_mode_select(const double *__restrict__ amp_re, const double *__restrict__ amp_
     }
     if (tid == 0) s_cut = 0x7fffffff;
 
-    // bitonic sort into ascending "sorts_before" order; slot p runs up when (p & size) == 0
-    for (int size = 2; size <= P; size <<= 1) {
+    // 1. each warp sorts its 128 slots (4 per lane) into ascending "sorts_before" order by a
+    //    bitonic network in registers and shuffles; below the last stage slot p runs up when
+    //    (p & size) == 0, the last stage runs up in every warp
+    for (int size = 2; size <= kSelectWarpSlots; size <<= 1) {
+        const bool last = size == kSelectWarpSlots;
         int stride = size >> 1;
-        if (stride >= kSelectWarpSlots) {
-            ulonglong2 *kv = reinterpret_cast<ulonglong2 *>(sel_key + p0);
-            kv[0] = make_ulonglong2(key[0], key[1]);
-            kv[1] = make_ulonglong2(key[2], key[3]);
-            *reinterpret_cast<int4 *>(sel_ix + p0) = make_int4(ix[0], ix[1], ix[2], ix[3]);
-            __syncthreads();
-            for (; stride >= kSelectWarpSlots; stride >>= 1) {
-                for (int q = tid; q < P / 2; q += nt) {
-                    const int lo = ((q & ~(stride - 1)) << 1) | (q & (stride - 1)), hi = lo + stride;
-                    unsigned long long ka = sel_key[lo], kb = sel_key[hi];
-                    int ia = sel_ix[lo], ib = sel_ix[hi];
-                    const bool up = (lo & size) == 0;
-                    const bool swap = up ? sorts_before(kb, ib, ka, ia) : sorts_before(ka, ia, kb, ib);
-                    if (swap) {
-                        sel_key[lo] = kb; sel_key[hi] = ka;
-                        sel_ix[lo] = ib; sel_ix[hi] = ia;
-                    }
-                }
-                __syncthreads();
-            }
-            const ulonglong2 a = kv[0], b = kv[1];
-            key[0] = a.x; key[1] = a.y; key[2] = b.x; key[3] = b.y;
-            const int4 v = *reinterpret_cast<const int4 *>(sel_ix + p0);
-            ix[0] = v.x; ix[1] = v.y; ix[2] = v.z; ix[3] = v.w;
-        }
         for (; stride >= kSelectPerThread; stride >>= 1) {
             const int lane_mask = stride / kSelectPerThread;
-            const bool is_lo = (p0 & stride) == 0, up = (p0 & size) == 0;
+            const bool is_lo = (p0 & stride) == 0, up = last || (p0 & size) == 0;
 #pragma unroll
             for (int r = 0; r < kSelectPerThread; ++r) {
                 const unsigned long long ko = __shfl_xor_sync(0xffffffffu, key[r], lane_mask);
@@ -140,14 +120,46 @@ k_mode_select(const double *__restrict__ amp_re, const double *__restrict__ amp_
             }
         }
         if (stride == 2) {
-            const bool up = (p0 & size) == 0;  // size >= 4: the same for all four slots
+            const bool up = last || (p0 & size) == 0;  // size >= 4: the same for all four slots
             cx_pair(key[0], ix[0], key[2], ix[2], up);
             cx_pair(key[1], ix[1], key[3], ix[3], up);
             stride = 1;
         }
         // stride 1: slots (0,1) and (2,3); for size 2 the direction alternates inside the thread
-        cx_pair(key[0], ix[0], key[1], ix[1], ((p0 + 0) & size) == 0);
-        cx_pair(key[2], ix[2], key[3], ix[3], ((p0 + 2) & size) == 0);
+        cx_pair(key[0], ix[0], key[1], ix[1], last || ((p0 + 0) & size) == 0);
+        cx_pair(key[2], ix[2], key[3], ix[3], last || ((p0 + 2) & size) == 0);
+    }
+    // 2. the sorted runs merged pairwise in shared memory, log2(P / 128) levels (merge path): a
+    //    thread finds by binary search how many of its 4 output ranks come from the first run,
+    //    merges them in registers and stores them once the whole level has been read.  Every
+    //    (key, index) pair of a real mode is distinct, so the order is the unique sorted one.
+    for (int L = kSelectWarpSlots; L < P; L <<= 1) {
+        ulonglong2 *kv = reinterpret_cast<ulonglong2 *>(sel_key + p0);
+        kv[0] = make_ulonglong2(key[0], key[1]);
+        kv[1] = make_ulonglong2(key[2], key[3]);
+        *reinterpret_cast<int4 *>(sel_ix + p0) = make_int4(ix[0], ix[1], ix[2], ix[3]);
+        __syncthreads();
+        const int base = p0 & ~(2 * L - 1), d = p0 - base;  // this thread's first output rank
+        const unsigned long long *ak = sel_key + base, *bk = ak + L;
+        const int *ai = sel_ix + base, *bi = ai + L;
+        int lo = d > L ? d - L : 0, hi = d < L ? d : L;
+        while (lo < hi) {  // first i whose A[i] does not precede B[d - 1 - i]
+            const int mid = (lo + hi) >> 1;
+            if (sorts_before(ak[mid], ai[mid], bk[d - 1 - mid], bi[d - 1 - mid]))
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        int i = lo, j = d - lo;
+#pragma unroll
+        for (int r = 0; r < kSelectPerThread; ++r) {
+            const bool take_a = j >= L || (i < L && sorts_before(ak[i], ai[i], bk[j], bi[j]));
+            key[r] = take_a ? ak[i] : bk[j];
+            ix[r] = take_a ? ai[i] : bi[j];
+            i += take_a ? 1 : 0;
+            j += take_a ? 0 : 1;
+        }
+        __syncthreads();  // every thread has read this level before any stores the next
     }
 
     // sorted powers to shared memory (slot j = rank j; padding holds +0)
