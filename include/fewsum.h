@@ -392,6 +392,26 @@ few_status few_plan_segments(const double *t_knots, int K, double t0, double dt,
  */
 few_status few_mode_slots(const int *l, const int *m, const int *n, int N, int *n_slots, int *n_rows);
 
+/*
+ * The summation's division of work among its CTAs, as few_waveform and few_batch_plan compute
+ * it: the concatenated (waveform, sample) space of n_waves waveforms is cut into `grid`
+ * contiguous slices at pass boundaries (a pass = `pass` consecutive samples of one segment,
+ * threads x samples per thread), each slice holding an equal share, to within one pass, of the
+ * total cost (each pass costs (slots + 16) per sample of a full pass, whether or not its segment
+ * ends first).
+ *   seg_start: the n_waves waveforms' segment sample ranges (few_plan_segments) concatenated,
+ *              K[w] entries for waveform w, the last one its sample count.
+ *   K [n_waves], n_slots [n_waves]: knots and harmonic slots (few_mode_slots) per waveform.
+ *   out_wave, out_sample [grid + 1]: CTA g starts at sample out_sample[g] of waveform
+ *              out_wave[g] (a start at or past the end of a waveform means the next one's
+ *              beginning); entry grid = (n_waves, 0), the end.
+ * Host only; errors: FEW_ERR_INVALID_ARG (null pointer, n_waves < 1, grid < 1, pass < 1,
+ * K < 2, n_slots < 1, decreasing segment starts).
+ */
+few_status few_plan_cta_slices(int n_waves, const int64_t *seg_start, const int *K,
+                               const int *n_slots, int grid, int pass, int *out_wave,
+                               int *out_sample);
+
 #ifdef __cplusplus
 }
 #endif

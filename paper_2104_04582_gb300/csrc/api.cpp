@@ -454,6 +454,52 @@ few_status build_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P)
     return FEW_OK;
 }
 
+// CTA slices of the concatenated (wave, sample) space of n waves (segs[q]: wave q's K[q]
+// segment starts, the last its sample count), cut at pass boundaries.  A pass is `pass`
+// consecutive samples of one segment, and it costs a full pass (one Horner step per slot plus the
+// fixed phase work, for every thread) even when its segment ends early; so every slice gets an
+// equal share of the total pass cost, to within one pass, rather than an equal share of the
+// samples (which left some slices several short passes more than others).  cta[grid] = (n, 0).
+void partition_ctas(int n, const int64_t *const *segs, const int *K, const int *slots, int grid,
+                    long long pass, CtaStart *cta)
+{
+    std::vector<long double> cost(n), cum(n + 1, 0.0L);
+    std::vector<long long> npass(n, 0);
+    auto seg_passes = [&](int q, int k) { return (segs[q][k + 1] - segs[q][k] + pass - 1) / pass; };
+    for (int q = 0; q < n; ++q) {
+        for (int k = 0; k + 1 < K[q]; ++k) npass[q] += seg_passes(q, k);
+        cost[q] = (long double)(slots[q] + 16);
+        cum[q + 1] = cum[q] + (long double)npass[q] * cost[q];
+    }
+    const long double total = cum[n];
+    int q = 0, sk = 0;
+    long long before = 0;  // passes of wave q before its segment sk
+    cta[grid] = CtaStart{n, 0};
+    for (int g = 0; g < grid; ++g) {
+        if (total <= 0.0L) {
+            cta[g] = CtaStart{n, 0};
+            continue;
+        }
+        const long double x = total * g / grid;
+        while (q < n - 1 && cum[q + 1] <= x) {
+            ++q;
+            sk = 0;
+            before = 0;
+        }
+        // first pass of wave q whose cost starts at or after x, then the segment holding it
+        long long k = (long long)std::ceil((x - cum[q]) / cost[q]);
+        k = std::max(0LL, std::min(k, npass[q]));
+        const int S = K[q] - 1;
+        while (sk < S && before + seg_passes(q, sk) <= k) {
+            before += seg_passes(q, sk);
+            ++sk;
+        }
+        const long long ns = segs[q][S];
+        const long long sample = sk < S ? segs[q][sk] + (k - before) * pass : ns;
+        cta[g] = CtaStart{q, (int)std::min<long long>(sample, ns)};
+    }
+}
+
 // Fill the blob now that the device addresses of blob and scratch are known.
 void fill_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P, unsigned char *blob_dev,
                 unsigned char *scratch_dev, void *const *outs)
@@ -511,48 +557,16 @@ void fill_image(few_ctx *c, const few_request *reqs, int n, PlanImage &P, unsign
     P.total_pairs = pair_begin;
     P.total_fold = fold_begin;
     P.total_anchor_segs = anchor_seg_begin;
-    // CTA slices of the concatenated (wave, sample) space, cut at pass boundaries.  A pass is
-    // threads x R consecutive samples of one segment, and it costs a full pass (one Horner step
-    // per slot plus the fixed phase work, for every thread) even when its segment ends early; so
-    // every slice gets an equal share of the total pass cost, to within one pass, rather than an
-    // equal share of the samples (which left some slices several short passes more than others).
-    const long long pass = (long long)P.threads * P.R;
-    std::vector<long double> cost(n), cum(n + 1, 0.0L);
-    std::vector<long long> npass(n, 0);
-    auto seg_passes = [&](int q, int k) {
-        return (P.seg[q][k + 1] - P.seg[q][k] + pass - 1) / pass;
-    };
-    for (int q = 0; q < n; ++q) {
-        const few_traj *tr = reqs[q].traj;
-        for (int k = 0; k + 1 < tr->K; ++k) npass[q] += seg_passes(q, k);
-        cost[q] = (long double)(tr->plan.n_slots + 16);
-        cum[q + 1] = cum[q] + (long double)npass[q] * cost[q];
-    }
-    const long double total = cum[n];
-    int q = 0, sk = 0;
-    long long before = 0;  // passes of wave q before its segment sk
-    cta[P.grid] = CtaStart{n, 0};
-    for (int g = 0; g < P.grid; ++g) {
-        if (total <= 0.0L) {
-            cta[g] = CtaStart{n, 0};
-            continue;
+    {
+        std::vector<const int64_t *> segs(n);
+        std::vector<int> Ks(n), slots(n);
+        for (int q = 0; q < n; ++q) {
+            segs[q] = P.seg[q].data();
+            Ks[q] = reqs[q].traj->K;
+            slots[q] = reqs[q].traj->plan.n_slots;
         }
-        const long double x = total * g / P.grid;
-        while (q < n - 1 && cum[q + 1] <= x) {
-            ++q;
-            sk = 0;
-            before = 0;
-        }
-        // first pass of wave q whose cost starts at or after x, then the segment holding it
-        long long k = (long long)std::ceil((x - cum[q]) / cost[q]);
-        k = std::max(0LL, std::min(k, npass[q]));
-        const int S = reqs[q].traj->K - 1;
-        while (sk < S && before + seg_passes(q, sk) <= k) {
-            before += seg_passes(q, sk);
-            ++sk;
-        }
-        const long long sample = sk < S ? P.seg[q][sk] + (k - before) * pass : reqs[q].n_samples;
-        cta[g] = CtaStart{q, (int)std::min<long long>(sample, reqs[q].n_samples)};
+        partition_ctas(n, segs.data(), Ks.data(), slots.data(), P.grid,
+                       (long long)P.threads * P.R, cta);
     }
     hdr->n_waves = n;
     hdr->total_pairs = P.total_pairs;
@@ -1486,6 +1500,32 @@ few_status few_mode_slots(const int *l, const int *m, const int *n, int N, int *
     if (st) return st;
     if (n_slots) *n_slots = P.n_slots;
     if (n_rows) *n_rows = (int)P.rows.size();
+    return FEW_OK;
+}
+
+few_status few_plan_cta_slices(int n_waves, const int64_t *seg_start, const int *K,
+                               const int *n_slots, int grid, int pass, int *out_wave,
+                               int *out_sample)
+{
+    if (!seg_start || !K || !n_slots || !out_wave || !out_sample || n_waves < 1 || grid < 1 ||
+        pass < 1)
+        return FEW_ERR_INVALID_ARG;
+    std::vector<const int64_t *> segs(n_waves);
+    size_t off = 0;
+    for (int q = 0; q < n_waves; ++q) {
+        if (K[q] < 2 || n_slots[q] < 1) return FEW_ERR_INVALID_ARG;
+        segs[q] = seg_start + off;
+        for (int k = 0; k + 1 < K[q]; ++k)
+            if (segs[q][k + 1] < segs[q][k] || segs[q][k] < 0) return FEW_ERR_INVALID_ARG;
+        if (segs[q][K[q] - 1] > 2147483647LL) return FEW_ERR_INVALID_ARG;
+        off += (size_t)K[q];
+    }
+    std::vector<CtaStart> cta((size_t)grid + 1);
+    partition_ctas(n_waves, segs.data(), K, n_slots, grid, pass, cta.data());
+    for (int g = 0; g <= grid; ++g) {
+        out_wave[g] = cta[g].wave;
+        out_sample[g] = cta[g].sample;
+    }
     return FEW_OK;
 }
 

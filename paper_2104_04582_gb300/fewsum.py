@@ -45,7 +45,7 @@ EXPORTED = [
     "few_get_tiles", "few_plan_segments", "few_mode_slots", "few_ctx_set_timing",
     "few_last_timing", "few_phase_samples", "few_waveform_noalloc",
     "few_mode_select", "few_direct_sum", "few_basis_create", "few_basis_release",
-    "few_rb_amplitudes", "few_selftest_wait_expiry",
+    "few_rb_amplitudes", "few_selftest_wait_expiry", "few_plan_cta_slices",
 ]
 
 
@@ -136,6 +136,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
             "few_plan_segments": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_int64, _i64p]),
             "few_mode_slots": (ctypes.c_int, [_ip, _ip, _ip, ctypes.c_int, _ip, _ip]),
+            "few_plan_cta_slices": (ctypes.c_int, [ctypes.c_int, _i64p, _ip, _ip, ctypes.c_int,
+                                                   ctypes.c_int, _ip, _ip]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -376,6 +378,22 @@ def few_plan_segments(t_knots, t0: float, dt: float, n_samples: int) -> np.ndarr
                                   int(n_samples), seg.ctypes.data_as(_i64p))
     _check("few_plan_segments", st)
     return seg
+
+
+def few_plan_cta_slices(seg_starts, n_slots, grid: int, pass_samples: int):
+    """CTA slices of the summation (host only): seg_starts a list of per-waveform segment start
+    arrays (few_plan_segments), n_slots per waveform.  Returns (wave, sample) int arrays of
+    length grid + 1."""
+    segs = [np.ascontiguousarray(np.asarray(x, dtype=np.int64)) for x in seg_starts]
+    cat = np.ascontiguousarray(np.concatenate(segs))
+    K = _i32([len(x) for x in segs])
+    sl = _i32(n_slots)
+    wv = np.zeros(grid + 1, dtype=np.int32)
+    sm = np.zeros(grid + 1, dtype=np.int32)
+    _check("few_plan_cta_slices", load().few_plan_cta_slices(
+        len(segs), cat.ctypes.data_as(_i64p), K.ctypes.data_as(_ip), sl.ctypes.data_as(_ip),
+        int(grid), int(pass_samples), wv.ctypes.data_as(_ip), sm.ctypes.data_as(_ip)))
+    return wv, sm
 
 
 def few_mode_slots(modes):
