@@ -529,7 +529,10 @@ def bench_e2e(ctx, w, tr, prec, sh, flush, steps, in_flight=1):
         ths = [threading.Thread(target=worker, args=(st, strm)) for st, strm in zip(sets, streams)]
         for th in ths:
             th.start()
-        go.wait()
+        try:
+            go.wait()
+        except threading.BrokenBarrierError:
+            pass  # a worker failed before the start; its error is raised below
         t0 = time.perf_counter()
         for th in ths:
             th.join()

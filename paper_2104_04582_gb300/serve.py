@@ -321,6 +321,7 @@ class GpuEngine:
             if tr is not None:
                 tr.release()
         self._owned = []
+        self._announced.clear()
 
     def tune_tiles(self, req: Request, cache_path: Optional[str] = tune.DEFAULT_CACHE) -> tuple:
         """Install the tile of `req`'s workload bucket (tuning on a cache miss, timed on `req`
