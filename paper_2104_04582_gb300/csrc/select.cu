@@ -241,25 +241,23 @@ k_mode_select(const double *__restrict__ amp_re, const double *__restrict__ amp_
         if (lane == 31) s_wsum[wid] = incl;
         if (tid == 0) s_exit = 0x7fffffff;
         __syncthreads();
-        if (wid == 0) {
-            unsigned long long v = lane < nt / 32 ? s_wsum[lane] : 0ull, w = v;
+        // every warp sums the totals of the warps before it itself (integer sums: exact in any
+        // order), so no second barrier is needed
+        unsigned long long wp = lane < wid ? s_wsum[lane] : 0ull;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long u = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += u;
-            }
-            if (lane < nt / 32) s_wsum[lane] = w - v;  // exclusive over warps
-        }
-        __syncthreads();
+        for (int o = 16; o > 0; o >>= 1) wp += __shfl_xor_sync(0xffffffffu, wp, o);
         unsigned long long M[kSelectPerThread];
-        unsigned long long m = Mc + s_wsum[wid] + (incl - run);
+        unsigned long long m = Mc + wp + (incl - run);
+        int jfirst = 0x7fffffff;  // this thread's first step that leaves the binade or ties
 #pragma unroll
         for (int r = 0; r < kSelectPerThread; ++r) {
             m += q[r];
             M[r] = m;
             const int j = p0 + r;
-            if (j >= a && j < N && (m >= kTop || tie[r])) atomicMin(&s_exit, j);
+            if (j >= a && j < N && (m >= kTop || tie[r]) && j < jfirst) jfirst = j;
         }
+        jfirst = __reduce_min_sync(0xffffffffu, jfirst);
+        if (lane == 0 && jfirst != 0x7fffffff) atomicMin(&s_exit, jfirst);
         __syncthreads();
         const int jx = s_exit;
         // c_j = M_j U for the steps inside the binade: exponent field E + 1022 plus M's bits
