@@ -468,6 +468,7 @@ struct RbMmaArgs {
     const int *aexp, *bexp;      // scaling exponents of the coefficient rows and basis columns
     const double *scale;         // [M] renormalisation s_k, applied in the epilogue (or null)
     int M, N, n_kb, m_tiles, n_tiles;
+    int k16_last;                // K = 16 steps of the last k-block holding real columns
     unsigned *err;
 };
 
@@ -561,10 +562,14 @@ __global__ void __launch_bounds__(kRbMmaThreads, 1) k_rb_mma(RbMmaArgs a)
                     if (!mbar_wait_bounded(&full[s], (g / kRbStages) & 1)) { s_abort = 1; ok = false; break; }
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(sA + s * kRbABytes), b0 = smem_u32(sB + s * kRbBBytes);
+                    // the last k-block's columns past 3 x 2 Nb are zero: their MMAs are skipped
+                    const int nk = kb + 1 < a.n_kb ? kRbTileK / 16 : a.k16_last;
 #pragma unroll
                     for (int k = 0; k < kRbTileK / 16; ++k)  // K = 16 per MMA: two core matrices
-                        tc_mma(d, smem_desc(a0 + k * 256, 128, 1024), smem_desc(b0 + k * 256, 128, 1024),
-                               kRbIdesc, (uint32_t)((kb | k) != 0));
+                        if (k < nk)
+                            tc_mma(d, smem_desc(a0 + k * 256, 128, 1024),
+                                   smem_desc(b0 + k * 256, 128, 1024), kRbIdesc,
+                                   (uint32_t)((kb | k) != 0));
                     tc_commit(&empty[s]);
                 }
                 if (!ok) break;
@@ -774,7 +779,9 @@ cudaError_t launch_rb(const double *are, const double *aim, int M, int Nb, int N
     e = cudaFuncSetAttribute(k_rb_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int tiles = L.m_tiles * L.n_tiles;
-    RbMmaArgs args{apack, bpack, ore, oim, aexp, bexp, sc, M, N, L.n_kb, L.m_tiles, L.n_tiles, err};
+    const int k_last = kRbParts * 2 * Nb - (L.n_kb - 1) * kRbTileK;  // real columns, last block
+    RbMmaArgs args{apack, bpack, ore, oim, aexp, bexp, sc, M, N, L.n_kb, L.m_tiles, L.n_tiles,
+                   (k_last + 15) / 16, err};
     k_rb_mma<<<tiles < sm_count ? tiles : sm_count, kRbMmaThreads, smem, st>>>(args);
     return cudaGetLastError();
 }
