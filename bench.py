@@ -678,9 +678,10 @@ def bench_batched_c3(ctx, dev, stream, sh, flush, n_waves, reps, tune_cache, ora
     return res
 
 
-def bench_stress_c5(ctx, dev, stream, sh, reps, tune_cache):
+def bench_stress_c5(ctx, dev, stream, sh, reps, tune_cache, in_flight=1):
     """4 yr at dt = 2 s (63,115,200 samples, complex64), K = 300, 3843 modes, mixed: the whole
-    step timed; mismatch of the full series against the FP64 GPU path."""
+    step timed (also with `in_flight` waveforms in flight); mismatch of the full series against
+    the FP64 GPU path."""
     import torch
     from paper_2104_04582_gb300 import fewsum as F
     from paper_2104_04582_gb300 import runtime as RT
@@ -702,6 +703,25 @@ def bench_stress_c5(ctx, dev, stream, sh, reps, tune_cache):
     step()
     torch.cuda.synchronize()
     ms = _timed(stream, step, reps)  # the 505 MB output is larger than L2
+    flight = None
+    if in_flight > 1:
+        sets = [(tr, dev_in, out, req)]
+        for _ in range(in_flight - 1):
+            t_ = RT.Trajectory(ctx, w.t_knots, w.modes)
+            d_ = t_.upload_inputs(w.phi_phi, w.phi_r, w.amp_re, w.amp_im)
+            o_ = RT.alloc_out(w.n_samples, True, dev.index)
+            sets.append((t_, d_, o_, RT.request(t_, o_, w.n_samples, w.t0, w.dt, w.theta, w.phi,
+                                                 F.FEW_MIXED)))
+        streams = [torch.cuda.Stream(device=dev) for _ in sets]
+        _in_flight(ctx, sets, streams, len(sets))  # warm-up
+        n_steps = reps * len(sets)
+        tot = _in_flight(ctx, sets, streams, n_steps)
+        flight = {"in_flight": len(sets), "steps": n_steps, "ms_per_waveform": tot / n_steps,
+                  "mode_samples_per_s": w.N * w.n_samples / (tot / n_steps * 1e-3),
+                  "note": "each waveform its own trajectory and output, on its own stream"}
+        for t_, _, _, _ in sets[1:]:
+            t_.release()
+        del sets
     out64 = RT.alloc_out(w.n_samples, False, dev.index)
     req64 = RT.request(tr, out64, w.n_samples, w.t0, w.dt, w.theta, w.phi, F.FEW_FP64)
     F.few_waveform(ctx.handle, req64, sh)
@@ -719,6 +739,8 @@ def bench_stress_c5(ctx, dev, stream, sh, reps, tune_cache):
            "mismatch_vs_fp64_gpu_full_series": 1.0 - overlap, "tile": list(tile),
            "tile_tuned_in_this_run": tuned_now,
            "step": "spline build + harmonics + fold + phase anchors + mode sum, complex64 output"}
+    if flight:
+        res["in_flight"] = flight
     del a, out, out64
     tr.release()
     torch.cuda.synchronize()
@@ -930,7 +952,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                 ctx, args.serving_requests, args.serving_budget_gb, tune_cache))
         if not args.no_stress:
             out["stress_c5"] = timed_part("stress_c5", lambda: bench_stress_c5(
-                ctx, dev, stream, sh, 3, tune_cache))
+                ctx, dev, stream, sh, 3, tune_cache, in_flight=args.in_flight))
         if args.direct_samples > 0:
             out["direct"] = timed_part("direct_sum", lambda: bench_direct(
                 ctx, w, dev, stream, sh, args.direct_samples))
