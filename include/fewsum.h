@@ -348,7 +348,7 @@ few_status few_selftest_wait_expiry(few_ctx *ctx, unsigned limit_us, void *strea
  *   threads_per_block: 128 or 256;
  *   stage_slots (the mode tile: harmonic slots per shared-memory stage through which each
  *     segment's table streams): a multiple of 16 in [16, 4096].
- * Defaults: FEW_FP64 (1, 256, 256), FEW_MIXED (4, 256, 1024).  Three stages of stage_slots x 64
+ * Defaults: FEW_FP64 (1, 256, 256), FEW_MIXED (8, 256, 1024).  Three stages of stage_slots x 64
  * bytes (FEW_FP64) or x 32 bytes (FEW_MIXED) must fit in one CTA's shared memory, else the
  * waveform calls return FEW_ERR_LIMIT.  Affects speed only: every configuration gives
  * bit-identical results.

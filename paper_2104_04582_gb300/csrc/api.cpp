@@ -113,7 +113,7 @@ struct few_ctx {
     std::set<few_batch *> batches;
     std::set<few_basis *> bases;
     PinnedPool pinned;
-    int tile_R[2] = {1, 4};
+    int tile_R[2] = {1, 8};
     int tile_T[2] = {256, 256};
     int tile_S[2] = {256, 1024};  // slots per ring stage (the mode tile)
     std::map<std::tuple<int, int, int, int>, int> occ_cache;

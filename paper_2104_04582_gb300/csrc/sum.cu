@@ -341,16 +341,20 @@ __device__ __forceinline__ void release_stage(const PlanHdr &h, const Walk &ahea
     }
 }
 
-// One pass of the consumer warps: samples p0 + tid * R + r of piece [.., i1), every tile of
-// the segment's table in turn (CTA stage indices k0, k0 + 1, ...).  Warps with no sample in the
-// pass still take part in the tile hand-over.  False if a wait gave up.
+// One pass of the consumer warps over piece [.., i1), every tile of the segment's table in turn
+// (CTA stage indices k0, k0 + 1, ...).  Warp w owns the 32 R samples from p0 + 32 R w, its lane
+// l the samples p0 + 32 R w + 32 r + l (r < R): each output store of the warp then covers 32
+// consecutive samples (whole 128-byte lines, which matters when the output is host memory
+// reached over the chip-to-chip link), and a warp past the end of a short pass skips it whole.
+// Warps with no sample in the pass still take part in the tile hand-over.  False if a wait gave
+// up.
 template <typename T, int R>
 __device__ bool consume_pass(const PlanHdr &h, const WaveDev &W, const PhaseSrc<T> &ps, int p0,
                              int i1, bool active, const Ring &rg, int k0, int n_tiles, Walk &ahead,
                              const CtaStart &end, int U)
 {
     const int tid = threadIdx.x;
-    const int base = p0 + tid * R;
+    const int base = p0 + (tid & ~31) * R + (tid & 31);  // sample r of the thread: base + 32 r
     T u[R], zr[R], zi[R], fr[R], fi[R], tr_[R], ti_[R], ar[R], ai[R];
     const int2 *__restrict__ rows = W.tr.rows;
     const int n_rows = W.tr.n_rows, n_slots = W.tr.n_slots;
@@ -358,7 +362,7 @@ __device__ bool consume_pass(const PlanHdr &h, const WaveDev &W, const PhaseSrc<
     if (active) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int i = min(base + r, i1 - 1);
+            const int i = min(base + 32 * r, i1 - 1);
             T sp_, cp, sr, cr;
             ps.at(i, u[r], cp, sp_, cr, sr);
             fr[r] = cp;   // z_phi = e^{-i 2 pi f_phi}
@@ -428,7 +432,7 @@ __device__ bool consume_pass(const PlanHdr &h, const WaveDev &W, const PhaseSrc<
     if (active) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int i = base + r;
+            const int i = base + 32 * r;
             if (i >= i1) break;
             // h = T z_phi^{m_last} z_r^{lo_last}
             T cg, sg;
@@ -445,19 +449,26 @@ __device__ bool consume_pass(const PlanHdr &h, const WaveDev &W, const PhaseSrc<
 }
 
 
-// R samples per thread; T the arithmetic type (float: FEW_MIXED, double: FEW_FP64).
-template <typename T, int R>
+// R samples per thread; T the arithmetic type (float: FEW_MIXED, double: FEW_FP64); MB the
+// resident CTAs per SM that the register budget is sized for.
+template <typename T, int R, int MB = 2>
 struct ScalarPass {
     using Scalar = T;
     static constexpr int kSamples = R;
+    static constexpr int kMinBlocks = MB;
 };
+
+// R = 8 holds four packed sample pairs of state and eight slots of coefficients in flight in
+// about 220 registers: one 256-thread CTA per SM (a budget for two caps it at 128 registers and
+// spills).  Eight warps per SM then run the packed FMA chain faster than sixteen at R = 4.
+using MixedR8 = ScalarPass<float, 8, 1>;
 
 }  // namespace
 
 // blockDim.x consumer threads (all of them compute; the refills are issued by whichever warp
 // releases a stage last).
 template <typename V>
-__global__ void __launch_bounds__(kSumMaxThreads, 2) k_sum(const PlanHdr *__restrict__ hp)
+__global__ void __launch_bounds__(kSumMaxThreads, V::kMinBlocks) k_sum(const PlanHdr *__restrict__ hp)
 {
     using T = typename V::Scalar;
     constexpr int R = V::kSamples;
@@ -603,7 +614,7 @@ cudaError_t sum_configure()
     if ((e = configure_one<ScalarPass<double, 2>>(max_dyn)) != cudaSuccess) return e;
     if ((e = configure_one<ScalarPass<float, 2>>(max_dyn)) != cudaSuccess) return e;
     if ((e = configure_one<ScalarPass<float, 4>>(max_dyn)) != cudaSuccess) return e;
-    if ((e = configure_one<ScalarPass<float, 8>>(max_dyn)) != cudaSuccess) return e;
+    if ((e = configure_one<MixedR8>(max_dyn)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -615,7 +626,7 @@ int sum_occupancy(int variant, int R, int threads, int smem)
     } else if (variant == kVariantScalar) {
         if (R == 2) return occupancy_one<ScalarPass<float, 2>>(threads, smem);
         if (R == 4) return occupancy_one<ScalarPass<float, 4>>(threads, smem);
-        if (R == 8) return occupancy_one<ScalarPass<float, 8>>(threads, smem);
+        if (R == 8) return occupancy_one<MixedR8>(threads, smem);
     }
     return 0;
 }
@@ -630,7 +641,7 @@ cudaError_t launch_sum(const PlanHdr *hdr_dev, int grid, int threads, int R, int
     } else if (variant == kVariantScalar) {
         if (R == 2) return launch_one<ScalarPass<float, 2>>(hdr_dev, grid, threads, smem, st);
         if (R == 4) return launch_one<ScalarPass<float, 4>>(hdr_dev, grid, threads, smem, st);
-        if (R == 8) return launch_one<ScalarPass<float, 8>>(hdr_dev, grid, threads, smem, st);
+        if (R == 8) return launch_one<MixedR8>(hdr_dev, grid, threads, smem, st);
     }
     return cudaErrorInvalidValue;
 }
