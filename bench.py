@@ -45,11 +45,11 @@ WORKLOAD = ("1-yr waveform, dt=10 s (3,155,760 samples), K=100 knots, 3843 modes
             "(l=2..10, m=0..l, n=-30..30), m<0 by symmetry")
 # DRAM bytes (read + write) of one summation launch on this workload, from the ncu capture
 # summarised in profiles/k_sum_mixed_1yr_3843modes.md; used only while the kernel source is the
-# one that was profiled (hash of sum.cu + phase_eval.cuh + async.cuh) and the launch shape (R,
-# threads) is the profiled one.  The stage size is left out: it changes how the L2-resident slot
+# one that was profiled (hash of the code of sum.cu + phase_eval.cuh + async.cuh, comments
+# left out) and the launch shape (R, threads) is the profiled one.  The stage size is left out: it changes how the L2-resident slot
 # tables are staged, not which bytes come from DRAM (the tables and anchors once, the output
 # still in L2 when the launch ends).
-PROFILED_TRAFFIC = {"source_sha256_16": "7baddf3cd09a51ec", "tile": (8, 256), "bytes": 13586432 + 0}
+PROFILED_TRAFFIC = {"source_sha256_16": "e6133ef944b76af9", "tile": (8, 256), "bytes": 13586432 + 0}
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 sub-partitions x 32)
 FP64_FMA_PER_SM_CLK = 2   # FP64 FMA per SM per clock on GB300 (1.25 TFLOP/s at 152 SMs, 2.07 GHz)
 
@@ -75,12 +75,18 @@ def device_peaks(dev_index: int) -> dict:
 
 
 def _kernel_source_hash() -> str:
+    """Hash of the summation kernel's code: its sources with line comments and blank lines
+    removed, so that a comment edit keeps a profiled figure while any code change drops it."""
     import hashlib
+    import re
     d = os.path.join(ROOT, "paper_2104_04582_gb300", "csrc")
     h = hashlib.sha256()
     for f in ("sum.cu", "phase_eval.cuh", "async.cuh"):
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(d, f), encoding="utf-8") as fh:
+            for line in fh:
+                code = re.sub(r"//.*$", "", line).rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

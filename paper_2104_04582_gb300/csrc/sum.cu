@@ -30,8 +30,9 @@
 // Work decomposition: a persistent grid; each CTA owns a contiguous slice of the concatenated
 // (waveform, sample) space, cut at pass boundaries with equal pass cost per slice (a pass costs
 // threads x R samples x slots whether or not its segment ends first), and walks it segment by
-// segment in passes of threads x R consecutive samples, R per thread, each thread holding its
-// samples' Horner state in registers.  The segment's folded coefficient table is streamed into
+// segment in passes of threads x R consecutive samples, R per thread (a warp owns 32 R of them,
+// its lanes strided by 32), each thread holding its samples' Horner state in registers.  The
+// segment's folded coefficient table is streamed into
 // shared memory once per pass, in tiles of stage_slots slots (the mode tile), through a ring of
 // `ring` stages: the last warp to release a stage issues the TMA bulk copies (cp.async.bulk with
 // mbarrier transaction counts) of the tile `ring` positions ahead into it, so no warp ever waits
