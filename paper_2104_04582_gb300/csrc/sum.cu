@@ -50,6 +50,9 @@ namespace fewsum {
 namespace {
 
 constexpr int kSlotUnroll = 8;  // slots per iteration of the Horner chain loop
+// R = 8 already issues 40 packed FMA per slot, so four slots per iteration keep the pipe fed and
+// leave a one-slot remainder on a 61-slot row instead of five (0.7 % faster than eight).
+constexpr int kSlotUnrollR8 = 4;
 constexpr int kBulkChunk = 32768;
 
 struct Piece {
@@ -208,7 +211,8 @@ __device__ __forceinline__ void horner_chain_f32x2(const float *__restrict__ cf,
         AR[q] = make_float2(ar[2 * q], ar[2 * q + 1]);
         AI[q] = make_float2(ai[2 * q], ai[2 * q + 1]);
     }
-#pragma unroll (kSlotUnroll)
+    constexpr int kUnroll = R >= 8 ? kSlotUnrollR8 : kSlotUnroll;
+#pragma unroll (kUnroll)
     for (int k = 0; k < n; ++k) {
         float c[8];
         Cf<float>::load(cf + 8 * k, c);
