@@ -74,20 +74,25 @@ def device_peaks(dev_index: int) -> dict:
             "source": f"{sms} SMs (device query) x lanes x 2 flop x {mhz:.0f} MHz"}
 
 
-def _kernel_source_hash() -> str:
-    """Hash of the summation kernel's code: its sources with line comments and blank lines
-    removed, so that a comment edit keeps a profiled figure while any code change drops it."""
+def _code_hash(paths) -> str:
+    """Hash of the code in C/CUDA sources: line comments, trailing blanks and blank lines left
+    out, so that a comment edit keeps the hash while any code change alters it."""
     import hashlib
     import re
-    d = os.path.join(ROOT, "paper_2104_04582_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("sum.cu", "phase_eval.cuh", "async.cuh"):
-        with open(os.path.join(d, f), encoding="utf-8") as fh:
+    for p in paths:
+        with open(p, encoding="utf-8") as fh:
             for line in fh:
                 code = re.sub(r"//.*$", "", line).rstrip()
                 if code:
                     h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
+
+
+def _kernel_source_hash() -> str:
+    """Code hash of the summation kernel's sources (the key of a profiled traffic figure)."""
+    d = os.path.join(ROOT, "paper_2104_04582_gb300", "csrc")
+    return _code_hash([os.path.join(d, f) for f in ("sum.cu", "phase_eval.cuh", "async.cuh")])
 
 
 def _peaks_file():

@@ -1,0 +1,33 @@
+"""Host logic of the benchmark (no GPU): the code hash that keys the profiled traffic figure."""
+import bench
+
+
+def _write(tmp_path, name, text):
+    p = tmp_path / name
+    p.write_text(text)
+    return str(p)
+
+
+def test_code_hash_ignores_comments_and_blank_lines(tmp_path):
+    a = _write(tmp_path, "a.cu", "int f(int x)\n{\n    return x + 1;  // one more\n}\n")
+    b = _write(tmp_path, "b.cu", "// a header comment\nint f(int x)\n{\n\n    return x + 1;   \n}\n")
+    assert bench._code_hash([a]) == bench._code_hash([b])
+
+
+def test_code_hash_sees_code_changes(tmp_path):
+    a = _write(tmp_path, "a.cu", "int f(int x)\n{\n    return x + 1;\n}\n")
+    b = _write(tmp_path, "b.cu", "int f(int x)\n{\n    return x + 2;\n}\n")
+    c = _write(tmp_path, "c.cu", "int f(int x)\n{\n    return x+1;\n}\n")  # spacing is code too
+    ha, hb, hc = (bench._code_hash([p]) for p in (a, b, c))
+    assert len({ha, hb, hc}) == 3
+
+
+def test_code_hash_depends_on_file_order(tmp_path):
+    a = _write(tmp_path, "a.cu", "int a;\n")
+    b = _write(tmp_path, "b.cu", "int b;\n")
+    assert bench._code_hash([a, b]) != bench._code_hash([b, a])
+
+
+def test_kernel_hash_is_well_formed():
+    h = bench._kernel_source_hash()
+    assert len(h) == 16 and int(h, 16) >= 0
