@@ -62,11 +62,13 @@ def _check(segs, slots, grid, P):
     return costs
 
 
-def test_one_year_waveform_slices():
+@pytest.mark.parametrize("grid,P", [(304, 1024), (152, 2048)])
+def test_one_year_waveform_slices(grid, P):
+    """The one-year waveform at R = 4 x 256 threads on 2 CTAs per SM and at the default R = 8 x
+    256 threads on one CTA per SM: 10 or 11 passes per CTA (equal-sample slices reached 13)."""
     w = W.config2()
     seg = F.few_plan_segments(w.t_knots, w.t0, w.dt, w.n_samples)
-    costs = _check([seg], [1281], 304, 1024)
-    # 10 or 11 passes per CTA (equal-sample slices reached 13)
+    costs = _check([seg], [1281], grid, P)
     assert sorted(set((costs // 1297).tolist())) == [10, 11]
 
 
