@@ -463,8 +463,8 @@ struct ScalarPass {
     static constexpr int kMinBlocks = MB;
 };
 
-// R = 8 holds four packed sample pairs of state and eight slots of coefficients in flight in
-// about 220 registers: one 256-thread CTA per SM (a budget for two caps it at 128 registers and
+// R = 8 holds four packed sample pairs of state and the coefficients of the slots in flight in
+// 218 registers: one 256-thread CTA per SM (a budget for two caps it at 128 registers and
 // spills).  Eight warps per SM then run the packed FMA chain faster than sixteen at R = 4.
 using MixedR8 = ScalarPass<float, 8, 1>;
 
