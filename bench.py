@@ -166,25 +166,29 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU baseline (oracle)
 
-def cpu_baseline(w, target_s: float = 12.0, max_samples=None):
-    """The oracle, as it stands, on a bounded prefix of the workload, all host cores.
+def cpu_baseline(w, target_s: float = 12.0, max_samples=None, threads=None,
+                 what: str = "the 1-yr 3843-mode waveform"):
+    """The oracle, as it stands, on a bounded prefix of the workload, on `threads` host threads
+    (default: all host cores).
 
     A call costs a fixed part (all splines and harmonics) plus a part per sample; two short calls
     fit both, a third call of about `target_s` measures the per-sample rate, and the whole
-    waveform's time is extrapolated as fixed + rate x N_s.
+    waveform's time is extrapolated as fixed + rate x N_s (no extrapolation when the third call
+    covers every sample).
     """
     import oracle
-    threads = os.cpu_count() or 1
+    threads = int(threads or os.cpu_count() or 1)
 
     def run(n):
         t0 = time.perf_counter()
         h = oracle.waveform_inputs(w, 0, n, nthreads=threads)
         return time.perf_counter() - t0, h
 
-    n1, n2 = 256, 2048
+    n2 = min(2048, w.n_samples)
+    n1 = max(1, min(256, n2 // 8))
     t1, _ = run(n1)
     t2, _ = run(n2)
-    per = max((t2 - t1) / (n2 - n1), 1e-12)
+    per = max((t2 - t1) / max(n2 - n1, 1), 1e-12)
     fixed = max(t1 - per * n1, 0.0)
     n = int(min(w.n_samples, max(n2, (target_s - fixed) / per)))
     if max_samples:
@@ -192,13 +196,35 @@ def cpu_baseline(w, target_s: float = 12.0, max_samples=None):
     el, h = run(n)
     per = max((el - fixed) / n, 1e-12)
     t_full = fixed + per * w.n_samples
+    rate = n * w.N / max(el - fixed, 1e-9)
+    if n >= w.n_samples:
+        t_full = el
+        rate = n * w.N / max(el, 1e-9)
+        how = f"all {n} samples of {what} ({n * w.N:.3g} mode-samples) in {el:.2f} s on {threads} " \
+              f"OpenMP threads"
+    else:
+        how = (f"first {n} of {w.n_samples} samples of {what} ({n * w.N:.3g} mode-samples) in "
+               f"{el:.1f} s on {threads} OpenMP threads; fixed cost {fixed:.2f} s + "
+               f"{per * 1e6:.1f} us/sample extrapolated to the whole waveform ({t_full:.0f} s)")
     return {"value": 1.0 / t_full, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first {n} of {w.n_samples} samples of the 1-yr 3843-mode waveform "
-                      f"({n * w.N:.3g} mode-samples) in {el:.1f} s on {threads} OpenMP threads; "
-                      f"fixed cost {fixed:.2f} s + {per * 1e6:.1f} us/sample extrapolated to the "
-                      f"whole waveform ({t_full:.0f} s)",
-            "mode_samples_per_s": n * w.N / max(el - fixed, 1e-9), "seconds": el,
+            "sample": how, "mode_samples_per_s": rate, "seconds": el,
             "seconds_full_waveform": t_full}, h
+
+
+def cpu_baseline_detail(w, target_s: float = 3.0) -> dict:
+    """The oracle's rate on one host thread and on all of them: the one-year waveform `w` on
+    one thread (a bounded prefix, extrapolated like cpu_baseline), the one-week 132-mode
+    waveform in full on all cores and on one."""
+    keep = ("value", "unit", "cores", "sample", "mode_samples_per_s", "seconds_full_waveform")
+    out = {}
+    cb, _ = cpu_baseline(w, target_s=target_s, threads=1)
+    out["one_year_single_thread"] = {k: cb[k] for k in keep}
+    w1 = W.config1()
+    for key, thr in (("one_week_all_cores", None), ("one_week_single_thread", 1)):
+        cb, _ = cpu_baseline(w1, target_s=target_s, threads=thr,
+                             what="the 1-week 132-mode waveform")
+        out[key] = {k: cb[k] for k in keep}
+    return out
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -1082,6 +1108,9 @@ def assemble_line(args, res, ms, world):
     if not args.no_cpu:
         cb, h_or = cpu_baseline(w, target_s=args.cpu_seconds)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        t_d = time.perf_counter()
+        line["cpu_baseline_detail"] = cpu_baseline_detail(w)
+        line["bench_sections_s"]["cpu_baseline_detail"] = round(time.perf_counter() - t_d, 2)
         import oracle
         n = len(h_or)
         acc["mismatch_vs_oracle_window"] = oracle.mismatch(res["h_fast"][:n], h_or)

@@ -31,3 +31,15 @@ def test_code_hash_depends_on_file_order(tmp_path):
 def test_kernel_hash_is_well_formed():
     h = bench._kernel_source_hash()
     assert len(h) == 16 and int(h, 16) >= 0
+
+
+def test_cpu_baseline_times_a_whole_small_waveform():
+    """The oracle baseline on a tiny workload: every sample computed (no extrapolation), on the
+    thread count asked for, with the result returned for the accuracy check."""
+    from paper_2104_04582_gb300 import workloads as W
+    w = W.tiny_inputs(5, K=6, n_samples=300)
+    cb, h = bench.cpu_baseline(w, target_s=0.5, threads=1, what="a tiny waveform")
+    assert cb["cores"] == 1 and cb["kind"] == "oracle" and cb["unit"] == bench.UNIT
+    assert cb["sample"].startswith("all 300 samples of a tiny waveform")
+    assert cb["seconds_full_waveform"] == cb["seconds"] and cb["value"] > 0
+    assert len(h) == 300
