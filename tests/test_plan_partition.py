@@ -72,7 +72,7 @@ def test_one_year_waveform_slices(grid, P):
     assert sorted(set((costs // 1297).tolist())) == [10, 11]
 
 
-@pytest.mark.parametrize("grid,P", [(304, 1024), (304, 2048), (152, 512), (608, 1024)])
+@pytest.mark.parametrize("grid,P", [(304, 1024), (304, 2048), (152, 512), (152, 2048), (608, 1024)])
 def test_batch_of_uneven_waveforms(grid, P):
     rng = np.random.default_rng(11 + grid + P)
     segs, slots = [], []
